@@ -1,0 +1,287 @@
+/*
+ * dock.h - C ABI of the GB300 (sm_103a) docking-registration library.
+ *
+ * Probe-aware contact registration by complementary-shape docking
+ * (arxiv 2605.21398).  Given an object mesh, a probe shape and a trajectory of
+ * probe poses {T_i} (Sec. III: "a sequence of probe poses ... in which a rigid
+ * probe attempts to touch the surface"), the library estimates the object
+ * pose T = (R, t) in SE(3) that "best aligns the object with the observed
+ * trajectory":
+ *   1. global docking search (Sec. IV): for every orientation sample, the
+ *      probe's swept volume is voxelised on a lattice rotated by that sample
+ *      and correlated over all translations with the object grid by 3-D FFT
+ *      (Eq. (5)-(9)); the best peaks survive;
+ *   2. local search in a geodesic ball around the best orientation
+ *      (Sec. IV-C/D, Algorithm 1);
+ *   3. continuous refinement on SE(3) (Sec. V, Eq. (13)-(28)).
+ *
+ * Conventions
+ *   - Units are mm and rad.  A pose is 7 doubles (qw, qx, qy, qz, tx, ty, tz);
+ *     probe poses map probe-local points to world points; the returned object
+ *     pose maps object-frame points to world points.
+ *   - The probe is a flat-ended cylinder: tip face centred at the local
+ *     origin, body along +z, z in [0, length], radius `radius`.
+ *   - Lattice arrays are indexed (k_z * N + k_y) * N + k_x.
+ *   - Host arrays passed in are borrowed for the duration of the call and
+ *     copied; they may be freed when the call returns.  Handles are owned by
+ *     the caller and released with the matching *_free call.
+ *   - Every call returns a dock_status.  A negative status leaves outputs
+ *     untouched and sets the context's last-error string.  No C++ exception
+ *     crosses this interface.
+ *   - Work is issued on the context's CUDA stream; calls that return host
+ *     results synchronise that stream before returning.
+ */
+#ifndef DOCK_H
+#define DOCK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#ifndef DOCK_API
+#define DOCK_API __attribute__((visibility("default")))
+#endif
+
+typedef int32_t dock_status;
+#define DOCK_OK            0
+#define DOCK_PENDING       1
+#define DOCK_E_INVALID    -1   /* bad argument: NaN/Inf, non-unit quaternion, empty input, size out of range */
+#define DOCK_E_NOMEM      -2   /* device or host allocation failed */
+#define DOCK_E_TOO_LARGE  -3   /* request can never fit the context's HBM budget */
+#define DOCK_E_CUDA       -4   /* a CUDA call failed; the context remains usable */
+#define DOCK_E_CUDA_FATAL -5   /* sticky CUDA error: the context is dead */
+#define DOCK_E_TIMEOUT    -6
+#define DOCK_E_CANCELLED  -7
+#define DOCK_E_BUSY       -8
+#define DOCK_E_OVERFLOW   -9   /* a fixed-capacity device list overflowed (reported, result not trusted) */
+
+typedef struct dock_ctx dock_ctx;
+typedef struct dock_object dock_object;
+typedef struct dock_sweep dock_sweep;
+
+/* Parameters.  Defaults (dock_params_default) are Table I of Sec. VI plus the
+ * readings noted beside each field. */
+typedef struct dock_params {
+    double tau_out1;     /* Eq. (1)-(2) outer band, mm (Table I: 0.5) */
+    double tau_in1;      /* Eq. (1) inner band, mm (Table I: 0.2) */
+    double deep_value;   /* Eq. (1) value for f <= -tau_in1 (Table I rho = -50, taken as the value) */
+    double tau_out2;     /* Eq. (18) outer threshold, mm (Table I: 0.2); also the Eq. (21) cutoff */
+    double tau_in2;      /* Eq. (18) inner threshold, mm (Table I: 0.03); r = tau_in2 / tau_out2 */
+    double k_slope;      /* Eq. (18) penalty slope k (15) */
+    double lambda;       /* Eq. (19) Tikhonov weight (Table I "10e-4", read as 1e-3) */
+    double mu;           /* Gauss-Newton damping added to the normal matrix, mm^-2 (1e-6) */
+    double b_t, b_r;     /* Eq. (20) box bounds: |u|_inf <= b_t mm, |w|_inf <= b_r rad (1.0, 5 deg) */
+    double step_t, step_r; /* per-iteration trust region on the Gauss-Newton step (0.05 mm, 0.5 deg) */
+    int32_t iters;       /* refinement iterations (20) */
+    int32_t tri_iters;   /* bisection steps per level of the per-triangle minimisation (FP32: 24) */
+} dock_params;
+
+typedef struct dock_probe {
+    int32_t kind;        /* 0 = flat-ended cylinder (the paper's bur, Sec. VI) */
+    double radius;       /* mm */
+    double length;       /* mm */
+} dock_probe;
+
+/* One surviving docking peak (Sec. IV-B/D, Eq. (8)). */
+typedef struct dock_candidate {
+    double q[4];         /* sampled orientation (w, x, y, z) */
+    double t[3];         /* translation R (h dk + o_s - o_o) */
+    float score;         /* correlation peak C[dk] (Eq. (7)) */
+    int32_t rot;         /* index of the orientation sample */
+    int32_t dk[3];       /* voxel shift (x, y, z), each in [-N, N-1] */
+    int32_t canvas_idx;  /* (c_z * M + c_y) * M + c_x on the M^3 canvas */
+} dock_candidate;
+
+/* Per-rotation peak (test and sharding hook). */
+typedef struct dock_peak {
+    float score;
+    int32_t canvas_idx;
+} dock_peak;
+
+enum { DOCK_SAMPLER_SF = 0, DOCK_SAMPLER_HOPF = 1, DOCK_SAMPLER_GEOBALL = 2, DOCK_SAMPLER_EXPLICIT = 3 };
+
+typedef struct dock_search_desc {
+    int32_t sampler;     /* DOCK_SAMPLER_* */
+    int32_t n;           /* number of orientation samples */
+    const double *quats; /* EXPLICIT: n x 4 unit quaternions (host), else NULL */
+    double q0[4];        /* GEOBALL: ball centre */
+    double theta;        /* GEOBALL: ball radius, quaternion half-angle (Eq. (10); Table I: 5 deg) */
+    double gamma;        /* GEOBALL: Algorithm 1 constant gamma (0 = n, the default reading) */
+    int32_t top_k;       /* candidates kept, 1..1024 */
+    int32_t rot_begin;   /* shard: evaluate samples [rot_begin, rot_end); rot_end = 0 means n */
+    int32_t rot_end;
+    int32_t batch;       /* rotations per pipeline batch (0 = automatic) */
+} dock_search_desc;
+
+/* Refined pose (Sec. V). */
+typedef struct dock_refined {
+    double q[4];         /* refined object orientation */
+    double t[3];         /* refined object translation */
+    double xi[6];        /* final twist (u, w) of Eq. (13) relative to the candidate */
+    double J;            /* Eq. (19) at xi */
+    int32_t cand;        /* index of the candidate it started from */
+    int32_t iters;
+} dock_refined;
+
+typedef struct dock_register_desc {
+    int32_t n_global;    /* global SF samples (Table I n_g) */
+    int32_t n_local;     /* local GeoBall-SF samples (Table I n_l; 0 = no local stage) */
+    double theta;        /* local ball radius (quaternion half-angle) */
+    int32_t top_k;       /* candidates refined */
+    int32_t sampler;     /* global sampler: DOCK_SAMPLER_SF or DOCK_SAMPLER_HOPF */
+} dock_register_desc;
+
+typedef struct dock_result {
+    double q[4], t[3];   /* final object pose (object -> world) */
+    double J;            /* objective at the final pose */
+    int32_t best_cand;   /* candidate index that won the refinement */
+    int32_t n_evals;     /* orientation samples evaluated */
+    dock_candidate best_search; /* best candidate of the search stages */
+} dock_result;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on `device`.  hbm_budget_bytes bounds the device memory
+ * the context may hold (0 = no bound).  cuda_stream is a cudaStream_t or NULL
+ * for a stream the context creates and owns. */
+DOCK_API dock_status dock_create(dock_ctx **out, int device, size_t hbm_budget_bytes, void *cuda_stream);
+DOCK_API void dock_destroy(dock_ctx *ctx);
+/* Last error message of the context (valid until the next call on ctx). */
+DOCK_API const char *dock_last_error(const dock_ctx *ctx);
+DOCK_API void dock_params_default(dock_params *p);
+/* Library version string. */
+DOCK_API const char *dock_version(void);
+
+/* ----------------------------------------------------------------- object */
+
+/*
+ * Object grid O[k] = min(O_t, O_m)(h k + o_o) of Sec. IV-A.1, Eq. (1)-(4),
+ * and its canvas spectrum conj(F(O)) for Eq. (9), kept resident on the device.
+ *   verts    V x 3 doubles (object frame, mm); tris T x 3 int32 (watertight,
+ *            any orientation); touchable: T bytes marking the touchable
+ *            sub-mesh of Eq. (2), or NULL for all triangles.
+ *   h, N     voxel size and lattice side; N in {32, 64, 96, 128}.  The
+ *            canvas side is M = 2 N (Sec. IV-B: n_o + n_s - 1 <= M).
+ *   o_o      = h round(c / h) - (N/2) h, c = the mesh AABB centre.
+ * The SDF is the exact point-triangle distance with the sign from the parity
+ * of +x ray crossings.  Returns DOCK_E_INVALID when the mesh AABB widened by
+ * tau_out1 does not fit the lattice.  Also builds the BVH used by the
+ * refinement (Sec. V-B) and sets the anchor a = AABB centre (Sec. V-A).
+ */
+DOCK_API dock_status dock_object_grid(dock_ctx *ctx, const double *verts, int64_t V, const int32_t *tris, int64_t T,
+                             const uint8_t *touchable, double h, int32_t N, const dock_params *params,
+                             dock_object **out);
+DOCK_API void dock_object_free(dock_object *obj);   /* before dock_destroy of its context */
+/* Copy O (N^3 floats) and o_o (3 doubles) to host memory (test hook). */
+DOCK_API dock_status dock_object_export_grid(dock_ctx *ctx, const dock_object *obj, float *grid, double *origin);
+
+/* ------------------------------------------------------------------ sweep */
+
+/*
+ * Probe + trajectory of Sec. IV-A.2 (Eq. (5)-(6)), resident on the device.
+ *   poses    P x 7 doubles, probe -> world; quaternions must be unit (1e-6).
+ *   contact  P labels (1 = contact, 0 = non-contact) or NULL.  Eq. (5) takes
+ *            the max over all poses, so the labels do not change the search.
+ *   h, N     must equal the object's when used together.
+ * The swept lattice for an orientation sample R has origin
+ * o_s,R = h round(R^T c_s / h) - (N/2) h, c_s = mean tip position.
+ */
+DOCK_API dock_status dock_sweep_grid(dock_ctx *ctx, const dock_probe *probe, const double *poses, const uint8_t *contact,
+                            int64_t P, double h, int32_t N, dock_sweep **out);
+DOCK_API void dock_sweep_free(dock_sweep *sw);
+/* Voxelise S_R for `n` quaternions (host n x 4) into host `bits`
+ * (n x N^3 bytes, 0/1) and their origins (n x 3 doubles).  Test hook. */
+DOCK_API dock_status dock_sweep_voxelise(dock_ctx *ctx, const dock_sweep *sw, const double *quats, int32_t n,
+                                uint8_t *bits, double *origins);
+
+/* ----------------------------------------------------------------- search */
+
+/*
+ * Docking search over orientation samples (Sec. IV-B..D): for each sample the
+ * rotated swept grid is correlated with O over all M^3 canvas shifts
+ * (Eq. (7), by FFT per Eq. (9)), the per-rotation argmax (ties: lowest
+ * linear index) is kept, and the top_k peaks over rotations (score
+ * descending, rotation index ascending) are written to `out` with their
+ * poses (Eq. (8) composed with the sample's rotation).  per_rot (host,
+ * n entries, nullable) receives every evaluated rotation's peak; entries
+ * outside [rot_begin, rot_end) are left untouched.
+ */
+DOCK_API dock_status dock_search_so3(dock_ctx *ctx, const dock_object *obj, const dock_sweep *sw,
+                            const dock_search_desc *desc, dock_candidate *out, dock_peak *per_rot);
+
+/* Full correlation field C (M^3 floats, host) for one quaternion.  Test hook. */
+DOCK_API dock_status dock_search_scores(dock_ctx *ctx, const dock_object *obj, const dock_sweep *sw, const double *quat,
+                               float *C);
+
+/* Orientation samples as the search generates them (host n x 4).  Test hook. */
+DOCK_API dock_status dock_sample_so3(const dock_search_desc *desc, double *quats);
+
+/* ------------------------------------------------------------- refinement */
+
+/*
+ * Continuous refinement of Sec. V for K candidates: twist xi (Eq. (13)),
+ * left perturbation about the anchor (Eq. (14)-(17)), proximity score
+ * (Eq. (18), C^1 coefficients), objective (Eq. (19)) under the box
+ * (Eq. (20)); per-pose distances by BVH pruning (Eq. (21)) and per-triangle
+ * minimisation of f_p (Eq. (22)-(23)); sensitivities (Eq. (24)-(28)).  The
+ * solver is a fixed-iteration projected Gauss-Newton step with an FP64 6x6
+ * Cholesky solve per candidate (replacing L-BFGS-B).  out[c] is the refined
+ * pose of in[c].
+ */
+DOCK_API dock_status dock_refine_se3(dock_ctx *ctx, const dock_object *obj, const dock_sweep *sw, const dock_candidate *in,
+                            int32_t K, const dock_params *params, dock_refined *out);
+
+/*
+ * Differentiable form of the refinement objective for B base poses.
+ * base_poses: B x 7 host doubles (object -> world), read before the call
+ * returns.  xi (B x 6 floats), J (B floats) and grad (B x 6 floats, nullable)
+ * are device pointers used on `stream` (a cudaStream_t; NULL = the context
+ * stream, cudaStreamLegacy = the legacy default stream); the call returns
+ * without synchronising it.  J[b] = Eq. (19) at
+ * twist xi[b] about base pose b (anchor a = the object's AABB centre),
+ * grad[b] = Eq. (28).
+ */
+DOCK_API dock_status dock_objective_fwd(dock_ctx *ctx, const dock_object *obj, const dock_sweep *sw,
+                                        const double *base_poses, const float *xi, int32_t B,
+                                        const dock_params *params, float *J, float *grad, void *stream);
+
+/* Adjoint of dock_objective_fwd: gxi[b] = gJ[b] * grad J(xi[b]) (Eq. (24)-(28)),
+ * recomputed by the sensitivity kernel.  gJ, gxi: device pointers. */
+DOCK_API dock_status dock_objective_bwd(dock_ctx *ctx, const dock_object *obj, const dock_sweep *sw,
+                                        const double *base_poses, const float *xi, int32_t B,
+                                        const dock_params *params, const float *gJ, float *gxi, void *stream);
+
+/* Per-pose distances d_i, world witnesses and normals for B object poses
+ * (host B x 7) into host arrays (B x P, B x P x 3, B x P x 3).  Test hook. */
+DOCK_API dock_status dock_distances(dock_ctx *ctx, const dock_object *obj, const dock_sweep *sw, const double *obj_poses,
+                           int32_t B, const dock_params *params, float *d, float *witness, float *normal);
+
+/* ------------------------------------------------------------ registration */
+
+/* The three-stage pipeline of Fig. 2: global search, local search around the
+ * best orientation, refinement of the top_k candidates; the lowest-J refined
+ * pose wins (ties: lower candidate index). */
+DOCK_API dock_status dock_register(dock_ctx *ctx, const dock_object *obj, const dock_sweep *sw, const dock_register_desc *desc,
+                          const dock_params *params, dock_result *out);
+
+/* --------------------------------------------------------------- profiling */
+
+/* Per-kernel CUDA-event timing on the context stream (off by default). */
+DOCK_API dock_status dock_set_profiling(dock_ctx *ctx, int enable);
+/* Copies up to `cap` entries: kernel name (<= 31 chars), launches, total ms. */
+typedef struct dock_kernel_stat {
+    char name[32];
+    int64_t launches;
+    double total_ms;
+} dock_kernel_stat;
+DOCK_API int32_t dock_get_kernel_stats(dock_ctx *ctx, dock_kernel_stat *stats, int32_t cap);
+DOCK_API void dock_reset_kernel_stats(dock_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DOCK_H */

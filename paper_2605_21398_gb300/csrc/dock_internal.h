@@ -1,0 +1,111 @@
+// Internal declarations shared by the host runtime and the CUDA kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+#include <map>
+
+#include "../../include/dock.h"
+
+namespace dock {
+
+// Per-rotation lattice set-up, FP64 (exact operation order) and FP32 copies.
+struct RotRec {
+    double R[9];   // rotation of the sample (row-major)
+    double o[3];   // swept-lattice origin o_s,R
+    float Rf[9];
+    float of[3];
+    int32_t rot;   // global sample index
+    int32_t pad;
+};
+
+// Per-pose data of a sweep: FP64 rotation/translation (exact recheck) and FP32.
+struct PoseRec {
+    double R[9];
+    double t[3];
+    float Rf[9];
+    float tf[3];
+};
+
+// Geometry of one search pipeline configuration.
+struct Geo {
+    int N;      // lattice side
+    int M;      // canvas side (2N)
+    int P;      // row pitch of half-spectrum arrays in complex elements (M/2 + 2)
+    double h;
+    float inv_h;
+    float rv;   // probe radius in voxels
+    float lv;   // probe length in voxels
+    double r, L;
+};
+
+struct Launcher;  // timing helper
+
+// Kernel launchers (k_search.cu)
+cudaError_t launch_rot_setup(const double *quats, int n, int rot0, const double *c_s, double h, int N, RotRec *out,
+                             cudaStream_t st);
+cudaError_t launch_vox_fwd(const Geo &g, const RotRec *rots, int B, const PoseRec *poses, int P, float2 *Y,
+                           const float2 *tw, const float2 *q, int *err, cudaStream_t st);
+cudaError_t launch_zpass(const Geo &g, int B, int group, const float2 *Y, const float2 *spec, float2 *Z,
+                         const float2 *tw, cudaStream_t st);
+cudaError_t launch_plane(const Geo &g, int B, const float2 *Z, const float2 *tw, const RotRec *rots,
+                         unsigned long long *keys, cudaStream_t st);
+cudaError_t launch_topk(const unsigned long long *keys, int n, int K, int N, int M, double h, const double *o_o,
+                        const double *quats, const RotRec *rots_all, dock_candidate *out, cudaStream_t st);
+cudaError_t launch_vox_export(const Geo &g, const RotRec *rots, int B, const PoseRec *poses, int P, uint8_t *bits,
+                              int *err, cudaStream_t st);
+cudaError_t launch_plane_export(const Geo &g, const float2 *Z, const float2 *tw, float *C, cudaStream_t st);
+
+// Object grid kernels (k_object.cu)
+struct ObjBins {
+    const int32_t *cell3_start;  // 3-D cells, CSR
+    const int32_t *cell3_items;
+    const int32_t *cell2_start;  // (y,z) cells, CSR
+    const int32_t *cell2_items;
+    int d3[3];
+    int d2[2];
+    double cs;                    // cell size
+};
+cudaError_t launch_object_grid(const double *V, const int32_t *T, const uint8_t *touch, const ObjBins &bins,
+                               int N, double h, const double *o, double tau_out, double tau_in, double deep,
+                               float *O, float *f_out, int *err, cudaStream_t st);
+cudaError_t launch_spectrum(const float *O, int N, int M, int P, double2 *work1, double2 *work2,
+                            const double2 *twd, float2 *spec, cudaStream_t st);
+
+// Refinement kernels (k_refine.cu)
+struct BvhNode {
+    float c[3];    // sphere centre (object frame)
+    float rad;     // sphere radius
+    int32_t left;  // child index, or -1 for a leaf
+    int32_t right; // right child, or the leaf's first slot in the triangle order
+    int32_t count; // leaf triangle count
+    int32_t pad;
+};
+struct RefineDev {
+    const float *Vf;          // V x 3
+    const int32_t *T;         // T x 3
+    const float *tri_sphere;  // T x 4 (centre, radius), object frame
+    const int32_t *tri_order; // leaf slot -> triangle index
+    const BvhNode *nodes;
+    const PoseRec *poses;
+    int P;
+    float r, L;
+    float tau_out, tau_in, k_slope;
+    float A, B, rr;           // Eq. (18) cubic coefficients and the ratio r
+    int tri_iters;
+};
+struct CandF;                 // per-candidate FP32 pose data (k_refine.cu)
+size_t cand_bytes();
+constexpr int REF_ST = 24;    // doubles of refinement state per candidate
+constexpr int REF_NACC = 28;  // accumulated J, grad (6), Gauss-Newton upper triangle (21)
+cudaError_t launch_refine_eval(const RefineDev &d, int K, const CandF *cands, double *acc_part, bool grad,
+                               float *dist_out, float *wit_out, float *nrm_out, cudaStream_t st);
+cudaError_t launch_refine_solve(int K, int nblk, double *state, const double *acc_part, const double *prm, int mode,
+                                CandF *cands, cudaStream_t st);
+cudaError_t launch_set_xi(int B, const float *xi, double *state, cudaStream_t st);
+cudaError_t launch_finish_objective(int B, int nblk, const double *state, const double *acc_part, double lam, float *J,
+                                    float *grad, const float *gJ, cudaStream_t st);
+
+}  // namespace dock

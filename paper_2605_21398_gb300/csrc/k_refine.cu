@@ -1,0 +1,499 @@
+// Continuous refinement (Sec. V) on the GPU.
+//
+// K10/K11 (k_refine_eval): one thread per (candidate, probe pose).  The probe
+// pose is expressed in the object frame, the mesh BVH is traversed with the
+// Eq. (21) test f_p(c) < r_node + eps (eps = tau_out2, so pruned geometry
+// can only have s = s' = 0), and each surviving triangle's minimum of f_p is
+// found by golden-section search over one barycentric coordinate with an inner
+// bisection on subgradient signs (f_p is convex).  From d*, the witness and
+// the SDF normal (Eq. (22)-(23)) the kernel forms the exact sensitivities of
+// d w.r.t. the twist (Eq. (24)-(27), rotational term through the left Jacobian
+// V(w), coupling term analytic), the score s(d) of Eq. (18) and its
+// derivatives, and reduces J, grad J (Eq. (28)) and the Gauss-Newton matrix
+// per candidate in FP64, deterministically (per-block partials, fixed order).
+// K12 (k_refine_solve): one thread per candidate, FP64: Cholesky 6x6 solve of
+// the normal equations, trust-region scaling, box projection (Eq. (20)), and
+// the pose data of the next iteration (Eq. (14)-(17)).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "dock_internal.h"
+
+namespace dock {
+
+#define KINK_EPS 1e-5f
+
+// per-candidate data read by the evaluation kernel (FP32)
+struct CandF {
+    float R[9], p[3];   // object pose T(xi)
+    float V[9];         // left Jacobian V(w)
+    float Mc[9];        // d(V(w) u)/dw
+    float c[3];         // pivot p0 + V u + R0 a
+    float pad[3];
+};
+
+// state layout (doubles): R0[9] p0[3] a[3] xi[6] -> 21, then J at 21, pad to 24
+constexpr int ST = 24;
+constexpr int NACC = 28;   // J, G[6], H upper triangle [21]
+
+__device__ __forceinline__ float sdf_cyl(float x, float y, float z, float r, float L, float *g)
+{
+    float rho = sqrtf(fmaf(x, x, y * y));
+    float ux = 1.f, uy = 0.f;
+    if (rho > 0.f) { ux = x / rho; uy = y / rho; }
+    float dr = rho - r;
+    float zlo = -z, zhi = z - L;
+    float dz = zlo >= zhi ? zlo : zhi;
+    float cz = zlo >= zhi ? -1.f : 1.f;
+    float f;
+    if (dr <= 0.f && dz <= 0.f) {
+        f = fmaxf(dr, dz);
+        if (g) {
+            if (fabsf(dr - dz) <= KINK_EPS) {
+                const float s = 0.70710678118654752f;
+                g[0] = ux * s; g[1] = uy * s; g[2] = cz * s;
+            } else if (dr > dz) {
+                g[0] = ux; g[1] = uy; g[2] = 0.f;
+            } else {
+                g[0] = 0.f; g[1] = 0.f; g[2] = cz;
+            }
+        }
+    } else if (dr > 0.f && dz > 0.f) {
+        f = sqrtf(fmaf(dr, dr, dz * dz));
+        if (g) { g[0] = dr * ux / f; g[1] = dr * uy / f; g[2] = dz * cz / f; }
+    } else if (dr > 0.f) {
+        f = dr;
+        if (g) { g[0] = ux; g[1] = uy; g[2] = 0.f; }
+    } else {
+        f = dz;
+        if (g) { g[0] = 0.f; g[1] = 0.f; g[2] = cz; }
+    }
+    return f;
+}
+
+__device__ __forceinline__ float dot3f(const float *a, const float *b) { return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2])); }
+
+// min over v in [0, 1-u] of f(v0 + u e1 + v e2): bisection on df/dv
+__device__ float inner_min(const float *v0, const float *e1, const float *e2, float u, float r, float L, int iters,
+                           float *v_out)
+{
+    float vmax = 1.f - u;
+    float x[3], g[3];
+    for (int a = 0; a < 3; ++a) x[a] = fmaf(u, e1[a], v0[a]);
+    float f0 = sdf_cyl(x[0], x[1], x[2], r, L, g);
+    if (vmax <= 0.f || dot3f(g, e2) >= 0.f) { *v_out = 0.f; return f0; }
+    float xe[3];
+    for (int a = 0; a < 3; ++a) xe[a] = fmaf(vmax, e2[a], x[a]);
+    float f1 = sdf_cyl(xe[0], xe[1], xe[2], r, L, g);
+    if (dot3f(g, e2) <= 0.f) { *v_out = vmax; return f1; }
+    float lo = 0.f, hi = vmax;
+    for (int k = 0; k < iters; ++k) {
+        float mid = 0.5f * (lo + hi);
+        float xm[3];
+        for (int a = 0; a < 3; ++a) xm[a] = fmaf(mid, e2[a], x[a]);
+        sdf_cyl(xm[0], xm[1], xm[2], r, L, g);
+        if (dot3f(g, e2) < 0.f) lo = mid; else hi = mid;
+    }
+    float v = 0.5f * (lo + hi);
+    for (int a = 0; a < 3; ++a) x[a] = fmaf(v, e2[a], x[a]);
+    *v_out = v;
+    return sdf_cyl(x[0], x[1], x[2], r, L, nullptr);
+}
+
+// min of f_p over the triangle (local coordinates); returns d, writes (u, v)
+__device__ float tri_min(const float *v0, const float *v1, const float *v2, float r, float L, int iters, float *uo,
+                         float *vo)
+{
+    float e1[3] = {v1[0] - v0[0], v1[1] - v0[1], v1[2] - v0[2]};
+    float e2[3] = {v2[0] - v0[0], v2[1] - v0[1], v2[2] - v0[2]};
+    const float ig = 0.6180339887498949f;
+    float a = 0.f, b = 1.f, vc, vd;
+    float c = b - ig * (b - a), d = a + ig * (b - a);
+    float fc = inner_min(v0, e1, e2, c, r, L, iters, &vc);
+    float fd = inner_min(v0, e1, e2, d, r, L, iters, &vd);
+    int steps = iters + iters / 2;
+    for (int k = 0; k < steps; ++k) {
+        if (fc <= fd) {
+            b = d; d = c; fd = fc; vd = vc;
+            c = b - ig * (b - a);
+            fc = inner_min(v0, e1, e2, c, r, L, iters, &vc);
+        } else {
+            a = c; c = d; fc = fd; vc = vd;
+            d = a + ig * (b - a);
+            fd = inner_min(v0, e1, e2, d, r, L, iters, &vd);
+        }
+    }
+    float u = fc <= fd ? c : d, v = fc <= fd ? vc : vd, best = fc <= fd ? fc : fd;
+    float vu0, vu1;
+    float f0 = inner_min(v0, e1, e2, 0.f, r, L, iters, &vu0);
+    float f1 = inner_min(v0, e1, e2, 1.f, r, L, iters, &vu1);
+    if (f0 < best) { best = f0; u = 0.f; v = vu0; }
+    if (f1 < best) { best = f1; u = 1.f; v = vu1; }
+    *uo = u;
+    *vo = v;
+    return best;
+}
+
+// Eq. (18): s(d), s'(d), s''(d) with r = tau_in / tau_out and C^1 coefficients
+__device__ __forceinline__ void score3(const RefineDev &D, float d, float *s, float *s1, float *s2)
+{
+    float it = 1.f / D.tau_out;
+    float t = d * it;
+    if (t > 1.f) { *s = 0.f; *s1 = 0.f; *s2 = 0.f; }
+    else if (t > 0.f) {
+        float cs = cospif(0.5f * t), sn = sinpif(0.5f * t);
+        *s = cs * cs;
+        *s1 = -3.14159265358979f * cs * sn * it;
+        *s2 = -0.5f * 9.8696044010893586f * cospif(t) * it * it;
+    } else if (t > -D.rr) {
+        *s = fmaf(D.A * t, t * t, D.B * t * t) + 1.f;
+        *s1 = (3.f * D.A * t * t + 2.f * D.B * t) * it;
+        *s2 = (6.f * D.A * t + 2.f * D.B) * it * it;
+    } else {
+        *s = D.k_slope * (t + D.rr);
+        *s1 = D.k_slope * it;
+        *s2 = 0.f;
+    }
+}
+
+// Distance query of one probe pose against the mesh for object pose (R, p).
+// Returns the triangle index or -1 (no triangle passes Eq. (21)); fills d,
+// the local witness and the local unit normal.
+__device__ int dist_query(const RefineDev &D, const float *A, const float *bvec, float *d_out, float *xw, float *nl)
+{
+    int stack[64];
+    int sp = 0;
+    stack[sp++] = 0;
+    float best = INFINITY;
+    int bt = -1;
+    float bx[3] = {0.f, 0.f, 0.f};
+    const float eps = D.tau_out;
+    while (sp > 0) {
+        int ni = stack[--sp];
+        BvhNode nd = D.nodes[ni];
+        float q[3] = {nd.c[0] - bvec[0], nd.c[1] - bvec[1], nd.c[2] - bvec[2]};
+        float loc[3];
+        for (int k = 0; k < 3; ++k) loc[k] = fmaf(A[0 * 3 + k], q[0], fmaf(A[1 * 3 + k], q[1], A[2 * 3 + k] * q[2]));
+        float fc = sdf_cyl(loc[0], loc[1], loc[2], D.r, D.L, nullptr);
+        if (!(fc < nd.rad + eps)) continue;             // Eq. (21)
+        if (fc - nd.rad > best) continue;               // cannot beat the current minimum
+        if (nd.left < 0) {
+            for (int k = 0; k < nd.count; ++k) {
+                int t = D.tri_order[nd.right + k];
+                const float *ts = D.tri_sphere + 4 * t;
+                float qs[3] = {ts[0] - bvec[0], ts[1] - bvec[1], ts[2] - bvec[2]};
+                float ls[3];
+                for (int a = 0; a < 3; ++a) ls[a] = fmaf(A[0 * 3 + a], qs[0], fmaf(A[1 * 3 + a], qs[1], A[2 * 3 + a] * qs[2]));
+                float ft = sdf_cyl(ls[0], ls[1], ls[2], D.r, D.L, nullptr);
+                if (!(ft < ts[3] + eps)) continue;      // Eq. (21) for the triangle's sphere
+                if (ft - ts[3] > best) continue;
+                float lv[3][3];
+                for (int m = 0; m < 3; ++m) {
+                    const float *v = D.Vf + 3 * D.T[3 * t + m];
+                    float qv[3] = {v[0] - bvec[0], v[1] - bvec[1], v[2] - bvec[2]};
+                    for (int a = 0; a < 3; ++a)
+                        lv[m][a] = fmaf(A[0 * 3 + a], qv[0], fmaf(A[1 * 3 + a], qv[1], A[2 * 3 + a] * qv[2]));
+                }
+                float u, v;
+                float dk = tri_min(lv[0], lv[1], lv[2], D.r, D.L, D.tri_iters, &u, &v);
+                if (dk < best || (dk == best && t < bt)) {
+                    best = dk;
+                    bt = t;
+                    float w0 = 1.f - u - v;
+                    for (int a = 0; a < 3; ++a) bx[a] = fmaf(w0, lv[0][a], fmaf(u, lv[1][a], v * lv[2][a]));
+                }
+            }
+        } else if (sp + 2 <= 64) {
+            stack[sp++] = nd.right;
+            stack[sp++] = nd.left;
+        }
+    }
+    *d_out = best;
+    if (bt >= 0) {
+        float g[3];
+        sdf_cyl(bx[0], bx[1], bx[2], D.r, D.L, g);
+        float gn = sqrtf(dot3f(g, g));
+        for (int a = 0; a < 3; ++a) { nl[a] = g[a] / gn; xw[a] = bx[a]; }
+    }
+    return bt;
+}
+
+// One thread per (candidate, pose).  acc_part[(c * nblk + blk) * NACC + k].
+template <bool GRAD>
+__global__ void __launch_bounds__(128)
+k_refine_eval(RefineDev D, const CandF *cands, double *acc_part, float *dist_out, float *wit_out, float *nrm_out)
+{
+    const int c = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc[NACC];
+#pragma unroll
+    for (int k = 0; k < NACC; ++k) acc[k] = 0.0;
+    if (i < D.P) {
+        const CandF &cf = cands[c];
+        const PoseRec &pr = D.poses[i];
+        // probe pose in the object frame: A = R^T R_i, b = R^T (t_i - p);
+        // a mesh point m maps to probe-local A^T (m - b)
+        float A[9], bvec[3];
+        for (int a = 0; a < 3; ++a)
+            for (int k = 0; k < 3; ++k)
+                A[a * 3 + k] = fmaf(cf.R[0 * 3 + a], pr.Rf[0 * 3 + k], fmaf(cf.R[1 * 3 + a], pr.Rf[1 * 3 + k], cf.R[2 * 3 + a] * pr.Rf[2 * 3 + k]));
+        float tp[3] = {pr.tf[0] - cf.p[0], pr.tf[1] - cf.p[1], pr.tf[2] - cf.p[2]};
+        for (int a = 0; a < 3; ++a) bvec[a] = fmaf(cf.R[0 * 3 + a], tp[0], fmaf(cf.R[1 * 3 + a], tp[1], cf.R[2 * 3 + a] * tp[2]));
+        float d, xl[3], nl[3];
+        int bt = dist_query(D, A, bvec, &d, xl, nl);
+        float n[3] = {0.f, 0.f, 0.f}, w[3] = {0.f, 0.f, 0.f};
+        if (bt >= 0) {
+            for (int a = 0; a < 3; ++a) {
+                n[a] = fmaf(pr.Rf[a * 3 + 0], nl[0], fmaf(pr.Rf[a * 3 + 1], nl[1], pr.Rf[a * 3 + 2] * nl[2]));
+                w[a] = fmaf(pr.Rf[a * 3 + 0], xl[0], fmaf(pr.Rf[a * 3 + 1], xl[1], fmaf(pr.Rf[a * 3 + 2], xl[2], pr.tf[a])));
+            }
+        }
+        if (dist_out) {
+            size_t o = (size_t)c * D.P + i;
+            dist_out[o] = bt >= 0 ? d : INFINITY;
+            for (int a = 0; a < 3; ++a) { wit_out[3 * o + a] = w[a]; nrm_out[3 * o + a] = n[a]; }
+        }
+        if (bt >= 0) {
+            float s, s1, s2;
+            score3(D, d, &s, &s1, &s2);
+            acc[0] = -(double)s;
+            if (GRAD && (s1 != 0.f || s2 != 0.f)) {
+                float g[6];
+                for (int j = 0; j < 3; ++j) g[j] = fmaf(cf.V[0 * 3 + j], n[0], fmaf(cf.V[1 * 3 + j], n[1], cf.V[2 * 3 + j] * n[2]));
+                float wc[3] = {w[0] - cf.c[0], w[1] - cf.c[1], w[2] - cf.c[2]};
+                float tq[3] = {wc[1] * n[2] - wc[2] * n[1], wc[2] * n[0] - wc[0] * n[2], wc[0] * n[1] - wc[1] * n[0]};
+                for (int j = 0; j < 3; ++j) {
+                    float a1 = fmaf(cf.V[0 * 3 + j], tq[0], fmaf(cf.V[1 * 3 + j], tq[1], cf.V[2 * 3 + j] * tq[2]));
+                    float a2 = fmaf(cf.Mc[0 * 3 + j], n[0], fmaf(cf.Mc[1 * 3 + j], n[1], cf.Mc[2 * 3 + j] * n[2]));
+                    g[3 + j] = a1 + a2;
+                }
+                for (int j = 0; j < 6; ++j) acc[1 + j] = -(double)s1 * (double)g[j];
+                double wgt = s2 < 0.f ? -(double)s2 : 0.0;
+                int k = 7;
+                for (int a = 0; a < 6; ++a)
+                    for (int b = a; b < 6; ++b) acc[k++] = wgt * (double)g[a] * (double)g[b];
+            }
+        }
+    }
+    // block reduction in a fixed order
+    __shared__ double red[4][NACC];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NACC; ++k) {
+        double v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+        if (lane == 0) red[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NACC) {
+        double v = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) v += red[q][threadIdx.x];
+        acc_part[((size_t)c * gridDim.x + blockIdx.x) * NACC + threadIdx.x] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 per-candidate step
+// ---------------------------------------------------------------------------
+__device__ void vcoef(double th, double *a, double *b, double *da, double *db)
+{
+    if (th < 1e-4) {
+        double t2 = th * th;
+        *a = 0.5 - t2 / 24.0 + t2 * t2 / 720.0;
+        *b = 1.0 / 6.0 - t2 / 120.0 + t2 * t2 / 5040.0;
+        *da = -1.0 / 12.0 + t2 / 180.0;
+        *db = -1.0 / 60.0 + t2 / 1260.0;
+    } else {
+        double s = sin(th), c = cos(th);
+        *a = (1.0 - c) / (th * th);
+        *b = (th - s) / (th * th * th);
+        *da = (th * s - 2.0 * (1.0 - c)) / (th * th * th * th);
+        *db = ((1.0 - c) * th - 3.0 * (th - s)) / (th * th * th * th * th);
+    }
+}
+
+// pose T(xi) (Eq. (14)-(17)) and the derivative data of the next evaluation
+__device__ void cand_from_state(const double *st, CandF *out)
+{
+    const double *R0 = st, *p0 = st + 9, *an = st + 12, *xi = st + 15;
+    const double *u = xi, *w = xi + 3;
+    double th = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    double a, b, da, db;
+    vcoef(th, &a, &b, &da, &db);
+    double sA = th < 1e-4 ? 1.0 - th * th / 6.0 + th * th * th * th / 120.0 : sin(th) / th;
+    double K[9] = {0.0, -w[2], w[1], w[2], 0.0, -w[0], -w[1], w[0], 0.0};
+    double K2[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) K2[3 * i + j] = K[3 * i] * K[j] + K[3 * i + 1] * K[3 + j] + K[3 * i + 2] * K[6 + j];
+    double dR[9], V[9];
+    for (int k = 0; k < 9; ++k) {
+        double I = (k % 4 == 0) ? 1.0 : 0.0;
+        dR[k] = I + sA * K[k] + a * K2[k];
+        V[k] = I + a * K[k] + b * K2[k];
+    }
+    double R[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) R[3 * i + j] = dR[3 * i] * R0[j] + dR[3 * i + 1] * R0[3 + j] + dR[3 * i + 2] * R0[6 + j];
+    double Ra[3], dRRa[3], Vu[3];
+    for (int i = 0; i < 3; ++i) Ra[i] = R0[3 * i] * an[0] + R0[3 * i + 1] * an[1] + R0[3 * i + 2] * an[2];
+    for (int i = 0; i < 3; ++i) dRRa[i] = dR[3 * i] * Ra[0] + dR[3 * i + 1] * Ra[1] + dR[3 * i + 2] * Ra[2];
+    for (int i = 0; i < 3; ++i) Vu[i] = V[3 * i] * u[0] + V[3 * i + 1] * u[1] + V[3 * i + 2] * u[2];
+    // d(V u)/dw = -a [u]x + (w x u) (a'/th) w^T + b((w.u) I + w u^T - 2 u w^T) + (w x (w x u)) (b'/th) w^T
+    double wxu[3] = {w[1] * u[2] - w[2] * u[1], w[2] * u[0] - w[0] * u[2], w[0] * u[1] - w[1] * u[0]};
+    double wd = w[0] * u[0] + w[1] * u[1] + w[2] * u[2], ww = th * th;
+    double wxwxu[3];
+    for (int k = 0; k < 3; ++k) wxwxu[k] = w[k] * wd - u[k] * ww;
+    double Ku[9] = {0.0, -u[2], u[1], u[2], 0.0, -u[0], -u[1], u[0], 0.0};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double I = (i == j) ? 1.0 : 0.0;
+            double t1 = -a * Ku[3 * i + j] + wxu[i] * da * w[j];
+            double t2 = b * ((wd * I + w[i] * u[j]) - 2.0 * u[i] * w[j]) + wxwxu[i] * db * w[j];
+            out->Mc[3 * i + j] = (float)(t1 + t2);
+        }
+    for (int k = 0; k < 9; ++k) { out->R[k] = (float)R[k]; out->V[k] = (float)V[k]; }
+    for (int i = 0; i < 3; ++i) {
+        out->p[i] = (float)(((p0[i] + Vu[i]) + Ra[i]) - dRRa[i]);
+        out->c[i] = (float)((p0[i] + Vu[i]) + Ra[i]);
+    }
+}
+
+__device__ bool chol6(const double *H, const double *b, double *x)
+{
+    double L[36];
+    for (int i = 0; i < 36; ++i) L[i] = 0.0;
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = H[6 * i + j];
+            for (int k = 0; k < j; ++k) s -= L[6 * i + k] * L[6 * j + k];
+            if (i == j) {
+                if (!(s > 0.0)) return false;
+                L[6 * i + i] = sqrt(s);
+            } else {
+                L[6 * i + j] = s / L[6 * j + j];
+            }
+        }
+    double y[6];
+    for (int i = 0; i < 6; ++i) {
+        double s = b[i];
+        for (int k = 0; k < i; ++k) s -= L[6 * i + k] * y[k];
+        y[i] = s / L[6 * i + i];
+    }
+    for (int i = 5; i >= 0; --i) {
+        double s = y[i];
+        for (int k = i + 1; k < 6; ++k) s -= L[6 * k + i] * x[k];
+        x[i] = s / L[6 * i + i];
+    }
+    return true;
+}
+
+// prm: lambda, mu, step_t, step_r, b_t, b_r
+// mode 0: only refresh the candidate data from the state
+// mode 1: sum the partials, record J, take one projected Gauss-Newton step
+// mode 2: sum the partials and record J (final evaluation)
+__global__ void k_refine_solve(int K, int nblk, double *state, const double *acc_part, const double *prm, int mode,
+                               CandF *cands)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= K) return;
+    double *st = state + (size_t)c * ST;
+    double *xi = st + 15;
+    if (mode != 0) {
+        double acc[NACC];
+        for (int k = 0; k < NACC; ++k) acc[k] = 0.0;
+        for (int q = 0; q < nblk; ++q)
+            for (int k = 0; k < NACC; ++k) acc[k] += acc_part[((size_t)c * nblk + q) * NACC + k];
+        const double lam = prm[0], mu = prm[1];
+        double xx = 0.0;
+        for (int j = 0; j < 6; ++j) xx += xi[j] * xi[j];
+        st[21] = acc[0] + lam * xx;   // J (Eq. (19))
+        if (mode == 1) {
+            double G[6], H[36];
+            for (int j = 0; j < 6; ++j) G[j] = acc[1 + j] + 2.0 * lam * xi[j];
+            int k = 7;
+            for (int a = 0; a < 6; ++a)
+                for (int b = a; b < 6; ++b) { H[6 * a + b] = acc[k]; H[6 * b + a] = acc[k]; ++k; }
+            for (int j = 0; j < 6; ++j) H[7 * j] += 2.0 * lam + mu;
+            double nb[6], dl[6];
+            for (int j = 0; j < 6; ++j) nb[j] = -G[j];
+            if (chol6(H, nb, dl)) {
+                double mt = 0.0, mr = 0.0;
+                for (int j = 0; j < 3; ++j) { mt = fmax(mt, fabs(dl[j])); mr = fmax(mr, fabs(dl[3 + j])); }
+                double sc = 1.0;
+                if (mt > prm[2]) sc = fmin(sc, prm[2] / mt);
+                if (mr > prm[3]) sc = fmin(sc, prm[3] / mr);
+                for (int j = 0; j < 6; ++j) {
+                    double v = xi[j] + sc * dl[j];
+                    double bb = j < 3 ? prm[4] : prm[5];
+                    if (v > bb) v = bb;
+                    if (v < -bb) v = -bb;
+                    xi[j] = v;
+                }
+            }
+        }
+    }
+    cand_from_state(st, &cands[c]);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_refine_eval(const RefineDev &d, int K, const CandF *cands, double *acc_part, bool grad,
+                               float *dist_out, float *wit_out, float *nrm_out, cudaStream_t st)
+{
+    dim3 grid((d.P + 127) / 128, K);
+    if (grad) k_refine_eval<true><<<grid, 128, 0, st>>>(d, cands, acc_part, dist_out, wit_out, nrm_out);
+    else k_refine_eval<false><<<grid, 128, 0, st>>>(d, cands, acc_part, dist_out, wit_out, nrm_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refine_solve(int K, int nblk, double *state, const double *acc_part, const double *prm, int mode,
+                                CandF *cands, cudaStream_t st)
+{
+    k_refine_solve<<<(K + 63) / 64, 64, 0, st>>>(K, nblk, state, acc_part, prm, mode, cands);
+    return cudaGetLastError();
+}
+
+size_t cand_bytes() { return sizeof(CandF); }
+
+// Twists from a device FP32 array into the state (the differentiable form).
+__global__ void k_set_xi(int B, const float *xi, double *state)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    for (int j = 0; j < 6; ++j) state[(size_t)b * ST + 15 + j] = (double)xi[6 * b + j];
+}
+
+// J[b] and grad[b] (Eq. (19), (28)) from the partials.
+__global__ void k_finish_objective(int B, int nblk, const double *state, const double *acc_part, double lam, float *J,
+                                   float *grad, const float *gJ)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const double *xi = state + (size_t)b * ST + 15;
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int q = 0; q < nblk; ++q)
+        for (int k = 0; k < 7; ++k) acc[k] += acc_part[((size_t)b * nblk + q) * NACC + k];
+    double xx = 0.0;
+    for (int j = 0; j < 6; ++j) xx += xi[j] * xi[j];
+    if (J) J[b] = (float)(acc[0] + lam * xx);
+    if (grad) {
+        double sc = gJ ? (double)gJ[b] : 1.0;
+        for (int j = 0; j < 6; ++j) grad[6 * b + j] = (float)(sc * (acc[1 + j] + 2.0 * lam * xi[j]));
+    }
+}
+
+cudaError_t launch_set_xi(int B, const float *xi, double *state, cudaStream_t st)
+{
+    k_set_xi<<<(B + 63) / 64, 64, 0, st>>>(B, xi, state);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish_objective(int B, int nblk, const double *state, const double *acc_part, double lam, float *J,
+                                    float *grad, const float *gJ, cudaStream_t st)
+{
+    k_finish_objective<<<(B + 63) / 64, 64, 0, st>>>(B, nblk, state, acc_part, lam, J, grad, gJ);
+    return cudaGetLastError();
+}
+
+}  // namespace dock

@@ -1,0 +1,808 @@
+// Docking search kernels (Sec. IV): rotated swept-volume voxeliser fused with
+// the forward 2-D FFT of each lattice slab, the z-pass with the conjugate
+// object-spectrum multiply, and the inverse plane pass with the C2R along x
+// and the per-rotation argmax.  Correlation per Eq. (7), computed as
+// C = F^-1(conj(F(O)) . F(S)) (Eq. (9) with the conjugate on the object, the
+// reading that agrees with Eq. (7)-(8)).
+//
+// Data layout (complex64, kx fastest):
+//   Y[b][z < N][ky < M][kx < P]   forward x,y transform of slab z of S_b
+//   Z[b][z < M][ky < M][kx < P]   after forward z, multiply, inverse z
+//   spec[chunk][kz < M][32]       conj(F(O)) / M^3, f = ky P + kx in chunks of 32
+// P = M/2 + 2 (16-byte aligned rows); entries kx in (M/2, P) are zero.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dock_internal.h"
+#include "fft.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace dock {
+
+// ---------------------------------------------------------------------------
+// exact FP64 helpers (no contraction: every product and sum rounded as written)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double dm(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double da(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double ds(double a, double b) { return __dsub_rn(a, b); }
+
+__device__ void quat_to_mat_exact(const double *q, double *R)
+{
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = ds(1.0, dm(2.0, da(dm(y, y), dm(z, z))));
+    R[1] = dm(2.0, ds(dm(x, y), dm(w, z)));
+    R[2] = dm(2.0, da(dm(x, z), dm(w, y)));
+    R[3] = dm(2.0, da(dm(x, y), dm(w, z)));
+    R[4] = ds(1.0, dm(2.0, da(dm(x, x), dm(z, z))));
+    R[5] = dm(2.0, ds(dm(y, z), dm(w, x)));
+    R[6] = dm(2.0, ds(dm(x, z), dm(w, y)));
+    R[7] = dm(2.0, da(dm(y, z), dm(w, x)));
+    R[8] = ds(1.0, dm(2.0, da(dm(x, x), dm(y, y))));
+}
+
+// R = R(q), o = h round(R^T c_s / h) - (N/2) h   (Sec. IV-A: lattice origin)
+__global__ void k_rot_setup(const double *quats, int n, int rot0, const double *c_s, double h, int N, RotRec *out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    RotRec rr;
+    double q[4] = {quats[4 * i], quats[4 * i + 1], quats[4 * i + 2], quats[4 * i + 3]};
+    quat_to_mat_exact(q, rr.R);
+    double c0 = c_s[0], c1 = c_s[1], c2 = c_s[2];
+    for (int a = 0; a < 3; ++a) {
+        double u = da(da(dm(rr.R[0 * 3 + a], c0), dm(rr.R[1 * 3 + a], c1)), dm(rr.R[2 * 3 + a], c2));
+        rr.o[a] = ds(dm(h, round(__ddiv_rn(u, h))), dm((double)(N / 2), h));
+    }
+    for (int k = 0; k < 9; ++k) rr.Rf[k] = (float)rr.R[k];
+    for (int a = 0; a < 3; ++a) rr.of[a] = (float)rr.o[a];
+    rr.rot = rot0 + i;
+    rr.pad = 0;
+    out[i] = rr;
+}
+
+cudaError_t launch_rot_setup(const double *quats, int n, int rot0, const double *c_s, double h, int N, RotRec *out,
+                             cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_rot_setup<<<(n + 127) / 128, 128, 0, st>>>(quats, n, rot0, c_s, h, N, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// swept-volume voxeliser (Eq. (5)-(6)) for one slab z of the rotated lattice
+// ---------------------------------------------------------------------------
+
+// Exact inside test of Eq. (5) at lattice voxel (jx, jy, jz): the same FP64
+// expression, in the same order, as the definition:
+//   p = h j + o ; x = R p ; d = x - t_i ; l = R_i^T d ;
+//   l0^2 + l1^2 <= r^2  and  0 <= l2 <= L.
+__device__ __noinline__ bool inside_exact(const RotRec &rr, const PoseRec &pr, double h, double r2, double L, int jx,
+                                          int jy, int jz)
+{
+    double p0 = da(dm(h, (double)jx), rr.o[0]);
+    double p1 = da(dm(h, (double)jy), rr.o[1]);
+    double p2 = da(dm(h, (double)jz), rr.o[2]);
+    double d[3];
+    for (int b = 0; b < 3; ++b)
+        d[b] = ds(da(da(dm(rr.R[b * 3 + 0], p0), dm(rr.R[b * 3 + 1], p1)), dm(rr.R[b * 3 + 2], p2)), pr.t[b]);
+    const double *Ri = pr.R;
+    double l0 = da(da(dm(Ri[0], d[0]), dm(Ri[3], d[1])), dm(Ri[6], d[2]));
+    double l1 = da(da(dm(Ri[1], d[0]), dm(Ri[4], d[1])), dm(Ri[7], d[2]));
+    double l2 = da(da(dm(Ri[2], d[0]), dm(Ri[5], d[1])), dm(Ri[8], d[2]));
+    return da(dm(l0, l0), dm(l1, l1)) <= r2 && 0.0 <= l2 && l2 <= L;
+}
+
+struct VoxCtx {
+    // FP32 pose frame in lattice voxel units: l(j) = B^T (j - c)
+    float B[9];   // B[a*3+k] = (R^T R_i)[a][k]
+    float c[3];
+};
+
+// Classify voxel jx on the row whose FP32 local coordinates at jx = 0 are l0
+// (step bx per voxel).  Margins cover the FP32 error of l (bounded well below
+// 2e-4 voxels for lattices of <= 256 voxels); inside the margin band the exact
+// FP64 predicate decides.
+__device__ __forceinline__ int classify(const float *l0, const float *bx, int jx, float rv2, float lv, float mr,
+                                        float mz, const RotRec &rr, const PoseRec &pr, double h, double r2d,
+                                        double Ld, int jy, int jz)
+{
+    float fx = (float)jx;
+    float a = fmaf(fx, bx[0], l0[0]);
+    float b = fmaf(fx, bx[1], l0[1]);
+    float z = fmaf(fx, bx[2], l0[2]);
+    float rad2 = fmaf(a, a, b * b);
+    if (rad2 <= rv2 - mr && z >= mz && z <= lv - mz) return 1;
+    if (rad2 > rv2 + mr || z < -mz || z > lv + mz) return 0;
+    return inside_exact(rr, pr, h, r2d, Ld, jx, jy, jz) ? 1 : 0;
+}
+
+__device__ __forceinline__ void set_bits(uint32_t *row, int lo, int hi)
+{
+    int w0 = lo >> 5, w1 = hi >> 5;
+    for (int w = w0; w <= w1; ++w) {
+        int a = (w == w0) ? (lo & 31) : 0;
+        int b = (w == w1) ? (hi & 31) : 31;
+        uint32_t m = (b == 31 ? 0xFFFFFFFFu : ((1u << (b + 1)) - 1u)) & ~((1u << a) - 1u);
+        atomicOr(&row[w], m);
+    }
+}
+
+// Fill bits[jy * NW + w] for slab jz with the union of all probe cylinders.
+template <int N>
+__device__ void voxelise_slab(const Geo &g, const RotRec &rr, const PoseRec *poses, int P, int jz, uint32_t *bits,
+                              int *err)
+{
+    constexpr int NW = N / 32 > 0 ? N / 32 : 1;
+    const float rv = g.rv, lv = g.lv, rv2 = rv * rv;
+    const float mz = 8e-4f, mr = 1.6e-3f * rv + 1e-3f;
+    const double h = g.h, r2d = g.r * g.r, Ld = g.L;
+    const float ih = g.inv_h;
+    const float *Rf = rr.Rf;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const PoseRec &pr = poses[i];
+        // tip in voxel coordinates and axis direction in the lattice frame
+        float tx = pr.tf[0], ty = pr.tf[1], tz = pr.tf[2];
+        float cz = (fmaf(Rf[2], tx, fmaf(Rf[5], ty, Rf[8] * tz)) - rr.of[2]) * ih;
+        float Az = fmaf(Rf[2], pr.Rf[2], fmaf(Rf[5], pr.Rf[5], Rf[8] * pr.Rf[8]));
+        float sz = rv * sqrtf(fmaxf(0.f, 1.f - Az * Az)) + 1.5f;
+        float z0 = fminf(cz, cz + lv * Az) - sz, z1 = fmaxf(cz, cz + lv * Az) + sz;
+        float fz = (float)jz;
+        if (fz < z0 || fz > z1) continue;
+        VoxCtx v;
+        for (int k = 0; k < 3; ++k)
+            for (int a = 0; a < 3; ++a)
+                v.B[a * 3 + k] = fmaf(Rf[0 * 3 + a], pr.Rf[0 * 3 + k], fmaf(Rf[1 * 3 + a], pr.Rf[1 * 3 + k], Rf[2 * 3 + a] * pr.Rf[2 * 3 + k]));
+        for (int a = 0; a < 3; ++a)
+            v.c[a] = (fmaf(Rf[0 * 3 + a], tx, fmaf(Rf[1 * 3 + a], ty, Rf[2 * 3 + a] * tz)) - rr.of[a]) * ih;
+        float Ax = v.B[0 * 3 + 2], Ay = v.B[1 * 3 + 2];
+        (void)Ax;
+        // axis-parameter range that reaches this slab, then the row range
+        float u0, u1;
+        if (fabsf(Az) > 1e-6f) {
+            float ua = (fz - v.c[2] - sz) / Az, ub = (fz - v.c[2] + sz) / Az;
+            u0 = fmaxf(0.f, fminf(ua, ub));
+            u1 = fminf(lv, fmaxf(ua, ub));
+            if (u0 > u1) continue;
+        } else {
+            u0 = 0.f;
+            u1 = lv;
+        }
+        float sy = rv * sqrtf(fmaxf(0.f, 1.f - Ay * Ay)) + 1.5f;
+        float ylo = v.c[1] + fminf(u0 * Ay, u1 * Ay) - sy, yhi = v.c[1] + fmaxf(u0 * Ay, u1 * Ay) + sy;
+        int jy0 = max(0, (int)ceilf(ylo)), jy1 = min(N - 1, (int)floorf(yhi));
+        const float bx[3] = {v.B[0], v.B[1], v.B[2]};   // B^T e_x
+        const float Aq = fmaf(bx[0], bx[0], bx[1] * bx[1]);
+        for (int jy = jy0; jy <= jy1; ++jy) {
+            float dyv = (float)jy - v.c[1], dzv = fz - v.c[2], dxv = -v.c[0];
+            float l0[3];
+            for (int k = 0; k < 3; ++k) l0[k] = fmaf(v.B[0 * 3 + k], dxv, fmaf(v.B[1 * 3 + k], dyv, v.B[2 * 3 + k] * dzv));
+            // candidate interval from the quadratic (radial) and linear (axial) constraints
+            float lo = -1e30f, hi = 1e30f;
+            int wide = 2;
+            if (Aq > 1e-6f) {
+                float Bq = fmaf(l0[0], bx[0], l0[1] * bx[1]);
+                float Cq = fmaf(l0[0], l0[0], l0[1] * l0[1]) - rv2;
+                float disc = fmaf(Bq, Bq, -Aq * Cq);
+                if (disc < -1e-3f * (Bq * Bq + fabsf(Aq * Cq)) - 1e-2f) continue;
+                float sq = sqrtf(fmaxf(disc, 0.f));
+                lo = (-Bq - sq) / Aq;
+                hi = (-Bq + sq) / Aq;
+                if (Aq < 0.05f) wide = N;
+            } else {
+                float Cq = fmaf(l0[0], l0[0], l0[1] * l0[1]) - rv2;
+                if (Cq > mr + 1e-2f) continue;
+                wide = N;
+            }
+            if (fabsf(bx[2]) > 1e-6f) {
+                float za = -l0[2] / bx[2], zb = (lv - l0[2]) / bx[2];
+                lo = fmaxf(lo, fminf(za, zb));
+                hi = fminf(hi, fmaxf(za, zb));
+            } else if (l0[2] < -0.01f || l0[2] > lv + 0.01f) {
+                continue;
+            }
+            if (lo > hi + 2.f) continue;
+            lo = fmaxf(lo, -4.f);
+            hi = fminf(hi, (float)N + 4.f);
+            int ja = max(0, (int)floorf(lo) - wide), jb = min(N - 1, (int)ceilf(hi) + wide);
+            if (ja > jb) continue;
+            int jl = ja;
+            if (classify(l0, bx, jl, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz)) {
+                while (jl > 0 && classify(l0, bx, jl - 1, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz)) --jl;
+            } else {
+                do { ++jl; } while (jl <= jb && !classify(l0, bx, jl, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz));
+                if (jl > jb) continue;
+            }
+            int jr = jb;
+            if (classify(l0, bx, jr, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz)) {
+                while (jr < N - 1 && classify(l0, bx, jr + 1, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz)) ++jr;
+            } else {
+                do { --jr; } while (jr > jl && !classify(l0, bx, jr, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz));
+            }
+            set_bits(bits + jy * NW, jl, jr);
+        }
+    }
+    (void)err;
+}
+
+// ---------------------------------------------------------------------------
+// K_A: voxelise slab z of rotation b and transform it along x (R2C, closed
+// form per run of set bits) and y (radix FFT); write Y[b][z].
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void __launch_bounds__(Plan<M>::T * 32)
+k_vox_fwd(Geo g, const RotRec *rots, const PoseRec *poses, int P, float2 *Y, const float2 *tw_g, const float2 *q_g,
+          int *err)
+{
+    constexpr int N = M / 2, H = M / 2, NW = N / 32, T = Plan<M>::T, COLS = 32, E = Plan<M>::E;
+    extern __shared__ __align__(16) unsigned char smem[];
+    cf *X = reinterpret_cast<cf *>(smem);                       // [N][H] packed columns
+    cf *xb = X + N * H;                                          // [M][COLS] exchange / staging
+    cf *tw = xb + M * COLS;                                      // [M]
+    uint32_t *bits = reinterpret_cast<uint32_t *>(tw + M);       // [N][NW]
+
+    const int jz = blockIdx.x, b = blockIdx.y;
+    const RotRec rr = rots[b];
+    for (int i = threadIdx.x; i < M; i += blockDim.x) { float2 w = tw_g[i]; tw[i] = cmake(w.x, w.y); }
+    for (int i = threadIdx.x; i < N * NW; i += blockDim.x) bits[i] = 0u;
+    __syncthreads();
+    voxelise_slab<N>(g, rr, poses, P, jz, bits, err);
+    __syncthreads();
+
+    // x: X[y][kx] = sum over runs [a, a+len) of sum_x exp(-2 pi i kx x / M)
+    //             = (w^(kx a) - w^(kx (a+len))) / (1 - w^kx)   (kx != 0)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    constexpr int KPL = H / 32;   // kx values per lane
+    cf qv[KPL];
+#pragma unroll
+    for (int m = 0; m < KPL; ++m) { float2 t = q_g[lane + 32 * m]; qv[m] = cmake(t.x, t.y); }
+    for (int y = warp; y < N; y += nwarp) {
+        cf acc[KPL];
+#pragma unroll
+        for (int m = 0; m < KPL; ++m) acc[m] = cmake(0.f, 0.f);
+        float nyq = 0.f;
+        uint32_t prevw = 0;
+        int open = -1;
+        for (int w = 0; w <= NW; ++w) {
+            uint32_t cur = (w < NW) ? bits[y * NW + w] : 0u;
+            uint32_t prev = (cur << 1) | (prevw >> 31);
+            uint32_t rise = cur & ~prev, fall = ~cur & prev;
+            // events in increasing bit order
+            uint32_t ev = rise | fall;
+            while (ev) {
+                int bpos = __ffs(ev) - 1;
+                ev &= ev - 1;
+                int xpos = w * 32 + bpos;
+                if ((rise >> bpos) & 1u) {
+                    open = xpos;
+                } else {
+                    int a = open, len = xpos - open;
+#pragma unroll
+                    for (int m = 0; m < KPL; ++m) {
+                        int kx = lane + 32 * m;
+                        if (kx == 0) {
+                            acc[m].x += (float)len;
+                        } else {
+                            int i0 = (kx * a) % M, i1 = (kx * (a + len)) % M;
+                            cf d = csub(tw[i0], tw[i1]);
+                            acc[m] = cadd(acc[m], cmul(d, qv[m]));
+                        }
+                    }
+                    if (len & 1) nyq += (a & 1) ? -1.f : 1.f;
+                    open = -1;
+                }
+            }
+            prevw = cur;
+        }
+#pragma unroll
+        for (int m = 0; m < KPL; ++m) {
+            int kx = lane + 32 * m;
+            cf val = acc[m];
+            if (kx == 0) val.y = nyq;          // pack the Nyquist column into column 0
+            X[y * H + kx] = val;
+        }
+    }
+    __syncthreads();
+
+    // y: FFT of each packed column (N non-zero inputs of M), then unpack
+    // column 0 into kx = 0 and kx = M/2 and write Y[b][jz][ky][kx].
+    float2 *Yb = Y + ((size_t)b * N + jz) * (size_t)M * g.P;
+    const int c = threadIdx.x % COLS, j = threadIdx.x / COLS;
+    for (int p0 = 0; p0 < H; p0 += COLS) {
+        cf v[E];
+#pragma unroll
+        for (int s = 0; s < E; ++s) {
+            int yy = in_index<M>(j, s);
+            v[s] = (yy < N) ? X[yy * H + p0 + c] : cmake(0.f, 0.f);
+        }
+        fft_column<M, false>(v, j, xb, c, COLS, tw);
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < E; ++s) xb[out_index<M>(j, s) * COLS + c] = v[s];
+        __syncthreads();
+        for (int e = threadIdx.x; e < M * COLS; e += blockDim.x) {
+            int ky = e / COLS, cc = e % COLS, kx = p0 + cc;
+            cf val = xb[ky * COLS + cc];
+            float2 *row = Yb + (size_t)ky * g.P;
+            if (kx == 0) {
+                cf o = xb[((M - ky) % M) * COLS];
+                cf oc = cconj(o);
+                cf y0 = cscale(cadd(val, oc), 0.5f);
+                cf w = csub(val, oc);
+                cf yn = cmake(0.5f * w.y, -0.5f * w.x);
+                row[0] = make_float2(y0.x, y0.y);
+                row[H] = make_float2(yn.x, yn.y);
+                for (int k = H + 1; k < g.P; ++k) row[k] = make_float2(0.f, 0.f);
+            } else {
+                row[kx] = make_float2(val.x, val.y);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int M>
+static size_t vox_fwd_smem()
+{
+    constexpr int N = M / 2, H = M / 2, NW = N / 32;
+    return sizeof(cf) * ((size_t)N * H + (size_t)M * 32 + M) + sizeof(uint32_t) * N * NW;
+}
+
+template <int M>
+static cudaError_t launch_vox_fwd_t(const Geo &g, const RotRec *rots, int B, const PoseRec *poses, int P, float2 *Y,
+                                    const float2 *tw, const float2 *q, int *err, cudaStream_t st)
+{
+    size_t sm = vox_fwd_smem<M>();
+    cudaError_t e = cudaFuncSetAttribute(k_vox_fwd<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    dim3 grid(M / 2, B);
+    k_vox_fwd<M><<<grid, Plan<M>::T * 32, sm, st>>>(g, rots, poses, P, Y, tw, q, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vox_fwd(const Geo &g, const RotRec *rots, int B, const PoseRec *poses, int P, float2 *Y,
+                           const float2 *tw, const float2 *q, int *err, cudaStream_t st)
+{
+    switch (g.M) {
+    case 64: return launch_vox_fwd_t<64>(g, rots, B, poses, P, Y, tw, q, err, st);
+    case 128: return launch_vox_fwd_t<128>(g, rots, B, poses, P, Y, tw, q, err, st);
+    case 192: return launch_vox_fwd_t<192>(g, rots, B, poses, P, Y, tw, q, err, st);
+    case 256: return launch_vox_fwd_t<256>(g, rots, B, poses, P, Y, tw, q, err, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// Bits of S_b to a byte array (test hook): one block per (slab, rotation).
+template <int N>
+__global__ void k_vox_export(Geo g, const RotRec *rots, const PoseRec *poses, int P, uint8_t *out, int *err)
+{
+    constexpr int NW = N / 32;
+    __shared__ uint32_t bits[N * NW];
+    const int jz = blockIdx.x, b = blockIdx.y;
+    for (int i = threadIdx.x; i < N * NW; i += blockDim.x) bits[i] = 0u;
+    __syncthreads();
+    voxelise_slab<N>(g, rots[b], poses, P, jz, bits, err);
+    __syncthreads();
+    uint8_t *o = out + ((size_t)b * N + jz) * N * N;
+    for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
+        int y = i / N, x = i % N;
+        o[i] = (bits[y * NW + (x >> 5)] >> (x & 31)) & 1u;
+    }
+}
+
+cudaError_t launch_vox_export(const Geo &g, const RotRec *rots, int B, const PoseRec *poses, int P, uint8_t *bits,
+                              int *err, cudaStream_t st)
+{
+    dim3 grid(g.N, B);
+    switch (g.N) {
+    case 32: k_vox_export<32><<<grid, 256, 0, st>>>(g, rots, poses, P, bits, err); break;
+    case 64: k_vox_export<64><<<grid, 256, 0, st>>>(g, rots, poses, P, bits, err); break;
+    case 96: k_vox_export<96><<<grid, 256, 0, st>>>(g, rots, poses, P, bits, err); break;
+    case 128: k_vox_export<128><<<grid, 256, 0, st>>>(g, rots, poses, P, bits, err); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// K_B: per chunk of 32 columns f = ky P + kx: forward FFT along z (N non-zero
+// inputs), multiply by conj(F(O)) / M^3, inverse FFT along z.  The spectrum
+// of the chunk stays in registers across the `group` rotations of the block.
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void __launch_bounds__(Plan<M>::T * 32)
+k_zpass(int P, int B, int group, const float2 *Y, const float2 *spec, float2 *Z, const float2 *tw_g)
+{
+    constexpr int N = M / 2, T = Plan<M>::T, E = Plan<M>::E, COLS = 32;
+    constexpr int R_LAST = Plan<M>::R(Plan<M>::S - 1);
+    extern __shared__ __align__(16) unsigned char smem[];
+    cf *xb = reinterpret_cast<cf *>(smem);   // [M][COLS]
+    cf *tw = xb + M * COLS;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) { float2 w = tw_g[i]; tw[i] = cmake(w.x, w.y); }
+    const int chunk = blockIdx.x;
+    const int c = threadIdx.x % COLS, j = threadIdx.x / COLS;
+    const size_t plane = (size_t)M * P;
+    const size_t f = (size_t)chunk * COLS + c;
+    // spectrum values in input-slot order of the inverse transform: slot s <-> kz = j + (M/E) s
+    cf sp[E];
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+        float2 t = spec[((size_t)chunk * M + (j + (M / E) * s)) * COLS + c];
+        sp[s] = cmake(t.x, t.y);
+    }
+    __syncthreads();
+    const int b0 = blockIdx.y * group;
+    for (int bi = 0; bi < group; ++bi) {
+        int b = b0 + bi;
+        if (b >= B) break;
+        const float2 *Yb = Y + (size_t)b * N * plane;
+        cf v[E];
+#pragma unroll
+        for (int s = 0; s < E; ++s) {
+            int z = in_index<M>(j, s);
+            if (z < N) { float2 t = Yb[(size_t)z * plane + f]; v[s] = cmake(t.x, t.y); }
+            else v[s] = cmake(0.f, 0.f);
+        }
+        fft_column<M, false>(v, j, xb, c, COLS, tw);
+        // forward output slot (bb, r) holds kz = j + (M/E)(bb + (E/R_LAST) r)
+        cf w[E];
+#pragma unroll
+        for (int bb = 0; bb < E / R_LAST; ++bb)
+#pragma unroll
+            for (int r = 0; r < R_LAST; ++r) {
+                int k = bb + (E / R_LAST) * r;
+                w[k] = cmul(v[bb * R_LAST + r], sp[k]);
+            }
+        __syncthreads();
+        fft_column<M, true>(w, j, xb, c, COLS, tw);
+        float2 *Zb = Z + (size_t)b * M * plane;
+#pragma unroll
+        for (int s = 0; s < E; ++s) {
+            int z = out_index<M>(j, s);
+            Zb[(size_t)z * plane + f] = make_float2(w[s].x, w[s].y);
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_zpass(const Geo &g, int B, int group, const float2 *Y, const float2 *spec, float2 *Z,
+                         const float2 *tw, cudaStream_t st)
+{
+    int chunks = g.M * g.P / 32;
+    dim3 grid(chunks, (B + group - 1) / group);
+    switch (g.M) {
+#define ZCASE(MM)                                                                                            \
+    case MM: {                                                                                               \
+        size_t sm = sizeof(cf) * ((size_t)MM * 32 + MM);                                                     \
+        cudaError_t e = cudaFuncSetAttribute(k_zpass<MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+        if (e != cudaSuccess) return e;                                                                      \
+        k_zpass<MM><<<grid, Plan<MM>::T * 32, sm, st>>>(g.P, B, group, Y, spec, Z, tw);                      \
+        break;                                                                                               \
+    }
+        ZCASE(64) ZCASE(128) ZCASE(192) ZCASE(256)
+#undef ZCASE
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// K_C: plane z of rotation b: inverse FFT along y of every packed column
+// (column 0 carries kx = 0 + i kx = M/2), then C2R along x of every row by a
+// half-length complex inverse FFT, and the argmax with the lowest linear
+// index on ties.  For M = 256 the plane (256 KB) is split over a 2-CTA
+// cluster; each CTA reads the other half of its rows through distributed
+// shared memory.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long pack_key(float v, uint32_t idx)
+{
+    uint32_t u = __float_as_uint(__fadd_rn(v, 0.0f));   // -0 -> +0: equal scores compare equal
+    uint32_t k = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    return ((unsigned long long)k << 32) | (unsigned long long)(0xFFFFFFFFu - idx);
+}
+
+template <int M> struct PlaneCfg {
+    static constexpr int CL = (M >= 256) ? 2 : 1;          // CTAs per plane
+    static constexpr int H = M / 2;
+    static constexpr int PC = H / CL;                      // packed columns per CTA
+    static constexpr int NT = Plan<M>::T * 32;             // threads
+};
+
+template <int M, bool EXPORT>
+__device__ __forceinline__ void plane_body(const float2 *Zp, const float2 *tw_g, unsigned long long *key, float *Cout,
+                                           int zc, cf *pb, cf *xb, cf *tw, int rank, cf *peer)
+{
+    constexpr int H = M / 2, CL = PlaneCfg<M>::CL, PC = PlaneCfg<M>::PC, E = Plan<M>::E;
+    constexpr int COLS = 32, PP = PC + 1;   // odd pitch: rows of one warp hit distinct banks
+    const int P = H + 2;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) { float2 w = tw_g[i]; tw[i] = cmake(w.x, w.y); }
+    __syncthreads();
+    // phase 1: inverse FFT along y of this CTA's packed columns
+    {
+        const int c = threadIdx.x % COLS, j = threadIdx.x / COLS;
+        for (int p0 = 0; p0 < PC; p0 += COLS) {
+            int pl = p0 + c;                   // local packed column
+            int pc = rank * PC + pl;           // global packed column
+            bool act = pl < PC;
+            cf v[E];
+#pragma unroll
+            for (int s = 0; s < E; ++s) {
+                int ky = in_index<M>(j, s);
+                cf val = cmake(0.f, 0.f);
+                if (act) {
+                    float2 t = Zp[(size_t)ky * P + pc];
+                    val = cmake(t.x, t.y);
+                    if (pc == 0) {
+                        float2 u = Zp[(size_t)ky * P + H];
+                        val = cmake(val.x - u.y, val.y + u.x);   // + i * Z[ky][M/2]
+                    }
+                }
+                v[s] = val;
+            }
+            fft_column<M, true>(v, j, xb, c, COLS, tw);
+            if (act) {
+#pragma unroll
+                for (int s = 0; s < E; ++s) pb[out_index<M>(j, s) * PP + pl] = v[s];
+            }
+            __syncthreads();
+        }
+    }
+    if constexpr (CL > 1) {
+        cg::this_cluster().sync();
+    } else {
+        __syncthreads();
+    }
+    // phase 2: C2R along x of rows [rank M/CL, (rank+1) M/CL)
+    {
+        constexpr int TH = Plan<H>::T, EH = Plan<H>::E, RPR = PlaneCfg<M>::NT / TH;   // rows per round
+        const int rowl = threadIdx.x % RPR, j = threadIdx.x / RPR;
+        const int rows = M / CL;
+        float best = -INFINITY;
+        uint32_t bidx = 0xFFFFFFFFu;
+        for (int r0 = 0; r0 < rows; r0 += RPR) {
+            int y = rank * rows + r0 + rowl;
+            bool act = (r0 + rowl) < rows;
+            cf v[EH];
+#pragma unroll
+            for (int s = 0; s < EH; ++s) {
+                int k = in_index<H>(j, s);
+                cf Ek = cmake(0.f, 0.f), Ok = cmake(0.f, 0.f);
+                if (act) {
+                    cf Wk, Wm;   // W[k], W[H - k]
+                    if (k == 0) {
+                        cf p = (CL > 1 && rank != 0) ? peer[y * PP + 0] : pb[y * PP + 0];
+                        Wk = cmake(p.x, 0.f);
+                        Wm = cmake(p.y, 0.f);
+                    } else {
+                        int o1 = k / PC, l1 = k % PC, k2 = H - k, o2 = k2 / PC, l2 = k2 % PC;
+                        Wk = (CL > 1 && o1 != rank) ? peer[y * PP + l1] : pb[y * PP + l1];
+                        Wm = (CL > 1 && o2 != rank) ? peer[y * PP + l2] : pb[y * PP + l2];
+                    }
+                    cf wc = cconj(Wm);
+                    Ek = cadd(Wk, wc);
+                    Ok = cmul(csub(Wk, wc), cconj(tw[k]));   // exp(+2 pi i k / M)
+                }
+                v[s] = cmake(Ek.x - Ok.y, Ek.y + Ok.x);   // E + i O
+            }
+            fft_column<H, true, 2>(v, j, xb, rowl, RPR, tw);
+            if (act) {
+#pragma unroll
+                for (int s = 0; s < EH; ++s) {
+                    int n = out_index<H>(j, s);
+                    uint32_t base = ((uint32_t)zc * M + (uint32_t)y) * M + 2u * n;
+                    if (EXPORT) {
+                        Cout[base] = v[s].x;
+                        Cout[base + 1] = v[s].y;
+                    }
+                    float a0 = v[s].x, a1 = v[s].y;
+                    if (a0 > best || (a0 == best && base < bidx)) { best = a0; bidx = base; }
+                    if (a1 > best || (a1 == best && base + 1 < bidx)) { best = a1; bidx = base + 1; }
+                }
+            }
+            __syncthreads();
+        }
+        if (!EXPORT) {
+            unsigned long long k = (bidx == 0xFFFFFFFFu) ? 0ull : pack_key(best, bidx);
+            for (int o = 16; o > 0; o >>= 1) {
+                unsigned long long k2 = __shfl_down_sync(0xFFFFFFFFu, k, o);
+                k = k2 > k ? k2 : k;
+            }
+            __shared__ unsigned long long wk[32];
+            int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            if (lane == 0) wk[warp] = k;
+            __syncthreads();
+            if (warp == 0) {
+                k = (lane < (int)(blockDim.x >> 5)) ? wk[lane] : 0ull;
+                for (int o = 16; o > 0; o >>= 1) {
+                    unsigned long long k2 = __shfl_down_sync(0xFFFFFFFFu, k, o);
+                    k = k2 > k ? k2 : k;
+                }
+                if (lane == 0 && k) atomicMax(key, k);
+            }
+        }
+    }
+    if constexpr (CL > 1) cg::this_cluster().sync();   // keep smem alive until the peer is done reading
+}
+
+template <int M>
+__global__ void __launch_bounds__(PlaneCfg<M>::NT)
+k_plane(int B, const float2 *Z, const float2 *tw_g, const RotRec *rots, unsigned long long *keys)
+{
+    constexpr int H = M / 2, CL = PlaneCfg<M>::CL, PC = PlaneCfg<M>::PC, COLS = 32;
+    extern __shared__ __align__(16) unsigned char smem[];
+    cf *pb = reinterpret_cast<cf *>(smem);    // [M][PC + 1]
+    cf *xb = pb + M * (PC + 1);               // [M][COLS] (>= [H][RPR])
+    cf *tw = xb + M * COLS;                   // [M]
+    const int zc = blockIdx.x / CL, b = blockIdx.y;
+    int rank = 0;
+    cf *peer = pb;
+    if constexpr (CL > 1) {
+        cg::cluster_group cl = cg::this_cluster();
+        rank = (int)cl.block_rank();
+        peer = cl.map_shared_rank(pb, rank ^ 1);
+    }
+    const size_t plane = (size_t)M * (H + 2);
+    const float2 *Zp = Z + ((size_t)b * M + zc) * plane;
+    plane_body<M, false>(Zp, tw_g, &keys[rots[b].rot], nullptr, zc, pb, xb, tw, rank, peer);
+}
+
+template <int M>
+__global__ void __launch_bounds__(PlaneCfg<M>::NT)
+k_plane_export(const float2 *Z, const float2 *tw_g, float *C)
+{
+    constexpr int H = M / 2, CL = PlaneCfg<M>::CL, PC = PlaneCfg<M>::PC, COLS = 32;
+    extern __shared__ __align__(16) unsigned char smem[];
+    cf *pb = reinterpret_cast<cf *>(smem);
+    cf *xb = pb + M * (PC + 1);
+    cf *tw = xb + M * COLS;
+    const int zc = blockIdx.x / CL;
+    int rank = 0;
+    cf *peer = pb;
+    if constexpr (CL > 1) {
+        cg::cluster_group cl = cg::this_cluster();
+        rank = (int)cl.block_rank();
+        peer = cl.map_shared_rank(pb, rank ^ 1);
+    }
+    const size_t plane = (size_t)M * (H + 2);
+    plane_body<M, true>(Z + (size_t)zc * plane, tw_g, nullptr, C, zc, pb, xb, tw, rank, peer);
+}
+
+template <int M>
+static size_t plane_smem() { return sizeof(cf) * ((size_t)M * (PlaneCfg<M>::PC + 1) + (size_t)M * 32 + M); }
+
+template <int M, bool EXPORT>
+static cudaError_t launch_plane_t(int B, const float2 *Z, const float2 *tw, const RotRec *rots,
+                                  unsigned long long *keys, float *C, cudaStream_t st)
+{
+    constexpr int CL = PlaneCfg<M>::CL;
+    size_t sm = plane_smem<M>();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(M * CL, EXPORT ? 1 : B);
+    cfg.blockDim = dim3(PlaneCfg<M>::NT);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e;
+    if (EXPORT) {
+        e = cudaFuncSetAttribute(k_plane_export<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        e = cudaLaunchKernelEx(&cfg, k_plane_export<M>, Z, tw, C);
+    } else {
+        e = cudaFuncSetAttribute(k_plane<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        e = cudaLaunchKernelEx(&cfg, k_plane<M>, B, Z, tw, rots, keys);
+    }
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plane(const Geo &g, int B, const float2 *Z, const float2 *tw, const RotRec *rots,
+                         unsigned long long *keys, cudaStream_t st)
+{
+    switch (g.M) {
+    case 64: return launch_plane_t<64, false>(B, Z, tw, rots, keys, nullptr, st);
+    case 128: return launch_plane_t<128, false>(B, Z, tw, rots, keys, nullptr, st);
+    case 192: return launch_plane_t<192, false>(B, Z, tw, rots, keys, nullptr, st);
+    case 256: return launch_plane_t<256, false>(B, Z, tw, rots, keys, nullptr, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_plane_export(const Geo &g, const float2 *Z, const float2 *tw, float *C, cudaStream_t st)
+{
+    switch (g.M) {
+    case 64: return launch_plane_t<64, true>(1, Z, tw, nullptr, nullptr, C, st);
+    case 128: return launch_plane_t<128, true>(1, Z, tw, nullptr, nullptr, C, st);
+    case 192: return launch_plane_t<192, true>(1, Z, tw, nullptr, nullptr, C, st);
+    case 256: return launch_plane_t<256, true>(1, Z, tw, nullptr, nullptr, C, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K9: top-K over rotations, score descending then rotation ascending, and the
+// candidate poses T = (R, R (h dk + o_s - o_o)) (Eq. (8)).
+// ---------------------------------------------------------------------------
+__global__ void k_topk(const unsigned long long *keys, int n, int K, int N, int M, double h, const double *o_o,
+                       const double *quats, const RotRec *rots_all, dock_candidate *out)
+{
+    __shared__ unsigned long long red[32];
+    __shared__ unsigned long long prev;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    if (tid == 0) prev = ~0ull;
+    __syncthreads();
+    for (int k = 0; k < K; ++k) {
+        // composite key: high 32 bits = ordered score, low 32 = ~rotation;
+        // unique per rotation, so the k-th best is the largest below the (k-1)-th
+        const unsigned long long lim = prev;
+        unsigned long long best = 0ull;
+        for (int i = tid; i < n; i += blockDim.x) {
+            unsigned long long key = keys[i];
+            if (!key) continue;
+            unsigned long long c = (key & 0xFFFFFFFF00000000ull) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)i);
+            if (c < lim && c > best) best = c;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long b2 = __shfl_down_sync(0xFFFFFFFFu, best, o);
+            best = b2 > best ? b2 : best;
+        }
+        if (lane == 0) red[warp] = best;
+        __syncthreads();
+        if (warp == 0) {
+            best = lane < nw ? red[lane] : 0ull;
+            for (int o = 16; o > 0; o >>= 1) {
+                unsigned long long b2 = __shfl_down_sync(0xFFFFFFFFu, best, o);
+                best = b2 > best ? b2 : best;
+            }
+            if (lane == 0) {
+                prev = best ? best : 0ull;
+                int rot = best ? (int)(0xFFFFFFFFu - (uint32_t)(best & 0xFFFFFFFFull)) : -1;
+                dock_candidate cd;
+                if (rot >= 0) {
+                    unsigned long long key = keys[rot];
+                    uint32_t sk = (uint32_t)(key >> 32);
+                    uint32_t u = (sk & 0x80000000u) ? (sk & 0x7FFFFFFFu) : ~sk;
+                    cd.score = __uint_as_float(u);
+                    uint32_t idx = 0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull);
+                    cd.canvas_idx = (int32_t)idx;
+                    int cz = idx / (M * M), cy = (idx / M) % M, cx = idx % M;
+                    cd.dk[0] = cx <= N - 1 ? cx : cx - M;
+                    cd.dk[1] = cy <= N - 1 ? cy : cy - M;
+                    cd.dk[2] = cz <= N - 1 ? cz : cz - M;
+                    cd.rot = rot;
+                    for (int a = 0; a < 4; ++a) cd.q[a] = quats[4 * rot + a];
+                    const RotRec &rr = rots_all[rot];
+                    double v[3];
+                    for (int a = 0; a < 3; ++a) v[a] = ds(da(dm(h, (double)cd.dk[a]), rr.o[a]), o_o[a]);
+                    for (int a = 0; a < 3; ++a)
+                        cd.t[a] = da(da(dm(rr.R[3 * a], v[0]), dm(rr.R[3 * a + 1], v[1])), dm(rr.R[3 * a + 2], v[2]));
+                } else {
+                    cd.score = -INFINITY;
+                    cd.canvas_idx = -1;
+                    cd.rot = -1;
+                    for (int a = 0; a < 3; ++a) { cd.dk[a] = 0; cd.t[a] = 0.0; }
+                    for (int a = 0; a < 4; ++a) cd.q[a] = 0.0;
+                }
+                out[k] = cd;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_topk(const unsigned long long *keys, int n, int K, int N, int M, double h, const double *o_o,
+                        const double *quats, const RotRec *rots_all, dock_candidate *out, cudaStream_t st)
+{
+    if (K > 1024) return cudaErrorInvalidValue;
+    k_topk<<<1, 1024, 0, st>>>(keys, n, K, N, M, h, o_o, quats, rots_all, out);
+    return cudaGetLastError();
+}
+
+}  // namespace dock
