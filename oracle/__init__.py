@@ -329,6 +329,13 @@ def probe_sdf(x, r, L):
     return f, g
 
 
+def probe_normal(x, r, L):
+    x = _c64(x)
+    n = np.empty(3)
+    lib().orc_probe_normal(_p(x), ctypes.c_double(r), ctypes.c_double(L), _p(n))
+    return n
+
+
 def tri_min(v0, v1, v2, r, L, iters=60):
     v0, v1, v2 = _c64(v0), _c64(v1), _c64(v2)
     lam = np.empty(3)

@@ -376,13 +376,10 @@ ORC_API void orc_sweep_grid(const double *poses, int64_t P, const double *q, dou
 /*
  * f_p of a flat-ended cylinder: radius r, tip face at z = 0, body z in [0, L].
  * dr = rho - r, dz = max(-z, z - L).  Inside (dr <= 0, dz <= 0): max(dr, dz);
- * outside: dr (side), dz (cap) or sqrt(dr^2 + dz^2) (rim).  Where the inside
- * value is within KINK_EPS of the medial surface dr == dz, the returned
- * (sub)gradient is the normalised bisector of the two branch gradients, so
- * that FP32 and FP64 evaluations pick the same normal; +x is the radial
- * direction on the axis.
+ * outside: dr (side), dz (cap) or sqrt(dr^2 + dz^2) (rim).  g receives a
+ * subgradient: the gradient of the active branch (the cap branch when
+ * dr == dz inside), +x as the radial direction on the axis.
  */
-#define KINK_EPS 1e-5
 ORC_API double orc_probe_sdf(const double *x, double r, double L, double *g)
 {
     double rho = sqrt(x[0] * x[0] + x[1] * x[1]);
@@ -394,16 +391,8 @@ ORC_API double orc_probe_sdf(const double *x, double r, double L, double *g)
     double cz = zlo >= zhi ? -1.0 : 1.0;
     double f;
     if (dr <= 0.0 && dz <= 0.0) {
-        f = dr > dz ? dr : dz;
-        if (g) {
-            if (fabs(dr - dz) <= KINK_EPS) {
-                g[0] = ux * M_SQRT1_2; g[1] = uy * M_SQRT1_2; g[2] = cz * M_SQRT1_2;
-            } else if (dr > dz) {
-                g[0] = ux; g[1] = uy; g[2] = 0.0;
-            } else {
-                g[0] = 0.0; g[1] = 0.0; g[2] = cz;
-            }
-        }
+        if (dr > dz) { f = dr; if (g) { g[0] = ux; g[1] = uy; g[2] = 0.0; } }
+        else { f = dz; if (g) { g[0] = 0.0; g[1] = 0.0; g[2] = cz; } }
     } else if (dr > 0.0 && dz > 0.0) {
         f = sqrt(dr * dr + dz * dz);
         if (g) { g[0] = dr * ux / f; g[1] = dr * uy / f; g[2] = dz * cz / f; }
@@ -415,6 +404,38 @@ ORC_API double orc_probe_sdf(const double *x, double r, double L, double *g)
         if (g) { g[0] = 0.0; g[1] = 0.0; g[2] = cz; }
     }
     return f;
+}
+
+/*
+ * Contact normal n* of Eq. (23) at x: the unit SDF gradient.  On the medial
+ * surface dr == dz inside the cylinder f_p is not differentiable; within
+ * KINK_BAND of it the normal blends the two branch gradients linearly in
+ * (dr - dz) and renormalises, so that it is continuous and FP32 and FP64
+ * evaluations of nearby points give nearby normals.
+ */
+#define KINK_BAND 1e-3
+ORC_API void orc_probe_normal(const double *x, double r, double L, double *n)
+{
+    double rho = sqrt(x[0] * x[0] + x[1] * x[1]);
+    double ux = 1.0, uy = 0.0;
+    if (rho > 0.0) { ux = x[0] / rho; uy = x[1] / rho; }
+    double dr = rho - r;
+    double zlo = -x[2], zhi = x[2] - L;
+    double dz = zlo >= zhi ? zlo : zhi;
+    double cz = zlo >= zhi ? -1.0 : 1.0;
+    if (dr <= 0.0 && dz <= 0.0) {
+        double wr = 0.5 + (dr - dz) / (2.0 * KINK_BAND);
+        if (wr > 1.0) wr = 1.0;
+        if (wr < 0.0) wr = 0.0;
+        double gx = wr * ux, gy = wr * uy, gz = (1.0 - wr) * cz;
+        double gn = sqrt((gx * gx + gy * gy) + gz * gz);
+        n[0] = gx / gn; n[1] = gy / gn; n[2] = gz / gn;
+    } else {
+        double g[3];
+        orc_probe_sdf(x, r, L, g);
+        double gn = sqrt((g[0] * g[0] + g[1] * g[1]) + g[2] * g[2]);
+        n[0] = g[0] / gn; n[1] = g[1] / gn; n[2] = g[2] / gn;
+    }
 }
 
 static void comb(const double *v0, const double *v1, const double *v2, const double *lam, double *x)
@@ -677,9 +698,7 @@ static int64_t dist_query(const query_t *Q, const double *V, const int32_t *T, i
     *d_out = best;
     if (bt >= 0) {
         double g[3];
-        orc_probe_sdf(bx, Q->r, Q->L, g);
-        double gn = sqrt(dot3(g, g));
-        for (int i = 0; i < 3; ++i) g[i] /= gn;
+        orc_probe_normal(bx, Q->r, Q->L, g);
         for (int i = 0; i < 3; ++i) {
             n_out[i] = (Ri[3 * i] * g[0] + Ri[3 * i + 1] * g[1]) + Ri[3 * i + 2] * g[2];
             w_out[i] = ((Ri[3 * i] * bx[0] + Ri[3 * i + 1] * bx[1]) + Ri[3 * i + 2] * bx[2]) + ti[i];

@@ -44,6 +44,8 @@ struct dock_ctx {
     // search scratch (grown on demand)
     float2 *Y = nullptr, *Z = nullptr;
     size_t yz_bytes = 0;
+    uint32_t *bits = nullptr;
+    size_t bits_n = 0;
     unsigned long long *keys = nullptr;
     size_t keys_n = 0;
     RotRec *rots = nullptr;
@@ -408,7 +410,7 @@ void dock_destroy(dock_ctx *c)
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     cudaFree(c->Y);
-    cudaFree(c->Z);
+    cudaFree(c->bits);
     cudaFree(c->keys);
     cudaFree(c->rots);
     cudaFree(c->quats);
@@ -985,7 +987,7 @@ extern "C" dock_status dock_sweep_voxelise(dock_ctx *ctx, const dock_sweep *sw, 
     cudaError_t e;
     {
         Prof pr(ctx, "vox_export");
-        e = launch_vox_export(g, ctx->rots, n, sw->poses, (int)sw->P, dbits, ctx->errflag, ctx->stream);
+        e = launch_vox_export(g, ctx->rots, n, sw->poses, (int)sw->P, dbits, ctx->stream);
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(bits, dbits, per * n, cudaMemcpyDeviceToHost, ctx->stream);
     std::vector<RotRec> rr(n);
@@ -1041,14 +1043,20 @@ static dock_status run_pipeline(dock_ctx *ctx, const dock_object *ob, const dock
         ctx->yz_bytes = need;
     }
     float2 *Y = ctx->Y, *Z = ctx->Y + ysz;
+    if ((s = ensure(ctx, (void **)&ctx->bits, &ctx->bits_n, (size_t)B * g.N * g.N * (g.N / 32), sizeof(uint32_t))) != DOCK_OK)
+        return s;
     int chunks = g.M * g.P / 32;
     for (int b0 = r0; b0 < r1; b0 += B) {
         int nb = std::min(B, r1 - b0);
         int groups_needed = (2 * 152 + chunks - 1) / chunks;
         int group = std::max(1, nb / groups_needed);
         {
-            Prof pr(ctx, "vox_fwd");
-            CK(ctx, launch_vox_fwd(g, ctx->rots + b0, nb, sw->poses, (int)sw->P, Y, tw, qt, ctx->errflag, ctx->stream));
+            Prof pr(ctx, "voxelise");
+            CK(ctx, launch_voxelise(g, ctx->rots + b0, nb, sw->poses, (int)sw->P, ctx->bits, ctx->stream));
+        }
+        {
+            Prof pr(ctx, "fwd2d");
+            CK(ctx, launch_fwd2d(g, nb, ctx->bits, Y, tw, qt, ctx->stream));
         }
         {
             Prof pr(ctx, "zpass");
@@ -1140,10 +1148,13 @@ extern "C" dock_status dock_search_scores(dock_ctx *ctx, const dock_object *ob, 
     size_t ysz = (size_t)g.N * g.M * g.P, zsz = (size_t)g.M * g.M * g.P, csz = (size_t)g.M * g.M * g.M;
     float2 *Y = nullptr;
     float *dC = nullptr;
+    if ((s = ensure(ctx, (void **)&ctx->bits, &ctx->bits_n, (size_t)g.N * g.N * (g.N / 32), sizeof(uint32_t))) != DOCK_OK)
+        return s;
     if ((s = dalloc(ctx, (void **)&Y, (ysz + zsz) * sizeof(float2), nullptr)) != DOCK_OK) return s;
     if ((s = dalloc(ctx, (void **)&dC, csz * sizeof(float), nullptr)) != DOCK_OK) { dfree(ctx, Y, (ysz + zsz) * sizeof(float2)); return s; }
     cudaError_t e = cudaMemsetAsync(ctx->errflag, 0, sizeof(int), ctx->stream);
-    if (e == cudaSuccess) e = launch_vox_fwd(g, ctx->rots, 1, sw->poses, (int)sw->P, Y, tw, qt, ctx->errflag, ctx->stream);
+    if (e == cudaSuccess) e = launch_voxelise(g, ctx->rots, 1, sw->poses, (int)sw->P, ctx->bits, ctx->stream);
+    if (e == cudaSuccess) e = launch_fwd2d(g, 1, ctx->bits, Y, tw, qt, ctx->stream);
     if (e == cudaSuccess) e = launch_zpass(g, 1, 1, Y, ob->spec, Y + ysz, tw, ctx->stream);
     if (e == cudaSuccess) e = launch_plane_export(g, Y + ysz, tw, dC, ctx->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(C, dC, csz * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);

@@ -46,8 +46,10 @@ struct Launcher;  // timing helper
 // Kernel launchers (k_search.cu)
 cudaError_t launch_rot_setup(const double *quats, int n, int rot0, const double *c_s, double h, int N, RotRec *out,
                              cudaStream_t st);
-cudaError_t launch_vox_fwd(const Geo &g, const RotRec *rots, int B, const PoseRec *poses, int P, float2 *Y,
-                           const float2 *tw, const float2 *q, int *err, cudaStream_t st);
+cudaError_t launch_voxelise(const Geo &g, const RotRec *rots, int B, const PoseRec *poses, int P, uint32_t *bits,
+                            cudaStream_t st);
+cudaError_t launch_fwd2d(const Geo &g, int B, const uint32_t *bits, float2 *Y, const float2 *tw, const float2 *q,
+                         cudaStream_t st);
 cudaError_t launch_zpass(const Geo &g, int B, int group, const float2 *Y, const float2 *spec, float2 *Z,
                          const float2 *tw, cudaStream_t st);
 cudaError_t launch_plane(const Geo &g, int B, const float2 *Z, const float2 *tw, const RotRec *rots,
@@ -55,7 +57,7 @@ cudaError_t launch_plane(const Geo &g, int B, const float2 *Z, const float2 *tw,
 cudaError_t launch_topk(const unsigned long long *keys, int n, int K, int N, int M, double h, const double *o_o,
                         const double *quats, const RotRec *rots_all, dock_candidate *out, cudaStream_t st);
 cudaError_t launch_vox_export(const Geo &g, const RotRec *rots, int B, const PoseRec *poses, int P, uint8_t *bits,
-                              int *err, cudaStream_t st);
+                              cudaStream_t st);
 cudaError_t launch_plane_export(const Geo &g, const float2 *Z, const float2 *tw, float *C, cudaStream_t st);
 
 // Object grid kernels (k_object.cu)

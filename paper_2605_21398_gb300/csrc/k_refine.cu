@@ -22,7 +22,7 @@
 
 namespace dock {
 
-#define KINK_EPS 1e-5f
+#define KINK_BAND 1e-3f   // width of the blend across the medial surface (mm)
 
 // per-candidate data read by the evaluation kernel (FP32)
 struct CandF {
@@ -37,6 +37,9 @@ struct CandF {
 constexpr int ST = 24;
 constexpr int NACC = 28;   // J, G[6], H upper triangle [21]
 
+// f_p of the flat-ended cylinder (tip face z = 0, body z in [0, L]) and, in g,
+// the gradient of the active branch (a valid subgradient: the cap branch on
+// the inside medial surface dr == dz, +x as the radial direction on the axis).
 __device__ __forceinline__ float sdf_cyl(float x, float y, float z, float r, float L, float *g)
 {
     float rho = sqrtf(fmaf(x, x, y * y));
@@ -48,17 +51,8 @@ __device__ __forceinline__ float sdf_cyl(float x, float y, float z, float r, flo
     float cz = zlo >= zhi ? -1.f : 1.f;
     float f;
     if (dr <= 0.f && dz <= 0.f) {
-        f = fmaxf(dr, dz);
-        if (g) {
-            if (fabsf(dr - dz) <= KINK_EPS) {
-                const float s = 0.70710678118654752f;
-                g[0] = ux * s; g[1] = uy * s; g[2] = cz * s;
-            } else if (dr > dz) {
-                g[0] = ux; g[1] = uy; g[2] = 0.f;
-            } else {
-                g[0] = 0.f; g[1] = 0.f; g[2] = cz;
-            }
-        }
+        if (dr > dz) { f = dr; if (g) { g[0] = ux; g[1] = uy; g[2] = 0.f; } }
+        else { f = dz; if (g) { g[0] = 0.f; g[1] = 0.f; g[2] = cz; } }
     } else if (dr > 0.f && dz > 0.f) {
         f = sqrtf(fmaf(dr, dr, dz * dz));
         if (g) { g[0] = dr * ux / f; g[1] = dr * uy / f; g[2] = dz * cz / f; }
@@ -70,6 +64,28 @@ __device__ __forceinline__ float sdf_cyl(float x, float y, float z, float r, flo
         if (g) { g[0] = 0.f; g[1] = 0.f; g[2] = cz; }
     }
     return f;
+}
+
+// Contact normal n* (Eq. (23)): the unit gradient; inside, within KINK_BAND
+// of the medial surface, a continuous blend of the two branch gradients.
+__device__ __forceinline__ void sdf_normal(const float *x, float r, float L, float *n)
+{
+    float rho = sqrtf(fmaf(x[0], x[0], x[1] * x[1]));
+    float ux = 1.f, uy = 0.f;
+    if (rho > 0.f) { ux = x[0] / rho; uy = x[1] / rho; }
+    float dr = rho - r;
+    float zlo = -x[2], zhi = x[2] - L;
+    float dz = zlo >= zhi ? zlo : zhi;
+    float cz = zlo >= zhi ? -1.f : 1.f;
+    float g[3];
+    if (dr <= 0.f && dz <= 0.f) {
+        float wr = fminf(1.f, fmaxf(0.f, 0.5f + (dr - dz) / (2.f * KINK_BAND)));
+        g[0] = wr * ux; g[1] = wr * uy; g[2] = (1.f - wr) * cz;
+    } else {
+        sdf_cyl(x[0], x[1], x[2], r, L, g);
+    }
+    float gn = sqrtf(fmaf(g[0], g[0], fmaf(g[1], g[1], g[2] * g[2])));
+    n[0] = g[0] / gn; n[1] = g[1] / gn; n[2] = g[2] / gn;
 }
 
 __device__ __forceinline__ float dot3f(const float *a, const float *b) { return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2])); }
@@ -101,7 +117,25 @@ __device__ float inner_min(const float *v0, const float *e1, const float *e2, fl
     return sdf_cyl(x[0], x[1], x[2], r, L, nullptr);
 }
 
-// min of f_p over the triangle (local coordinates); returns d, writes (u, v)
+// dphi/du at u for the partial minimum phi(u) = min_v f(v0 + u e1 + v e2)
+// (Danskin; valid where f is differentiable at the inner minimiser).
+__device__ float outer_slope(const float *v0, const float *e1, const float *e2, float u, float r, float L, int iters)
+{
+    float v;
+    inner_min(v0, e1, e2, u, r, L, iters, &v);
+    float x[3], g[3];
+    for (int a = 0; a < 3; ++a) x[a] = fmaf(v, e2[a], fmaf(u, e1[a], v0[a]));
+    sdf_cyl(x[0], x[1], x[2], r, L, g);
+    float s = dot3f(g, e1);
+    if (v >= 1.f - u && v > 0.f) s -= dot3f(g, e2);
+    return s;
+}
+
+// min of f_p over the triangle (local coordinates); returns d, writes (u, v).
+// Golden-section search on phi(u) (values only: robust on the non-smooth
+// medial surface), then, for a minimum outside the probe (f is C^1 there), a
+// bisection on dphi/du inside a bracket that stays outside: value-based search
+// locates a smooth minimum only to ~sqrt(FP32 eps), the slope to ~eps.
 __device__ float tri_min(const float *v0, const float *v1, const float *v2, float r, float L, int iters, float *uo,
                          float *vo)
 {
@@ -130,9 +164,42 @@ __device__ float tri_min(const float *v0, const float *v1, const float *v2, floa
     float f1 = inner_min(v0, e1, e2, 1.f, r, L, iters, &vu1);
     if (f0 < best) { best = f0; u = 0.f; v = vu0; }
     if (f1 < best) { best = f1; u = 1.f; v = vu1; }
+    float le = sqrtf(dot3f(e1, e1));
+    if (best > 1e-4f && le > 0.f) {
+        float w = fminf(2e-3f, 0.5f * best / le);
+        float lo = fmaxf(0.f, u - w), hi = fminf(1.f, u + w);
+        if (outer_slope(v0, e1, e2, lo, r, L, iters) >= 0.f) {
+            hi = lo;
+        } else if (outer_slope(v0, e1, e2, hi, r, L, iters) <= 0.f) {
+            lo = hi;
+        } else {
+            for (int k = 0; k < 16; ++k) {
+                float mid = 0.5f * (lo + hi);
+                if (outer_slope(v0, e1, e2, mid, r, L, iters) < 0.f) lo = mid; else hi = mid;
+            }
+        }
+        float up = 0.5f * (lo + hi), vp;
+        float fp = inner_min(v0, e1, e2, up, r, L, iters, &vp);
+        if (fp <= best) { best = fp; u = up; v = vp; }
+    }
     *uo = u;
     *vo = v;
     return best;
+}
+
+// Lower bound of min f over the triangle: the linearisation at the centroid
+// with a subgradient there (f is convex).
+__device__ __forceinline__ float lin_lower_bound(const float lv[3][3], float r, float L)
+{
+    float c[3], g[3];
+    for (int a = 0; a < 3; ++a) c[a] = (lv[0][a] + lv[1][a] + lv[2][a]) * (1.f / 3.f);
+    float fc = sdf_cyl(c[0], c[1], c[2], r, L, g);
+    float m = INFINITY;
+    for (int k = 0; k < 3; ++k) {
+        float d[3] = {lv[k][0] - c[0], lv[k][1] - c[1], lv[k][2] - c[2]};
+        m = fminf(m, dot3f(g, d));
+    }
+    return fc + m;
 }
 
 // Eq. (18): s(d), s'(d), s''(d) with r = tau_in / tau_out and C^1 coefficients
@@ -157,66 +224,89 @@ __device__ __forceinline__ void score3(const RefineDev &D, float d, float *s, fl
     }
 }
 
+__device__ __forceinline__ void local_vertices(const RefineDev &D, int t, const float *A, const float *bvec,
+                                               float lv[3][3])
+{
+    for (int m = 0; m < 3; ++m) {
+        const float *v = D.Vf + 3 * D.T[3 * t + m];
+        float qv[3] = {v[0] - bvec[0], v[1] - bvec[1], v[2] - bvec[2]};
+        for (int a = 0; a < 3; ++a) lv[m][a] = fmaf(A[0 * 3 + a], qv[0], fmaf(A[1 * 3 + a], qv[1], A[2 * 3 + a] * qv[2]));
+    }
+}
+
 // Distance query of one probe pose against the mesh for object pose (R, p).
-// Returns the triangle index or -1 (no triangle passes Eq. (21)); fills d,
-// the local witness and the local unit normal.
+// Two BVH passes under the Eq. (21) test f_p(c) < r_node + eps: the first
+// takes the smallest vertex value as an upper bound UB of d*, the second
+// minimises f_p only over triangles whose linearised lower bound does not
+// exceed min(UB, best so far) (a triangle attaining d* is never skipped;
+// ties in d keep the lower triangle index).  Returns the triangle index or
+// -1; fills d*, the local witness and the local contact normal.
 __device__ int dist_query(const RefineDev &D, const float *A, const float *bvec, float *d_out, float *xw, float *nl)
 {
     int stack[64];
-    int sp = 0;
-    stack[sp++] = 0;
-    float best = INFINITY;
-    int bt = -1;
-    float bx[3] = {0.f, 0.f, 0.f};
     const float eps = D.tau_out;
-    while (sp > 0) {
-        int ni = stack[--sp];
-        BvhNode nd = D.nodes[ni];
-        float q[3] = {nd.c[0] - bvec[0], nd.c[1] - bvec[1], nd.c[2] - bvec[2]};
-        float loc[3];
-        for (int k = 0; k < 3; ++k) loc[k] = fmaf(A[0 * 3 + k], q[0], fmaf(A[1 * 3 + k], q[1], A[2 * 3 + k] * q[2]));
-        float fc = sdf_cyl(loc[0], loc[1], loc[2], D.r, D.L, nullptr);
-        if (!(fc < nd.rad + eps)) continue;             // Eq. (21)
-        if (fc - nd.rad > best) continue;               // cannot beat the current minimum
-        if (nd.left < 0) {
-            for (int k = 0; k < nd.count; ++k) {
-                int t = D.tri_order[nd.right + k];
-                const float *ts = D.tri_sphere + 4 * t;
-                float qs[3] = {ts[0] - bvec[0], ts[1] - bvec[1], ts[2] - bvec[2]};
-                float ls[3];
-                for (int a = 0; a < 3; ++a) ls[a] = fmaf(A[0 * 3 + a], qs[0], fmaf(A[1 * 3 + a], qs[1], A[2 * 3 + a] * qs[2]));
-                float ft = sdf_cyl(ls[0], ls[1], ls[2], D.r, D.L, nullptr);
-                if (!(ft < ts[3] + eps)) continue;      // Eq. (21) for the triangle's sphere
-                if (ft - ts[3] > best) continue;
-                float lv[3][3];
-                for (int m = 0; m < 3; ++m) {
-                    const float *v = D.Vf + 3 * D.T[3 * t + m];
-                    float qv[3] = {v[0] - bvec[0], v[1] - bvec[1], v[2] - bvec[2]};
+    float UB = INFINITY;
+    for (int pass = 0; pass < 2; ++pass) {
+        int sp = 0;
+        stack[sp++] = 0;
+        float best = INFINITY;
+        int bt = -1;
+        float bx[3] = {0.f, 0.f, 0.f};
+        while (sp > 0) {
+            int ni = stack[--sp];
+            BvhNode nd = D.nodes[ni];
+            float q[3] = {nd.c[0] - bvec[0], nd.c[1] - bvec[1], nd.c[2] - bvec[2]};
+            float loc[3];
+            for (int k = 0; k < 3; ++k) loc[k] = fmaf(A[0 * 3 + k], q[0], fmaf(A[1 * 3 + k], q[1], A[2 * 3 + k] * q[2]));
+            float fc = sdf_cyl(loc[0], loc[1], loc[2], D.r, D.L, nullptr);
+            if (!(fc < nd.rad + eps)) continue;             // Eq. (21)
+            if (fc - nd.rad > fminf(UB, best)) continue;    // cannot hold the minimum
+            if (nd.left < 0) {
+                for (int k = 0; k < nd.count; ++k) {
+                    int t = D.tri_order[nd.right + k];
+                    const float *ts = D.tri_sphere + 4 * t;
+                    float qs[3] = {ts[0] - bvec[0], ts[1] - bvec[1], ts[2] - bvec[2]};
+                    float ls[3];
                     for (int a = 0; a < 3; ++a)
-                        lv[m][a] = fmaf(A[0 * 3 + a], qv[0], fmaf(A[1 * 3 + a], qv[1], A[2 * 3 + a] * qv[2]));
+                        ls[a] = fmaf(A[0 * 3 + a], qs[0], fmaf(A[1 * 3 + a], qs[1], A[2 * 3 + a] * qs[2]));
+                    float ft = sdf_cyl(ls[0], ls[1], ls[2], D.r, D.L, nullptr);
+                    if (!(ft < ts[3] + eps)) continue;      // Eq. (21) for the triangle's sphere
+                    if (ft - ts[3] > fminf(UB, best)) continue;
+                    float lv[3][3];
+                    local_vertices(D, t, A, bvec, lv);
+                    if (pass == 0) {
+                        for (int m = 0; m < 3; ++m) UB = fminf(UB, sdf_cyl(lv[m][0], lv[m][1], lv[m][2], D.r, D.L, nullptr));
+                        continue;
+                    }
+                    if (lin_lower_bound(lv, D.r, D.L) > fminf(UB, best)) continue;
+                    float u, v;
+                    float dk = tri_min(lv[0], lv[1], lv[2], D.r, D.L, D.tri_iters, &u, &v);
+                    if (dk < best || (dk == best && t < bt)) {
+                        best = dk;
+                        bt = t;
+                        float w0 = 1.f - u - v;
+                        for (int a = 0; a < 3; ++a) bx[a] = fmaf(w0, lv[0][a], fmaf(u, lv[1][a], v * lv[2][a]));
+                    }
                 }
-                float u, v;
-                float dk = tri_min(lv[0], lv[1], lv[2], D.r, D.L, D.tri_iters, &u, &v);
-                if (dk < best || (dk == best && t < bt)) {
-                    best = dk;
-                    bt = t;
-                    float w0 = 1.f - u - v;
-                    for (int a = 0; a < 3; ++a) bx[a] = fmaf(w0, lv[0][a], fmaf(u, lv[1][a], v * lv[2][a]));
-                }
+            } else if (sp + 2 <= 64) {
+                stack[sp++] = nd.right;
+                stack[sp++] = nd.left;
             }
-        } else if (sp + 2 <= 64) {
-            stack[sp++] = nd.right;
-            stack[sp++] = nd.left;
+        }
+        if (pass == 1) {
+            *d_out = best;
+            if (bt >= 0) {
+                sdf_normal(bx, D.r, D.L, nl);
+                for (int a = 0; a < 3; ++a) xw[a] = bx[a];
+            }
+            return bt;
+        }
+        if (!(UB < INFINITY)) {   // no triangle passes Eq. (21)
+            *d_out = INFINITY;
+            return -1;
         }
     }
-    *d_out = best;
-    if (bt >= 0) {
-        float g[3];
-        sdf_cyl(bx[0], bx[1], bx[2], D.r, D.L, g);
-        float gn = sqrtf(dot3f(g, g));
-        for (int a = 0; a < 3; ++a) { nl[a] = g[a] / gn; xw[a] = bx[a]; }
-    }
-    return bt;
+    return -1;
 }
 
 // One thread per (candidate, pose).  acc_part[(c * nblk + blk) * NACC + k].

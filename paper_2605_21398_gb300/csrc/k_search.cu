@@ -129,125 +129,187 @@ __device__ __forceinline__ void set_bits(uint32_t *row, int lo, int hi)
     }
 }
 
-// Fill bits[jy * NW + w] for slab jz with the union of all probe cylinders.
-template <int N>
-__device__ void voxelise_slab(const Geo &g, const RotRec &rr, const PoseRec *poses, int P, int jz, uint32_t *bits,
-                              int *err)
+// Pose frame of pose i in lattice voxel units for rotation rr (FP32):
+// l(j) = B^T (j - c), B = R^T R_i, c = (R^T t_i - o) / h.
+__device__ __forceinline__ void pose_frame(const RotRec &rr, const PoseRec &pr, float ih, float *B, float *c)
 {
-    constexpr int NW = N / 32 > 0 ? N / 32 : 1;
+    const float *Rf = rr.Rf;
+    for (int k = 0; k < 3; ++k)
+        for (int a = 0; a < 3; ++a)
+            B[a * 3 + k] = fmaf(Rf[0 * 3 + a], pr.Rf[0 * 3 + k], fmaf(Rf[1 * 3 + a], pr.Rf[1 * 3 + k], Rf[2 * 3 + a] * pr.Rf[2 * 3 + k]));
+    for (int a = 0; a < 3; ++a)
+        c[a] = (fmaf(Rf[0 * 3 + a], pr.tf[0], fmaf(Rf[1 * 3 + a], pr.tf[1], Rf[2 * 3 + a] * pr.tf[2])) - rr.of[a]) * ih;
+}
+
+// One lattice row (jy, jz) of one pose: set the bits of the voxels inside the
+// probe.  The FP32 interval from the radial quadratic and the axial slab is
+// only a starting point: the exact end voxels are found by classifying
+// neighbours (an interval, since the cylinder is convex), with the exact
+// FP64 predicate deciding inside the FP32 error band.
+template <int N>
+__device__ __forceinline__ void vox_row(const float *B, const float *c, int jy, int jz, float rv2, float lv, float mr,
+                                        float mz, const RotRec &rr, const PoseRec &pr, double h, double r2d, double Ld,
+                                        uint32_t *row)
+{
+    const float bx[3] = {B[0], B[1], B[2]};   // B^T e_x
+    const float Aq = fmaf(bx[0], bx[0], bx[1] * bx[1]);
+    float dyv = (float)jy - c[1], dzv = (float)jz - c[2], dxv = -c[0];
+    float l0[3];
+    for (int k = 0; k < 3; ++k) l0[k] = fmaf(B[0 * 3 + k], dxv, fmaf(B[1 * 3 + k], dyv, B[2 * 3 + k] * dzv));
+    float lo = -1e30f, hi = 1e30f;
+    int wide = 2;
+    if (Aq > 1e-6f) {
+        float Bq = fmaf(l0[0], bx[0], l0[1] * bx[1]);
+        float Cq = fmaf(l0[0], l0[0], l0[1] * l0[1]) - rv2;
+        float disc = fmaf(Bq, Bq, -Aq * Cq);
+        if (disc < -1e-3f * (Bq * Bq + fabsf(Aq * Cq)) - 1e-2f) return;
+        float sq = sqrtf(fmaxf(disc, 0.f));
+        lo = (-Bq - sq) / Aq;
+        hi = (-Bq + sq) / Aq;
+        if (Aq < 0.05f) wide = N;
+    } else {
+        float Cq = fmaf(l0[0], l0[0], l0[1] * l0[1]) - rv2;
+        if (Cq > mr + 1e-2f) return;
+        wide = N;
+    }
+    if (fabsf(bx[2]) > 1e-6f) {
+        float za = -l0[2] / bx[2], zb = (lv - l0[2]) / bx[2];
+        lo = fmaxf(lo, fminf(za, zb));
+        hi = fminf(hi, fmaxf(za, zb));
+    } else if (l0[2] < -0.01f || l0[2] > lv + 0.01f) {
+        return;
+    }
+    if (lo > hi + 2.f) return;
+    lo = fmaxf(lo, -4.f);
+    hi = fminf(hi, (float)N + 4.f);
+    const int jmax = min(N - 1, (int)ceilf(hi) + wide);
+    int jl = min(N - 1, max(0, (int)ceilf(lo)));
+    if (wide > 2) jl = max(0, (int)floorf(lo) - wide);
+    if (jl > jmax) return;
+    if (classify(l0, bx, jl, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz)) {
+        while (jl > 0 && classify(l0, bx, jl - 1, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz)) --jl;
+    } else {
+        do { ++jl; } while (jl <= jmax && !classify(l0, bx, jl, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz));
+        if (jl > jmax) return;
+    }
+    int jr = max(jl, min(N - 1, (int)floorf(hi)));
+    if (classify(l0, bx, jr, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz)) {
+        while (jr < N - 1 && classify(l0, bx, jr + 1, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz)) ++jr;
+    } else {
+        do { --jr; } while (jr > jl && !classify(l0, bx, jr, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz));
+    }
+    set_bits(row, jl, jr);
+}
+
+// Fill bits[jy * NW + w] for slab jz with the union of all probe cylinders.
+// A warp tests 32 poses at once against the slab (ballot); for each pose that
+// reaches the slab the pose frame is broadcast and the lanes take its rows.
+template <int N>
+__device__ void voxelise_slab(const Geo &g, const RotRec &rr, const PoseRec *poses, int P, int jz, uint32_t *bits)
+{
+    constexpr int NW = N / 32;
     const float rv = g.rv, lv = g.lv, rv2 = rv * rv;
     const float mz = 8e-4f, mr = 1.6e-3f * rv + 1e-3f;
     const double h = g.h, r2d = g.r * g.r, Ld = g.L;
     const float ih = g.inv_h;
     const float *Rf = rr.Rf;
-    for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        const PoseRec &pr = poses[i];
-        // tip in voxel coordinates and axis direction in the lattice frame
-        float tx = pr.tf[0], ty = pr.tf[1], tz = pr.tf[2];
-        float cz = (fmaf(Rf[2], tx, fmaf(Rf[5], ty, Rf[8] * tz)) - rr.of[2]) * ih;
-        float Az = fmaf(Rf[2], pr.Rf[2], fmaf(Rf[5], pr.Rf[5], Rf[8] * pr.Rf[8]));
-        float sz = rv * sqrtf(fmaxf(0.f, 1.f - Az * Az)) + 1.5f;
-        float z0 = fminf(cz, cz + lv * Az) - sz, z1 = fmaxf(cz, cz + lv * Az) + sz;
-        float fz = (float)jz;
-        if (fz < z0 || fz > z1) continue;
-        VoxCtx v;
-        for (int k = 0; k < 3; ++k)
-            for (int a = 0; a < 3; ++a)
-                v.B[a * 3 + k] = fmaf(Rf[0 * 3 + a], pr.Rf[0 * 3 + k], fmaf(Rf[1 * 3 + a], pr.Rf[1 * 3 + k], Rf[2 * 3 + a] * pr.Rf[2 * 3 + k]));
-        for (int a = 0; a < 3; ++a)
-            v.c[a] = (fmaf(Rf[0 * 3 + a], tx, fmaf(Rf[1 * 3 + a], ty, Rf[2 * 3 + a] * tz)) - rr.of[a]) * ih;
-        float Ax = v.B[0 * 3 + 2], Ay = v.B[1 * 3 + 2];
-        (void)Ax;
-        // axis-parameter range that reaches this slab, then the row range
-        float u0, u1;
-        if (fabsf(Az) > 1e-6f) {
-            float ua = (fz - v.c[2] - sz) / Az, ub = (fz - v.c[2] + sz) / Az;
-            u0 = fmaxf(0.f, fminf(ua, ub));
-            u1 = fminf(lv, fmaxf(ua, ub));
-            if (u0 > u1) continue;
-        } else {
-            u0 = 0.f;
-            u1 = lv;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const float fz = (float)jz;
+    for (int base = warp * 32; base < P; base += nwarp * 32) {
+        int i = base + lane;
+        bool hit = false;
+        float B[9], c[3];
+        if (i < P) {
+            const PoseRec &pr = poses[i];
+            float cz = (fmaf(Rf[2], pr.tf[0], fmaf(Rf[5], pr.tf[1], Rf[8] * pr.tf[2])) - rr.of[2]) * ih;
+            float Az = fmaf(Rf[2], pr.Rf[2], fmaf(Rf[5], pr.Rf[5], Rf[8] * pr.Rf[8]));
+            float sz = rv * sqrtf(fmaxf(0.f, 1.f - Az * Az)) + 1.5f;
+            float z0 = fminf(cz, cz + lv * Az) - sz, z1 = fmaxf(cz, cz + lv * Az) + sz;
+            hit = !(fz < z0 || fz > z1);
+            if (hit) pose_frame(rr, pr, ih, B, c);
         }
-        float sy = rv * sqrtf(fmaxf(0.f, 1.f - Ay * Ay)) + 1.5f;
-        float ylo = v.c[1] + fminf(u0 * Ay, u1 * Ay) - sy, yhi = v.c[1] + fmaxf(u0 * Ay, u1 * Ay) + sy;
-        int jy0 = max(0, (int)ceilf(ylo)), jy1 = min(N - 1, (int)floorf(yhi));
-        const float bx[3] = {v.B[0], v.B[1], v.B[2]};   // B^T e_x
-        const float Aq = fmaf(bx[0], bx[0], bx[1] * bx[1]);
-        for (int jy = jy0; jy <= jy1; ++jy) {
-            float dyv = (float)jy - v.c[1], dzv = fz - v.c[2], dxv = -v.c[0];
-            float l0[3];
-            for (int k = 0; k < 3; ++k) l0[k] = fmaf(v.B[0 * 3 + k], dxv, fmaf(v.B[1 * 3 + k], dyv, v.B[2 * 3 + k] * dzv));
-            // candidate interval from the quadratic (radial) and linear (axial) constraints
-            float lo = -1e30f, hi = 1e30f;
-            int wide = 2;
-            if (Aq > 1e-6f) {
-                float Bq = fmaf(l0[0], bx[0], l0[1] * bx[1]);
-                float Cq = fmaf(l0[0], l0[0], l0[1] * l0[1]) - rv2;
-                float disc = fmaf(Bq, Bq, -Aq * Cq);
-                if (disc < -1e-3f * (Bq * Bq + fabsf(Aq * Cq)) - 1e-2f) continue;
-                float sq = sqrtf(fmaxf(disc, 0.f));
-                lo = (-Bq - sq) / Aq;
-                hi = (-Bq + sq) / Aq;
-                if (Aq < 0.05f) wide = N;
+        unsigned mask = __ballot_sync(0xFFFFFFFFu, hit);
+        while (mask) {
+            int src = __ffs(mask) - 1;
+            mask &= mask - 1;
+            float Bs[9], cs[3];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) Bs[k] = __shfl_sync(0xFFFFFFFFu, B[k], src);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) cs[k] = __shfl_sync(0xFFFFFFFFu, c[k], src);
+            const PoseRec &pr = poses[base + src];
+            // rows of this slab the cylinder can reach
+            float Az = Bs[2 * 3 + 2], Ay = Bs[1 * 3 + 2];
+            float sz = rv * sqrtf(fmaxf(0.f, 1.f - Az * Az)) + 1.5f;
+            float u0, u1;
+            if (fabsf(Az) > 1e-6f) {
+                float ua = (fz - cs[2] - sz) / Az, ub = (fz - cs[2] + sz) / Az;
+                u0 = fmaxf(0.f, fminf(ua, ub));
+                u1 = fminf(lv, fmaxf(ua, ub));
             } else {
-                float Cq = fmaf(l0[0], l0[0], l0[1] * l0[1]) - rv2;
-                if (Cq > mr + 1e-2f) continue;
-                wide = N;
+                u0 = 0.f;
+                u1 = lv;
             }
-            if (fabsf(bx[2]) > 1e-6f) {
-                float za = -l0[2] / bx[2], zb = (lv - l0[2]) / bx[2];
-                lo = fmaxf(lo, fminf(za, zb));
-                hi = fminf(hi, fmaxf(za, zb));
-            } else if (l0[2] < -0.01f || l0[2] > lv + 0.01f) {
-                continue;
-            }
-            if (lo > hi + 2.f) continue;
-            lo = fmaxf(lo, -4.f);
-            hi = fminf(hi, (float)N + 4.f);
-            int ja = max(0, (int)floorf(lo) - wide), jb = min(N - 1, (int)ceilf(hi) + wide);
-            if (ja > jb) continue;
-            int jl = ja;
-            if (classify(l0, bx, jl, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz)) {
-                while (jl > 0 && classify(l0, bx, jl - 1, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz)) --jl;
-            } else {
-                do { ++jl; } while (jl <= jb && !classify(l0, bx, jl, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz));
-                if (jl > jb) continue;
-            }
-            int jr = jb;
-            if (classify(l0, bx, jr, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz)) {
-                while (jr < N - 1 && classify(l0, bx, jr + 1, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz)) ++jr;
-            } else {
-                do { --jr; } while (jr > jl && !classify(l0, bx, jr, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz));
-            }
-            set_bits(bits + jy * NW, jl, jr);
+            if (u0 > u1) continue;
+            float sy = rv * sqrtf(fmaxf(0.f, 1.f - Ay * Ay)) + 1.5f;
+            float ylo = cs[1] + fminf(u0 * Ay, u1 * Ay) - sy, yhi = cs[1] + fmaxf(u0 * Ay, u1 * Ay) + sy;
+            int jy0 = max(0, (int)ceilf(ylo)), jy1 = min(N - 1, (int)floorf(yhi));
+            for (int jy = jy0 + lane; jy <= jy1; jy += 32)
+                vox_row<N>(Bs, cs, jy, jz, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, bits + jy * NW);
         }
     }
-    (void)err;
+}
+
+// S_b slab bits to global memory: bits[((b * N + jz) * N + jy) * NW + w].
+template <int N>
+__global__ void __launch_bounds__(256)
+k_voxelise(Geo g, const RotRec *rots, const PoseRec *poses, int P, uint32_t *bits_out)
+{
+    constexpr int NW = N / 32;
+    __shared__ uint32_t bits[N * NW];
+    const int jz = blockIdx.x, b = blockIdx.y;
+    for (int i = threadIdx.x; i < N * NW; i += blockDim.x) bits[i] = 0u;
+    __syncthreads();
+    voxelise_slab<N>(g, rots[b], poses, P, jz, bits);
+    __syncthreads();
+    uint32_t *o = bits_out + ((size_t)b * N + jz) * N * NW;
+    for (int i = threadIdx.x; i < N * NW; i += blockDim.x) o[i] = bits[i];
+}
+
+cudaError_t launch_voxelise(const Geo &g, const RotRec *rots, int B, const PoseRec *poses, int P, uint32_t *bits,
+                            cudaStream_t st)
+{
+    dim3 grid(g.N, B);
+    switch (g.N) {
+    case 32: k_voxelise<32><<<grid, 256, 0, st>>>(g, rots, poses, P, bits); break;
+    case 64: k_voxelise<64><<<grid, 256, 0, st>>>(g, rots, poses, P, bits); break;
+    case 96: k_voxelise<96><<<grid, 256, 0, st>>>(g, rots, poses, P, bits); break;
+    case 128: k_voxelise<128><<<grid, 256, 0, st>>>(g, rots, poses, P, bits); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// K_A: voxelise slab z of rotation b and transform it along x (R2C, closed
-// form per run of set bits) and y (radix FFT); write Y[b][z].
+// K_A: forward transform of slab z of S_b along x (R2C in closed form per run
+// of set bits) and y (radix FFT, N non-zero inputs of M); writes Y[b][z].
 // ---------------------------------------------------------------------------
 template <int M>
 __global__ void __launch_bounds__(Plan<M>::T * 32)
-k_vox_fwd(Geo g, const RotRec *rots, const PoseRec *poses, int P, float2 *Y, const float2 *tw_g, const float2 *q_g,
-          int *err)
+k_fwd2d(int P, const uint32_t *bits_g, float2 *Y, const float2 *tw_g, const float2 *q_g)
 {
-    constexpr int N = M / 2, H = M / 2, NW = N / 32, T = Plan<M>::T, COLS = 32, E = Plan<M>::E;
+    constexpr int N = M / 2, H = M / 2, NW = N / 32, COLS = 32, E = Plan<M>::E;
     extern __shared__ __align__(16) unsigned char smem[];
     cf *X = reinterpret_cast<cf *>(smem);                       // [N][H] packed columns
-    cf *xb = X + N * H;                                          // [M][COLS] exchange / staging
+    cf *xb = X + N * H;                                          // [M][COLS] exchange
     cf *tw = xb + M * COLS;                                      // [M]
-    uint32_t *bits = reinterpret_cast<uint32_t *>(tw + M);       // [N][NW]
+    cf *c0 = tw + M;                                             // [M] packed column 0 after the y FFT
+    uint32_t *bits = reinterpret_cast<uint32_t *>(c0 + M);       // [N][NW]
 
     const int jz = blockIdx.x, b = blockIdx.y;
-    const RotRec rr = rots[b];
+    const uint32_t *bg = bits_g + ((size_t)b * N + jz) * N * NW;
     for (int i = threadIdx.x; i < M; i += blockDim.x) { float2 w = tw_g[i]; tw[i] = cmake(w.x, w.y); }
-    for (int i = threadIdx.x; i < N * NW; i += blockDim.x) bits[i] = 0u;
-    __syncthreads();
-    voxelise_slab<N>(g, rr, poses, P, jz, bits, err);
+    for (int i = threadIdx.x; i < N * NW; i += blockDim.x) bits[i] = bg[i];
     __syncthreads();
 
     // x: X[y][kx] = sum over runs [a, a+len) of sum_x exp(-2 pi i kx x / M)
@@ -268,7 +330,6 @@ k_vox_fwd(Geo g, const RotRec *rots, const PoseRec *poses, int P, float2 *Y, con
             uint32_t cur = (w < NW) ? bits[y * NW + w] : 0u;
             uint32_t prev = (cur << 1) | (prevw >> 31);
             uint32_t rise = cur & ~prev, fall = ~cur & prev;
-            // events in increasing bit order
             uint32_t ev = rise | fall;
             while (ev) {
                 int bpos = __ffs(ev) - 1;
@@ -285,8 +346,7 @@ k_vox_fwd(Geo g, const RotRec *rots, const PoseRec *poses, int P, float2 *Y, con
                             acc[m].x += (float)len;
                         } else {
                             int i0 = (kx * a) % M, i1 = (kx * (a + len)) % M;
-                            cf d = csub(tw[i0], tw[i1]);
-                            acc[m] = cadd(acc[m], cmul(d, qv[m]));
+                            acc[m] = cadd(acc[m], cmul(csub(tw[i0], tw[i1]), qv[m]));
                         }
                     }
                     if (len & 1) nyq += (a & 1) ? -1.f : 1.f;
@@ -305,9 +365,11 @@ k_vox_fwd(Geo g, const RotRec *rots, const PoseRec *poses, int P, float2 *Y, con
     }
     __syncthreads();
 
-    // y: FFT of each packed column (N non-zero inputs of M), then unpack
-    // column 0 into kx = 0 and kx = M/2 and write Y[b][jz][ky][kx].
-    float2 *Yb = Y + ((size_t)b * N + jz) * (size_t)M * g.P;
+    // y: FFT of each packed column; thread (c, j) of a round of 32 columns
+    // stores ky = out_index(j, s) for column p0 + c: a warp writes 32
+    // consecutive kx (256 contiguous bytes).  Column 0 carries kx = 0 + i kx = M/2
+    // and is unpacked from its ky and M - ky outputs.
+    float2 *Yb = Y + ((size_t)b * N + jz) * (size_t)M * P;
     const int c = threadIdx.x % COLS, j = threadIdx.x / COLS;
     for (int p0 = 0; p0 < H; p0 += COLS) {
         cf v[E];
@@ -317,72 +379,66 @@ k_vox_fwd(Geo g, const RotRec *rots, const PoseRec *poses, int P, float2 *Y, con
             v[s] = (yy < N) ? X[yy * H + p0 + c] : cmake(0.f, 0.f);
         }
         fft_column<M, false>(v, j, xb, c, COLS, tw);
-        __syncthreads();
+        const int kx = p0 + c;
 #pragma unroll
-        for (int s = 0; s < E; ++s) xb[out_index<M>(j, s) * COLS + c] = v[s];
-        __syncthreads();
-        for (int e = threadIdx.x; e < M * COLS; e += blockDim.x) {
-            int ky = e / COLS, cc = e % COLS, kx = p0 + cc;
-            cf val = xb[ky * COLS + cc];
-            float2 *row = Yb + (size_t)ky * g.P;
-            if (kx == 0) {
-                cf o = xb[((M - ky) % M) * COLS];
-                cf oc = cconj(o);
-                cf y0 = cscale(cadd(val, oc), 0.5f);
-                cf w = csub(val, oc);
-                cf yn = cmake(0.5f * w.y, -0.5f * w.x);
-                row[0] = make_float2(y0.x, y0.y);
-                row[H] = make_float2(yn.x, yn.y);
-                for (int k = H + 1; k < g.P; ++k) row[k] = make_float2(0.f, 0.f);
-            } else {
-                row[kx] = make_float2(val.x, val.y);
-            }
+        for (int s = 0; s < E; ++s) {
+            int ky = out_index<M>(j, s);
+            if (kx == 0) c0[ky] = v[s];
+            else Yb[ky * P + kx] = make_float2(v[s].x, v[s].y);
         }
         __syncthreads();
+    }
+    for (int ky = threadIdx.x; ky < M; ky += blockDim.x) {
+        cf val = c0[ky], oc = cconj(c0[(M - ky) % M]);
+        cf y0 = cscale(cadd(val, oc), 0.5f);
+        cf w = csub(val, oc);
+        float2 *row = Yb + ky * P;
+        row[0] = make_float2(y0.x, y0.y);
+        row[H] = make_float2(0.5f * w.y, -0.5f * w.x);
+        for (int k2 = H + 1; k2 < P; ++k2) row[k2] = make_float2(0.f, 0.f);
     }
 }
 
 template <int M>
-static size_t vox_fwd_smem()
+static size_t fwd2d_smem()
 {
     constexpr int N = M / 2, H = M / 2, NW = N / 32;
-    return sizeof(cf) * ((size_t)N * H + (size_t)M * 32 + M) + sizeof(uint32_t) * N * NW;
+    return sizeof(cf) * ((size_t)N * H + (size_t)M * 32 + 2 * M) + sizeof(uint32_t) * N * NW;
 }
 
 template <int M>
-static cudaError_t launch_vox_fwd_t(const Geo &g, const RotRec *rots, int B, const PoseRec *poses, int P, float2 *Y,
-                                    const float2 *tw, const float2 *q, int *err, cudaStream_t st)
+static cudaError_t launch_fwd2d_t(const Geo &g, int B, const uint32_t *bits, float2 *Y, const float2 *tw,
+                                  const float2 *q, cudaStream_t st)
 {
-    size_t sm = vox_fwd_smem<M>();
-    cudaError_t e = cudaFuncSetAttribute(k_vox_fwd<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    size_t sm = fwd2d_smem<M>();
+    cudaError_t e = cudaFuncSetAttribute(k_fwd2d<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    dim3 grid(M / 2, B);
-    k_vox_fwd<M><<<grid, Plan<M>::T * 32, sm, st>>>(g, rots, poses, P, Y, tw, q, err);
+    k_fwd2d<M><<<dim3(M / 2, B), Plan<M>::T * 32, sm, st>>>(g.P, bits, Y, tw, q);
     return cudaGetLastError();
 }
 
-cudaError_t launch_vox_fwd(const Geo &g, const RotRec *rots, int B, const PoseRec *poses, int P, float2 *Y,
-                           const float2 *tw, const float2 *q, int *err, cudaStream_t st)
+cudaError_t launch_fwd2d(const Geo &g, int B, const uint32_t *bits, float2 *Y, const float2 *tw, const float2 *q,
+                         cudaStream_t st)
 {
     switch (g.M) {
-    case 64: return launch_vox_fwd_t<64>(g, rots, B, poses, P, Y, tw, q, err, st);
-    case 128: return launch_vox_fwd_t<128>(g, rots, B, poses, P, Y, tw, q, err, st);
-    case 192: return launch_vox_fwd_t<192>(g, rots, B, poses, P, Y, tw, q, err, st);
-    case 256: return launch_vox_fwd_t<256>(g, rots, B, poses, P, Y, tw, q, err, st);
+    case 64: return launch_fwd2d_t<64>(g, B, bits, Y, tw, q, st);
+    case 128: return launch_fwd2d_t<128>(g, B, bits, Y, tw, q, st);
+    case 192: return launch_fwd2d_t<192>(g, B, bits, Y, tw, q, st);
+    case 256: return launch_fwd2d_t<256>(g, B, bits, Y, tw, q, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
 // Bits of S_b to a byte array (test hook): one block per (slab, rotation).
 template <int N>
-__global__ void k_vox_export(Geo g, const RotRec *rots, const PoseRec *poses, int P, uint8_t *out, int *err)
+__global__ void __launch_bounds__(256) k_vox_export(Geo g, const RotRec *rots, const PoseRec *poses, int P, uint8_t *out)
 {
     constexpr int NW = N / 32;
     __shared__ uint32_t bits[N * NW];
     const int jz = blockIdx.x, b = blockIdx.y;
     for (int i = threadIdx.x; i < N * NW; i += blockDim.x) bits[i] = 0u;
     __syncthreads();
-    voxelise_slab<N>(g, rots[b], poses, P, jz, bits, err);
+    voxelise_slab<N>(g, rots[b], poses, P, jz, bits);
     __syncthreads();
     uint8_t *o = out + ((size_t)b * N + jz) * N * N;
     for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
@@ -392,14 +448,14 @@ __global__ void k_vox_export(Geo g, const RotRec *rots, const PoseRec *poses, in
 }
 
 cudaError_t launch_vox_export(const Geo &g, const RotRec *rots, int B, const PoseRec *poses, int P, uint8_t *bits,
-                              int *err, cudaStream_t st)
+                              cudaStream_t st)
 {
     dim3 grid(g.N, B);
     switch (g.N) {
-    case 32: k_vox_export<32><<<grid, 256, 0, st>>>(g, rots, poses, P, bits, err); break;
-    case 64: k_vox_export<64><<<grid, 256, 0, st>>>(g, rots, poses, P, bits, err); break;
-    case 96: k_vox_export<96><<<grid, 256, 0, st>>>(g, rots, poses, P, bits, err); break;
-    case 128: k_vox_export<128><<<grid, 256, 0, st>>>(g, rots, poses, P, bits, err); break;
+    case 32: k_vox_export<32><<<grid, 256, 0, st>>>(g, rots, poses, P, bits); break;
+    case 64: k_vox_export<64><<<grid, 256, 0, st>>>(g, rots, poses, P, bits); break;
+    case 96: k_vox_export<96><<<grid, 256, 0, st>>>(g, rots, poses, P, bits); break;
+    case 128: k_vox_export<128><<<grid, 256, 0, st>>>(g, rots, poses, P, bits); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -506,19 +562,26 @@ template <int M> struct PlaneCfg {
     static constexpr int CL = (M >= 256) ? 2 : 1;          // CTAs per plane
     static constexpr int H = M / 2;
     static constexpr int PC = H / CL;                      // packed columns per CTA
+    static constexpr int PP = PC + 1;                      // odd pitch: a warp's rows hit distinct banks
     static constexpr int NT = Plan<M>::T * 32;             // threads
+    static constexpr int RPR = NT / Plan<H>::T;            // rows per round of the C2R
+    static constexpr int S1 = M * 32;                      // phase-1 exchange
+    static constexpr int S2 = (M / CL) * PP;               // peer rows (cluster)
+    static constexpr int S3 = H * RPR;                     // phase-2 exchange (single CTA)
+    static constexpr int STG = S1 > S2 ? (S1 > S3 ? S1 : S3) : (S2 > S3 ? S2 : S3);
+    static constexpr size_t SMEM = sizeof(cf) * ((size_t)M * PP + STG + M);
 };
 
 template <int M, bool EXPORT>
 __device__ __forceinline__ void plane_body(const float2 *Zp, const float2 *tw_g, unsigned long long *key, float *Cout,
-                                           int zc, cf *pb, cf *xb, cf *tw, int rank, cf *peer)
+                                           int zc, cf *pb, cf *stg, cf *tw, int rank)
 {
-    constexpr int H = M / 2, CL = PlaneCfg<M>::CL, PC = PlaneCfg<M>::PC, E = Plan<M>::E;
-    constexpr int COLS = 32, PP = PC + 1;   // odd pitch: rows of one warp hit distinct banks
+    using C = PlaneCfg<M>;
+    constexpr int H = M / 2, CL = C::CL, PC = C::PC, PP = C::PP, E = Plan<M>::E, COLS = 32;
     const int P = H + 2;
     for (int i = threadIdx.x; i < M; i += blockDim.x) { float2 w = tw_g[i]; tw[i] = cmake(w.x, w.y); }
     __syncthreads();
-    // phase 1: inverse FFT along y of this CTA's packed columns
+    // phase 1: inverse FFT along y of this CTA's packed columns -> pb[y][local column]
     {
         const int c = threadIdx.x % COLS, j = threadIdx.x / COLS;
         for (int p0 = 0; p0 < PC; p0 += COLS) {
@@ -531,16 +594,16 @@ __device__ __forceinline__ void plane_body(const float2 *Zp, const float2 *tw_g,
                 int ky = in_index<M>(j, s);
                 cf val = cmake(0.f, 0.f);
                 if (act) {
-                    float2 t = Zp[(size_t)ky * P + pc];
+                    float2 t = Zp[ky * P + pc];
                     val = cmake(t.x, t.y);
                     if (pc == 0) {
-                        float2 u = Zp[(size_t)ky * P + H];
+                        float2 u = Zp[ky * P + H];
                         val = cmake(val.x - u.y, val.y + u.x);   // + i * Z[ky][M/2]
                     }
                 }
                 v[s] = val;
             }
-            fft_column<M, true>(v, j, xb, c, COLS, tw);
+            fft_column<M, true>(v, j, stg, c, COLS, tw);
             if (act) {
 #pragma unroll
                 for (int s = 0; s < E; ++s) pb[out_index<M>(j, s) * PP + pl] = v[s];
@@ -548,36 +611,54 @@ __device__ __forceinline__ void plane_body(const float2 *Zp, const float2 *tw_g,
             __syncthreads();
         }
     }
+    // my rows [rank M/CL, (rank+1) M/CL); with a cluster, the peer's columns of
+    // those rows are copied once (coalesced) into stg, and after a second
+    // barrier the half of pb the peer read is free for the C2R exchange
+    const int rows = M / CL, row0 = rank * rows;
+    cf *xb2 = stg;
     if constexpr (CL > 1) {
-        cg::this_cluster().sync();
+        cg::cluster_group cl = cg::this_cluster();
+        cl.sync();
+        const cf *peer = cl.map_shared_rank(pb, rank ^ 1);
+        for (int e = threadIdx.x; e < rows * PC; e += blockDim.x) {
+            int r = e / PC, col = e % PC;
+            stg[r * PP + col] = peer[(row0 + r) * PP + col];
+        }
+        cl.sync();
+        xb2 = pb + (rank ^ 1) * rows * PP;
     } else {
         __syncthreads();
     }
-    // phase 2: C2R along x of rows [rank M/CL, (rank+1) M/CL)
+    // phase 2: C2R along x of my rows by a half-length complex inverse FFT
     {
-        constexpr int TH = Plan<H>::T, EH = Plan<H>::E, RPR = PlaneCfg<M>::NT / TH;   // rows per round
+        constexpr int EH = Plan<H>::E, RPR = C::RPR;
         const int rowl = threadIdx.x % RPR, j = threadIdx.x / RPR;
-        const int rows = M / CL;
         float best = -INFINITY;
         uint32_t bidx = 0xFFFFFFFFu;
         for (int r0 = 0; r0 < rows; r0 += RPR) {
-            int y = rank * rows + r0 + rowl;
-            bool act = (r0 + rowl) < rows;
+            int yl = r0 + rowl;
+            int y = row0 + yl;
+            bool act = yl < rows;
             cf v[EH];
 #pragma unroll
             for (int s = 0; s < EH; ++s) {
                 int k = in_index<H>(j, s);
                 cf Ek = cmake(0.f, 0.f), Ok = cmake(0.f, 0.f);
                 if (act) {
-                    cf Wk, Wm;   // W[k], W[H - k]
+                    // W[k] and W[H - k]; column 0 holds W[0] + i W[H]
+                    cf Wk, Wm;
+                    auto fetch = [&](int col) -> cf {
+                        int own = col / PC, l = col % PC;
+                        if (CL == 1 || own == rank) return pb[y * PP + l];
+                        return stg[yl * PP + l];
+                    };
                     if (k == 0) {
-                        cf p = (CL > 1 && rank != 0) ? peer[y * PP + 0] : pb[y * PP + 0];
+                        cf p = fetch(0);
                         Wk = cmake(p.x, 0.f);
                         Wm = cmake(p.y, 0.f);
                     } else {
-                        int o1 = k / PC, l1 = k % PC, k2 = H - k, o2 = k2 / PC, l2 = k2 % PC;
-                        Wk = (CL > 1 && o1 != rank) ? peer[y * PP + l1] : pb[y * PP + l1];
-                        Wm = (CL > 1 && o2 != rank) ? peer[y * PP + l2] : pb[y * PP + l2];
+                        Wk = fetch(k);
+                        Wm = fetch(H - k);
                     }
                     cf wc = cconj(Wm);
                     Ek = cadd(Wk, wc);
@@ -585,7 +666,7 @@ __device__ __forceinline__ void plane_body(const float2 *Zp, const float2 *tw_g,
                 }
                 v[s] = cmake(Ek.x - Ok.y, Ek.y + Ok.x);   // E + i O
             }
-            fft_column<H, true, 2>(v, j, xb, rowl, RPR, tw);
+            fft_column<H, true, 2>(v, j, xb2, rowl, RPR, tw);
             if (act) {
 #pragma unroll
                 for (int s = 0; s < EH; ++s) {
@@ -603,73 +684,62 @@ __device__ __forceinline__ void plane_body(const float2 *Zp, const float2 *tw_g,
             __syncthreads();
         }
         if (!EXPORT) {
-            unsigned long long k = (bidx == 0xFFFFFFFFu) ? 0ull : pack_key(best, bidx);
+            unsigned long long kk = (bidx == 0xFFFFFFFFu) ? 0ull : pack_key(best, bidx);
             for (int o = 16; o > 0; o >>= 1) {
-                unsigned long long k2 = __shfl_down_sync(0xFFFFFFFFu, k, o);
-                k = k2 > k ? k2 : k;
+                unsigned long long k2 = __shfl_down_sync(0xFFFFFFFFu, kk, o);
+                kk = k2 > kk ? k2 : kk;
             }
             __shared__ unsigned long long wk[32];
             int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-            if (lane == 0) wk[warp] = k;
+            if (lane == 0) wk[warp] = kk;
             __syncthreads();
             if (warp == 0) {
-                k = (lane < (int)(blockDim.x >> 5)) ? wk[lane] : 0ull;
+                kk = (lane < (int)(blockDim.x >> 5)) ? wk[lane] : 0ull;
                 for (int o = 16; o > 0; o >>= 1) {
-                    unsigned long long k2 = __shfl_down_sync(0xFFFFFFFFu, k, o);
-                    k = k2 > k ? k2 : k;
+                    unsigned long long k2 = __shfl_down_sync(0xFFFFFFFFu, kk, o);
+                    kk = k2 > kk ? k2 : kk;
                 }
-                if (lane == 0 && k) atomicMax(key, k);
+                if (lane == 0 && kk) atomicMax(key, kk);
             }
         }
     }
-    if constexpr (CL > 1) cg::this_cluster().sync();   // keep smem alive until the peer is done reading
 }
 
 template <int M>
 __global__ void __launch_bounds__(PlaneCfg<M>::NT)
 k_plane(int B, const float2 *Z, const float2 *tw_g, const RotRec *rots, unsigned long long *keys)
 {
-    constexpr int H = M / 2, CL = PlaneCfg<M>::CL, PC = PlaneCfg<M>::PC, COLS = 32;
+    using C = PlaneCfg<M>;
     extern __shared__ __align__(16) unsigned char smem[];
-    cf *pb = reinterpret_cast<cf *>(smem);    // [M][PC + 1]
-    cf *xb = pb + M * (PC + 1);               // [M][COLS] (>= [H][RPR])
-    cf *tw = xb + M * COLS;                   // [M]
-    const int zc = blockIdx.x / CL, b = blockIdx.y;
+    cf *pb = reinterpret_cast<cf *>(smem);    // [M][PP]
+    cf *stg = pb + M * C::PP;                 // [STG]
+    cf *tw = stg + C::STG;                    // [M]
+    const int zc = blockIdx.x / C::CL, b = blockIdx.y;
     int rank = 0;
-    cf *peer = pb;
-    if constexpr (CL > 1) {
-        cg::cluster_group cl = cg::this_cluster();
-        rank = (int)cl.block_rank();
-        peer = cl.map_shared_rank(pb, rank ^ 1);
-    }
-    const size_t plane = (size_t)M * (H + 2);
+    if constexpr (C::CL > 1) rank = (int)cg::this_cluster().block_rank();
+    const size_t plane = (size_t)M * (M / 2 + 2);
     const float2 *Zp = Z + ((size_t)b * M + zc) * plane;
-    plane_body<M, false>(Zp, tw_g, &keys[rots[b].rot], nullptr, zc, pb, xb, tw, rank, peer);
+    plane_body<M, false>(Zp, tw_g, &keys[rots[b].rot], nullptr, zc, pb, stg, tw, rank);
 }
 
 template <int M>
 __global__ void __launch_bounds__(PlaneCfg<M>::NT)
 k_plane_export(const float2 *Z, const float2 *tw_g, float *C)
 {
-    constexpr int H = M / 2, CL = PlaneCfg<M>::CL, PC = PlaneCfg<M>::PC, COLS = 32;
+    using Cf = PlaneCfg<M>;
     extern __shared__ __align__(16) unsigned char smem[];
     cf *pb = reinterpret_cast<cf *>(smem);
-    cf *xb = pb + M * (PC + 1);
-    cf *tw = xb + M * COLS;
-    const int zc = blockIdx.x / CL;
+    cf *stg = pb + M * Cf::PP;
+    cf *tw = stg + Cf::STG;
+    const int zc = blockIdx.x / Cf::CL;
     int rank = 0;
-    cf *peer = pb;
-    if constexpr (CL > 1) {
-        cg::cluster_group cl = cg::this_cluster();
-        rank = (int)cl.block_rank();
-        peer = cl.map_shared_rank(pb, rank ^ 1);
-    }
-    const size_t plane = (size_t)M * (H + 2);
-    plane_body<M, true>(Z + (size_t)zc * plane, tw_g, nullptr, C, zc, pb, xb, tw, rank, peer);
+    if constexpr (Cf::CL > 1) rank = (int)cg::this_cluster().block_rank();
+    const size_t plane = (size_t)M * (M / 2 + 2);
+    plane_body<M, true>(Z + (size_t)zc * plane, tw_g, nullptr, C, zc, pb, stg, tw, rank);
 }
 
 template <int M>
-static size_t plane_smem() { return sizeof(cf) * ((size_t)M * (PlaneCfg<M>::PC + 1) + (size_t)M * 32 + M); }
+static size_t plane_smem() { return PlaneCfg<M>::SMEM; }
 
 template <int M, bool EXPORT>
 static cudaError_t launch_plane_t(int B, const float2 *Z, const float2 *tw, const RotRec *rots,

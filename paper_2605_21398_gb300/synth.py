@@ -346,19 +346,36 @@ class Trajectory:
 
 
 def contact_trajectory(obj: StarObject, n_poses, radius, length, seed,
-                       noncontact_frac=0.0, lift_range=(0.5, 2.0), sweep=4.0):
+                       noncontact_frac=0.0, lift_range=(0.5, 2.0), sweep=4.5, axes_mode="ortho", wobble=2.0):
     """Three drop-to-contact segments with different tool-axis directions.
 
-    Segment s uses tool axis a_s (pointing from the tip to the shank) and moves
-    the tool line across the object face seen from a_s: lateral offset
-    sweep*(2 tau - 1) along e1 plus a small wobble along e2.  With
-    `noncontact_frac` > 0, contiguous runs of poses are lifted along the axis by
-    U(lift_range) mm on a half-sine profile and labelled non-contact.
+    axes_mode "ortho": the three columns of a random rotation, each tilted by
+    a random 10-20 degrees (no exact symmetry between segments); "cone":
+    three axes inside a 60 degree cone (probing from one side).  Segment s
+    uses tool axis a_s (pointing from the tip to the shank) and moves the tool
+    line across the object face seen from a_s: lateral offset
+    sweep*(2 tau - 1) along e1 plus a wobble of up to `wobble` mm along e2.
+    With `noncontact_frac` > 0, contiguous runs of poses are lifted along the
+    axis by U(lift_range) mm on a half-sine profile and labelled non-contact.
     """
     rng = np.random.default_rng(seed)
     q = random_quat(rng)
     Rm = quat_to_mat(q)
-    axes = Rm.T.copy()                           # three orthonormal directions
+    if axes_mode == "cone":
+        t60 = math.radians(60.0)
+        local = np.array([[0.0, 0.0, 1.0],
+                          [math.sin(t60), 0.0, math.cos(t60)],
+                          [math.sin(t60) * math.cos(math.radians(135)), math.sin(t60) * math.sin(math.radians(135)),
+                           math.cos(t60)]])
+        axes = local @ Rm.T
+    else:
+        axes = Rm.T.copy()
+        for s_ in range(3):
+            tilt = math.radians(rng.uniform(10.0, 20.0))
+            v = rng.normal(size=3)
+            v -= axes[s_] * (v @ axes[s_])
+            v /= np.linalg.norm(v)
+            axes[s_] = math.cos(tilt) * axes[s_] + math.sin(tilt) * v
     sizes = [n_poses // 3 + (1 if s < n_poses % 3 else 0) for s in range(3)]
     poses, geom = [], []
     for s in range(3):
@@ -367,7 +384,7 @@ def contact_trajectory(obj: StarObject, n_poses, radius, length, seed,
         dc = _DropCutter(obj.verts, obj.tris, a, radius)
         qa = _axis_quat(a, e1)
         n = sizes[s]
-        wob = 0.6 * rng.random()
+        wob = wobble * rng.random()
         ph = 2 * np.pi * rng.random()
         lifted = np.zeros(n)
         if noncontact_frac > 0 and n > 0:

@@ -152,9 +152,10 @@ def test_refined_poses_match_oracle(ctx, workload):
 def test_register_recovers_the_planted_pose(ctx, workload):
     w = workload("free64")
     ob, sw = _gpu_pair(ctx, w)
-    res = ctx.register(ob, sw, n_global=4096, n_local=1024, theta=math.radians(5), top_k=8)
+    # Table I sample counts: n_g = 20000 global, n_l = 5000 local, theta = 5 deg
+    res = ctx.register(ob, sw, n_global=20000, n_local=5000, theta=math.radians(5), top_k=8)
     a = O.mesh_anchor(w.obj.verts)
     dt, dr = _pose_err(res["q"], res["t"], w.gt_q, w.gt_t, a)
     # pose noise of 0.1 mm / 0.5 deg per probe pose bounds the attainable accuracy
     assert dt < 0.25 and dr < 3.0, (dt, dr)
-    assert res["n_evals"] == 4096 + 1024
+    assert res["n_evals"] == 20000 + 5000
