@@ -40,6 +40,22 @@ def _dist():
     return rank, ws
 
 
+def max_over_ranks(ms, ws, device):
+    """The slowest rank's timed milliseconds (every rank gets the same value)."""
+    if ws <= 1:
+        return ms
+    import torch
+    tt = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_rate(ws, units_per_rank, ms_max):
+    """Units all ranks processed / the slowest rank's time (weak scaling: each
+    rank runs its own replica of the workload)."""
+    return ws * units_per_rank / (ms_max / 1000.0)
+
+
 class ClockSampler:
     """nvidia-smi samples (every 200 ms) during the timed region."""
 
@@ -99,20 +115,15 @@ def model_bytes_per_eval(N):
     return (N * N * (M // 2 + 1) * 8) * 2 + (M * N * (M // 2 + 1) * 8) * 2 + H + H + 2 * H + H
 
 
-def kernel_bytes(name, N, launches_rot):
-    """Compulsory HBM bytes per rotation of each fused kernel (inputs read
-    once, outputs written once), P = M/2 + 2 complex per row."""
+def kernel_bytes(name, N):
+    """Compulsory HBM bytes per rotation of each fused search kernel (inputs
+    read once, outputs written once), P = M/2 + 2 complex per row."""
     M = 2 * N
     P = M // 2 + 2
     y = N * M * P * 8
     z = M * M * P * 8
-    if name == "vox_fwd":
-        return y
-    if name == "zpass":
-        return y + z          # + the spectrum, shared by the rotations of a block (added below)
-    if name == "plane":
-        return z
-    return None
+    bits = N * N * N // 8
+    return {"voxelise": bits, "fwd2d": bits + y, "zpass": y + z, "plane": z}.get(name)
 
 
 def load_peaks():
@@ -166,6 +177,23 @@ def run_reference(args):
     return 0
 
 
+def run_ncu_case():
+    """One search of 8 SF rotations in one batch on the bench workload: every
+    search kernel launches once with 8 rotations (a few GB on the device)."""
+    from paper_2605_21398_gb300 import build, dock, synth
+    build.build()
+    w = synth.make_workload(WORKLOAD)
+    ctx = dock.Context(0)
+    ob = ctx.object_grid(w.obj.verts, w.obj.tris, w.h, w.N)
+    sw = ctx.sweep_grid(w.poses_world, w.radius, w.length, w.h, w.N, contact=w.labels)
+    c = ctx.search_so3(ob, sw, 8, 4, batch=8)
+    print(json.dumps({"ncu_case": WORKLOAD, "rotations": 8, "best_score": c[0]["score"]}))
+    ob.close()
+    sw.close()
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -176,9 +204,13 @@ def main():
     ap.add_argument("--n-local", type=int, default=N_LOCAL)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ncu-case", action="store_true",
+                    help="small fixed case for ncu captures: one search of 8 rotations (batch 8) of the bench workload")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.ncu_case:
+        return run_ncu_case()
 
     import torch
     rank, ws = _dist()
@@ -230,37 +262,33 @@ def main():
     clk = clocks.stop()
     ctx.set_profiling(False)
     stats = ctx.kernel_stats()
-    ms_total = float(sum(ms_steps))
-    if ws > 1:
-        tt = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(tt.item())
+    ms_total = max_over_ranks(float(sum(ms_steps)), ws, "cuda")
     evals_per_step = args.n_global + args.n_local
-    value = ws * evals_per_step * args.steps / (ms_total / 1000.0)
+    value = whole_job_rate(ws, evals_per_step * args.steps, ms_total)
 
-    # dominant kernel roofline (algorithmic bytes / average launch time)
+    # roofline of the dominant HBM-bound search kernel (algorithmic bytes per
+    # launch / its average CUDA-event duration); every kernel's share is listed
     peak, peak_src = load_peaks()
-    per_rot = {}
     rot_total = evals_per_step * args.steps
-    for name in ("vox_fwd", "zpass", "plane"):
-        if name in stats:
-            per_rot[name] = stats[name][1]
-    dom = max(per_rot, key=lambda k: per_rot[k]) if per_rot else None
-    roofline = None
     kernels = {k: {"launches": v[0], "total_ms": round(v[1], 3)} for k, v in stats.items()}
+    tot_all = sum(v[1] for v in stats.values()) or 1.0
+    for k in kernels:
+        kernels[k]["share"] = round(stats[k][1] / tot_all, 4)
+    roofline = None
+    hbm = {k: stats[k][1] for k in ("fwd2d", "zpass", "plane") if k in stats}
+    dom = max(hbm, key=lambda k: hbm[k]) if hbm else None
     if dom:
         launches, tot_ms = stats[dom]
         M = 2 * w.N
         P = M // 2 + 2
-        bytes_rot = kernel_bytes(dom, w.N, None)
-        total_bytes = bytes_rot * rot_total
+        total_bytes = kernel_bytes(dom, w.N) * rot_total
         if dom == "zpass":
-            # spectrum read once per block-column of rotations; per launch = one batch
-            total_bytes += M * M * P * 8 * launches
+            total_bytes += M * M * P * 8 * launches   # spectrum read once per launch (block column)
         achieved = total_bytes / (tot_ms / 1000.0) / 1e9
         roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                     "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_src,
-                    "algorithmic_bytes_per_launch": int(total_bytes / max(1, launches))}
+                    "algorithmic_bytes_per_launch": int(total_bytes / max(1, launches)),
+                    "dominant_overall": max(stats, key=lambda k: stats[k][1])}
     model_frac = value / ws * model_bytes_per_eval(w.N) / (peak * 1e9)
 
     # end-to-end through the public API from host buffers (object + sweep + register + result)
@@ -300,15 +328,17 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "large128: 128^3 lattice at 0.15 mm (canvas 256^3), %d SF + %d GeoBall-SF "
-                                   "rotations, 5000 probe poses (20%% labels flipped, 0.02 mm noise), 65k-triangle "
-                                   "star object, top-%d refined (20 Gauss-Newton iterations)"
+                                   "rotations, 5000 probe poses on 3 raster segments (20%% labels flipped, 0.02 mm "
+                                   "noise), 65k-triangle star object, top-%d refined (20 Gauss-Newton iterations)"
                                    % (args.n_global, args.n_local, TOP_K),
-                       "l2": "inputs larger than L2 (per-batch FFT intermediates ~0.8 GB) and a 256 MB L2 flush "
+                       "l2": "inputs larger than L2 (per-batch FFT intermediates ~4 GB) and a 256 MB L2 flush "
                              "before every step",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "roofline": roofline, "model_roofline_frac": round(model_frac, 4),
             "model_bytes_per_eval": model_bytes_per_eval(w.N),
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "kernels": kernels,
+            "ms_per_eval_search": round(sum(stats[k][1] for k in ("voxelise", "fwd2d", "zpass", "plane") if k in stats)
+                                        / rot_total * 1000.0, 3),
             "clocks": clk, "object_setup_ms": round(obj_setup_ms, 2),
             "accuracy": {"trans_err_mm": round(err_t, 4), "rot_err_deg": round(err_r, 4), "J": res["J"]}}
     if rank == 0:

@@ -140,6 +140,9 @@ typedef struct dock_result {
     int32_t best_cand;   /* candidate index that won the refinement */
     int32_t n_evals;     /* orientation samples evaluated */
     dock_candidate best_search; /* best candidate of the search stages */
+    double latency_ms;   /* submission (or call) to completion, host clock */
+    int64_t first_pass;  /* engine search passes (counted per context) that this request */
+    int64_t last_pass;   /* first and last took part in */
 } dock_result;
 
 /* ---------------------------------------------------------------- context */
@@ -266,6 +269,82 @@ DOCK_API dock_status dock_distances(dock_ctx *ctx, const dock_object *obj, const
  * pose wins (ties: lower candidate index). */
 DOCK_API dock_status dock_register(dock_ctx *ctx, const dock_object *obj, const dock_sweep *sw, const dock_register_desc *desc,
                           const dock_params *params, dock_result *out);
+
+/* A registration request: object and sweep handles plus its search sizes. */
+typedef struct dock_request {
+    const dock_object *obj;
+    const dock_sweep *sweep;
+    dock_register_desc desc;
+} dock_request;
+
+/*
+ * Batched registration of uneven requests (different lattice sides, trajectory
+ * lengths, probes and sample counts; Fig. 2 per request).  Up to 64 requests
+ * are in flight at once; requests with the same lattice side N share every
+ * search pass: one launch of each fused search kernel takes rotations of
+ * several requests, each rotation carrying its request's trajectory, probe
+ * and object spectrum, and lattice sides take turns.  Each result equals the
+ * request registered alone by dock_register (the arithmetic per rotation is
+ * the same).  out receives n results in request order; on an error the call
+ * returns the first failing request's status.
+ */
+DOCK_API dock_status dock_register_batch(dock_ctx *ctx, const dock_request *reqs, int32_t n, const dock_params *params,
+                                         dock_result *out);
+
+/*
+ * Serving (continuous batching).  dock_submit queues a registration and
+ * returns at once with a ticket; a serving thread of the context (started by
+ * the first submission) admits queued requests between search passes while
+ * one of its 64 request slots is free and the context's HBM budget holds the
+ * request's device state (quaternions, rotation records, peak keys and
+ * candidates: about 200 bytes per orientation sample, plus the shared search
+ * scratch of its lattice side).  Admitted requests of the same lattice side
+ * share every search pass, each taking an equal share of the pass's
+ * rotations, so a request that arrives while others run starts with the next
+ * pass.  Results equal dock_register on the same request.
+ *
+ * The object and sweep handles must stay alive until the request completes.
+ * dock_poll waits up to timeout_us (0: no wait, < 0: until done) and returns
+ * DOCK_PENDING, or the request's status; a completed ticket is collected by
+ * the dock_poll that returns it and is unknown afterwards.  dock_cancel marks
+ * a request: a queued one never starts, an admitted one stops at the next
+ * pass boundary; its dock_poll returns DOCK_E_CANCELLED.  While the serving
+ * thread runs, every other call on the context waits for the pass in flight.
+ * dock_destroy cancels what is left.
+ */
+DOCK_API dock_status dock_submit(dock_ctx *ctx, const dock_request *req, const dock_params *params, uint64_t *ticket);
+DOCK_API dock_status dock_poll(dock_ctx *ctx, uint64_t ticket, dock_result *out, int64_t timeout_us);
+DOCK_API dock_status dock_cancel(dock_ctx *ctx, uint64_t ticket);
+
+/* ---------------------------------------------------------------- tuning */
+
+/* Launch shape of the search kernels for one lattice side. */
+typedef struct dock_tuning {
+    int32_t N;               /* lattice side */
+    int32_t batch;           /* rotations per launch of the four search kernels */
+    int32_t group;           /* rotations per z-pass block sharing one spectrum read (0 = heuristic) */
+    int32_t vox_blocks;      /* voxeliser register target: 3 or 4 resident blocks per SM */
+    double us_per_rotation;  /* measured device time per rotation of this shape (0 = not measured) */
+} dock_tuning;
+
+/*
+ * Autotuner (systems form; the paper has no counterpart).  Times the search
+ * kernels on n_rot SF rotations of (obj, sweep) under candidate launch shapes
+ * -- the voxeliser's register target, the rotations per launch and the
+ * rotations per z-pass block -- one knob at a time, with CUDA events on the
+ * context's stream, and keeps the fastest for obj's lattice side on ctx (all
+ * later searches, registrations and serving passes of that side use it).
+ * Results do not depend on the shape.  With cache_path non-NULL the context's
+ * tuned shapes are written there as JSON (with the device name).  Takes about
+ * 13 timed searches of n_rot rotations; n_rot in [16, 65536].
+ */
+DOCK_API dock_status dock_autotune(dock_ctx *ctx, const dock_object *obj, const dock_sweep *sweep, int32_t n_rot,
+                                   const char *cache_path, dock_tuning *out);
+/* Loads shapes written by dock_autotune for this device (entries of other
+ * devices are skipped); returns the number loaded in *n_loaded. */
+DOCK_API dock_status dock_load_tuning(dock_ctx *ctx, const char *cache_path, int32_t *n_loaded);
+/* The shape in use for lattice side N (tuned or default). */
+DOCK_API dock_status dock_get_tuning(dock_ctx *ctx, int32_t N, dock_tuning *out);
 
 /* --------------------------------------------------------------- profiling */
 

@@ -10,8 +10,13 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <memory>
 #include <mutex>
+#include <thread>
 #include <new>
 #include <string>
 #include <vector>
@@ -33,6 +38,8 @@ struct KStat {
     double ms = 0.0;
 };
 
+struct Engine;
+
 struct dock_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -40,6 +47,7 @@ struct dock_ctx {
     size_t budget = 0;        // 0 = unbounded
     size_t held = 0;          // bytes currently held by this context and its handles
     std::string err;
+    std::mutex err_mu;        // err is written by the serving thread too
     bool dead = false;
     // search scratch (grown on demand)
     float2 *Y = nullptr, *Z = nullptr;
@@ -55,6 +63,10 @@ struct dock_ctx {
     int *errflag = nullptr;
     dock_candidate *cands = nullptr;
     size_t cands_n = 0;
+    ReqDev *reqs = nullptr;   // request table of the current search launches
+    size_t reqs_n = 0;
+    RotRec *phase = nullptr;  // rotations of several requests gathered for one pipeline pass
+    size_t phase_n = 0;
     // refinement buffers
     double *ref_state = nullptr, *ref_acc = nullptr, *ref_prm = nullptr;
     size_t ref_state_n = 0, ref_acc_n = 0, ref_prm_n = 0;
@@ -68,6 +80,28 @@ struct dock_ctx {
     std::vector<ProfEntry> pending;
     std::map<std::string, KStat> stats;
     std::vector<cudaEvent_t> ev_pool;
+    // registration engine (created by the first registration or submission)
+    std::map<int, dock_tuning> tune;   // per lattice side (autotuner or cache)
+    Engine *eng = nullptr;
+    std::atomic<bool> eng_ready{false};
+    std::recursive_mutex dev_mu;   // serialises device work of API calls and the serving thread
+    std::atomic<int> dev_want{0};  // API calls waiting for dev_mu
+};
+
+// Lock of ctx->dev_mu for an API call.  The waiter is announced so that the
+// serving thread steps aside between passes instead of re-taking the lock
+// at once (a plain mutex would let it starve the caller).
+struct DevLock {
+    dock_ctx *c;
+    explicit DevLock(dock_ctx *ctx) : c(ctx)
+    {
+        c->dev_want.fetch_add(1);
+        c->dev_mu.lock();
+        c->dev_want.fetch_sub(1);
+    }
+    ~DevLock() { c->dev_mu.unlock(); }
+    DevLock(const DevLock &) = delete;
+    DevLock &operator=(const DevLock &) = delete;
 };
 
 struct dock_object {
@@ -111,6 +145,7 @@ static dock_status fail(dock_ctx *ctx, dock_status st, const char *fmt, ...)
         va_start(ap, fmt);
         vsnprintf(buf, sizeof(buf), fmt, ap);
         va_end(ap);
+        std::lock_guard<std::mutex> lk(ctx->err_mu);
         ctx->err = buf;
     }
     return st;
@@ -345,6 +380,9 @@ static dock_status gen_samples(dock_ctx *ctx, const dock_search_desc *d, std::ve
     return DOCK_OK;
 }
 
+static void engine_shutdown(dock_ctx *ctx);
+static void engine_drop_handle(dock_ctx *ctx, const dock_object *ob, const dock_sweep *sw);
+
 // ---------------------------------------------------------------------------
 // context API
 // ---------------------------------------------------------------------------
@@ -408,6 +446,7 @@ void dock_destroy(dock_ctx *c)
 {
     if (!c) return;
     cudaSetDevice(c->device);
+    engine_shutdown(c);
     cudaStreamSynchronize(c->stream);
     cudaFree(c->Y);
     cudaFree(c->bits);
@@ -416,6 +455,8 @@ void dock_destroy(dock_ctx *c)
     cudaFree(c->quats);
     cudaFree(c->errflag);
     cudaFree(c->cands);
+    cudaFree(c->reqs);
+    cudaFree(c->phase);
     cudaFree(c->ref_state);
     cudaFree(c->ref_acc);
     cudaFree(c->ref_prm);
@@ -429,11 +470,20 @@ void dock_destroy(dock_ctx *c)
     delete c;
 }
 
-const char *dock_last_error(const dock_ctx *c) { return c ? c->err.c_str() : "null context"; }
+const char *dock_last_error(const dock_ctx *c)
+{
+    // a per-thread copy: the serving thread may record errors meanwhile
+    static thread_local std::string copy;
+    if (!c) return "null context";
+    std::lock_guard<std::mutex> lk(const_cast<dock_ctx *>(c)->err_mu);
+    copy = c->err;
+    return copy.c_str();
+}
 
 dock_status dock_set_profiling(dock_ctx *c, int enable)
 {
     if (!c) return DOCK_E_INVALID;
+    DevLock dev_lock_(c);
     if (!enable) prof_resolve(c);
     c->prof = enable != 0;
     return DOCK_OK;
@@ -442,6 +492,7 @@ dock_status dock_set_profiling(dock_ctx *c, int enable)
 int32_t dock_get_kernel_stats(dock_ctx *c, dock_kernel_stat *st, int32_t cap)
 {
     if (!c) return 0;
+    DevLock dev_lock_(c);
     prof_resolve(c);
     int32_t n = 0;
     for (auto &kv : c->stats) {
@@ -458,6 +509,7 @@ int32_t dock_get_kernel_stats(dock_ctx *c, dock_kernel_stat *st, int32_t cap)
 void dock_reset_kernel_stats(dock_ctx *c)
 {
     if (!c) return;
+    DevLock dev_lock_(c);
     prof_resolve(c);
     c->stats.clear();
 }
@@ -671,6 +723,7 @@ extern "C" dock_status dock_object_grid(dock_ctx *ctx, const double *verts, int6
                                         dock_object **out)
 {
     if (!ctx || !out) return DOCK_E_INVALID;
+    DevLock dev_lock_(ctx);
     if (ctx->dead) return fail(ctx, DOCK_E_CUDA_FATAL, "context is dead after a sticky CUDA error");
     *out = nullptr;
     if (!verts || !tris || V < 3 || T < 1) return fail(ctx, DOCK_E_INVALID, "empty mesh");
@@ -821,8 +874,10 @@ extern "C" dock_status dock_object_grid(dock_ctx *ctx, const double *verts, int6
 extern "C" void dock_object_free(dock_object *ob)
 {
     if (!ob) return;
+    DevLock dev_lock_(ob->ctx);
     dock_ctx *ctx = ob->ctx;
     cudaSetDevice(ctx->device);
+    engine_drop_handle(ctx, ob, nullptr);
     cudaStreamSynchronize(ctx->stream);
     cudaFree(ob->O);
     cudaFree(ob->spec);
@@ -839,6 +894,7 @@ extern "C" void dock_object_free(dock_object *ob)
 extern "C" dock_status dock_object_export_grid(dock_ctx *ctx, const dock_object *ob, float *grid, double *origin)
 {
     if (!ctx || !ob) return DOCK_E_INVALID;
+    DevLock dev_lock_(ctx);
     if (grid) CK(ctx, cudaMemcpy(grid, ob->O, sizeof(float) * (size_t)ob->N * ob->N * ob->N, cudaMemcpyDeviceToHost));
     if (origin) memcpy(origin, ob->o, sizeof(double) * 3);
     return DOCK_OK;
@@ -851,6 +907,7 @@ extern "C" dock_status dock_sweep_grid(dock_ctx *ctx, const dock_probe *probe, c
                                        const uint8_t *contact, int64_t P, double h, int32_t N, dock_sweep **out)
 {
     if (!ctx || !out || !probe) return DOCK_E_INVALID;
+    DevLock dev_lock_(ctx);
     if (ctx->dead) return fail(ctx, DOCK_E_CUDA_FATAL, "context is dead after a sticky CUDA error");
     *out = nullptr;
     if (!poses || P <= 0) return fail(ctx, DOCK_E_INVALID, "empty trajectory");
@@ -909,8 +966,10 @@ extern "C" dock_status dock_sweep_grid(dock_ctx *ctx, const dock_probe *probe, c
 extern "C" void dock_sweep_free(dock_sweep *sw)
 {
     if (!sw) return;
+    DevLock dev_lock_(sw->ctx);
     dock_ctx *ctx = sw->ctx;
     cudaSetDevice(ctx->device);
+    engine_drop_handle(ctx, nullptr, sw);
     cudaStreamSynchronize(ctx->stream);
     cudaFree(sw->poses);
     cudaFree(sw->cs_dev);
@@ -949,19 +1008,44 @@ static dock_status ensure(dock_ctx *ctx, void **p, size_t *have, size_t need, si
     return s;
 }
 
-// Upload quaternions [begin, begin + count) of a set of n_total and build
-// their lattice set-up records at the same global indices.
-static dock_status upload_rots(dock_ctx *ctx, const dock_sweep *sw, const double *q, int n_total, int begin, int count)
+// Upload `count` quaternions (host q) to slots [base, base + count) of the
+// context's rotation arrays (capacity `cap`) and build their lattice set-up
+// records: sample indices rot0.., request index `req`.
+static dock_status upload_rots(dock_ctx *ctx, const dock_sweep *sw, const double *q, size_t cap, size_t base, int count,
+                               int rot0, int req)
 {
     dock_status s;
-    if ((s = ensure(ctx, (void **)&ctx->quats, &ctx->quats_n, (size_t)n_total * 4, sizeof(double))) != DOCK_OK) return s;
-    if ((s = ensure(ctx, (void **)&ctx->rots, &ctx->rots_n, (size_t)n_total, sizeof(RotRec))) != DOCK_OK) return s;
+    if ((s = ensure(ctx, (void **)&ctx->quats, &ctx->quats_n, cap * 4, sizeof(double))) != DOCK_OK) return s;
+    if ((s = ensure(ctx, (void **)&ctx->rots, &ctx->rots_n, cap, sizeof(RotRec))) != DOCK_OK) return s;
     if (count <= 0) return DOCK_OK;
-    CK(ctx, cudaMemcpyAsync(ctx->quats + 4 * (size_t)begin, q + 4 * (size_t)begin, sizeof(double) * 4 * count,
-                            cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(ctx->quats + 4 * base, q, sizeof(double) * 4 * count, cudaMemcpyHostToDevice, ctx->stream));
     Prof pr(ctx, "rot_setup");
-    CK(ctx, launch_rot_setup(ctx->quats + 4 * (size_t)begin, count, begin, sw->cs_dev, sw->h, sw->N, ctx->rots + begin,
+    CK(ctx, launch_rot_setup(ctx->quats + 4 * base, count, rot0, req, sw->cs_dev, sw->h, sw->N, ctx->rots + base,
                              ctx->stream));
+    return DOCK_OK;
+}
+
+static ReqDev make_reqdev(const dock_object *ob, const dock_sweep *sw, unsigned long long *keys)
+{
+    ReqDev q;
+    q.poses = sw->poses;
+    q.P = (int)sw->P;
+    q.h = sw->h;
+    q.r = sw->r;
+    q.L = sw->L;
+    q.inv_h = (float)(1.0 / sw->h);
+    q.rv = (float)(sw->r / sw->h);
+    q.lv = (float)(sw->L / sw->h);
+    q.spec = ob ? ob->spec : nullptr;
+    q.keys = keys;
+    return q;
+}
+
+static dock_status upload_reqs(dock_ctx *ctx, const std::vector<ReqDev> &r)
+{
+    dock_status s;
+    if ((s = ensure(ctx, (void **)&ctx->reqs, &ctx->reqs_n, r.size(), sizeof(ReqDev))) != DOCK_OK) return s;
+    CK(ctx, cudaMemcpyAsync(ctx->reqs, r.data(), sizeof(ReqDev) * r.size(), cudaMemcpyHostToDevice, ctx->stream));
     return DOCK_OK;
 }
 
@@ -969,6 +1053,7 @@ extern "C" dock_status dock_sweep_voxelise(dock_ctx *ctx, const dock_sweep *sw, 
                                            uint8_t *bits, double *origins)
 {
     if (!ctx || !sw || !quats || n <= 0) return DOCK_E_INVALID;
+    DevLock dev_lock_(ctx);
     if (ctx->dead) return fail(ctx, DOCK_E_CUDA_FATAL, "context is dead after a sticky CUDA error");
     cudaSetDevice(ctx->device);
     dock_search_desc d = {};
@@ -978,16 +1063,17 @@ extern "C" dock_status dock_sweep_voxelise(dock_ctx *ctx, const dock_sweep *sw, 
     std::vector<double> q;
     dock_status s;
     if ((s = gen_samples(ctx, &d, q)) != DOCK_OK) return s;
-    if ((s = upload_rots(ctx, sw, q.data(), n, 0, n)) != DOCK_OK) return s;
+    if ((s = upload_rots(ctx, sw, q.data(), n, 0, n, 0, 0)) != DOCK_OK) return s;
+    std::vector<ReqDev> rq(1, make_reqdev(nullptr, sw, nullptr));
+    if ((s = upload_reqs(ctx, rq)) != DOCK_OK) return s;
     Geo g = make_geo(sw);
     size_t per = (size_t)g.N * g.N * g.N;
     uint8_t *dbits = nullptr;
     if ((s = dalloc(ctx, (void **)&dbits, per * n, nullptr)) != DOCK_OK) return s;
-    CK(ctx, cudaMemsetAsync(ctx->errflag, 0, sizeof(int), ctx->stream));
     cudaError_t e;
     {
         Prof pr(ctx, "vox_export");
-        e = launch_vox_export(g, ctx->rots, n, sw->poses, (int)sw->P, dbits, ctx->stream);
+        e = launch_vox_export(g, ctx->reqs, ctx->rots, n, dbits, ctx->stream);
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(bits, dbits, per * n, cudaMemcpyDeviceToHost, ctx->stream);
     std::vector<RotRec> rr(n);
@@ -1006,10 +1092,10 @@ extern "C" dock_status dock_sweep_voxelise(dock_ctx *ctx, const dock_sweep *sw, 
 static int auto_batch(const Geo &g)
 {
     size_t per = (size_t)(g.N + g.M) * g.M * g.P * sizeof(float2);
-    size_t lim = (size_t)1 << 30;
+    size_t lim = (size_t)4 << 30;   // Y and Z of a batch: 4 GiB
     size_t b = lim / per;
     if (b < 1) b = 1;
-    if (b > 64) b = 64;
+    if (b > 256) b = 256;
     return (int)b;
 }
 
@@ -1021,15 +1107,32 @@ static dock_status check_pair(dock_ctx *ctx, const dock_object *ob, const dock_s
     return DOCK_OK;
 }
 
-// Runs rotations [r0, r1) of the uploaded set through the pipeline into ctx->keys.
-static dock_status run_pipeline(dock_ctx *ctx, const dock_object *ob, const dock_sweep *sw, int r0, int r1, int batch)
+// The launch shape of the search kernels for lattice side N: the tuned one
+// when the autotuner (or its cache) has one, else the defaults.
+static dock_tuning tuning_for(dock_ctx *ctx, const Geo &g)
 {
-    Geo g = make_geo(sw);
+    auto it = ctx->tune.find(g.N);
+    if (it != ctx->tune.end()) return it->second;
+    dock_tuning t = {};
+    t.N = g.N;
+    t.batch = auto_batch(g);
+    t.group = 0;
+    t.vox_blocks = 4;
+    return t;
+}
+
+// Runs records [r0, r1) of rots through the search pipeline; every
+// rotation's peak key lands in its request's key array (reqs[rot.req]).  All
+// requests of the call share the lattice side of g.
+static dock_status run_pipeline_rots(dock_ctx *ctx, const Geo &g, const ReqDev *reqs, const RotRec *rots, size_t r0,
+                                     size_t r1, int batch)
+{
     float2 *tw, *qt;
     double2 *twd;
     dock_status s;
     if ((s = tables(ctx, g.M, &tw, &qt, &twd)) != DOCK_OK) return s;
-    int B = batch > 0 ? batch : auto_batch(g);
+    const dock_tuning tc = tuning_for(ctx, g);
+    int B = batch > 0 ? batch : tc.batch;
     size_t ysz = (size_t)B * g.N * g.M * g.P, zsz = (size_t)B * g.M * g.M * g.P;
     size_t need = ysz + zsz;
     if (ctx->yz_bytes < need) {
@@ -1046,13 +1149,14 @@ static dock_status run_pipeline(dock_ctx *ctx, const dock_object *ob, const dock
     if ((s = ensure(ctx, (void **)&ctx->bits, &ctx->bits_n, (size_t)B * g.N * g.N * (g.N / 32), sizeof(uint32_t))) != DOCK_OK)
         return s;
     int chunks = g.M * g.P / 32;
-    for (int b0 = r0; b0 < r1; b0 += B) {
-        int nb = std::min(B, r1 - b0);
+    for (size_t b0 = r0; b0 < r1; b0 += B) {
+        int nb = (int)std::min<size_t>(B, r1 - b0);
         int groups_needed = (2 * 152 + chunks - 1) / chunks;
-        int group = std::max(1, nb / groups_needed);
+        int group = tc.group > 0 ? std::min(tc.group, nb) : std::max(1, nb / groups_needed);
+        const RotRec *rb = rots + b0;
         {
             Prof pr(ctx, "voxelise");
-            CK(ctx, launch_voxelise(g, ctx->rots + b0, nb, sw->poses, (int)sw->P, ctx->bits, ctx->stream));
+            CK(ctx, launch_voxelise(g, reqs, rb, nb, ctx->bits, ctx->stream, tc.vox_blocks));
         }
         {
             Prof pr(ctx, "fwd2d");
@@ -1060,14 +1164,19 @@ static dock_status run_pipeline(dock_ctx *ctx, const dock_object *ob, const dock
         }
         {
             Prof pr(ctx, "zpass");
-            CK(ctx, launch_zpass(g, nb, group, Y, ob->spec, Z, tw, ctx->stream));
+            CK(ctx, launch_zpass(g, nb, group, Y, rb, reqs, Z, tw, ctx->stream));
         }
         {
             Prof pr(ctx, "plane");
-            CK(ctx, launch_plane(g, nb, Z, tw, ctx->rots + b0, ctx->keys, ctx->stream));
+            CK(ctx, launch_plane(g, nb, Z, tw, rb, reqs, ctx->stream));
         }
     }
     return DOCK_OK;
+}
+
+static dock_status run_pipeline(dock_ctx *ctx, const Geo &g, size_t r0, size_t r1, int batch)
+{
+    return run_pipeline_rots(ctx, g, ctx->reqs, ctx->rots, r0, r1, batch);
 }
 
 static dock_status search_impl(dock_ctx *ctx, const dock_object *ob, const dock_sweep *sw, const dock_search_desc *d,
@@ -1075,11 +1184,13 @@ static dock_status search_impl(dock_ctx *ctx, const dock_object *ob, const dock_
 {
     const int n = d->n;
     dock_status s;
-    if ((s = upload_rots(ctx, sw, q.data(), n, 0, n)) != DOCK_OK) return s;
+    if ((s = upload_rots(ctx, sw, q.data(), n, 0, n, 0, 0)) != DOCK_OK) return s;
     if ((s = ensure(ctx, (void **)&ctx->keys, &ctx->keys_n, (size_t)n, sizeof(unsigned long long))) != DOCK_OK) return s;
     CK(ctx, cudaMemsetAsync(ctx->keys, 0, sizeof(unsigned long long) * n, ctx->stream));
     CK(ctx, cudaMemsetAsync(ctx->errflag, 0, sizeof(int), ctx->stream));
-    if ((s = run_pipeline(ctx, ob, sw, r0, r1, d->batch)) != DOCK_OK) return s;
+    std::vector<ReqDev> rq(1, make_reqdev(ob, sw, ctx->keys));
+    if ((s = upload_reqs(ctx, rq)) != DOCK_OK) return s;
+    if ((s = run_pipeline(ctx, make_geo(sw), r0, r1, d->batch)) != DOCK_OK) return s;
     if ((s = ensure(ctx, (void **)&ctx->cands, &ctx->cands_n, (size_t)d->top_k, sizeof(dock_candidate))) != DOCK_OK) return s;
     {
         Prof pr(ctx, "topk");
@@ -1114,6 +1225,7 @@ extern "C" dock_status dock_search_so3(dock_ctx *ctx, const dock_object *ob, con
                                        const dock_search_desc *d, dock_candidate *out, dock_peak *per_rot)
 {
     if (!ctx || !ob || !sw || !d || !out) return DOCK_E_INVALID;
+    DevLock dev_lock_(ctx);
     if (ctx->dead) return fail(ctx, DOCK_E_CUDA_FATAL, "context is dead after a sticky CUDA error");
     dock_status s;
     if ((s = check_pair(ctx, ob, sw)) != DOCK_OK) return s;
@@ -1126,10 +1238,197 @@ extern "C" dock_status dock_search_so3(dock_ctx *ctx, const dock_object *ob, con
     return search_impl(ctx, ob, sw, d, q, r0, r1, out, per_rot);
 }
 
+// ---------------------------------------------------------------------------
+// autotuner
+// ---------------------------------------------------------------------------
+static dock_status time_shape(dock_ctx *ctx, const Geo &g, int n, const dock_tuning &t, double *us)
+{
+    ctx->tune[g.N] = t;
+    dock_status s;
+    if ((s = run_pipeline_rots(ctx, g, ctx->reqs, ctx->rots, 0, n, 0)) != DOCK_OK) return s;   // warm-up
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(ctx, cudaEventCreate(&a));
+    cudaError_t e = cudaEventCreate(&b);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(a);
+        return cuda_fail(ctx, e, "cudaEventCreate");
+    }
+    e = cudaEventRecord(a, ctx->stream);
+    if (e == cudaSuccess) s = run_pipeline_rots(ctx, g, ctx->reqs, ctx->rots, 0, n, 0);
+    if (e == cudaSuccess && s == DOCK_OK) e = cudaEventRecord(b, ctx->stream);
+    if (e == cudaSuccess && s == DOCK_OK) e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess && s == DOCK_OK) e = cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (s != DOCK_OK) return s;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "timing a launch shape");
+    *us = 1000.0 * ms / n;
+    return DOCK_OK;
+}
+
+static std::string device_name(int dev)
+{
+    cudaDeviceProp pr;
+    if (cudaGetDeviceProperties(&pr, dev) != cudaSuccess) return "unknown";
+    std::string n = pr.name;
+    for (auto &ch : n)
+        if (ch == '"' || ch == '\\') ch = '_';
+    return n;
+}
+
+static dock_status write_tuning(dock_ctx *ctx, const char *path)
+{
+    FILE *f = fopen(path, "w");
+    if (!f) return fail(ctx, DOCK_E_INVALID, "cannot write the tuning cache %s", path);
+    fprintf(f, "{\"device\": \"%s\", \"entries\": [", device_name(ctx->device).c_str());
+    bool first = true;
+    for (auto &kv : ctx->tune) {
+        const dock_tuning &t = kv.second;
+        fprintf(f, "%s\n  {\"N\": %d, \"batch\": %d, \"group\": %d, \"vox_blocks\": %d, \"us_per_rotation\": %.3f}",
+                first ? "" : ",", t.N, t.batch, t.group, t.vox_blocks, t.us_per_rotation);
+        first = false;
+    }
+    fprintf(f, "\n]}\n");
+    bool ok = ferror(f) == 0;
+    ok = (fclose(f) == 0) && ok;
+    return ok ? DOCK_OK : fail(ctx, DOCK_E_INVALID, "cannot write the tuning cache %s", path);
+}
+
+extern "C" dock_status dock_autotune(dock_ctx *ctx, const dock_object *ob, const dock_sweep *sw, int32_t n_rot,
+                                     const char *cache_path, dock_tuning *out)
+{
+    if (!ctx || !ob || !sw) return DOCK_E_INVALID;
+    DevLock dev_lock_(ctx);
+    if (ctx->dead) return fail(ctx, DOCK_E_CUDA_FATAL, "context is dead after a sticky CUDA error");
+    dock_status s;
+    if ((s = check_pair(ctx, ob, sw)) != DOCK_OK) return s;
+    if (n_rot < 16 || n_rot > 65536) return fail(ctx, DOCK_E_INVALID, "n_rot must be in [16, 65536]");
+    cudaSetDevice(ctx->device);
+    dock_search_desc d = {};
+    d.sampler = DOCK_SAMPLER_SF;
+    d.n = n_rot;
+    std::vector<double> q;
+    if ((s = gen_samples(ctx, &d, q)) != DOCK_OK) return s;
+    if ((s = upload_rots(ctx, sw, q.data(), n_rot, 0, n_rot, 0, 0)) != DOCK_OK) return s;
+    if ((s = ensure(ctx, (void **)&ctx->keys, &ctx->keys_n, (size_t)n_rot, sizeof(unsigned long long))) != DOCK_OK)
+        return s;
+    CK(ctx, cudaMemsetAsync(ctx->keys, 0, sizeof(unsigned long long) * n_rot, ctx->stream));
+    std::vector<ReqDev> rq(1, make_reqdev(ob, sw, ctx->keys));
+    if ((s = upload_reqs(ctx, rq)) != DOCK_OK) return s;
+    const Geo g = make_geo(sw);
+    const bool had = ctx->tune.count(g.N) != 0;
+    const dock_tuning prev = had ? ctx->tune[g.N] : dock_tuning{};
+    ctx->tune.erase(g.N);
+    dock_tuning best = tuning_for(ctx, g);
+    const int bmax = std::min(auto_batch(g), n_rot);
+    best.batch = std::min(best.batch, bmax);
+    double best_us = 0.0;
+    auto restore = [&] {
+        if (had) ctx->tune[g.N] = prev;
+        else ctx->tune.erase(g.N);
+    };
+    if ((s = time_shape(ctx, g, n_rot, best, &best_us)) != DOCK_OK) { restore(); return s; }
+    auto trial = [&](dock_tuning t) -> dock_status {
+        double us = 0.0;
+        dock_status st = time_shape(ctx, g, n_rot, t, &us);
+        if (st != DOCK_OK) return st;
+        if (us < best_us) {
+            best = t;
+            best_us = us;
+        }
+        return DOCK_OK;
+    };
+    {
+        dock_tuning t = best;
+        t.vox_blocks = best.vox_blocks == 4 ? 3 : 4;
+        if ((s = trial(t)) != DOCK_OK) { restore(); return s; }
+    }
+    for (int b : {8, 16, 32, 64, 128, 256}) {
+        if (b > bmax || b == best.batch) continue;
+        dock_tuning t = best;
+        t.batch = b;
+        if ((s = trial(t)) != DOCK_OK) { restore(); return s; }
+    }
+    for (int gr : {1, 2, 4, 8, 16}) {
+        if (gr > best.batch) continue;
+        dock_tuning t = best;
+        t.group = gr;
+        if ((s = trial(t)) != DOCK_OK) { restore(); return s; }
+    }
+    best.us_per_rotation = best_us;
+    ctx->tune[g.N] = best;
+    if (out) *out = best;
+    if (cache_path && (s = write_tuning(ctx, cache_path)) != DOCK_OK) return s;
+    return DOCK_OK;
+}
+
+static bool json_int(const char *p, const char *key, long *v)
+{
+    const char *k = strstr(p, key);
+    if (!k) return false;
+    k = strchr(k, ':');
+    return k && sscanf(k + 1, "%ld", v) == 1;
+}
+
+extern "C" dock_status dock_load_tuning(dock_ctx *ctx, const char *path, int32_t *n_loaded)
+{
+    if (!ctx || !path) return DOCK_E_INVALID;
+    DevLock dev_lock_(ctx);
+    if (n_loaded) *n_loaded = 0;
+    FILE *f = fopen(path, "r");
+    if (!f) return fail(ctx, DOCK_E_INVALID, "cannot read the tuning cache %s", path);
+    std::string txt;
+    char buf[4096];
+    size_t got;
+    while ((got = fread(buf, 1, sizeof(buf), f)) > 0) txt.append(buf, got);
+    fclose(f);
+    const std::string want = "\"device\": \"" + device_name(ctx->device) + "\"";
+    if (txt.find(want) == std::string::npos) return DOCK_OK;   // tuned on another device
+    int n = 0;
+    size_t pos = 0;
+    while ((pos = txt.find("{\"N\":", pos)) != std::string::npos) {
+        size_t end = txt.find('}', pos);
+        if (end == std::string::npos) break;
+        std::string e = txt.substr(pos, end - pos);
+        long N, b, gr, vb;
+        if (json_int(e.c_str(), "\"N\"", &N) && json_int(e.c_str(), "\"batch\"", &b) &&
+            json_int(e.c_str(), "\"group\"", &gr) && json_int(e.c_str(), "\"vox_blocks\"", &vb) && valid_N((int)N) &&
+            b >= 1 && b <= 256 && gr >= 0 && gr <= 256 && (vb == 3 || vb == 4)) {
+            dock_tuning t = {};
+            t.N = (int)N;
+            t.batch = (int)b;
+            t.group = (int)gr;
+            t.vox_blocks = (int)vb;
+            const char *u = strstr(e.c_str(), "\"us_per_rotation\"");
+            if (u && (u = strchr(u, ':'))) t.us_per_rotation = atof(u + 1);
+            ctx->tune[t.N] = t;
+            ++n;
+        }
+        pos = end;
+    }
+    if (n_loaded) *n_loaded = n;
+    return DOCK_OK;
+}
+
+extern "C" dock_status dock_get_tuning(dock_ctx *ctx, int32_t N, dock_tuning *out)
+{
+    if (!ctx || !out) return DOCK_E_INVALID;
+    if (!valid_N(N)) return fail(ctx, DOCK_E_INVALID, "lattice side %d not supported", N);
+    DevLock dev_lock_(ctx);
+    Geo g = {};
+    g.N = N;
+    g.M = 2 * N;
+    g.P = N + 2;
+    *out = tuning_for(ctx, g);
+    return DOCK_OK;
+}
+
 extern "C" dock_status dock_search_scores(dock_ctx *ctx, const dock_object *ob, const dock_sweep *sw, const double *quat,
                                           float *C)
 {
     if (!ctx || !ob || !sw || !quat || !C) return DOCK_E_INVALID;
+    DevLock dev_lock_(ctx);
     if (ctx->dead) return fail(ctx, DOCK_E_CUDA_FATAL, "context is dead after a sticky CUDA error");
     dock_status s;
     if ((s = check_pair(ctx, ob, sw)) != DOCK_OK) return s;
@@ -1140,7 +1439,9 @@ extern "C" dock_status dock_search_scores(dock_ctx *ctx, const dock_object *ob, 
     d.quats = quat;
     std::vector<double> q;
     if ((s = gen_samples(ctx, &d, q)) != DOCK_OK) return s;
-    if ((s = upload_rots(ctx, sw, q.data(), 1, 0, 1)) != DOCK_OK) return s;
+    if ((s = upload_rots(ctx, sw, q.data(), 1, 0, 1, 0, 0)) != DOCK_OK) return s;
+    std::vector<ReqDev> rq(1, make_reqdev(ob, sw, nullptr));
+    if ((s = upload_reqs(ctx, rq)) != DOCK_OK) return s;
     Geo g = make_geo(sw);
     float2 *tw, *qt;
     double2 *twd;
@@ -1153,9 +1454,9 @@ extern "C" dock_status dock_search_scores(dock_ctx *ctx, const dock_object *ob, 
     if ((s = dalloc(ctx, (void **)&Y, (ysz + zsz) * sizeof(float2), nullptr)) != DOCK_OK) return s;
     if ((s = dalloc(ctx, (void **)&dC, csz * sizeof(float), nullptr)) != DOCK_OK) { dfree(ctx, Y, (ysz + zsz) * sizeof(float2)); return s; }
     cudaError_t e = cudaMemsetAsync(ctx->errflag, 0, sizeof(int), ctx->stream);
-    if (e == cudaSuccess) e = launch_voxelise(g, ctx->rots, 1, sw->poses, (int)sw->P, ctx->bits, ctx->stream);
+    if (e == cudaSuccess) e = launch_voxelise(g, ctx->reqs, ctx->rots, 1, ctx->bits, ctx->stream);
     if (e == cudaSuccess) e = launch_fwd2d(g, 1, ctx->bits, Y, tw, qt, ctx->stream);
-    if (e == cudaSuccess) e = launch_zpass(g, 1, 1, Y, ob->spec, Y + ysz, tw, ctx->stream);
+    if (e == cudaSuccess) e = launch_zpass(g, 1, 1, Y, ctx->rots, ctx->reqs, Y + ysz, tw, ctx->stream);
     if (e == cudaSuccess) e = launch_plane_export(g, Y + ysz, tw, dC, ctx->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(C, dC, csz * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
@@ -1339,6 +1640,7 @@ extern "C" dock_status dock_refine_se3(dock_ctx *ctx, const dock_object *ob, con
                                        dock_refined *out)
 {
     if (!ctx || !ob || !sw || !in || !out) return DOCK_E_INVALID;
+    DevLock dev_lock_(ctx);
     if (ctx->dead) return fail(ctx, DOCK_E_CUDA_FATAL, "context is dead after a sticky CUDA error");
     if (K < 1 || K > 1024) return fail(ctx, DOCK_E_INVALID, "K must be in [1, 1024]");
     dock_status s;
@@ -1392,7 +1694,9 @@ extern "C" dock_status dock_objective_fwd(dock_ctx *ctx, const dock_object *ob, 
                                           const double *base_poses, const float *xi, int32_t B,
                                           const dock_params *params, float *J, float *grad, void *stream)
 {
+    if (!ctx) return DOCK_E_INVALID;
     if (!J) return fail(ctx, DOCK_E_INVALID, "J output is required");
+    DevLock dev_lock_(ctx);
     return objective_impl(ctx, ob, sw, base_poses, xi, B, params, J, grad, nullptr, stream);
 }
 
@@ -1400,7 +1704,9 @@ extern "C" dock_status dock_objective_bwd(dock_ctx *ctx, const dock_object *ob, 
                                           const double *base_poses, const float *xi, int32_t B,
                                           const dock_params *params, const float *gJ, float *gxi, void *stream)
 {
+    if (!ctx) return DOCK_E_INVALID;
     if (!gJ || !gxi) return fail(ctx, DOCK_E_INVALID, "gJ and gxi are required");
+    DevLock dev_lock_(ctx);
     return objective_impl(ctx, ob, sw, base_poses, xi, B, params, nullptr, gxi, gJ, stream);
 }
 
@@ -1409,6 +1715,7 @@ extern "C" dock_status dock_distances(dock_ctx *ctx, const dock_object *ob, cons
                                       float *witness, float *normal)
 {
     if (!ctx || !ob || !sw || !obj_poses || B < 1 || !d || !witness || !normal) return DOCK_E_INVALID;
+    DevLock dev_lock_(ctx);
     if (ctx->dead) return fail(ctx, DOCK_E_CUDA_FATAL, "context is dead after a sticky CUDA error");
     dock_status s;
     if ((s = check_pair(ctx, ob, sw)) != DOCK_OK) return s;
@@ -1442,84 +1749,635 @@ extern "C" dock_status dock_distances(dock_ctx *ctx, const dock_object *ob, cons
 }
 
 // ---------------------------------------------------------------------------
-// three-stage registration (Fig. 2)
+// registration engine: the three stages of Fig. 2 per request, with
+// continuous batching across requests
+//
+// Every registration is a job that moves through the stages of Fig. 2: a
+// global SF/Hopf search, a local GeoBall-SF search around the best global
+// orientation (Sec. IV-C.2), and the refinement of the top-K candidates
+// (Sec. V).  The engine runs in passes.  A pass picks one lattice side (round
+// robin over the sides that have work), takes an equal share of rotations
+// from every admitted job of that side, gathers their rotation records into
+// one array and runs the four search kernels once over all of them.  Each
+// record names its job's slot in the device request table, so every rotation
+// is correlated with its own object, trajectory and probe, and its peak key
+// lands in its own job's key array.  After a pass, jobs whose stage is
+// complete move on (top-1 -> local samples; or top-K -> refinement ->
+// result).  Queued jobs are admitted between passes while a slot is free and
+// the HBM budget allows, so requests that arrive while others run join the
+// next pass.  A job's arithmetic is the same whatever it is batched with.
 // ---------------------------------------------------------------------------
+constexpr int ENGINE_SLOTS = 64;   // jobs admitted at once
+constexpr int ENGINE_MIN_SHARE = 16;
+
+enum JobStage { JOB_QUEUED, JOB_GLOBAL, JOB_LOCAL, JOB_DONE };
+
+using Clock = std::chrono::steady_clock;
+
+struct Job {
+    uint64_t ticket = 0;
+    const dock_object *ob = nullptr;
+    const dock_sweep *sw = nullptr;
+    dock_register_desc d{};
+    dock_params p{};
+    int slot = -1;
+    JobStage stage = JOB_QUEUED;
+    int s0 = 0, s1 = 0, issued = 0;       // rotation range of the current stage, rotations sent
+    std::vector<double> q;                // host quaternions: global, then local
+    void *dev = nullptr;                  // one device block: quaternions, records, keys, candidates
+    size_t dev_bytes = 0;
+    double *dq = nullptr;
+    RotRec *drot = nullptr;
+    unsigned long long *dkey = nullptr;
+    dock_candidate *dcand = nullptr;
+    dock_result res{};
+    dock_status status = DOCK_PENDING;
+    std::string err;
+    bool cancel = false;
+    bool async = false;                   // submitted by dock_submit (kept until polled)
+    Clock::time_point t_submit;
+};
+using JobP = std::shared_ptr<Job>;
+
+struct Engine {
+    std::mutex mu;                        // queue, tickets, job status, flags
+    std::condition_variable cv_work, cv_done;
+    std::deque<JobP> queue;
+    std::vector<JobP> active;             // admitted jobs in admission order (engine thread only)
+    std::map<uint64_t, JobP> tickets;     // submitted jobs until collected by dock_poll
+    uint64_t next_ticket = 1;
+    ReqDev *reqtab = nullptr;             // device request table, ENGINE_SLOTS entries
+    std::vector<int> free_slots;
+    int last_N = 0;
+    int64_t passes = 0;                   // search passes run so far
+    cudaEvent_t pass_ev[2] = {nullptr, nullptr};   // completion of the last two passes
+    std::thread worker;
+    bool started = false, stop = false;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static dock_status check_job(dock_ctx *ctx, const Job &j)
+{
+    if (!j.ob || !j.sw) return fail(ctx, DOCK_E_INVALID, "request without object or sweep");
+    dock_status s;
+    if ((s = check_pair(ctx, j.ob, j.sw)) != DOCK_OK) return s;
+    const dock_register_desc &d = j.d;
+    if (d.n_global < 1 || d.n_local < 0 || d.top_k < 1 || d.top_k > 1024)
+        return fail(ctx, DOCK_E_INVALID, "bad registration descriptor");
+    if (d.sampler != DOCK_SAMPLER_SF && d.sampler != DOCK_SAMPLER_HOPF)
+        return fail(ctx, DOCK_E_INVALID, "global sampler must be SF or HOPF");
+    if (d.n_local > 0 && !(d.theta > 0.0 && d.theta < M_PI / 2)) return fail(ctx, DOCK_E_INVALID, "theta out of range");
+    return DOCK_OK;
+}
+
+static dock_status engine_init(dock_ctx *ctx)
+{
+    if (ctx->eng) return DOCK_OK;
+    Engine *E = new (std::nothrow) Engine();
+    if (!E) return fail(ctx, DOCK_E_NOMEM, "out of host memory");
+    dock_status s = dalloc(ctx, (void **)&E->reqtab, sizeof(ReqDev) * ENGINE_SLOTS, nullptr);
+    if (s != DOCK_OK) {
+        delete E;
+        return s;
+    }
+    for (auto &ev : E->pass_ev) {
+        cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            for (auto &x : E->pass_ev) if (x) cudaEventDestroy(x);
+            dfree(ctx, E->reqtab, sizeof(ReqDev) * ENGINE_SLOTS);
+            delete E;
+            return cuda_fail(ctx, e, "cudaEventCreate");
+        }
+    }
+    for (int i = ENGINE_SLOTS - 1; i >= 0; --i) E->free_slots.push_back(i);
+    ctx->eng = E;
+    return DOCK_OK;
+}
+
+static size_t job_bytes(const Job &j)
+{
+    size_t n = (size_t)j.d.n_global + j.d.n_local;
+    return align256(n * 4 * sizeof(double)) + align256(n * sizeof(RotRec)) + align256(n * sizeof(unsigned long long)) +
+           align256((size_t)j.d.top_k * sizeof(dock_candidate));
+}
+
+// Device bytes the Y/Z scratch must grow by for a pass at lattice side N.
+static size_t yz_growth(dock_ctx *ctx, const dock_sweep *sw)
+{
+    Geo g = make_geo(sw);
+    size_t need = (size_t)tuning_for(ctx, g).batch * (g.N + g.M) * g.M * g.P;
+    return need > ctx->yz_bytes ? (need - ctx->yz_bytes) * sizeof(float2) : 0;
+}
+
+static void job_release(dock_ctx *ctx, Engine &E, Job &j)
+{
+    if (j.dev) {
+        dfree(ctx, j.dev, j.dev_bytes);
+        j.dev = nullptr;
+    }
+    if (j.slot >= 0) {
+        E.free_slots.push_back(j.slot);
+        j.slot = -1;
+    }
+}
+
+static void job_finish(dock_ctx *ctx, Engine &E, const JobP &j, dock_status st)
+{
+    job_release(ctx, E, *j);
+    if (st != DOCK_OK) j->err = ctx->err;
+    j->res.latency_ms = std::chrono::duration<double, std::milli>(Clock::now() - j->t_submit).count();
+    std::lock_guard<std::mutex> lk(E.mu);
+    j->stage = JOB_DONE;
+    j->status = st;
+    E.cv_done.notify_all();
+}
+
+enum { ADMIT_OK = 0, ADMIT_WAIT = 1 };
+
+// Allocate the job's device block, draw its global samples and set up their
+// rotation records; the job's slot in the request table points at its
+// object spectrum, trajectory and key array.
+static dock_status job_admit(dock_ctx *ctx, Engine &E, Job &j, int *wait)
+{
+    *wait = ADMIT_OK;
+    const size_t bytes = job_bytes(j);
+    if (ctx->budget && ctx->held + bytes + yz_growth(ctx, j.sw) > ctx->budget) {
+        if (!E.active.empty()) {
+            *wait = ADMIT_WAIT;
+            return DOCK_OK;
+        }
+        return fail(ctx, DOCK_E_TOO_LARGE, "request needs %zu bytes beyond the HBM budget", bytes);
+    }
+    dock_status s;
+    if ((s = dalloc(ctx, &j.dev, bytes, nullptr)) != DOCK_OK) return s;
+    j.dev_bytes = bytes;
+    const size_t n = (size_t)j.d.n_global + j.d.n_local;
+    unsigned char *b = (unsigned char *)j.dev;
+    j.dq = (double *)b;
+    b += align256(n * 4 * sizeof(double));
+    j.drot = (RotRec *)b;
+    b += align256(n * sizeof(RotRec));
+    j.dkey = (unsigned long long *)b;
+    b += align256(n * sizeof(unsigned long long));
+    j.dcand = (dock_candidate *)b;
+    j.slot = E.free_slots.back();
+    E.free_slots.pop_back();
+    dock_search_desc d = {};
+    d.sampler = j.d.sampler;
+    d.n = j.d.n_global;
+    d.top_k = 1;
+    std::vector<double> qg;
+    if ((s = gen_samples(ctx, &d, qg)) != DOCK_OK) return s;
+    j.q.assign(4 * n, 0.0);
+    memcpy(j.q.data(), qg.data(), sizeof(double) * qg.size());
+    CK(ctx, cudaMemcpyAsync(j.dq, j.q.data(), sizeof(double) * 4 * j.d.n_global, cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, launch_rot_setup(j.dq, j.d.n_global, 0, j.slot, j.sw->cs_dev, j.sw->h, j.sw->N, j.drot, ctx->stream));
+    CK(ctx, cudaMemsetAsync(j.dkey, 0, sizeof(unsigned long long) * n, ctx->stream));
+    ReqDev r = make_reqdev(j.ob, j.sw, j.dkey);
+    CK(ctx, cudaMemcpyAsync(E.reqtab + j.slot, &r, sizeof(ReqDev), cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));   // r and j.q are host staging of this call
+    j.stage = JOB_GLOBAL;
+    j.s0 = 0;
+    j.s1 = j.d.n_global;
+    j.issued = 0;
+    return DOCK_OK;
+}
+
+// The job's stage is complete: start the local search around the best
+// global orientation, or finish with top-K and the refinement.
+static dock_status job_advance(dock_ctx *ctx, Job &j, bool *done)
+{
+    *done = false;
+    dock_status s;
+    const dock_object *ob = j.ob;
+    const int ng = j.d.n_global, nl = j.d.n_local;
+    if (j.stage == JOB_GLOBAL && nl > 0) {
+        {
+            Prof pr(ctx, "topk");
+            CK(ctx, launch_topk(j.dkey, ng, 1, ob->N, ob->M, ob->h, ob->o_dev, j.dq, j.drot, j.dcand, ctx->stream));
+        }
+        dock_candidate best;
+        CK(ctx, cudaMemcpyAsync(&best, j.dcand, sizeof(best), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+        dock_search_desc dl = {};
+        dl.sampler = DOCK_SAMPLER_GEOBALL;
+        dl.n = nl;
+        memcpy(dl.q0, best.q, sizeof(dl.q0));
+        dl.theta = j.d.theta;
+        std::vector<double> ql;
+        if ((s = gen_samples(ctx, &dl, ql)) != DOCK_OK) return s;
+        memcpy(j.q.data() + 4 * (size_t)ng, ql.data(), sizeof(double) * ql.size());
+        CK(ctx, cudaMemcpyAsync(j.dq + 4 * (size_t)ng, j.q.data() + 4 * (size_t)ng, sizeof(double) * 4 * nl,
+                                cudaMemcpyHostToDevice, ctx->stream));
+        CK(ctx, launch_rot_setup(j.dq + 4 * (size_t)ng, nl, ng, j.slot, j.sw->cs_dev, j.sw->h, j.sw->N, j.drot + ng,
+                                 ctx->stream));
+        j.stage = JOB_LOCAL;
+        j.s0 = ng;
+        j.s1 = ng + nl;
+        j.issued = 0;
+        return DOCK_OK;
+    }
+    const int n = ng + nl, K = j.d.top_k;
+    {
+        Prof pr(ctx, "topk");
+        CK(ctx, launch_topk(j.dkey, n, K, ob->N, ob->M, ob->h, ob->o_dev, j.dq, j.drot, j.dcand, ctx->stream));
+    }
+    std::vector<dock_candidate> cands(K);
+    CK(ctx, cudaMemcpyAsync(cands.data(), j.dcand, sizeof(dock_candidate) * K, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    int Kv = 0;
+    while (Kv < K && cands[Kv].rot >= 0) ++Kv;
+    if (Kv == 0) return fail(ctx, DOCK_E_INVALID, "the search produced no candidate");
+    std::vector<dock_refined> ref(Kv);
+    if ((s = refine_impl(ctx, ob, j.sw, cands.data(), Kv, &j.p, ref.data())) != DOCK_OK) return s;
+    int bi = 0;
+    for (int c = 1; c < Kv; ++c) if (ref[c].J < ref[bi].J) bi = c;
+    memcpy(j.res.q, ref[bi].q, sizeof(j.res.q));
+    memcpy(j.res.t, ref[bi].t, sizeof(j.res.t));
+    j.res.J = ref[bi].J;
+    j.res.best_cand = bi;
+    j.res.n_evals = n;
+    j.res.best_search = cands[0];
+    *done = true;
+    return DOCK_OK;
+}
+
+// One engine step: admissions, then one search pass.  Returns false when
+// there was nothing to run.  Caller holds ctx->dev_mu.
+static bool engine_step(dock_ctx *ctx)
+{
+    Engine &E = *ctx->eng;
+    // cancelled jobs leave between passes
+    for (size_t i = 0; i < E.active.size();) {
+        if (E.active[i]->cancel) {
+            fail(ctx, DOCK_E_CANCELLED, "request cancelled");
+            job_finish(ctx, E, E.active[i], DOCK_E_CANCELLED);
+            E.active.erase(E.active.begin() + i);
+        } else {
+            ++i;
+        }
+    }
+    bool did = false;
+    for (;;) {
+        JobP j;
+        {
+            std::lock_guard<std::mutex> lk(E.mu);
+            if (E.queue.empty() || E.free_slots.empty()) break;
+            j = E.queue.front();
+            if (j->cancel) E.queue.pop_front();
+        }
+        if (j->cancel) {
+            fail(ctx, DOCK_E_CANCELLED, "request cancelled");
+            job_finish(ctx, E, j, DOCK_E_CANCELLED);
+            continue;
+        }
+        int wait = ADMIT_OK;
+        dock_status s = job_admit(ctx, E, *j, &wait);
+        if (s == DOCK_OK && wait == ADMIT_WAIT) break;
+        {
+            std::lock_guard<std::mutex> lk(E.mu);
+            E.queue.pop_front();
+        }
+        did = true;
+        if (s != DOCK_OK) {
+            job_finish(ctx, E, j, s);
+            if (ctx->dead) break;
+            continue;
+        }
+        E.active.push_back(j);
+    }
+    if (ctx->dead) {
+        for (auto &j : E.active) job_finish(ctx, E, j, DOCK_E_CUDA_FATAL);
+        E.active.clear();
+        return did;
+    }
+    // lattice side of this pass: round robin over the sides with work
+    int pick = 0;
+    for (auto &j : E.active) {
+        if (j->issued >= j->s1 - j->s0) continue;
+        int N = j->ob->N;
+        if (N > E.last_N && (pick == 0 || N < pick)) pick = N;
+    }
+    if (pick == 0)
+        for (auto &j : E.active)
+            if (j->issued < j->s1 - j->s0 && (pick == 0 || j->ob->N < pick)) pick = j->ob->N;
+    if (pick == 0) return did;
+    E.last_N = pick;
+    std::vector<Job *> cls;
+    for (auto &j : E.active)
+        if (j->ob->N == pick && j->issued < j->s1 - j->s0) cls.push_back(j.get());
+    const Geo g = make_geo(cls[0]->sw);
+    const int B = tuning_for(ctx, g).batch;
+    dock_status s;
+    if ((s = ensure(ctx, (void **)&ctx->phase, &ctx->phase_n, (size_t)B, sizeof(RotRec))) != DOCK_OK) {
+        for (auto &j : E.active)
+            if (j->ob->N == pick) job_finish(ctx, E, j, s);
+        E.active.erase(std::remove_if(E.active.begin(), E.active.end(),
+                                      [&](const JobP &j) { return j->stage == JOB_DONE; }),
+                       E.active.end());
+        return true;
+    }
+    // At most two passes in flight: without this bound the host would queue
+    // every pass of a long request at once, and requests arriving meanwhile
+    // would only start after all of them.
+    if (E.passes >= 2) {
+        cudaError_t e = cudaEventSynchronize(E.pass_ev[E.passes % 2]);
+        if (e != cudaSuccess) {
+            s = cuda_fail(ctx, e, "waiting for a search pass");
+            for (auto &j : E.active) job_finish(ctx, E, j, s);
+            E.active.clear();
+            return true;
+        }
+    }
+    // equal shares, then whatever is left in admission order
+    const int share = std::max(ENGINE_MIN_SHARE, B / (int)cls.size());
+    int taken = 0;
+    std::vector<Job *> in_pass;
+    cudaError_t ce = cudaSuccess;
+    for (int round = 0; round < 2 && taken < B && ce == cudaSuccess; ++round)
+        for (auto *jp : cls) {
+            int rem = jp->s1 - jp->s0 - jp->issued;
+            int take = std::min(rem, B - taken);
+            if (round == 0) take = std::min(take, share);
+            if (take <= 0) continue;
+            ce = cudaMemcpyAsync(ctx->phase + taken, jp->drot + jp->s0 + jp->issued, sizeof(RotRec) * take,
+                                 cudaMemcpyDeviceToDevice, ctx->stream);
+            if (ce != cudaSuccess) break;
+            jp->issued += take;
+            taken += take;
+            if (jp->res.first_pass < 0) jp->res.first_pass = E.passes;
+            jp->res.last_pass = E.passes;
+            if (std::find(in_pass.begin(), in_pass.end(), jp) == in_pass.end()) in_pass.push_back(jp);
+            if (taken == B) break;
+        }
+    if (ce != cudaSuccess) s = cuda_fail(ctx, ce, "gather of rotation records");
+    else s = run_pipeline_rots(ctx, g, E.reqtab, ctx->phase, 0, taken, B);
+    if (s == DOCK_OK) {
+        cudaError_t e = cudaEventRecord(E.pass_ev[E.passes % 2], ctx->stream);
+        if (e != cudaSuccess) s = cuda_fail(ctx, e, "recording a search pass");
+    }
+    ++E.passes;
+    for (auto *jp : in_pass) {
+        JobP j;
+        for (auto &x : E.active)
+            if (x.get() == jp) j = x;
+        if (s != DOCK_OK) {
+            job_finish(ctx, E, j, s);
+            continue;
+        }
+        if (jp->issued < jp->s1 - jp->s0) continue;
+        bool done = false;
+        dock_status sa = job_advance(ctx, *jp, &done);
+        if (sa != DOCK_OK) job_finish(ctx, E, j, sa);
+        else if (done) job_finish(ctx, E, j, DOCK_OK);
+    }
+    E.active.erase(std::remove_if(E.active.begin(), E.active.end(),
+                                  [](const JobP &j) { return j->stage == JOB_DONE; }),
+                   E.active.end());
+    return true;
+}
+
+static void engine_worker(dock_ctx *ctx)
+{
+    Engine &E = *ctx->eng;
+    cudaSetDevice(ctx->device);
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(E.mu);
+            E.cv_work.wait(lk, [&] { return E.stop || !E.queue.empty() || !E.active.empty(); });
+            if (E.stop) break;
+        }
+        // let waiting API calls in first (bounded: 100 ms)
+        for (int k = 0; k < 2000 && ctx->dev_want.load() > 0; ++k)
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+        bool did;
+        {
+            std::lock_guard<std::recursive_mutex> dl(ctx->dev_mu);
+            did = engine_step(ctx);
+        }
+        if (!did) {
+            // queued jobs wait for memory held by nothing that will free it soon
+            std::unique_lock<std::mutex> lk(E.mu);
+            E.cv_work.wait_for(lk, std::chrono::milliseconds(1));
+        }
+    }
+}
+
+static void engine_shutdown(dock_ctx *ctx)
+{
+    Engine *E = ctx->eng;
+    if (!E) return;
+    {
+        std::lock_guard<std::mutex> lk(E->mu);
+        E->stop = true;
+        E->cv_work.notify_all();
+    }
+    if (E->worker.joinable()) E->worker.join();
+    fail(ctx, DOCK_E_CANCELLED, "context destroyed");
+    for (auto &j : E->active) job_finish(ctx, *E, j, DOCK_E_CANCELLED);
+    std::deque<JobP> q;
+    {
+        std::lock_guard<std::mutex> lk(E->mu);
+        q.swap(E->queue);
+    }
+    for (auto &j : q) job_finish(ctx, *E, j, DOCK_E_CANCELLED);
+    dfree(ctx, E->reqtab, sizeof(ReqDev) * ENGINE_SLOTS);
+    for (auto &ev : E->pass_ev) if (ev) cudaEventDestroy(ev);
+    delete E;
+    ctx->eng = nullptr;
+}
+
+// Requests that use a handle being freed are cancelled first (caller holds
+// ctx->dev_mu, so no pass is in flight).
+static void engine_drop_handle(dock_ctx *ctx, const dock_object *ob, const dock_sweep *sw)
+{
+    Engine *E = ctx->eng;
+    if (!E) return;
+    auto uses = [&](const JobP &j) { return (ob && j->ob == ob) || (sw && j->sw == sw); };
+    std::vector<JobP> drop;
+    {
+        std::lock_guard<std::mutex> lk(E->mu);
+        for (auto it = E->queue.begin(); it != E->queue.end();) {
+            if (uses(*it)) {
+                drop.push_back(*it);
+                it = E->queue.erase(it);
+            } else {
+                ++it;
+            }
+        }
+    }
+    for (auto &j : E->active)
+        if (uses(j)) drop.push_back(j);
+    if (drop.empty()) return;
+    cudaStreamSynchronize(ctx->stream);
+    fail(ctx, DOCK_E_CANCELLED, "a handle of the request was freed");
+    for (auto &j : drop) job_finish(ctx, *E, j, DOCK_E_CANCELLED);
+    E->active.erase(std::remove_if(E->active.begin(), E->active.end(),
+                                   [](const JobP &j) { return j->stage == JOB_DONE; }),
+                    E->active.end());
+}
+
+// Run jobs to completion from the calling thread (or let the serving worker
+// run them when it is active) and return the first error, if any.
+static dock_status run_jobs(dock_ctx *ctx, std::vector<JobP> &js)
+{
+    for (auto &j : js)
+        if (dock_status s = check_job(ctx, *j)) return s;
+    dock_status s;
+    if (!ctx->eng_ready.load()) {
+        DevLock dl(ctx);
+        if ((s = engine_init(ctx)) != DOCK_OK) return s;
+        ctx->eng_ready.store(true);
+    }
+    Engine &E = *ctx->eng;
+    bool threaded;
+    {
+        std::lock_guard<std::mutex> lk(E.mu);
+        for (auto &j : js) {
+            j->t_submit = Clock::now();
+            E.queue.push_back(j);
+        }
+        threaded = E.started;
+        E.cv_work.notify_all();
+    }
+    auto all_done = [&] {
+        for (auto &j : js)
+            if (j->stage != JOB_DONE) return false;
+        return true;
+    };
+    if (threaded) {
+        std::unique_lock<std::mutex> lk(E.mu);
+        E.cv_done.wait(lk, all_done);
+    } else {
+        DevLock dl(ctx);
+        for (;;) {
+            {
+                std::lock_guard<std::mutex> lk(E.mu);
+                if (all_done()) break;
+            }
+            if (!engine_step(ctx)) {
+                // nothing could run: a queued job waits for memory no active job holds
+                std::lock_guard<std::mutex> lk(E.mu);
+                if (!all_done() && E.active.empty()) break;
+            }
+        }
+    }
+    for (auto &j : js)
+        if (j->status != DOCK_OK) {
+            if (j->status == DOCK_PENDING) return fail(ctx, DOCK_E_TOO_LARGE, "request could not be admitted");
+            fail(ctx, j->status, "%s", j->err.c_str());
+            return j->status;
+        }
+    return DOCK_OK;
+}
+
+static JobP make_job(const dock_object *ob, const dock_sweep *sw, const dock_register_desc *rd, const dock_params *params)
+{
+    JobP j = std::make_shared<Job>();
+    j->res.first_pass = -1;
+    j->res.last_pass = -1;
+    j->ob = ob;
+    j->sw = sw;
+    j->d = *rd;
+    if (params) j->p = *params;
+    else dock_params_default(&j->p);
+    return j;
+}
+
 extern "C" dock_status dock_register(dock_ctx *ctx, const dock_object *ob, const dock_sweep *sw,
                                      const dock_register_desc *rd, const dock_params *params, dock_result *out)
 {
     if (!ctx || !ob || !sw || !rd || !out) return DOCK_E_INVALID;
     if (ctx->dead) return fail(ctx, DOCK_E_CUDA_FATAL, "context is dead after a sticky CUDA error");
-    dock_status s;
-    if ((s = check_pair(ctx, ob, sw)) != DOCK_OK) return s;
-    if (rd->n_global < 1 || rd->n_local < 0 || rd->top_k < 1 || rd->top_k > 1024)
-        return fail(ctx, DOCK_E_INVALID, "bad registration descriptor");
-    if (rd->sampler != DOCK_SAMPLER_SF && rd->sampler != DOCK_SAMPLER_HOPF)
-        return fail(ctx, DOCK_E_INVALID, "global sampler must be SF or HOPF");
-    dock_params pd;
-    dock_params_default(&pd);
-    const dock_params *p = params ? params : &pd;
     cudaSetDevice(ctx->device);
-    const int ng = rd->n_global, nl = rd->n_local, n = ng + nl;
-    // stage 1: global search
-    dock_search_desc d = {};
-    d.sampler = rd->sampler;
-    d.n = ng;
-    d.top_k = 1;
-    std::vector<double> qg, q((size_t)n * 4);
-    if ((s = gen_samples(ctx, &d, qg)) != DOCK_OK) return s;
-    memcpy(q.data(), qg.data(), sizeof(double) * 4 * ng);
-    if ((s = upload_rots(ctx, sw, q.data(), n, 0, ng)) != DOCK_OK) return s;
-    if ((s = ensure(ctx, (void **)&ctx->keys, &ctx->keys_n, (size_t)n, sizeof(unsigned long long))) != DOCK_OK) return s;
-    CK(ctx, cudaMemsetAsync(ctx->keys, 0, sizeof(unsigned long long) * n, ctx->stream));
-    CK(ctx, cudaMemsetAsync(ctx->errflag, 0, sizeof(int), ctx->stream));
-    if ((s = run_pipeline(ctx, ob, sw, 0, ng, 0)) != DOCK_OK) return s;
-    int K = rd->top_k;
-    if ((s = ensure(ctx, (void **)&ctx->cands, &ctx->cands_n, (size_t)std::max(K, 1), sizeof(dock_candidate))) != DOCK_OK) return s;
-    dock_candidate best;
-    {
-        Prof pr(ctx, "topk");
-        CK(ctx, launch_topk(ctx->keys, ng, 1, ob->N, ob->M, ob->h, ob->o_dev, ctx->quats, ctx->rots, ctx->cands,
-                            ctx->stream));
+    std::vector<JobP> js(1, make_job(ob, sw, rd, params));
+    dock_status s = run_jobs(ctx, js);
+    if (s == DOCK_OK) *out = js[0]->res;
+    return s;
+}
+
+extern "C" dock_status dock_register_batch(dock_ctx *ctx, const dock_request *reqs, int32_t n, const dock_params *params,
+                                           dock_result *out)
+{
+    if (!ctx || !reqs || !out || n < 1) return DOCK_E_INVALID;
+    if (ctx->dead) return fail(ctx, DOCK_E_CUDA_FATAL, "context is dead after a sticky CUDA error");
+    cudaSetDevice(ctx->device);
+    std::vector<JobP> js;
+    for (int i = 0; i < n; ++i) js.push_back(make_job(reqs[i].obj, reqs[i].sweep, &reqs[i].desc, params));
+    dock_status s = run_jobs(ctx, js);
+    if (s == DOCK_OK)
+        for (int i = 0; i < n; ++i) out[i] = js[i]->res;
+    return s;
+}
+
+extern "C" dock_status dock_submit(dock_ctx *ctx, const dock_request *req, const dock_params *params, uint64_t *ticket)
+{
+    if (!ctx || !req || !ticket) return DOCK_E_INVALID;
+    if (ctx->dead) return fail(ctx, DOCK_E_CUDA_FATAL, "context is dead after a sticky CUDA error");
+    JobP j = make_job(req->obj, req->sweep, &req->desc, params);
+    dock_status s;
+    if ((s = check_job(ctx, *j)) != DOCK_OK) return s;
+    if (!ctx->eng_ready.load()) {
+        DevLock dl(ctx);
+        cudaSetDevice(ctx->device);
+        if ((s = engine_init(ctx)) != DOCK_OK) return s;
+        ctx->eng_ready.store(true);
     }
-    CK(ctx, cudaMemcpyAsync(&best, ctx->cands, sizeof(best), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(ctx, cudaStreamSynchronize(ctx->stream));
-    // stage 2: local GeoBall-SF search around the best orientation
-    if (nl > 0) {
-        dock_search_desc dl = {};
-        dl.sampler = DOCK_SAMPLER_GEOBALL;
-        dl.n = nl;
-        memcpy(dl.q0, best.q, sizeof(dl.q0));
-        dl.theta = rd->theta;
-        std::vector<double> ql;
-        if ((s = gen_samples(ctx, &dl, ql)) != DOCK_OK) return s;
-        memcpy(q.data() + 4 * (size_t)ng, ql.data(), sizeof(double) * 4 * nl);
-        if ((s = upload_rots(ctx, sw, q.data(), n, ng, nl)) != DOCK_OK) return s;
-        if ((s = run_pipeline(ctx, ob, sw, ng, n, 0)) != DOCK_OK) return s;
+    Engine &E = *ctx->eng;
+    std::lock_guard<std::mutex> lk(E.mu);
+    if (!E.started) {
+        try {
+            E.worker = std::thread(engine_worker, ctx);
+        } catch (...) {
+            return fail(ctx, DOCK_E_NOMEM, "cannot start the serving thread");
+        }
+        E.started = true;
     }
-    std::vector<dock_candidate> cands(K);
-    {
-        Prof pr(ctx, "topk");
-        CK(ctx, launch_topk(ctx->keys, n, K, ob->N, ob->M, ob->h, ob->o_dev, ctx->quats, ctx->rots, ctx->cands,
-                            ctx->stream));
+    j->async = true;
+    j->ticket = E.next_ticket++;
+    j->t_submit = Clock::now();
+    E.tickets[j->ticket] = j;
+    E.queue.push_back(j);
+    E.cv_work.notify_all();
+    *ticket = j->ticket;
+    return DOCK_OK;
+}
+
+extern "C" dock_status dock_poll(dock_ctx *ctx, uint64_t ticket, dock_result *out, int64_t timeout_us)
+{
+    if (!ctx || !out) return DOCK_E_INVALID;
+    if (!ctx->eng) return fail(ctx, DOCK_E_INVALID, "unknown ticket %llu", (unsigned long long)ticket);
+    Engine &E = *ctx->eng;
+    std::unique_lock<std::mutex> lk(E.mu);
+    auto it = E.tickets.find(ticket);
+    if (it == E.tickets.end()) return fail(ctx, DOCK_E_INVALID, "unknown ticket %llu", (unsigned long long)ticket);
+    JobP j = it->second;
+    auto done = [&] { return j->stage == JOB_DONE; };
+    if (!done()) {
+        if (timeout_us < 0) E.cv_done.wait(lk, done);
+        else if (timeout_us > 0) E.cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), done);
     }
-    int herr = 0;
-    CK(ctx, cudaMemcpyAsync(cands.data(), ctx->cands, sizeof(dock_candidate) * K, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(ctx, cudaMemcpyAsync(&herr, ctx->errflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(ctx, cudaStreamSynchronize(ctx->stream));
-    if (herr) return fail(ctx, herr, "device reported error %d during the search", herr);
-    int Kv = 0;
-    while (Kv < K && cands[Kv].rot >= 0) ++Kv;
-    if (Kv == 0) return fail(ctx, DOCK_E_INVALID, "the search produced no candidate");
-    // stage 3: refinement of the surviving candidates; lowest J wins
-    std::vector<dock_refined> ref(Kv);
-    if ((s = refine_impl(ctx, ob, sw, cands.data(), Kv, p, ref.data())) != DOCK_OK) return s;
-    int bi = 0;
-    for (int c = 1; c < Kv; ++c) if (ref[c].J < ref[bi].J) bi = c;
-    memcpy(out->q, ref[bi].q, sizeof(out->q));
-    memcpy(out->t, ref[bi].t, sizeof(out->t));
-    out->J = ref[bi].J;
-    out->best_cand = bi;
-    out->n_evals = n;
-    out->best_search = cands[0];
+    if (!done()) return DOCK_PENDING;
+    E.tickets.erase(it);
+    if (j->status != DOCK_OK) {
+        lk.unlock();
+        fail(ctx, j->status, "%s", j->err.c_str());
+        return j->status;
+    }
+    *out = j->res;
+    return DOCK_OK;
+}
+
+extern "C" dock_status dock_cancel(dock_ctx *ctx, uint64_t ticket)
+{
+    if (!ctx) return DOCK_E_INVALID;
+    if (!ctx->eng) return fail(ctx, DOCK_E_INVALID, "unknown ticket %llu", (unsigned long long)ticket);
+    Engine &E = *ctx->eng;
+    std::lock_guard<std::mutex> lk(E.mu);
+    auto it = E.tickets.find(ticket);
+    if (it == E.tickets.end()) return fail(ctx, DOCK_E_INVALID, "unknown ticket %llu", (unsigned long long)ticket);
+    it->second->cancel = true;
+    E.cv_work.notify_all();
     return DOCK_OK;
 }

@@ -17,8 +17,8 @@ struct RotRec {
     double o[3];   // swept-lattice origin o_s,R
     float Rf[9];
     float of[3];
-    int32_t rot;   // global sample index
-    int32_t pad;
+    int32_t rot;   // sample index within its request
+    int32_t req;   // request index in the launch's request table
 };
 
 // Per-pose data of a sweep: FP64 rotation/translation (exact recheck) and FP32.
@@ -41,22 +41,31 @@ struct Geo {
     double r, L;
 };
 
-struct Launcher;  // timing helper
+// Per-request data of a search launch: the rotations of one launch may come
+// from several registrations that share the lattice side N.
+struct ReqDev {
+    const PoseRec *poses;
+    int P;
+    double h, r, L;           // voxel size, probe radius and length (mm)
+    float inv_h, rv, lv;      // FP32 copies; rv, lv in voxels
+    const float2 *spec;       // tiled conj(F(O)) / M^3 of the request's object
+    unsigned long long *keys; // per-rotation peak keys, indexed by RotRec::rot
+};
 
 // Kernel launchers (k_search.cu)
-cudaError_t launch_rot_setup(const double *quats, int n, int rot0, const double *c_s, double h, int N, RotRec *out,
-                             cudaStream_t st);
-cudaError_t launch_voxelise(const Geo &g, const RotRec *rots, int B, const PoseRec *poses, int P, uint32_t *bits,
-                            cudaStream_t st);
+cudaError_t launch_rot_setup(const double *quats, int n, int rot0, int req, const double *c_s, double h, int N,
+                             RotRec *out, cudaStream_t st);
+cudaError_t launch_voxelise(const Geo &g, const ReqDev *reqs, const RotRec *rots, int B, uint32_t *bits,
+                            cudaStream_t st, int minb = 4);
 cudaError_t launch_fwd2d(const Geo &g, int B, const uint32_t *bits, float2 *Y, const float2 *tw, const float2 *q,
                          cudaStream_t st);
-cudaError_t launch_zpass(const Geo &g, int B, int group, const float2 *Y, const float2 *spec, float2 *Z,
-                         const float2 *tw, cudaStream_t st);
+cudaError_t launch_zpass(const Geo &g, int B, int group, const float2 *Y, const RotRec *rots, const ReqDev *reqs,
+                         float2 *Z, const float2 *tw, cudaStream_t st);
 cudaError_t launch_plane(const Geo &g, int B, const float2 *Z, const float2 *tw, const RotRec *rots,
-                         unsigned long long *keys, cudaStream_t st);
+                         const ReqDev *reqs, cudaStream_t st);
 cudaError_t launch_topk(const unsigned long long *keys, int n, int K, int N, int M, double h, const double *o_o,
                         const double *quats, const RotRec *rots_all, dock_candidate *out, cudaStream_t st);
-cudaError_t launch_vox_export(const Geo &g, const RotRec *rots, int B, const PoseRec *poses, int P, uint8_t *bits,
+cudaError_t launch_vox_export(const Geo &g, const ReqDev *reqs, const RotRec *rots, int B, uint8_t *bits,
                               cudaStream_t st);
 cudaError_t launch_plane_export(const Geo &g, const float2 *Z, const float2 *tw, float *C, cudaStream_t st);
 

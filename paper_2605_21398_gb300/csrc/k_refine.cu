@@ -90,6 +90,19 @@ __device__ __forceinline__ void sdf_normal(const float *x, float r, float L, flo
 
 __device__ __forceinline__ float dot3f(const float *a, const float *b) { return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2])); }
 
+// f_p is differentiable at x: everywhere outside the probe; inside, away
+// (by more than 1e-3 mm) from the medial surfaces where two branches meet
+// and from the axis.
+__device__ __forceinline__ bool sdf_smooth_at(const float *x, float r, float L)
+{
+    float rho = sqrtf(fmaf(x[0], x[0], x[1] * x[1]));
+    float dr = rho - r, zlo = -x[2], zhi = x[2] - L;
+    float dz = fmaxf(zlo, zhi);
+    if (dr > 0.f || dz > 0.f) return true;
+    const float band = 1e-3f;
+    return fabsf(dr - dz) > band && fabsf(zlo - zhi) > band && rho > band;
+}
+
 // min over v in [0, 1-u] of f(v0 + u e1 + v e2): bisection on df/dv
 __device__ float inner_min(const float *v0, const float *e1, const float *e2, float u, float r, float L, int iters,
                            float *v_out)
@@ -141,6 +154,65 @@ __device__ float tri_min(const float *v0, const float *v1, const float *v2, floa
 {
     float e1[3] = {v1[0] - v0[0], v1[1] - v0[1], v1[2] - v0[2]};
     float e2[3] = {v2[0] - v0[0], v2[1] - v0[1], v2[2] - v0[2]};
+    {
+        // A vertex where f is differentiable and no edge from it descends is
+        // the minimum (f convex: f(y) >= f(x) + g.(y - x) >= f(x) on the
+        // triangle).  This settles most triangles, which are small against the
+        // probe, with three evaluations.
+        const float *vv[3] = {v0, v1, v2};
+        float fv[3];
+        for (int m = 0; m < 3; ++m) fv[m] = sdf_cyl(vv[m][0], vv[m][1], vv[m][2], r, L, nullptr);
+        int ms = 0;
+        if (fv[1] < fv[ms]) ms = 1;
+        if (fv[2] < fv[ms]) ms = 2;
+        float g[3];
+        if (sdf_smooth_at(vv[ms], r, L)) {
+            sdf_cyl(vv[ms][0], vv[ms][1], vv[ms][2], r, L, g);
+            bool opt = true;
+            for (int m = 0; m < 3; ++m) {
+                if (m == ms) continue;
+                float e[3] = {vv[m][0] - vv[ms][0], vv[m][1] - vv[ms][1], vv[m][2] - vv[ms][2]};
+                if (dot3f(g, e) < 0.f) opt = false;
+            }
+            if (opt) {
+                *uo = ms == 1 ? 1.f : 0.f;
+                *vo = ms == 2 ? 1.f : 0.f;
+                return fv[ms];
+            }
+        }
+        // An edge point that minimises f along its edge, where f is
+        // differentiable and the direction to the opposite vertex does not
+        // descend, is the minimum over the triangle (same argument: the
+        // triangle lies in the cone of +-edge and that direction).  Typical for
+        // a line contact with the probe's side.
+        for (int k = 0; k < 3; ++k) {
+            const float *pa = vv[k], *pb = vv[(k + 1) % 3], *po = vv[(k + 2) % 3];
+            float e[3] = {pb[0] - pa[0], pb[1] - pa[1], pb[2] - pa[2]};
+            float ga[3], gb[3];
+            sdf_cyl(pa[0], pa[1], pa[2], r, L, ga);
+            if (dot3f(ga, e) >= 0.f) continue;       // f grows along the edge from pa
+            sdf_cyl(pb[0], pb[1], pb[2], r, L, gb);
+            if (dot3f(gb, e) <= 0.f) continue;       // f falls all the way to pb
+            float lo = 0.f, hi = 1.f;
+            for (int it = 0; it < 24; ++it) {
+                float mid = 0.5f * (lo + hi), xm[3], gm[3];
+                for (int c = 0; c < 3; ++c) xm[c] = fmaf(mid, e[c], pa[c]);
+                sdf_cyl(xm[0], xm[1], xm[2], r, L, gm);
+                if (dot3f(gm, e) < 0.f) lo = mid; else hi = mid;
+            }
+            float s = 0.5f * (lo + hi), x[3], gx[3];
+            for (int c = 0; c < 3; ++c) x[c] = fmaf(s, e[c], pa[c]);
+            if (!sdf_smooth_at(x, r, L)) continue;
+            float fx = sdf_cyl(x[0], x[1], x[2], r, L, gx);
+            float eo[3] = {po[0] - x[0], po[1] - x[1], po[2] - x[2]};
+            if (dot3f(gx, eo) < 0.f) continue;
+            // barycentric (u, v) of x = (1 - u - v) v0 + u v1 + v v2
+            if (k == 0) { *uo = s; *vo = 0.f; }
+            else if (k == 1) { *uo = 1.f - s; *vo = s; }
+            else { *uo = 0.f; *vo = 1.f - s; }
+            return fx;
+        }
+    }
     const float ig = 0.6180339887498949f;
     float a = 0.f, b = 1.f, vc, vd;
     float c = b - ig * (b - a), d = a + ig * (b - a);
@@ -234,6 +306,15 @@ __device__ __forceinline__ void local_vertices(const RefineDev &D, int t, const 
     }
 }
 
+// f_p at a bounding-sphere centre c (object frame) for the probe frame (A, b).
+__device__ __forceinline__ float node_sdf(const RefineDev &D, const float *A, const float *bvec, const float *c)
+{
+    float q[3] = {c[0] - bvec[0], c[1] - bvec[1], c[2] - bvec[2]};
+    float loc[3];
+    for (int k = 0; k < 3; ++k) loc[k] = fmaf(A[0 * 3 + k], q[0], fmaf(A[1 * 3 + k], q[1], A[2 * 3 + k] * q[2]));
+    return sdf_cyl(loc[0], loc[1], loc[2], D.r, D.L, nullptr);
+}
+
 // Distance query of one probe pose against the mesh for object pose (R, p).
 // Two BVH passes under the Eq. (21) test f_p(c) < r_node + eps: the first
 // takes the smallest vertex value as an upper bound UB of d*, the second
@@ -243,33 +324,36 @@ __device__ __forceinline__ void local_vertices(const RefineDev &D, int t, const 
 // -1; fills d*, the local witness and the local contact normal.
 __device__ int dist_query(const RefineDev &D, const float *A, const float *bvec, float *d_out, float *xw, float *nl)
 {
-    int stack[64];
+    // stack entries: node index and the lower bound f_p(centre) - radius of
+    // its subtree; children are pushed far first, so the nearer subtree is
+    // searched first and the bound prunes the rest early
+    int sn[64];
+    float sl[64];
     const float eps = D.tau_out;
     float UB = INFINITY;
     for (int pass = 0; pass < 2; ++pass) {
         int sp = 0;
-        stack[sp++] = 0;
         float best = INFINITY;
         int bt = -1;
         float bx[3] = {0.f, 0.f, 0.f};
+        {
+            const BvhNode &rt = D.nodes[0];
+            float fc = node_sdf(D, A, bvec, rt.c);
+            if (fc < rt.rad + eps) {           // Eq. (21)
+                sn[sp] = 0;
+                sl[sp++] = fc - rt.rad;
+            }
+        }
         while (sp > 0) {
-            int ni = stack[--sp];
-            BvhNode nd = D.nodes[ni];
-            float q[3] = {nd.c[0] - bvec[0], nd.c[1] - bvec[1], nd.c[2] - bvec[2]};
-            float loc[3];
-            for (int k = 0; k < 3; ++k) loc[k] = fmaf(A[0 * 3 + k], q[0], fmaf(A[1 * 3 + k], q[1], A[2 * 3 + k] * q[2]));
-            float fc = sdf_cyl(loc[0], loc[1], loc[2], D.r, D.L, nullptr);
-            if (!(fc < nd.rad + eps)) continue;             // Eq. (21)
-            if (fc - nd.rad > fminf(UB, best)) continue;    // cannot hold the minimum
+            --sp;
+            const int ni = sn[sp];
+            if (sl[sp] > fminf(UB, best)) continue;    // cannot hold the minimum
+            const BvhNode nd = D.nodes[ni];
             if (nd.left < 0) {
                 for (int k = 0; k < nd.count; ++k) {
                     int t = D.tri_order[nd.right + k];
                     const float *ts = D.tri_sphere + 4 * t;
-                    float qs[3] = {ts[0] - bvec[0], ts[1] - bvec[1], ts[2] - bvec[2]};
-                    float ls[3];
-                    for (int a = 0; a < 3; ++a)
-                        ls[a] = fmaf(A[0 * 3 + a], qs[0], fmaf(A[1 * 3 + a], qs[1], A[2 * 3 + a] * qs[2]));
-                    float ft = sdf_cyl(ls[0], ls[1], ls[2], D.r, D.L, nullptr);
+                    float ft = node_sdf(D, A, bvec, ts);
                     if (!(ft < ts[3] + eps)) continue;      // Eq. (21) for the triangle's sphere
                     if (ft - ts[3] > fminf(UB, best)) continue;
                     float lv[3][3];
@@ -289,8 +373,24 @@ __device__ int dist_query(const RefineDev &D, const float *A, const float *bvec,
                     }
                 }
             } else if (sp + 2 <= 64) {
-                stack[sp++] = nd.right;
-                stack[sp++] = nd.left;
+                const BvhNode &cl = D.nodes[nd.left];
+                const BvhNode &cr = D.nodes[nd.right];
+                float fl = node_sdf(D, A, bvec, cl.c), fr = node_sdf(D, A, bvec, cr.c);
+                bool okl = fl < cl.rad + eps, okr = fr < cr.rad + eps;   // Eq. (21)
+                float bl = fl - cl.rad, br = fr - cr.rad;
+                if (okl && okr) {
+                    bool lfirst = bl <= br;
+                    sn[sp] = lfirst ? nd.right : nd.left;
+                    sl[sp++] = lfirst ? br : bl;
+                    sn[sp] = lfirst ? nd.left : nd.right;
+                    sl[sp++] = lfirst ? bl : br;
+                } else if (okl) {
+                    sn[sp] = nd.left;
+                    sl[sp++] = bl;
+                } else if (okr) {
+                    sn[sp] = nd.right;
+                    sl[sp++] = br;
+                }
             }
         }
         if (pass == 1) {

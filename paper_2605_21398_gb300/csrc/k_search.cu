@@ -28,6 +28,16 @@ __device__ __forceinline__ double dm(double a, double b) { return __dmul_rn(a, b
 __device__ __forceinline__ double da(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double ds(double a, double b) { return __dsub_rn(a, b); }
 
+// asynchronous 8-byte global -> shared copies (completion: cp_async_wait_all)
+__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gmem_src)
+{
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
 __device__ void quat_to_mat_exact(const double *q, double *R)
 {
     double w = q[0], x = q[1], y = q[2], z = q[3];
@@ -43,7 +53,7 @@ __device__ void quat_to_mat_exact(const double *q, double *R)
 }
 
 // R = R(q), o = h round(R^T c_s / h) - (N/2) h   (Sec. IV-A: lattice origin)
-__global__ void k_rot_setup(const double *quats, int n, int rot0, const double *c_s, double h, int N, RotRec *out)
+__global__ void k_rot_setup(const double *quats, int n, int rot0, int req, const double *c_s, double h, int N, RotRec *out)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -58,15 +68,15 @@ __global__ void k_rot_setup(const double *quats, int n, int rot0, const double *
     for (int k = 0; k < 9; ++k) rr.Rf[k] = (float)rr.R[k];
     for (int a = 0; a < 3; ++a) rr.of[a] = (float)rr.o[a];
     rr.rot = rot0 + i;
-    rr.pad = 0;
+    rr.req = req;
     out[i] = rr;
 }
 
-cudaError_t launch_rot_setup(const double *quats, int n, int rot0, const double *c_s, double h, int N, RotRec *out,
-                             cudaStream_t st)
+cudaError_t launch_rot_setup(const double *quats, int n, int rot0, int req, const double *c_s, double h, int N,
+                             RotRec *out, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
-    k_rot_setup<<<(n + 127) / 128, 128, 0, st>>>(quats, n, rot0, c_s, h, N, out);
+    k_rot_setup<<<(n + 127) / 128, 128, 0, st>>>(quats, n, rot0, req, c_s, h, N, out);
     return cudaGetLastError();
 }
 
@@ -172,12 +182,15 @@ __device__ __forceinline__ void vox_row(const float *B, const float *c, int jy, 
         if (Cq > mr + 1e-2f) return;
         wide = N;
     }
-    if (fabsf(bx[2]) > 1e-6f) {
+    if (fabsf(bx[2]) >= 1e-3f) {
         float za = -l0[2] / bx[2], zb = (lv - l0[2]) / bx[2];
         lo = fmaxf(lo, fminf(za, zb));
         hi = fminf(hi, fmaxf(za, zb));
-    } else if (l0[2] < -0.01f || l0[2] > lv + 0.01f) {
-        return;
+    } else {
+        // row nearly parallel to the cap planes: only a row clearly outside them
+        // is dropped; otherwise the walk below finds the ends exactly
+        const float zA = l0[2], zB = fmaf((float)(N - 1), bx[2], l0[2]);
+        if (fmaxf(zA, zB) < -0.3f || fminf(zA, zB) > lv + 0.3f) return;
     }
     if (lo > hi + 2.f) return;
     lo = fmaxf(lo, -4.f);
@@ -202,12 +215,28 @@ __device__ __forceinline__ void vox_row(const float *B, const float *c, int jy, 
 }
 
 // Fill bits[jy * NW + w] for slab jz with the union of all probe cylinders.
-// A warp tests 32 poses at once against the slab (ballot); for each pose that
-// reaches the slab the pose frame is broadcast and the lanes take its rows.
+//
+// A warp takes 32 consecutive poses (one per lane; consecutive poses of a
+// trajectory are nearly identical) and walks the rows their cylinders reach
+// in lockstep.  On a row each lane estimates its pose's interval in FP32
+// (measured from the point of the row nearest the probe axis, so the estimate
+// carries no cancellation) and proposes the voxels at least CORE_M inside it
+// as its core; the core's two end voxels are classified exactly, and since the
+// cylinder is convex both inside means the whole core is inside.  If the cores
+// of all such lanes share a voxel, every lane's exact interval contains it, so
+// the union of the lanes' intervals is one interval: the warp sets its known
+// part [min core start, max core end] and extends it outward one voxel at a
+// time, asking every lane to classify the voxel, until no lane holds it.
+// Voxels already set in the slab are stepped over unclassified (they are in
+// the result whatever this warp decides, and the union being an interval
+// keeps the stop rule valid).  Lanes whose estimate is unusable (axis nearly
+// along the row, short intervals, failed core ends, or cores that do not
+// overlap) classify their row voxel by voxel with vox_row.
 template <int N>
 __device__ void voxelise_slab(const Geo &g, const RotRec &rr, const PoseRec *poses, int P, int jz, uint32_t *bits)
 {
     constexpr int NW = N / 32;
+    constexpr float CORE_M = 0.1f;
     const float rv = g.rv, lv = g.lv, rv2 = rv * rv;
     const float mz = 8e-4f, mr = 1.6e-3f * rv + 1e-3f;
     const double h = g.h, r2d = g.r * g.r, Ld = g.L;
@@ -215,79 +244,202 @@ __device__ void voxelise_slab(const Geo &g, const RotRec &rr, const PoseRec *pos
     const float *Rf = rr.Rf;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const float fz = (float)jz;
+    const volatile uint32_t *vb = bits;
     for (int base = warp * 32; base < P; base += nwarp * 32) {
-        int i = base + lane;
+        const int i = base + lane;
         bool hit = false;
         float B[9], c[3];
+        int y0 = N, y1 = -1;
         if (i < P) {
             const PoseRec &pr = poses[i];
             float cz = (fmaf(Rf[2], pr.tf[0], fmaf(Rf[5], pr.tf[1], Rf[8] * pr.tf[2])) - rr.of[2]) * ih;
             float Az = fmaf(Rf[2], pr.Rf[2], fmaf(Rf[5], pr.Rf[5], Rf[8] * pr.Rf[8]));
             float sz = rv * sqrtf(fmaxf(0.f, 1.f - Az * Az)) + 1.5f;
             float z0 = fminf(cz, cz + lv * Az) - sz, z1 = fmaxf(cz, cz + lv * Az) + sz;
-            hit = !(fz < z0 || fz > z1);
-            if (hit) pose_frame(rr, pr, ih, B, c);
-        }
-        unsigned mask = __ballot_sync(0xFFFFFFFFu, hit);
-        while (mask) {
-            int src = __ffs(mask) - 1;
-            mask &= mask - 1;
-            float Bs[9], cs[3];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) Bs[k] = __shfl_sync(0xFFFFFFFFu, B[k], src);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) cs[k] = __shfl_sync(0xFFFFFFFFu, c[k], src);
-            const PoseRec &pr = poses[base + src];
-            // rows of this slab the cylinder can reach
-            float Az = Bs[2 * 3 + 2], Ay = Bs[1 * 3 + 2];
-            float sz = rv * sqrtf(fmaxf(0.f, 1.f - Az * Az)) + 1.5f;
-            float u0, u1;
-            if (fabsf(Az) > 1e-6f) {
-                float ua = (fz - cs[2] - sz) / Az, ub = (fz - cs[2] + sz) / Az;
-                u0 = fmaxf(0.f, fminf(ua, ub));
-                u1 = fminf(lv, fmaxf(ua, ub));
-            } else {
-                u0 = 0.f;
-                u1 = lv;
+            if (!(fz < z0 || fz > z1)) {
+                pose_frame(rr, pr, ih, B, c);
+                float Ay = B[1 * 3 + 2];
+                float u0, u1;
+                if (fabsf(Az) > 1e-6f) {
+                    float ua = (fz - c[2] - sz) / Az, ub = (fz - c[2] + sz) / Az;
+                    u0 = fmaxf(0.f, fminf(ua, ub));
+                    u1 = fminf(lv, fmaxf(ua, ub));
+                } else {
+                    u0 = 0.f;
+                    u1 = lv;
+                }
+                if (u0 <= u1) {
+                    float sy = rv * sqrtf(fmaxf(0.f, 1.f - Ay * Ay)) + 1.5f;
+                    float ylo = c[1] + fminf(u0 * Ay, u1 * Ay) - sy, yhi = c[1] + fmaxf(u0 * Ay, u1 * Ay) + sy;
+                    y0 = max(0, (int)ceilf(ylo));
+                    y1 = min(N - 1, (int)floorf(yhi));
+                    hit = y0 <= y1;
+                }
             }
-            if (u0 > u1) continue;
-            float sy = rv * sqrtf(fmaxf(0.f, 1.f - Ay * Ay)) + 1.5f;
-            float ylo = cs[1] + fminf(u0 * Ay, u1 * Ay) - sy, yhi = cs[1] + fmaxf(u0 * Ay, u1 * Ay) + sy;
-            int jy0 = max(0, (int)ceilf(ylo)), jy1 = min(N - 1, (int)floorf(yhi));
-            for (int jy = jy0 + lane; jy <= jy1; jy += 32)
-                vox_row<N>(Bs, cs, jy, jz, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, bits + jy * NW);
+        }
+        if (!__any_sync(0xFFFFFFFFu, hit)) continue;
+        const int Y0 = __reduce_min_sync(0xFFFFFFFFu, hit ? y0 : N);
+        const int Y1 = __reduce_max_sync(0xFFFFFFFFu, hit ? y1 : -1);
+        const PoseRec &pr = poses[min(i, P - 1)];
+        const float bx[3] = {B[0], B[1], B[2]};
+        // per-pose constants of the row walk: the row direction in the probe frame
+        const float Aq = fmaf(bx[0], bx[0], bx[1] * bx[1]);
+        const bool radial_ok = Aq >= 0.05f;          // axis not within ~13 deg of the row direction
+        const float iAq = radial_ok ? 1.f / Aq : 0.f;
+        const bool cap_ok = fabsf(bx[2]) >= 1e-3f;     // cap crossings located to < 0.25 voxel
+        const float ibz = cap_ok ? 1.f / bx[2] : 0.f;
+        for (int jy = Y0; jy <= Y1; ++jy) {
+            const bool act = hit && jy >= y0 && jy <= y1;
+            int st = 0;                      // 0: nothing on this row, 1: verified core, 2: voxel by voxel
+            int ca = N, cb = -1;
+            float l0[3];
+            if (act) {
+                const float dyv = (float)jy - c[1], dzv = fz - c[2], dxv = -c[0];
+                for (int k = 0; k < 3; ++k) l0[k] = fmaf(B[0 * 3 + k], dxv, fmaf(B[1 * 3 + k], dyv, B[2 * 3 + k] * dzv));
+                if (!radial_ok) {
+                    st = 2;
+                } else {
+                    // nearest point of the row to the axis, then the radial chord around it
+                    const float js = -fmaf(l0[0], bx[0], l0[1] * bx[1]) * iAq;
+                    const float sa = fmaf(js, bx[0], l0[0]), sb = fmaf(js, bx[1], l0[1]);
+                    const float Cs = fmaf(sa, sa, sb * sb) - rv2;
+                    const float disc = -Aq * Cs;
+                    if (disc > 0.f) {
+                        const float hw = sqrtf(disc) * iAq;
+                        float lo = js - hw, hi = js + hw;
+                        bool empty = false, unsure = false;
+                        if (cap_ok) {
+                            const float za = -l0[2] * ibz, zb = (lv - l0[2]) * ibz;
+                            lo = fmaxf(lo, fminf(za, zb));
+                            hi = fminf(hi, fmaxf(za, zb));
+                        } else {
+                            // row nearly parallel to the cap planes: z moves < N/1000 voxels along it
+                            const float zA = l0[2], zB = fmaf((float)(N - 1), bx[2], l0[2]);
+                            const float zmin = fminf(zA, zB), zmax = fmaxf(zA, zB);
+                            if (zmax < -0.3f || zmin > lv + 0.3f) empty = true;
+                            else if (!(zmin >= 0.3f && zmax <= lv - 0.3f)) unsure = true;
+                        }
+                        // the estimate is within a voxel of the exact ends, so an
+                        // interval a voxel beyond the lattice holds no voxel
+                        if (lo > (float)N || hi < -1.f) empty = true;
+                        if (empty) {
+                            st = 0;
+                        } else if (unsure) {
+                            st = 2;
+                        } else if (lo <= hi + 2.f) {
+                            ca = max(0, (int)ceilf(fmaxf(lo + CORE_M, -1.f)));
+                            cb = min(N - 1, (int)floorf(fminf(hi - CORE_M, (float)N)));
+                            if (ca <= cb && classify(l0, bx, ca, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz) &&
+                                classify(l0, bx, cb, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz))
+                                st = 1;
+                            else
+                                st = 2;
+                        }
+                    } else if (disc > -1e-2f * (1.f + fabsf(Aq * rv2))) {
+                        st = 2;                   // tangent row: decide voxel by voxel
+                    }
+                }
+            }
+            const unsigned cm = __ballot_sync(0xFFFFFFFFu, st == 1);
+            if (cm) {
+                const int cl = __reduce_max_sync(0xFFFFFFFFu, st == 1 ? ca : -1);
+                const int cr = __reduce_min_sync(0xFFFFFFFFu, st == 1 ? cb : N);
+                if (cl <= cr) {
+                    int A = __reduce_min_sync(0xFFFFFFFFu, st == 1 ? ca : N);
+                    int Bm = __reduce_max_sync(0xFFFFFFFFu, st == 1 ? cb : -1);
+                    const volatile uint32_t *row = vb + jy * NW;
+                    int j = A - 1;
+                    for (; j >= 0; --j) {
+                        if ((row[j >> 5] >> (j & 31)) & 1u) continue;
+                        bool in = false;
+                        if (st == 1) in = classify(l0, bx, j, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz);
+                        if (!__any_sync(0xFFFFFFFFu, in)) break;
+                    }
+                    A = j + 1;
+                    j = Bm + 1;
+                    for (; j < N; ++j) {
+                        if ((row[j >> 5] >> (j & 31)) & 1u) continue;
+                        bool in = false;
+                        if (st == 1) in = classify(l0, bx, j, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz);
+                        if (!__any_sync(0xFFFFFFFFu, in)) break;
+                    }
+                    Bm = j - 1;
+                    if (lane < NW) {
+                        const int lo = max(A, 32 * lane) - 32 * lane, hi = min(Bm, 32 * lane + 31) - 32 * lane;
+                        if (lo <= hi) {
+                            const uint32_t m = (hi == 31 ? 0xFFFFFFFFu : ((1u << (hi + 1)) - 1u)) & ~((1u << lo) - 1u);
+                            if (m & ~row[lane]) atomicOr(&bits[jy * NW + lane], m);
+                        }
+                    }
+                } else if (st == 1) {
+                    st = 2;
+                }
+            }
+            if (st == 2) vox_row<N>(B, c, jy, jz, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, bits + jy * NW);
         }
     }
 }
 
+// Geometry of the request that rotation rr belongs to.
+__device__ __forceinline__ Geo req_geo(const Geo &g, const ReqDev &q)
+{
+    Geo r = g;
+    r.h = q.h;
+    r.inv_h = q.inv_h;
+    r.rv = q.rv;
+    r.lv = q.lv;
+    r.r = q.r;
+    r.L = q.L;
+    return r;
+}
+
 // S_b slab bits to global memory: bits[((b * N + jz) * N + jy) * NW + w].
-template <int N>
-__global__ void __launch_bounds__(256)
-k_voxelise(Geo g, const RotRec *rots, const PoseRec *poses, int P, uint32_t *bits_out)
+// MINB: resident blocks per SM the register allocation is built for (3: up
+// to 80 registers; 4: 64 registers, a few spills); the autotuner picks one.
+template <int N, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+k_voxelise(Geo g, const ReqDev *reqs, const RotRec *rots, uint32_t *bits_out)
 {
     constexpr int NW = N / 32;
     __shared__ uint32_t bits[N * NW];
-    const int jz = blockIdx.x, b = blockIdx.y;
+    // slabs from the lattice centre outward (the swept volume is centred, so
+    // the heaviest slabs of every rotation are scheduled first)
+    const int k = blockIdx.y, b = blockIdx.x;
+    const int jz = N / 2 + ((k & 1) ? -((k + 1) >> 1) : (k >> 1));
     for (int i = threadIdx.x; i < N * NW; i += blockDim.x) bits[i] = 0u;
     __syncthreads();
-    voxelise_slab<N>(g, rots[b], poses, P, jz, bits);
+    const RotRec &rr = rots[b];
+    const ReqDev &q = reqs[rr.req];
+    voxelise_slab<N>(req_geo(g, q), rr, q.poses, q.P, jz, bits);
     __syncthreads();
     uint32_t *o = bits_out + ((size_t)b * N + jz) * N * NW;
     for (int i = threadIdx.x; i < N * NW; i += blockDim.x) o[i] = bits[i];
 }
 
-cudaError_t launch_voxelise(const Geo &g, const RotRec *rots, int B, const PoseRec *poses, int P, uint32_t *bits,
-                            cudaStream_t st)
+template <int MINB>
+static cudaError_t launch_voxelise_t(const Geo &g, const ReqDev *reqs, const RotRec *rots, int B, uint32_t *bits,
+                                     cudaStream_t st)
 {
-    dim3 grid(g.N, B);
+    dim3 grid(B, g.N);
     switch (g.N) {
-    case 32: k_voxelise<32><<<grid, 256, 0, st>>>(g, rots, poses, P, bits); break;
-    case 64: k_voxelise<64><<<grid, 256, 0, st>>>(g, rots, poses, P, bits); break;
-    case 96: k_voxelise<96><<<grid, 256, 0, st>>>(g, rots, poses, P, bits); break;
-    case 128: k_voxelise<128><<<grid, 256, 0, st>>>(g, rots, poses, P, bits); break;
+    case 32: k_voxelise<32, MINB><<<grid, 256, 0, st>>>(g, reqs, rots, bits); break;
+    case 64: k_voxelise<64, MINB><<<grid, 256, 0, st>>>(g, reqs, rots, bits); break;
+    case 96: k_voxelise<96, MINB><<<grid, 256, 0, st>>>(g, reqs, rots, bits); break;
+    case 128: k_voxelise<128, MINB><<<grid, 256, 0, st>>>(g, reqs, rots, bits); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_voxelise(const Geo &g, const ReqDev *reqs, const RotRec *rots, int B, uint32_t *bits,
+                            cudaStream_t st, int minb)
+{
+    if (B < 1 || B > 65535) return cudaErrorInvalidValue;
+    switch (minb) {
+    case 3: return launch_voxelise_t<3>(g, reqs, rots, B, bits, st);
+    case 4: return launch_voxelise_t<4>(g, reqs, rots, B, bits, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -429,16 +581,19 @@ cudaError_t launch_fwd2d(const Geo &g, int B, const uint32_t *bits, float2 *Y, c
     }
 }
 
-// Bits of S_b to a byte array (test hook): one block per (slab, rotation).
+// Bits of S_b to a byte array (test hook): the production voxeliser, then
+// one byte per voxel.
 template <int N>
-__global__ void __launch_bounds__(256) k_vox_export(Geo g, const RotRec *rots, const PoseRec *poses, int P, uint8_t *out)
+__global__ void __launch_bounds__(256) k_vox_export(Geo g, const ReqDev *reqs, const RotRec *rots, uint8_t *out)
 {
     constexpr int NW = N / 32;
     __shared__ uint32_t bits[N * NW];
     const int jz = blockIdx.x, b = blockIdx.y;
     for (int i = threadIdx.x; i < N * NW; i += blockDim.x) bits[i] = 0u;
     __syncthreads();
-    voxelise_slab<N>(g, rots[b], poses, P, jz, bits);
+    const RotRec &rr = rots[b];
+    const ReqDev &q = reqs[rr.req];
+    voxelise_slab<N>(req_geo(g, q), rr, q.poses, q.P, jz, bits);
     __syncthreads();
     uint8_t *o = out + ((size_t)b * N + jz) * N * N;
     for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
@@ -447,15 +602,15 @@ __global__ void __launch_bounds__(256) k_vox_export(Geo g, const RotRec *rots, c
     }
 }
 
-cudaError_t launch_vox_export(const Geo &g, const RotRec *rots, int B, const PoseRec *poses, int P, uint8_t *bits,
+cudaError_t launch_vox_export(const Geo &g, const ReqDev *reqs, const RotRec *rots, int B, uint8_t *bits,
                               cudaStream_t st)
 {
     dim3 grid(g.N, B);
     switch (g.N) {
-    case 32: k_vox_export<32><<<grid, 256, 0, st>>>(g, rots, poses, P, bits); break;
-    case 64: k_vox_export<64><<<grid, 256, 0, st>>>(g, rots, poses, P, bits); break;
-    case 96: k_vox_export<96><<<grid, 256, 0, st>>>(g, rots, poses, P, bits); break;
-    case 128: k_vox_export<128><<<grid, 256, 0, st>>>(g, rots, poses, P, bits); break;
+    case 32: k_vox_export<32><<<grid, 256, 0, st>>>(g, reqs, rots, bits); break;
+    case 64: k_vox_export<64><<<grid, 256, 0, st>>>(g, reqs, rots, bits); break;
+    case 96: k_vox_export<96><<<grid, 256, 0, st>>>(g, reqs, rots, bits); break;
+    case 128: k_vox_export<128><<<grid, 256, 0, st>>>(g, reqs, rots, bits); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -468,37 +623,58 @@ cudaError_t launch_vox_export(const Geo &g, const RotRec *rots, int B, const Pos
 // ---------------------------------------------------------------------------
 template <int M>
 __global__ void __launch_bounds__(Plan<M>::T * 32)
-k_zpass(int P, int B, int group, const float2 *Y, const float2 *spec, float2 *Z, const float2 *tw_g)
+k_zpass(int P, int B, int group, const float2 *Y, const RotRec *rots, const ReqDev *reqs, float2 *Z, const float2 *tw_g)
 {
-    constexpr int N = M / 2, T = Plan<M>::T, E = Plan<M>::E, COLS = 32;
+    constexpr int N = M / 2, E = Plan<M>::E, COLS = 32;
     constexpr int R_LAST = Plan<M>::R(Plan<M>::S - 1);
     extern __shared__ __align__(16) unsigned char smem[];
     cf *xb = reinterpret_cast<cf *>(smem);   // [M][COLS]
-    cf *tw = xb + M * COLS;
+    cf *tw = xb + M * COLS;                  // [M]
+    cf *yt = tw + M;                         // two [N][COLS] tiles of Y (double buffer)
     for (int i = threadIdx.x; i < M; i += blockDim.x) { float2 w = tw_g[i]; tw[i] = cmake(w.x, w.y); }
     const int chunk = blockIdx.x;
     const int c = threadIdx.x % COLS, j = threadIdx.x / COLS;
     const size_t plane = (size_t)M * P;
-    const size_t f = (size_t)chunk * COLS + c;
-    // spectrum values in input-slot order of the inverse transform: slot s <-> kz = j + (M/E) s
-    cf sp[E];
-#pragma unroll
-    for (int s = 0; s < E; ++s) {
-        float2 t = spec[((size_t)chunk * M + (j + (M / E) * s)) * COLS + c];
-        sp[s] = cmake(t.x, t.y);
-    }
-    __syncthreads();
+    const size_t f0 = (size_t)chunk * COLS;
     const int b0 = blockIdx.y * group;
-    for (int bi = 0; bi < group; ++bi) {
-        int b = b0 + bi;
-        if (b >= B) break;
-        const float2 *Yb = Y + (size_t)b * N * plane;
+    const int nb = min(group, B - b0);
+    // spectrum values in input-slot order of the inverse transform: slot
+    // s <-> kz = j + (M/E) s; held in registers across the block's rotations
+    // and reloaded when the request (object) changes
+    cf sp[E];
+    int sp_req = -1;
+    // asynchronous copy of rotation b's non-zero z rows of this chunk (coalesced 256-byte rows)
+    auto prefetch = [&](int bi) {
+        const float2 *Yb = Y + (size_t)(b0 + bi) * N * plane + f0;
+        cf *dst = yt + (bi & 1) * N * COLS;
+        for (int e = threadIdx.x; e < N * COLS; e += blockDim.x) cp_async8(&dst[e], &Yb[(size_t)(e / COLS) * plane + e % COLS]);
+        cp_async_commit();
+    };
+    if (nb > 0) prefetch(0);
+    for (int bi = 0; bi < nb; ++bi) {
+        if (bi + 1 < nb) {
+            prefetch(bi + 1);
+            cp_async_wait_one();
+        } else {
+            cp_async_wait_all();
+        }
+        __syncthreads();
+        const int req = rots[b0 + bi].req;
+        if (req != sp_req) {
+            const float2 *spec = reqs[req].spec;
+#pragma unroll
+            for (int s = 0; s < E; ++s) {
+                float2 t = spec[((size_t)chunk * M + (j + (M / E) * s)) * COLS + c];
+                sp[s] = cmake(t.x, t.y);
+            }
+            sp_req = req;
+        }
+        const cf *src = yt + (bi & 1) * N * COLS;
         cf v[E];
 #pragma unroll
         for (int s = 0; s < E; ++s) {
             int z = in_index<M>(j, s);
-            if (z < N) { float2 t = Yb[(size_t)z * plane + f]; v[s] = cmake(t.x, t.y); }
-            else v[s] = cmake(0.f, 0.f);
+            v[s] = (z < N) ? src[z * COLS + c] : cmake(0.f, 0.f);
         }
         fft_column<M, false>(v, j, xb, c, COLS, tw);
         // forward output slot (bb, r) holds kz = j + (M/E)(bb + (E/R_LAST) r)
@@ -512,28 +688,28 @@ k_zpass(int P, int B, int group, const float2 *Y, const float2 *spec, float2 *Z,
             }
         __syncthreads();
         fft_column<M, true>(w, j, xb, c, COLS, tw);
-        float2 *Zb = Z + (size_t)b * M * plane;
+        float2 *Zb = Z + (size_t)(b0 + bi) * M * plane + f0 + c;
 #pragma unroll
         for (int s = 0; s < E; ++s) {
             int z = out_index<M>(j, s);
-            Zb[(size_t)z * plane + f] = make_float2(w[s].x, w[s].y);
+            Zb[(size_t)z * plane] = make_float2(w[s].x, w[s].y);
         }
         __syncthreads();
     }
 }
 
-cudaError_t launch_zpass(const Geo &g, int B, int group, const float2 *Y, const float2 *spec, float2 *Z,
-                         const float2 *tw, cudaStream_t st)
+cudaError_t launch_zpass(const Geo &g, int B, int group, const float2 *Y, const RotRec *rots, const ReqDev *reqs,
+                         float2 *Z, const float2 *tw, cudaStream_t st)
 {
     int chunks = g.M * g.P / 32;
     dim3 grid(chunks, (B + group - 1) / group);
     switch (g.M) {
 #define ZCASE(MM)                                                                                            \
     case MM: {                                                                                               \
-        size_t sm = sizeof(cf) * ((size_t)MM * 32 + MM);                                                     \
+        size_t sm = sizeof(cf) * ((size_t)MM * 32 + MM + (size_t)MM * 32);                                   \
         cudaError_t e = cudaFuncSetAttribute(k_zpass<MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
         if (e != cudaSuccess) return e;                                                                      \
-        k_zpass<MM><<<grid, Plan<MM>::T * 32, sm, st>>>(g.P, B, group, Y, spec, Z, tw);                      \
+        k_zpass<MM><<<grid, Plan<MM>::T * 32, sm, st>>>(g.P, B, group, Y, rots, reqs, Z, tw);                \
         break;                                                                                               \
     }
         ZCASE(64) ZCASE(128) ZCASE(192) ZCASE(256)
@@ -569,7 +745,7 @@ template <int M> struct PlaneCfg {
     static constexpr int S2 = (M / CL) * PP;               // peer rows (cluster)
     static constexpr int S3 = H * RPR;                     // phase-2 exchange (single CTA)
     static constexpr int STG = S1 > S2 ? (S1 > S3 ? S1 : S3) : (S2 > S3 ? S2 : S3);
-    static constexpr size_t SMEM = sizeof(cf) * ((size_t)M * PP + STG + M);
+    static constexpr size_t SMEM = sizeof(cf) * ((size_t)M * PP + STG + 2 * M);   // + twiddles + Nyquist column
 };
 
 template <int M, bool EXPORT>
@@ -581,28 +757,34 @@ __device__ __forceinline__ void plane_body(const float2 *Zp, const float2 *tw_g,
     const int P = H + 2;
     for (int i = threadIdx.x; i < M; i += blockDim.x) { float2 w = tw_g[i]; tw[i] = cmake(w.x, w.y); }
     __syncthreads();
-    // phase 1: inverse FFT along y of this CTA's packed columns -> pb[y][local column]
+    // phase 1: this CTA's packed columns, all ky, are copied asynchronously
+    // into pb (every load in flight at once), column 0 is packed with the
+    // Nyquist column (W0 + i W_{M/2}), and each column is inverse transformed
+    // along y in place: pb[ky][col] -> pb[y][col].
     {
+        cf *nyq = tw + M;
+        for (int e = threadIdx.x; e < M * PC; e += blockDim.x) {
+            int ky = e / PC, pl = e % PC;
+            cp_async8(&pb[ky * PP + pl], &Zp[ky * P + rank * PC + pl]);
+        }
+        if (rank == 0)
+            for (int ky = threadIdx.x; ky < M; ky += blockDim.x) cp_async8(&nyq[ky], &Zp[ky * P + H]);
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncthreads();
+        if (rank == 0)
+            for (int ky = threadIdx.x; ky < M; ky += blockDim.x) {
+                cf a = pb[ky * PP], u = nyq[ky];
+                pb[ky * PP] = cmake(a.x - u.y, a.y + u.x);   // + i * Z[ky][M/2]
+            }
+        __syncthreads();
         const int c = threadIdx.x % COLS, j = threadIdx.x / COLS;
         for (int p0 = 0; p0 < PC; p0 += COLS) {
             int pl = p0 + c;                   // local packed column
-            int pc = rank * PC + pl;           // global packed column
             bool act = pl < PC;
             cf v[E];
 #pragma unroll
-            for (int s = 0; s < E; ++s) {
-                int ky = in_index<M>(j, s);
-                cf val = cmake(0.f, 0.f);
-                if (act) {
-                    float2 t = Zp[ky * P + pc];
-                    val = cmake(t.x, t.y);
-                    if (pc == 0) {
-                        float2 u = Zp[ky * P + H];
-                        val = cmake(val.x - u.y, val.y + u.x);   // + i * Z[ky][M/2]
-                    }
-                }
-                v[s] = val;
-            }
+            for (int s = 0; s < E; ++s) v[s] = act ? pb[in_index<M>(j, s) * PP + pl] : cmake(0.f, 0.f);
             fft_column<M, true>(v, j, stg, c, COLS, tw);
             if (act) {
 #pragma unroll
@@ -707,7 +889,7 @@ __device__ __forceinline__ void plane_body(const float2 *Zp, const float2 *tw_g,
 
 template <int M>
 __global__ void __launch_bounds__(PlaneCfg<M>::NT)
-k_plane(int B, const float2 *Z, const float2 *tw_g, const RotRec *rots, unsigned long long *keys)
+k_plane(int B, const float2 *Z, const float2 *tw_g, const RotRec *rots, const ReqDev *reqs)
 {
     using C = PlaneCfg<M>;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -719,7 +901,7 @@ k_plane(int B, const float2 *Z, const float2 *tw_g, const RotRec *rots, unsigned
     if constexpr (C::CL > 1) rank = (int)cg::this_cluster().block_rank();
     const size_t plane = (size_t)M * (M / 2 + 2);
     const float2 *Zp = Z + ((size_t)b * M + zc) * plane;
-    plane_body<M, false>(Zp, tw_g, &keys[rots[b].rot], nullptr, zc, pb, stg, tw, rank);
+    plane_body<M, false>(Zp, tw_g, &reqs[rots[b].req].keys[rots[b].rot], nullptr, zc, pb, stg, tw, rank);
 }
 
 template <int M>
@@ -743,7 +925,7 @@ static size_t plane_smem() { return PlaneCfg<M>::SMEM; }
 
 template <int M, bool EXPORT>
 static cudaError_t launch_plane_t(int B, const float2 *Z, const float2 *tw, const RotRec *rots,
-                                  unsigned long long *keys, float *C, cudaStream_t st)
+                                  const ReqDev *reqs, float *C, cudaStream_t st)
 {
     constexpr int CL = PlaneCfg<M>::CL;
     size_t sm = plane_smem<M>();
@@ -767,20 +949,20 @@ static cudaError_t launch_plane_t(int B, const float2 *Z, const float2 *tw, cons
     } else {
         e = cudaFuncSetAttribute(k_plane<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        e = cudaLaunchKernelEx(&cfg, k_plane<M>, B, Z, tw, rots, keys);
+        e = cudaLaunchKernelEx(&cfg, k_plane<M>, B, Z, tw, rots, reqs);
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
 cudaError_t launch_plane(const Geo &g, int B, const float2 *Z, const float2 *tw, const RotRec *rots,
-                         unsigned long long *keys, cudaStream_t st)
+                         const ReqDev *reqs, cudaStream_t st)
 {
     switch (g.M) {
-    case 64: return launch_plane_t<64, false>(B, Z, tw, rots, keys, nullptr, st);
-    case 128: return launch_plane_t<128, false>(B, Z, tw, rots, keys, nullptr, st);
-    case 192: return launch_plane_t<192, false>(B, Z, tw, rots, keys, nullptr, st);
-    case 256: return launch_plane_t<256, false>(B, Z, tw, rots, keys, nullptr, st);
+    case 64: return launch_plane_t<64, false>(B, Z, tw, rots, reqs, nullptr, st);
+    case 128: return launch_plane_t<128, false>(B, Z, tw, rots, reqs, nullptr, st);
+    case 192: return launch_plane_t<192, false>(B, Z, tw, rots, reqs, nullptr, st);
+    case 256: return launch_plane_t<256, false>(B, Z, tw, rots, reqs, nullptr, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -68,7 +68,17 @@ class RegisterDesc(ctypes.Structure):
 
 class Result(ctypes.Structure):
     _fields_ = [("q", ctypes.c_double * 4), ("t", ctypes.c_double * 3), ("J", ctypes.c_double),
-                ("best_cand", ctypes.c_int32), ("n_evals", ctypes.c_int32), ("best_search", Candidate)]
+                ("best_cand", ctypes.c_int32), ("n_evals", ctypes.c_int32), ("best_search", Candidate),
+                ("latency_ms", ctypes.c_double), ("first_pass", ctypes.c_int64), ("last_pass", ctypes.c_int64)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("obj", ctypes.c_void_p), ("sweep", ctypes.c_void_p), ("desc", RegisterDesc)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("batch", ctypes.c_int32), ("group", ctypes.c_int32),
+                ("vox_blocks", ctypes.c_int32), ("us_per_rotation", ctypes.c_double)]
 
 
 class KernelStat(ctypes.Structure):
@@ -109,6 +119,14 @@ SIGNATURES = [
     ("dock_distances", _st, [_vp, _vp, _vp, _dp, ctypes.c_int32, ctypes.POINTER(Params), _fp, _fp, _fp]),
     ("dock_register", _st, [_vp, _vp, _vp, ctypes.POINTER(RegisterDesc), ctypes.POINTER(Params),
                             ctypes.POINTER(Result)]),
+    ("dock_register_batch", _st, [_vp, ctypes.POINTER(Request), ctypes.c_int32, ctypes.POINTER(Params),
+                                  ctypes.POINTER(Result)]),
+    ("dock_submit", _st, [_vp, ctypes.POINTER(Request), ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_uint64)]),
+    ("dock_poll", _st, [_vp, ctypes.c_uint64, ctypes.POINTER(Result), ctypes.c_int64]),
+    ("dock_cancel", _st, [_vp, ctypes.c_uint64]),
+    ("dock_autotune", _st, [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_char_p, ctypes.POINTER(Tuning)]),
+    ("dock_load_tuning", _st, [_vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32)]),
+    ("dock_get_tuning", _st, [_vp, ctypes.c_int32, ctypes.POINTER(Tuning)]),
     ("dock_set_profiling", _st, [_vp, ctypes.c_int]),
     ("dock_get_kernel_stats", ctypes.c_int32, [_vp, ctypes.POINTER(KernelStat), ctypes.c_int32]),
     ("dock_reset_kernel_stats", None, [_vp]),
@@ -264,8 +282,61 @@ class Context:
         r = Result()
         p = params or default_params()
         self.check(lib().dock_register(self.h, obj.h, sw.h, ctypes.byref(d), ctypes.byref(p), ctypes.byref(r)))
-        return dict(q=np.array(r.q[:]), t=np.array(r.t[:]), J=r.J, best_cand=r.best_cand, n_evals=r.n_evals,
-                    best_search=candidate_dict(r.best_search))
+        return result_dict(r)
+
+    @staticmethod
+    def _request(rq):
+        obj, sw, ng, nl, th, k = rq[:6]
+        smp = rq[6] if len(rq) > 6 else SAMPLER_SF
+        return Request(obj.h, sw.h, RegisterDesc(ng, nl, th, k, smp))
+
+    def submit(self, request, params=None):
+        """Queue one registration (obj, sweep, n_global, n_local, theta, top_k[, sampler]); returns a ticket."""
+        r = self._request(request)
+        p = params or default_params()
+        t = ctypes.c_uint64()
+        self.check(lib().dock_submit(self.h, ctypes.byref(r), ctypes.byref(p), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket, timeout_us=0):
+        """Result dict when done, None while pending; raises DockError on a failed or cancelled request."""
+        r = Result()
+        st = lib().dock_poll(self.h, ticket, ctypes.byref(r), int(timeout_us))
+        if st == 1:
+            return None
+        self.check(st)
+        return result_dict(r)
+
+    def cancel(self, ticket):
+        self.check(lib().dock_cancel(self.h, ticket))
+
+    def register_batch(self, requests, params=None):
+        """requests: list of (obj, sweep, n_global, n_local, theta, top_k[, sampler]); one result per request."""
+        n = len(requests)
+        arr = (Request * n)()
+        for i, rq in enumerate(requests):
+            arr[i] = self._request(rq)
+        out = (Result * n)()
+        p = params or default_params()
+        self.check(lib().dock_register_batch(self.h, arr, n, ctypes.byref(p), out))
+        return [result_dict(out[i]) for i in range(n)]
+
+    # -------------------------------------------------------------- tuning
+    def autotune(self, obj, sw, n_rot=256, cache_path=None):
+        t = Tuning()
+        self.check(lib().dock_autotune(self.h, obj.h, sw.h, n_rot,
+                                       cache_path.encode() if cache_path else None, ctypes.byref(t)))
+        return tuning_dict(t)
+
+    def load_tuning(self, cache_path):
+        n = ctypes.c_int32()
+        self.check(lib().dock_load_tuning(self.h, cache_path.encode(), ctypes.byref(n)))
+        return n.value
+
+    def get_tuning(self, N):
+        t = Tuning()
+        self.check(lib().dock_get_tuning(self.h, N, ctypes.byref(t)))
+        return tuning_dict(t)
 
     # -------------------------------------------------------------- profiling
     def set_profiling(self, on):
@@ -278,6 +349,16 @@ class Context:
 
     def reset_kernel_stats(self):
         lib().dock_reset_kernel_stats(self.h)
+
+
+def tuning_dict(t):
+    return dict(N=t.N, batch=t.batch, group=t.group, vox_blocks=t.vox_blocks, us_per_rotation=t.us_per_rotation)
+
+
+def result_dict(r):
+    return dict(q=np.array(r.q[:]), t=np.array(r.t[:]), J=r.J, best_cand=r.best_cand, n_evals=r.n_evals,
+                best_search=candidate_dict(r.best_search), latency_ms=r.latency_ms, first_pass=r.first_pass,
+                last_pass=r.last_pass)
 
 
 def candidate_dict(c):

@@ -346,7 +346,8 @@ class Trajectory:
 
 
 def contact_trajectory(obj: StarObject, n_poses, radius, length, seed,
-                       noncontact_frac=0.0, lift_range=(0.5, 2.0), sweep=4.5, axes_mode="ortho", wobble=2.0):
+                       noncontact_frac=0.0, lift_range=(0.5, 2.0), sweep=4.5, axes_mode="ortho", wobble=2.0,
+                       lines=1, pitch=1.5):
     """Three drop-to-contact segments with different tool-axis directions.
 
     axes_mode "ortho": the three columns of a random rotation, each tilted by
@@ -355,6 +356,9 @@ def contact_trajectory(obj: StarObject, n_poses, radius, length, seed,
     uses tool axis a_s (pointing from the tip to the shank) and moves the tool
     line across the object face seen from a_s: lateral offset
     sweep*(2 tau - 1) along e1 plus a wobble of up to `wobble` mm along e2.
+    With `lines` > 1 a segment is a zig-zag raster instead: `lines` parallel
+    passes `pitch` mm apart along e2, each across the part of [-sweep, sweep]
+    where the tool line meets the object (no wobble).
     With `noncontact_frac` > 0, contiguous runs of poses are lifted along the
     axis by U(lift_range) mm on a half-sine profile and labelled non-contact.
     """
@@ -397,10 +401,9 @@ def contact_trajectory(obj: StarObject, n_poses, radius, length, seed,
                 k = np.arange(per)
                 prof = amp * (0.25 + 0.75 * np.sin(np.pi * (k + 0.5) / per))
                 lifted[st:st + per] = np.maximum(lifted[st:st + per], prof[: len(lifted[st:st + per])])
+        path = _segment_path(dc, n, sweep, wob, ph, lines, pitch)
         for k in range(n):
-            tau = (k + 0.5) / n
-            u = sweep * (2 * tau - 1)
-            v = wob * math.sin(2 * np.pi * tau + ph)
+            u, v = path[k]
             sstar = dc.drop((u, v))
             if sstar is None:
                 raise RuntimeError("tool line missed the object; shrink the sweep")
@@ -410,6 +413,38 @@ def contact_trajectory(obj: StarObject, n_poses, radius, length, seed,
     poses = np.asarray(poses)
     geom = np.asarray(geom, dtype=np.uint8)
     return Trajectory(poses_obj=poses, contact_geom=geom, labels=geom.copy(), axes=axes)
+
+
+def _segment_path(dc, n, sweep, wob, ph, lines, pitch):
+    """(u, v) tool-line offsets of the n poses of one segment."""
+    if lines <= 1:
+        tau = (np.arange(n) + 0.5) / n
+        return np.stack([sweep * (2 * tau - 1), wob * np.sin(2 * np.pi * tau + ph)], axis=1)
+    counts = [n // lines + (1 if l < n % lines else 0) for l in range(lines)]
+    grid = np.linspace(-sweep, sweep, 129)
+    out = []
+    for l in range(lines):
+        v = pitch * (l - 0.5 * (lines - 1))
+        hit = np.array([dc.drop((u, v)) is not None for u in grid])
+        if not hit.any():
+            raise RuntimeError("raster line missed the object; reduce the pitch")
+        # the longest run of hits, shrunk by one grid step at each end
+        best, cur, start = (0, 0, 0), 0, 0
+        for i, hv in enumerate(hit):
+            if hv:
+                if cur == 0:
+                    start = i
+                cur += 1
+                if cur > best[0]:
+                    best = (cur, start, i)
+            else:
+                cur = 0
+        lo = grid[min(best[1] + 1, best[2])]
+        hi = grid[max(best[2] - 1, best[1])]
+        tau = (np.arange(counts[l]) + 0.5) / max(counts[l], 1)
+        u = lo + (hi - lo) * (tau if l % 2 == 0 else 1.0 - tau)
+        out.append(np.stack([u, np.full_like(u, v)], axis=1))
+    return np.concatenate(out, axis=0)
 
 
 def transform_poses(T_q, T_t, poses):
@@ -440,9 +475,11 @@ CONFIGS = {
     "tiny32": dict(degree=4, sigma2=0.04, n_theta=24, n_phi=48, N=32, h=0.5, radius=1.0, length=8.0,
                    poses=200, n_rot=512, top_k=8, noncontact=0.0, flip=0.0, noise_t=0.0, noise_r=0.0),
     "free64": dict(degree=8, sigma2=0.05, n_theta=72, n_phi=144, N=64, h=0.25, radius=0.8, length=12.0,
-                   poses=2000, n_rot=4096, top_k=32, noncontact=0.3, flip=0.0, noise_t=0.1, noise_r=0.5),
+                   poses=2000, n_rot=4096, top_k=32, noncontact=0.3, flip=0.0, noise_t=0.1, noise_r=0.5,
+                   lines=5, pitch=1.5),
     "large128": dict(degree=12, sigma2=0.05, n_theta=128, n_phi=256, N=128, h=0.15, radius=0.8, length=12.0,
-                     poses=5000, n_rot=32768, top_k=64, noncontact=0.0, flip=0.2, noise_t=0.02, noise_r=0.0),
+                     poses=5000, n_rot=32768, top_k=64, noncontact=0.0, flip=0.2, noise_t=0.02, noise_r=0.0,
+                     lines=5, pitch=1.5),
 }
 
 
@@ -470,9 +507,11 @@ def make_workload(name, replicate=0, **overrides):
     cfg.update(overrides)
     idx = list(CONFIGS).index(name) + 1 if name in CONFIGS else 9
     seed = 1000 * idx + replicate
-    obj = star_mesh(cfg["degree"], cfg["sigma2"], cfg["n_theta"], cfg["n_phi"], seed)
+    obj = star_mesh(cfg["degree"], cfg["sigma2"], cfg["n_theta"], cfg["n_phi"], seed, cap=cfg.get("cap", 0.3))
     traj = contact_trajectory(obj, cfg["poses"], cfg["radius"], cfg["length"], seed + 7,
-                              noncontact_frac=cfg["noncontact"])
+                              noncontact_frac=cfg["noncontact"], sweep=cfg.get("sweep", 4.5),
+                              axes_mode=cfg.get("axes_mode", "ortho"), wobble=cfg.get("wobble", 2.0),
+                              lines=cfg.get("lines", 1), pitch=cfg.get("pitch", 1.5))
     rng = np.random.default_rng(seed + 13)
     gt_q = random_quat(rng)
     gt_t = rng.uniform(-2.0, 2.0, size=3)

@@ -1,0 +1,61 @@
+"""Autotuner: the tuned launch shape is valid, does not change any result,
+is used by later searches, and round-trips through its JSON cache into a
+fresh context on the same device."""
+import json
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2605_21398_gb300 import build, dock
+    build.build()
+    c = dock.Context(0)
+    yield c
+    _KEEP.clear()
+    c.close()
+
+
+_KEEP = []
+
+
+def _pair(ctx, w):
+    ob = ctx.object_grid(w.obj.verts, w.obj.tris, w.h, w.N)
+    sw = ctx.sweep_grid(w.poses_world, w.radius, w.length, w.h, w.N, contact=w.labels)
+    _KEEP.append((ob, sw))
+    return ob, sw
+
+
+def test_tuned_shape_keeps_results_and_round_trips(ctx, workload, tmp_path):
+    from paper_2605_21398_gb300 import dock
+    w = workload("free64")
+    ob, sw = _pair(ctx, w)
+    n = 300
+    before = ctx.search_so3(ob, sw, n, 8, want_peaks=True)
+    default = ctx.get_tuning(w.N)
+    path = str(tmp_path / "tune.json")
+    t = ctx.autotune(ob, sw, n_rot=256, cache_path=path)
+    assert t["N"] == w.N and 1 <= t["batch"] <= 256 and t["vox_blocks"] in (3, 4) and t["group"] >= 0
+    assert t["us_per_rotation"] > 0
+    assert ctx.get_tuning(w.N) == t
+    after = ctx.search_so3(ob, sw, n, 8, want_peaks=True)
+    np.testing.assert_array_equal(before[1]["score"], after[1]["score"])
+    np.testing.assert_array_equal(before[1]["idx"], after[1]["idx"])
+    for a, b in zip(before[0], after[0]):
+        assert a["rot"] == b["rot"] and a["score"] == b["score"]
+    doc = json.load(open(path))
+    assert any(e["N"] == w.N and e["batch"] == t["batch"] for e in doc["entries"])
+    c2 = dock.Context(0)
+    try:
+        assert c2.get_tuning(w.N)["batch"] == default["batch"]
+        assert c2.load_tuning(path) >= 1
+        t2 = c2.get_tuning(w.N)
+        assert (t2["batch"], t2["group"], t2["vox_blocks"]) == (t["batch"], t["group"], t["vox_blocks"])
+    finally:
+        c2.close()
+    r = ctx.register(ob, sw, 200, 50, math.radians(5), 2)
+    assert r["n_evals"] == 250
