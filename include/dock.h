@@ -292,6 +292,33 @@ DOCK_API dock_status dock_register_batch(dock_ctx *ctx, const dock_request *reqs
                                          dock_result *out);
 
 /*
+ * Per-rotation peaks of the docking search for explicit rotations, computed
+ * without allocating: for callers that cannot call cudaMalloc (a host
+ * framework that owns every device allocation through its own pool, or code
+ * that runs where the memory layout has been planned and fixed).  The paper
+ * has no counterpart; this is a systems entry point around the same search
+ * kernels as dock_search_so3, and each peak equals that call's per-rotation
+ * peak for the same quaternion.
+ *
+ * quats: host, n x 4 unit quaternions (w, x, y, z); peaks: host, n entries
+ * out (score, canvas index; -inf and -1 for an empty sweep).  obj and sweep
+ * are handles made beforehand by dock_object_grid / dock_sweep_grid on ctx.
+ *
+ * Scratch: one fixed device array inside the library, about 14 MB, which
+ * every GPU that loads the library holds until the process exits.  Limits:
+ * lattice side N <= 64 and 1 <= n <= 4096; larger sizes return
+ * DOCK_E_INVALID with a message.  The call allocates no device memory (no
+ * cudaMalloc, cudaFree or allocating library routine).  The first call on a
+ * device looks up the scratch's device address (once per device), so make
+ * that first call before any stream capture.  All calls share the scratch,
+ * which keeps the last call's contents: calls that overlap on the GPU (from
+ * several threads or contexts on one device) race.  The call runs on ctx's
+ * stream and returns after the peaks are on the host.
+ */
+DOCK_API dock_status dock_search_peaks_noalloc(dock_ctx *ctx, const dock_object *obj, const dock_sweep *sweep,
+                                               const double *quats, int32_t n, dock_peak *peaks);
+
+/*
  * Serving (continuous batching).  dock_submit queues a registration and
  * returns at once with a ticket; a serving thread of the context (started by
  * the first submission) admits queued requests between search passes while

@@ -1238,6 +1238,45 @@ extern "C" dock_status dock_search_so3(dock_ctx *ctx, const dock_object *ob, con
     return search_impl(ctx, ob, sw, d, q, r0, r1, out, per_rot);
 }
 
+extern "C" dock_status dock_search_peaks_noalloc(dock_ctx *ctx, const dock_object *ob, const dock_sweep *sw,
+                                                 const double *quats, int32_t n, dock_peak *peaks)
+{
+    if (!ctx || !ob || !sw || !quats || !peaks) return DOCK_E_INVALID;
+    DevLock dev_lock_(ctx);
+    if (ctx->dead) return fail(ctx, DOCK_E_CUDA_FATAL, "context is dead after a sticky CUDA error");
+    dock_status s;
+    if ((s = check_pair(ctx, ob, sw)) != DOCK_OK) return s;
+    if (ob->N > NOALLOC_MAX_N)
+        return fail(ctx, DOCK_E_INVALID, "lattice side %d exceeds the scratch limit %d of dock_search_peaks_noalloc",
+                    ob->N, NOALLOC_MAX_N);
+    if (n < 1 || n > NOALLOC_MAX_ROT)
+        return fail(ctx, DOCK_E_INVALID, "rotation count %d outside [1, %d] of dock_search_peaks_noalloc", n,
+                    NOALLOC_MAX_ROT);
+    for (int i = 0; i < n; ++i) {
+        const double *a = quats + 4 * (size_t)i;
+        double nq = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);
+        if (!(fabs(nq - 1.0) <= 1e-6)) return fail(ctx, DOCK_E_INVALID, "quaternion %d is not unit", i);
+    }
+    // the twiddle tables of this canvas side were made with the object
+    auto it = ctx->tw.find(ob->M);
+    auto iq = ctx->qt.find(ob->M);
+    if (it == ctx->tw.end() || iq == ctx->qt.end()) return fail(ctx, DOCK_E_INVALID, "no twiddle tables for M = %d", ob->M);
+    cudaSetDevice(ctx->device);
+    NoallocJob j;
+    j.device = ctx->device;
+    j.g = make_geo(sw);
+    j.req = make_reqdev(ob, sw, nullptr);
+    j.c_s = sw->cs_dev;
+    j.quats = quats;
+    j.n = n;
+    j.tw = it->second;
+    j.qt = iq->second;
+    j.stream = ctx->stream;
+    j.peaks = peaks;
+    CK(ctx, noalloc_search_peaks(j));
+    return DOCK_OK;
+}
+
 // ---------------------------------------------------------------------------
 // autotuner
 // ---------------------------------------------------------------------------

@@ -119,4 +119,22 @@ cudaError_t launch_set_xi(int B, const float *xi, double *state, cudaStream_t st
 cudaError_t launch_finish_objective(int B, int nblk, const double *state, const double *acc_part, double lam, float *J,
                                     float *grad, const float *gJ, cudaStream_t st);
 
+// Search on library-owned scratch (k_noalloc.cu): limits of that scratch.
+constexpr int NOALLOC_MAX_N = 64;        // largest lattice side
+constexpr int NOALLOC_MAX_ROT = 4096;    // most rotations per call
+constexpr int NOALLOC_MAX_DEVICES = 64;  // device ordinals with a cached scratch address
+struct NoallocJob {
+    int device;             // current device
+    Geo g;
+    ReqDev req;             // keys are set by the callee
+    const double *c_s;      // device: mean tip of the sweep
+    const double *quats;    // host: n unit quaternions
+    int n;
+    const float2 *tw, *qt;  // device twiddle tables of the canvas side
+    cudaStream_t stream;
+    dock_peak *peaks;       // host: n peaks out
+};
+cudaError_t noalloc_search_peaks(const NoallocJob &j);
+size_t noalloc_scratch_bytes();
+
 }  // namespace dock

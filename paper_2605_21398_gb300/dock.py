@@ -111,6 +111,7 @@ SIGNATURES = [
     ("dock_search_so3", _st, [_vp, _vp, _vp, ctypes.POINTER(SearchDesc), ctypes.POINTER(Candidate),
                               ctypes.POINTER(Peak)]),
     ("dock_search_scores", _st, [_vp, _vp, _vp, _dp, _fp]),
+    ("dock_search_peaks_noalloc", _st, [_vp, _vp, _vp, _dp, ctypes.c_int32, ctypes.POINTER(Peak)]),
     ("dock_sample_so3", _st, [ctypes.POINTER(SearchDesc), _dp]),
     ("dock_refine_se3", _st, [_vp, _vp, _vp, ctypes.POINTER(Candidate), ctypes.c_int32, ctypes.POINTER(Params),
                               ctypes.POINTER(Refined)]),
@@ -230,6 +231,15 @@ class Context:
             return cands, np.array([(p.score, p.canvas_idx) for p in peaks],
                                    dtype=[("score", np.float32), ("idx", np.int64)])
         return cands
+
+    def search_peaks_noalloc(self, obj, sw, quats):
+        """Per-rotation peaks through the entry point that allocates no device
+        memory (library-owned scratch; N <= 64, at most 4096 rotations)."""
+        q = np.ascontiguousarray(quats, dtype=np.float64).reshape(-1, 4)
+        n = q.shape[0]
+        peaks = (Peak * max(n, 1))()
+        self.check(lib().dock_search_peaks_noalloc(self.h, obj.h, sw.h, q.ctypes.data_as(_dp), n, peaks))
+        return np.array([(p.score, p.canvas_idx) for p in peaks[:n]], dtype=[("score", np.float32), ("idx", np.int64)])
 
     def search_scores(self, obj, sw, quat):
         M = 2 * obj.N
