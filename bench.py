@@ -40,6 +40,90 @@ def _dist():
     return rank, ws
 
 
+SERVE_SIZES = (32, 64, 96, 128)
+
+
+def serving_mix(synth, n_req=24, seed=11):
+    """Uneven requests shaped like the batched workload: lattice side uniform
+    over {32, 64, 96, 128} at h = 16 mm / N, trajectories of 100-2000 poses,
+    probe radius 0.5-1.5 mm (length 12 mm), 1000-4000 global SF rotations plus
+    a quarter as many local ones, top-8 refined; 8 objects (two per side),
+    each with its own trajectory, shared by the requests."""
+    rng = np.random.default_rng(seed)
+    works = []
+    for k, N in enumerate(SERVE_SIZES * 2):
+        works.append(synth.make_workload("free64", replicate=100 + k, N=N, h=16.0 / N, n_theta=48, n_phi=96,
+                                         poses=int(rng.integers(100, 2001)), radius=float(rng.uniform(0.5, 1.5)),
+                                         noncontact=0.0, noise_t=0.02, noise_r=0.0, lines=3, pitch=1.5))
+    reqs = []
+    for _ in range(n_req):
+        wi = int(rng.integers(0, len(works)))
+        ng = int(rng.integers(1000, 4001))
+        reqs.append((wi, ng, ng // 4))
+    return works, reqs
+
+
+def serving_experiment(ctx, synth):
+    """Plain loop (dock_register one request at a time) against the serving
+    engine (dock_submit/dock_poll): a burst of all requests for throughput,
+    then Poisson arrivals at 80 % of the burst rate for latency."""
+    works, reqs = serving_mix(synth)
+    handles = [(ctx.object_grid(w.obj.verts, w.obj.tris, w.h, w.N),
+                ctx.sweep_grid(w.poses_world, w.radius, w.length, w.h, w.N, contact=w.labels)) for w in works]
+    req_t = [(handles[wi][0], handles[wi][1], ng, nl, THETA, 8) for wi, ng, nl in reqs]
+    try:
+        ctx.register(*req_t[0])                      # warm-up of every code path
+        t0 = time.perf_counter()
+        plain = [ctx.register(*r) for r in req_t]
+        t_plain = time.perf_counter() - t0
+
+        def serve(arrivals):
+            tickets, done = {}, {}
+            t0 = time.perf_counter()
+            nxt = 0
+            while len(done) < len(req_t):
+                now = time.perf_counter() - t0
+                while nxt < len(req_t) and arrivals[nxt] <= now:
+                    tickets[ctx.submit(req_t[nxt])] = nxt
+                    nxt += 1
+                for t, i in list(tickets.items()):
+                    r = ctx.poll(t, timeout_us=0)
+                    if r is not None:
+                        done[i] = r
+                        del tickets[t]
+                time.sleep(0.0005)
+            return [done[i] for i in range(len(req_t))], time.perf_counter() - t0
+
+        burst, t_burst = serve([0.0] * len(req_t))
+        rate = 0.8 * len(req_t) / t_burst
+        gaps = np.random.default_rng(5).exponential(1.0 / rate, size=len(req_t))
+        poisson, t_pois = serve(list(np.cumsum(gaps) - gaps[0]))
+        same = all(np.array_equal(a["q"], b["q"]) and np.array_equal(a["t"], b["t"]) and a["J"] == b["J"]
+                   for a, b in zip(plain, burst)) and \
+            all(np.array_equal(a["q"], b["q"]) and a["J"] == b["J"] for a, b in zip(plain, poisson))
+        lat = np.array([r["latency_ms"] for r in poisson])
+        evals = sum(ng + nl for _, ng, nl in reqs)
+        return {"requests": len(req_t), "evals": evals,
+                "mix": "N uniform over {32,64,96,128}, 100-2000 poses, r 0.5-1.5 mm, 1000-4000 + 25% rotations, top-8",
+                "plain_regs_per_s": round(len(req_t) / t_plain, 3),
+                "served_regs_per_s": round(len(req_t) / t_burst, 3),
+                "served_vs_plain": round(t_plain / t_burst, 3),
+                "poisson_rate_per_s": round(rate, 3), "poisson_regs_per_s": round(len(req_t) / t_pois, 3),
+                "p50_ms": round(float(np.percentile(lat, 50)), 2), "p99_ms": round(float(np.percentile(lat, 99)), 2),
+                "p999_ms": round(float(np.percentile(lat, 99.9)), 2), "results_equal_plain": bool(same)}
+    finally:
+        for ob, sw in handles:
+            ob.close()
+            sw.close()
+
+
+# DRAM bytes (read + write) per rotation of the HBM passes, from one ncu capture of an 8-rotation
+# launch on this workload (profiles/search_kernels_large128_8rot.md); traffic grows in proportion
+# to the rotations of a launch (the z-pass adds one spectrum read per launch).
+NCU_DRAM_BYTES_PER_ROT = {"plane": (545374976 + 3644928) / 8, "fwd2d": (4043776 + 214467584) / 8,
+                          "zpass": (340874240 - 68157440 + 489620992) / 8}
+
+
 def max_over_ranks(ms, ws, device):
     """The slowest rank's timed milliseconds (every rank gets the same value)."""
     if ws <= 1:
@@ -178,8 +262,9 @@ def run_reference(args):
 
 
 def run_ncu_case():
-    """One search of 8 SF rotations in one batch on the bench workload: every
-    search kernel launches once with 8 rotations (a few GB on the device)."""
+    """One search of 8 SF rotations in one batch on the bench workload (every
+    search kernel launches once with 8 rotations, a few GB on the device), then
+    a refinement of 8 candidates near the planted pose."""
     from paper_2605_21398_gb300 import build, dock, synth
     build.build()
     w = synth.make_workload(WORKLOAD)
@@ -187,7 +272,14 @@ def run_ncu_case():
     ob = ctx.object_grid(w.obj.verts, w.obj.tris, w.h, w.N)
     sw = ctx.sweep_grid(w.poses_world, w.radius, w.length, w.h, w.N, contact=w.labels)
     c = ctx.search_so3(ob, sw, 8, 4, batch=8)
-    print(json.dumps({"ncu_case": WORKLOAD, "rotations": 8, "best_score": c[0]["score"]}))
+    # refinement of 8 candidates near the planted pose (every refinement kernel launches)
+    rng = np.random.default_rng(3)
+    cands = []
+    for _ in range(8):
+        dq = synth.axis_angle_quat(np.radians(rng.normal(0.0, 1.0, 3)))
+        cands.append(dict(q=synth.quat_mul(dq, w.gt_q), t=w.gt_t + rng.normal(0.0, 0.05, 3)))
+    r = ctx.refine_se3(ob, sw, cands)
+    print(json.dumps({"ncu_case": WORKLOAD, "rotations": 8, "best_score": c[0]["score"], "refined": len(r)}))
     ob.close()
     sw.close()
     ctx.close()
@@ -204,6 +296,7 @@ def main():
     ap.add_argument("--n-local", type=int, default=N_LOCAL)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--ncu-case", action="store_true",
                     help="small fixed case for ncu captures: one search of 8 rotations (batch 8) of the bench workload")
     args = ap.parse_args()
@@ -285,8 +378,12 @@ def main():
         if dom == "zpass":
             total_bytes += M * M * P * 8 * launches   # spectrum read once per launch (block column)
         achieved = total_bytes / (tot_ms / 1000.0) / 1e9
+        rot_per_launch = rot_total / max(1, launches)
+        traffic = NCU_DRAM_BYTES_PER_ROT[dom] * rot_per_launch
+        if dom == "zpass":
+            traffic += M * M * P * 8
         roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                    "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_src,
+                    "frac": round(achieved / peak, 4), "traffic": int(traffic), "peak_source": peak_src,
                     "algorithmic_bytes_per_launch": int(total_bytes / max(1, launches)),
                     "dominant_overall": max(stats, key=lambda k: stats[k][1])}
     model_frac = value / ws * model_bytes_per_eval(w.N) / (peak * 1e9)
@@ -309,6 +406,13 @@ def main():
         e2e = {"value": evals_per_step * len(t_e) / sum(t_e), "unit": "evals/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": d2h}
 
+    serving = None
+    if rank == 0 and not args.no_serving:
+        try:
+            serving = serving_experiment(ctx, synth)
+        except Exception as exc:   # reported, not fatal to the throughput line
+            serving = {"error": "%s: %s" % (type(exc).__name__, exc)}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         n_cpu = 4
@@ -319,8 +423,7 @@ def main():
 
     a = np.asarray(w.obj.verts).min(0) * 0.5 + np.asarray(w.obj.verts).max(0) * 0.5
     res = results[-1]
-    from oracle import quat_to_mat  # host-side accuracy report only
-    Rr, Rg = quat_to_mat(res["q"]), quat_to_mat(w.gt_q)
+    Rr, Rg = synth.quat_to_mat(res["q"]), synth.quat_to_mat(w.gt_q)
     err_t = float(np.linalg.norm(Rr @ a + res["t"] - (Rg @ a + w.gt_t)))
     err_r = math.degrees(math.acos(max(-1.0, min(1.0, (np.trace(Rr @ Rg.T) - 1) / 2))))
     launches = int(sum(v[0] for v in stats.values()))
@@ -339,7 +442,7 @@ def main():
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "kernels": kernels,
             "ms_per_eval_search": round(sum(stats[k][1] for k in ("voxelise", "fwd2d", "zpass", "plane") if k in stats)
                                         / rot_total * 1000.0, 3),
-            "clocks": clk, "object_setup_ms": round(obj_setup_ms, 2),
+            "clocks": clk, "object_setup_ms": round(obj_setup_ms, 2), "serving": serving,
             "accuracy": {"trans_err_mm": round(err_t, 4), "rot_err_deg": round(err_r, 4), "J": res["J"]}}
     if rank == 0:
         print(json.dumps(line))

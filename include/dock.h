@@ -76,7 +76,8 @@ typedef struct dock_params {
     double b_t, b_r;     /* Eq. (20) box bounds: |u|_inf <= b_t mm, |w|_inf <= b_r rad (1.0, 5 deg) */
     double step_t, step_r; /* per-iteration trust region on the Gauss-Newton step (0.05 mm, 0.5 deg) */
     int32_t iters;       /* refinement iterations (20) */
-    int32_t tri_iters;   /* bisection steps per level of the per-triangle minimisation (FP32: 24) */
+    int32_t tri_iters;   /* inner bisection steps of the per-triangle search (outer golden steps: 1.5x);
+                            default 20: u and v to ~1e-6 of the triangle */
 } dock_params;
 
 typedef struct dock_probe {

@@ -72,6 +72,10 @@ struct dock_ctx {
     size_t ref_state_n = 0, ref_acc_n = 0, ref_prm_n = 0;
     void *ref_cands = nullptr;
     size_t ref_cands_n = 0;
+    RefineDev *ref_dev = nullptr;   // per-request refinement tables of a launch
+    size_t ref_dev_n = 0;
+    int32_t *ref_grp = nullptr;     // candidate -> request
+    size_t ref_grp_n = 0;
     // twiddle tables per canvas size
     std::map<int, float2 *> tw, qt;
     std::map<int, double2 *> twd;
@@ -405,7 +409,7 @@ void dock_params_default(dock_params *p)
     p->step_t = 0.05;
     p->step_r = 0.5 * M_PI / 180.0;
     p->iters = 20;
-    p->tri_iters = 24;
+    p->tri_iters = 20;
 }
 
 dock_status dock_create(dock_ctx **out, int device, size_t hbm_budget_bytes, void *cuda_stream)
@@ -461,6 +465,8 @@ void dock_destroy(dock_ctx *c)
     cudaFree(c->ref_acc);
     cudaFree(c->ref_prm);
     cudaFree(c->ref_cands);
+    cudaFree(c->ref_dev);
+    cudaFree(c->ref_grp);
     for (auto &kv : c->tw) cudaFree(kv.second);
     for (auto &kv : c->qt) cudaFree(kv.second);
     for (auto &kv : c->twd) cudaFree(kv.second);
@@ -1539,7 +1545,7 @@ static RefineDev make_refine_dev(const dock_object *ob, const dock_sweep *sw, co
     D.rr = (float)r;
     D.A = (float)(k / (r * r) - 2.0 / (r * r * r));
     D.B = (float)(k / r - 3.0 / (r * r));
-    D.tri_iters = p->tri_iters > 0 ? p->tri_iters : 24;
+    D.tri_iters = p->tri_iters > 0 ? p->tri_iters : 20;
     return D;
 }
 
@@ -1616,54 +1622,101 @@ static void pose_of_state(const double *st, double *R, double *p)
 
 // Runs `iters` projected Gauss-Newton iterations on the K states in
 // ctx->ref_state, then a final evaluation that records J at the final twist.
-static dock_status refine_loop(dock_ctx *ctx, const RefineDev &D, int K, int iters, const dock_params *p, cudaStream_t st)
+// Uploads the per-request tables of one refinement launch (staged copies:
+// the host vectors may be released once the copies are issued).
+static dock_status upload_refdev(dock_ctx *ctx, const std::vector<RefineDev> &Ds, const std::vector<int32_t> &grp,
+                                 cudaStream_t st)
 {
-    int nblk = (D.P + 127) / 128;
+    dock_status s;
+    if ((s = ensure(ctx, (void **)&ctx->ref_dev, &ctx->ref_dev_n, Ds.size(), sizeof(RefineDev))) != DOCK_OK) return s;
+    if ((s = ensure(ctx, (void **)&ctx->ref_grp, &ctx->ref_grp_n, std::max<size_t>(1, grp.size()), sizeof(int32_t))) !=
+        DOCK_OK)
+        return s;
+    CK(ctx, cudaMemcpyAsync(ctx->ref_dev, Ds.data(), sizeof(RefineDev) * Ds.size(), cudaMemcpyHostToDevice, st));
+    if (!grp.empty())
+        CK(ctx, cudaMemcpyAsync(ctx->ref_grp, grp.data(), sizeof(int32_t) * grp.size(), cudaMemcpyHostToDevice, st));
+    return DOCK_OK;
+}
+
+static dock_status refine_loop(dock_ctx *ctx, int K, int nblk, int iters, const dock_params *p, cudaStream_t st)
+{
     double prm[6] = {p->lambda, p->mu, p->step_t, p->step_r, p->b_t, p->b_r};
     CK(ctx, cudaMemcpyAsync(ctx->ref_prm, prm, sizeof(prm), cudaMemcpyHostToDevice, st));
     CandF *cf = (CandF *)ctx->ref_cands;
-    CK(ctx, launch_refine_solve(K, nblk, ctx->ref_state, ctx->ref_acc, ctx->ref_prm, 0, cf, st));
+    CK(ctx, launch_refine_solve(K, nblk * REF_WARPS, ctx->ref_state, ctx->ref_acc, ctx->ref_prm, 0, cf, st));
     for (int it = 0; it < iters; ++it) {
         {
             Prof pr(ctx, "refine_eval");
-            CK(ctx, launch_refine_eval(D, K, cf, ctx->ref_acc, true, nullptr, nullptr, nullptr, st));
+            CK(ctx, launch_refine_eval(ctx->ref_dev, ctx->ref_grp, K, nblk, cf, ctx->ref_acc, true, nullptr, nullptr,
+                                       nullptr, st));
         }
         Prof pr(ctx, "refine_solve");
-        CK(ctx, launch_refine_solve(K, nblk, ctx->ref_state, ctx->ref_acc, ctx->ref_prm, 1, cf, st));
+        CK(ctx, launch_refine_solve(K, nblk * REF_WARPS, ctx->ref_state, ctx->ref_acc, ctx->ref_prm, 1, cf, st));
     }
     {
         Prof pr(ctx, "refine_eval");
-        CK(ctx, launch_refine_eval(D, K, cf, ctx->ref_acc, false, nullptr, nullptr, nullptr, st));
+        CK(ctx, launch_refine_eval(ctx->ref_dev, ctx->ref_grp, K, nblk, cf, ctx->ref_acc, false, nullptr, nullptr,
+                                   nullptr, st));
     }
-    CK(ctx, launch_refine_solve(K, nblk, ctx->ref_state, ctx->ref_acc, ctx->ref_prm, 2, cf, st));
+    CK(ctx, launch_refine_solve(K, nblk * REF_WARPS, ctx->ref_state, ctx->ref_acc, ctx->ref_prm, 2, cf, st));
+    return DOCK_OK;
+}
+
+// One group of candidates of one request: candidates [c0, c0 + K).
+struct RefGroup {
+    const dock_object *ob;
+    const dock_sweep *sw;
+    int c0, K;
+};
+
+// Refines the candidates of several requests (same parameters) in shared
+// launches; each candidate's arithmetic is the same as refined alone.
+static dock_status refine_many(dock_ctx *ctx, const std::vector<RefGroup> &groups, const dock_candidate *in,
+                               const dock_params *p, dock_refined *out)
+{
+    int K = 0, nblk = 1;
+    for (auto &gr : groups) {
+        K += gr.K;
+        nblk = std::max(nblk, ((int)gr.sw->P + 127) / 128);
+    }
+    dock_status s;
+    if ((s = ref_buffers(ctx, K, nblk * REF_WARPS)) != DOCK_OK) return s;
+    std::vector<double> st((size_t)K * REF_ST);
+    std::vector<RefineDev> Ds;
+    std::vector<int32_t> grp(K);
+    for (size_t g = 0; g < groups.size(); ++g) {
+        const RefGroup &gr = groups[g];
+        Ds.push_back(make_refine_dev(gr.ob, gr.sw, p));
+        for (int c = gr.c0; c < gr.c0 + gr.K; ++c) {
+            state_from_pose(in[c].q, in[c].t, gr.ob->anchor, st.data() + (size_t)c * REF_ST);
+            grp[c] = (int32_t)g;
+        }
+    }
+    CK(ctx, cudaMemcpyAsync(ctx->ref_state, st.data(), sizeof(double) * st.size(), cudaMemcpyHostToDevice, ctx->stream));
+    if ((s = upload_refdev(ctx, Ds, grp, ctx->stream)) != DOCK_OK) return s;
+    if ((s = refine_loop(ctx, K, nblk, p->iters, p, ctx->stream)) != DOCK_OK) return s;
+    CK(ctx, cudaMemcpyAsync(st.data(), ctx->ref_state, sizeof(double) * st.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (auto &gr : groups)
+        for (int c = gr.c0; c < gr.c0 + gr.K; ++c) {
+            const double *x = st.data() + (size_t)c * REF_ST;
+            double R[9], t[3];
+            pose_of_state(x, R, t);
+            mat_to_quat(R, out[c].q);
+            memcpy(out[c].t, t, sizeof(t));
+            memcpy(out[c].xi, x + 15, sizeof(double) * 6);
+            out[c].J = x[21];
+            out[c].cand = c - gr.c0;
+            out[c].iters = p->iters;
+        }
     return DOCK_OK;
 }
 
 static dock_status refine_impl(dock_ctx *ctx, const dock_object *ob, const dock_sweep *sw, const dock_candidate *in,
                                int K, const dock_params *p, dock_refined *out)
 {
-    int nblk = ((int)sw->P + 127) / 128;
-    dock_status s;
-    if ((s = ref_buffers(ctx, K, nblk)) != DOCK_OK) return s;
-    std::vector<double> st((size_t)K * REF_ST);
-    for (int c = 0; c < K; ++c) state_from_pose(in[c].q, in[c].t, ob->anchor, st.data() + (size_t)c * REF_ST);
-    CK(ctx, cudaMemcpyAsync(ctx->ref_state, st.data(), sizeof(double) * st.size(), cudaMemcpyHostToDevice, ctx->stream));
-    RefineDev D = make_refine_dev(ob, sw, p);
-    if ((s = refine_loop(ctx, D, K, p->iters, p, ctx->stream)) != DOCK_OK) return s;
-    CK(ctx, cudaMemcpyAsync(st.data(), ctx->ref_state, sizeof(double) * st.size(), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(ctx, cudaStreamSynchronize(ctx->stream));
-    for (int c = 0; c < K; ++c) {
-        const double *x = st.data() + (size_t)c * REF_ST;
-        double R[9], t[3];
-        pose_of_state(x, R, t);
-        mat_to_quat(R, out[c].q);
-        memcpy(out[c].t, t, sizeof(t));
-        memcpy(out[c].xi, x + 15, sizeof(double) * 6);
-        out[c].J = x[21];
-        out[c].cand = c;
-        out[c].iters = p->iters;
-    }
-    return DOCK_OK;
+    std::vector<RefGroup> g(1, RefGroup{ob, sw, 0, K});
+    return refine_many(ctx, g, in, p, out);
 }
 
 static dock_status check_quat_pose(dock_ctx *ctx, const double *q)
@@ -1712,20 +1765,22 @@ static dock_status objective_impl(dock_ctx *ctx, const dock_object *ob, const do
     cudaSetDevice(ctx->device);
     cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
     int nblk = ((int)sw->P + 127) / 128;
-    if ((s = ref_buffers(ctx, B, nblk)) != DOCK_OK) return s;
+    if ((s = ref_buffers(ctx, B, nblk * REF_WARPS)) != DOCK_OK) return s;
     std::vector<double> stv((size_t)B * REF_ST);
     for (int b = 0; b < B; ++b) state_from_pose(base + 7 * b, base + 7 * b + 4, ob->anchor, stv.data() + (size_t)b * REF_ST);
     CK(ctx, cudaMemcpyAsync(ctx->ref_state, stv.data(), sizeof(double) * stv.size(), cudaMemcpyHostToDevice, st));
-    CK(ctx, cudaStreamSynchronize(st));   // the host staging vector is released on return
+    std::vector<RefineDev> Ds(1, make_refine_dev(ob, sw, p));
+    if ((s = upload_refdev(ctx, Ds, std::vector<int32_t>(), st)) != DOCK_OK) return s;
+    CK(ctx, cudaStreamSynchronize(st));   // the host staging vectors are released on return
     CK(ctx, launch_set_xi(B, xi, ctx->ref_state, st));
     CandF *cf = (CandF *)ctx->ref_cands;
-    CK(ctx, launch_refine_solve(B, nblk, ctx->ref_state, ctx->ref_acc, ctx->ref_prm, 0, cf, st));
-    RefineDev D = make_refine_dev(ob, sw, p);
+    CK(ctx, launch_refine_solve(B, nblk * REF_WARPS, ctx->ref_state, ctx->ref_acc, ctx->ref_prm, 0, cf, st));
     {
         Prof pr(ctx, grad ? "objective_adjoint" : "objective_fwd");
-        CK(ctx, launch_refine_eval(D, B, cf, ctx->ref_acc, grad != nullptr, nullptr, nullptr, nullptr, st));
+        CK(ctx, launch_refine_eval(ctx->ref_dev, nullptr, B, nblk, cf, ctx->ref_acc, grad != nullptr, nullptr, nullptr,
+                                   nullptr, st));
     }
-    CK(ctx, launch_finish_objective(B, nblk, ctx->ref_state, ctx->ref_acc, p->lambda, J, grad, gJ, st));
+    CK(ctx, launch_finish_objective(B, nblk * REF_WARPS, ctx->ref_state, ctx->ref_acc, p->lambda, J, grad, gJ, st));
     return DOCK_OK;
 }
 
@@ -1763,7 +1818,7 @@ extern "C" dock_status dock_distances(dock_ctx *ctx, const dock_object *ob, cons
     const dock_params *p = params ? params : &pd;
     cudaSetDevice(ctx->device);
     int nblk = ((int)sw->P + 127) / 128;
-    if ((s = ref_buffers(ctx, B, nblk)) != DOCK_OK) return s;
+    if ((s = ref_buffers(ctx, B, nblk * REF_WARPS)) != DOCK_OK) return s;
     std::vector<double> stv((size_t)B * REF_ST);
     for (int b = 0; b < B; ++b) {
         if ((s = check_quat_pose(ctx, obj_poses + 7 * b)) != DOCK_OK) return s;
@@ -1774,10 +1829,15 @@ extern "C" dock_status dock_distances(dock_ctx *ctx, const dock_object *ob, cons
     if ((s = dalloc(ctx, (void **)&buf, sizeof(float) * 7 * n, nullptr)) != DOCK_OK) return s;
     cudaStream_t st = ctx->stream;
     CandF *cf = (CandF *)ctx->ref_cands;
-    RefineDev D = make_refine_dev(ob, sw, p);
+    std::vector<RefineDev> Ds(1, make_refine_dev(ob, sw, p));
+    if ((s = upload_refdev(ctx, Ds, std::vector<int32_t>(), st)) != DOCK_OK) {
+        dfree(ctx, buf, sizeof(float) * 7 * n);
+        return s;
+    }
     cudaError_t e = cudaMemcpyAsync(ctx->ref_state, stv.data(), sizeof(double) * stv.size(), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = launch_refine_solve(B, nblk, ctx->ref_state, ctx->ref_acc, ctx->ref_prm, 0, cf, st);
-    if (e == cudaSuccess) e = launch_refine_eval(D, B, cf, ctx->ref_acc, false, buf, buf + n, buf + 4 * n, st);
+    if (e == cudaSuccess) e = launch_refine_solve(B, nblk * REF_WARPS, ctx->ref_state, ctx->ref_acc, ctx->ref_prm, 0, cf, st);
+    if (e == cudaSuccess)
+        e = launch_refine_eval(ctx->ref_dev, nullptr, B, nblk, cf, ctx->ref_acc, false, buf, buf + n, buf + 4 * n, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d, buf, sizeof(float) * n, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(witness, buf + n, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(normal, buf + 4 * n, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, st);
@@ -1823,6 +1883,7 @@ struct Job {
     JobStage stage = JOB_QUEUED;
     int s0 = 0, s1 = 0, issued = 0;       // rotation range of the current stage, rotations sent
     std::vector<double> q;                // host quaternions: global, then local
+    std::vector<dock_candidate> cands;    // top-K of the search stages
     void *dev = nullptr;                  // one device block: quaternions, records, keys, candidates
     size_t dev_bytes = 0;
     double *dq = nullptr;
@@ -1849,6 +1910,8 @@ struct Engine {
     std::vector<int> free_slots;
     int last_N = 0;
     int64_t passes = 0;                   // search passes run so far
+    std::vector<JobP> refine_wait;        // searches done, refinement pending
+    Clock::time_point refine_since;       // when the oldest of them finished its search
     cudaEvent_t pass_ev[2] = {nullptr, nullptr};   // completion of the last two passes
     std::thread worker;
     bool started = false, stop = false;
@@ -1984,10 +2047,12 @@ static dock_status job_admit(dock_ctx *ctx, Engine &E, Job &j, int *wait)
 }
 
 // The job's stage is complete: start the local search around the best
-// global orientation, or finish with top-K and the refinement.
-static dock_status job_advance(dock_ctx *ctx, Job &j, bool *done)
+// global orientation, or take its top-K candidates (*final set; the
+// refinement runs afterwards, batched with other jobs finishing in the same
+// pass).
+static dock_status job_advance(dock_ctx *ctx, Job &j, bool *final)
 {
-    *done = false;
+    *final = false;
     dock_status s;
     const dock_object *ob = j.ob;
     const int ng = j.d.n_global, nl = j.d.n_local;
@@ -2022,24 +2087,92 @@ static dock_status job_advance(dock_ctx *ctx, Job &j, bool *done)
         Prof pr(ctx, "topk");
         CK(ctx, launch_topk(j.dkey, n, K, ob->N, ob->M, ob->h, ob->o_dev, j.dq, j.drot, j.dcand, ctx->stream));
     }
-    std::vector<dock_candidate> cands(K);
-    CK(ctx, cudaMemcpyAsync(cands.data(), j.dcand, sizeof(dock_candidate) * K, cudaMemcpyDeviceToHost, ctx->stream));
+    j.cands.assign(K, dock_candidate());
+    CK(ctx, cudaMemcpyAsync(j.cands.data(), j.dcand, sizeof(dock_candidate) * K, cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
     int Kv = 0;
-    while (Kv < K && cands[Kv].rot >= 0) ++Kv;
+    while (Kv < K && j.cands[Kv].rot >= 0) ++Kv;
     if (Kv == 0) return fail(ctx, DOCK_E_INVALID, "the search produced no candidate");
-    std::vector<dock_refined> ref(Kv);
-    if ((s = refine_impl(ctx, ob, j.sw, cands.data(), Kv, &j.p, ref.data())) != DOCK_OK) return s;
-    int bi = 0;
-    for (int c = 1; c < Kv; ++c) if (ref[c].J < ref[bi].J) bi = c;
-    memcpy(j.res.q, ref[bi].q, sizeof(j.res.q));
-    memcpy(j.res.t, ref[bi].t, sizeof(j.res.t));
-    j.res.J = ref[bi].J;
-    j.res.best_cand = bi;
-    j.res.n_evals = n;
-    j.res.best_search = cands[0];
-    *done = true;
+    j.cands.resize(Kv);
+    *final = true;
     return DOCK_OK;
+}
+
+// Refines the top-K candidates of jobs whose searches are complete, in shared
+// launches per parameter set; the lowest J wins (ties: lower candidate index).
+static void jobs_refine(dock_ctx *ctx, Engine &E, std::vector<JobP> &done)
+{
+    std::vector<bool> used(done.size(), false);
+    for (size_t i = 0; i < done.size(); ++i) {
+        if (used[i]) continue;
+        std::vector<size_t> grp_jobs;
+        for (size_t k = i; k < done.size(); ++k)
+            if (!used[k] && memcmp(&done[k]->p, &done[i]->p, sizeof(dock_params)) == 0) {
+                used[k] = true;
+                grp_jobs.push_back(k);
+            }
+        std::vector<RefGroup> groups;
+        std::vector<dock_candidate> cands;
+        for (size_t k : grp_jobs) {
+            Job &j = *done[k];
+            groups.push_back(RefGroup{j.ob, j.sw, (int)cands.size(), (int)j.cands.size()});
+            cands.insert(cands.end(), j.cands.begin(), j.cands.end());
+        }
+        std::vector<dock_refined> ref(cands.size());
+        dock_status s = refine_many(ctx, groups, cands.data(), &done[i]->p, ref.data());
+        for (size_t g = 0; g < grp_jobs.size(); ++g) {
+            const JobP &jp = done[grp_jobs[g]];
+            if (s != DOCK_OK) {
+                job_finish(ctx, E, jp, s);
+                continue;
+            }
+            Job &j = *jp;
+            const dock_refined *r = ref.data() + groups[g].c0;
+            int bi = 0;
+            for (int c = 1; c < groups[g].K; ++c) if (r[c].J < r[bi].J) bi = c;
+            memcpy(j.res.q, r[bi].q, sizeof(j.res.q));
+            memcpy(j.res.t, r[bi].t, sizeof(j.res.t));
+            j.res.J = r[bi].J;
+            j.res.best_cand = bi;
+            j.res.n_evals = j.d.n_global + j.d.n_local;
+            j.res.best_search = j.cands[0];
+            job_finish(ctx, E, jp, DOCK_OK);
+        }
+    }
+}
+
+// Refinements of several requests share launches, which a single request's
+// few candidates cannot fill.  Finished searches wait (in admission order)
+// until 16 of them are ready, no search work is left, or the oldest has
+// waited 50 ms.
+constexpr size_t ENGINE_REFINE_BATCH = 16;
+constexpr double ENGINE_REFINE_WAIT_MS = 50.0;
+
+static void engine_refine_now(dock_ctx *ctx, Engine &E)
+{
+    std::vector<JobP> batch;
+    for (auto &j : E.refine_wait)
+        if (j->stage != JOB_DONE) batch.push_back(j);   // an error may have ended some meanwhile
+    E.refine_wait.clear();
+    if (!batch.empty()) jobs_refine(ctx, E, batch);
+    E.active.erase(std::remove_if(E.active.begin(), E.active.end(),
+                                  [](const JobP &j) { return j->stage == JOB_DONE; }),
+                   E.active.end());
+}
+
+static void engine_refine_if_due(dock_ctx *ctx, Engine &E)
+{
+    if (E.refine_wait.empty()) return;
+    bool search_left = false;
+    for (auto &j : E.active)
+        if (j->stage != JOB_DONE && j->issued < j->s1 - j->s0) search_left = true;
+    {
+        std::lock_guard<std::mutex> lk(E.mu);
+        if (!E.queue.empty()) search_left = true;
+    }
+    const double waited = std::chrono::duration<double, std::milli>(Clock::now() - E.refine_since).count();
+    if (!search_left || E.refine_wait.size() >= ENGINE_REFINE_BATCH || waited >= ENGINE_REFINE_WAIT_MS)
+        engine_refine_now(ctx, E);
 }
 
 // One engine step: admissions, then one search pass.  Returns false when
@@ -2048,6 +2181,9 @@ static bool engine_step(dock_ctx *ctx)
 {
     Engine &E = *ctx->eng;
     // cancelled jobs leave between passes
+    E.refine_wait.erase(std::remove_if(E.refine_wait.begin(), E.refine_wait.end(),
+                                       [](const JobP &j) { return j->cancel; }),
+                        E.refine_wait.end());
     for (size_t i = 0; i < E.active.size();) {
         if (E.active[i]->cancel) {
             fail(ctx, DOCK_E_CANCELLED, "request cancelled");
@@ -2089,6 +2225,7 @@ static bool engine_step(dock_ctx *ctx)
     if (ctx->dead) {
         for (auto &j : E.active) job_finish(ctx, E, j, DOCK_E_CUDA_FATAL);
         E.active.clear();
+        E.refine_wait.clear();
         return did;
     }
     // lattice side of this pass: round robin over the sides with work
@@ -2101,7 +2238,14 @@ static bool engine_step(dock_ctx *ctx)
     if (pick == 0)
         for (auto &j : E.active)
             if (j->issued < j->s1 - j->s0 && (pick == 0 || j->ob->N < pick)) pick = j->ob->N;
-    if (pick == 0) return did;
+    if (pick == 0) {
+        // no search work: refine whatever waits
+        if (!E.refine_wait.empty()) {
+            engine_refine_now(ctx, E);
+            return true;
+        }
+        return did;
+    }
     E.last_N = pick;
     std::vector<Job *> cls;
     for (auto &j : E.active)
@@ -2126,6 +2270,7 @@ static bool engine_step(dock_ctx *ctx)
             s = cuda_fail(ctx, e, "waiting for a search pass");
             for (auto &j : E.active) job_finish(ctx, E, j, s);
             E.active.clear();
+            E.refine_wait.clear();
             return true;
         }
     }
@@ -2157,6 +2302,7 @@ static bool engine_step(dock_ctx *ctx)
         if (e != cudaSuccess) s = cuda_fail(ctx, e, "recording a search pass");
     }
     ++E.passes;
+    std::vector<JobP> &finals = E.refine_wait;
     for (auto *jp : in_pass) {
         JobP j;
         for (auto &x : E.active)
@@ -2166,11 +2312,15 @@ static bool engine_step(dock_ctx *ctx)
             continue;
         }
         if (jp->issued < jp->s1 - jp->s0) continue;
-        bool done = false;
-        dock_status sa = job_advance(ctx, *jp, &done);
+        bool final = false;
+        dock_status sa = job_advance(ctx, *jp, &final);
         if (sa != DOCK_OK) job_finish(ctx, E, j, sa);
-        else if (done) job_finish(ctx, E, j, DOCK_OK);
+        else if (final) {
+            finals.push_back(j);
+            if (finals.size() == 1) E.refine_since = Clock::now();
+        }
     }
+    engine_refine_if_due(ctx, E);
     E.active.erase(std::remove_if(E.active.begin(), E.active.end(),
                                   [](const JobP &j) { return j->stage == JOB_DONE; }),
                    E.active.end());
@@ -2248,6 +2398,7 @@ static void engine_drop_handle(dock_ctx *ctx, const dock_object *ob, const dock_
     }
     for (auto &j : E->active)
         if (uses(j)) drop.push_back(j);
+    E->refine_wait.erase(std::remove_if(E->refine_wait.begin(), E->refine_wait.end(), uses), E->refine_wait.end());
     if (drop.empty()) return;
     cudaStreamSynchronize(ctx->stream);
     fail(ctx, DOCK_E_CANCELLED, "a handle of the request was freed");

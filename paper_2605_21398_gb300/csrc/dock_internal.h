@@ -111,8 +111,10 @@ struct CandF;                 // per-candidate FP32 pose data (k_refine.cu)
 size_t cand_bytes();
 constexpr int REF_ST = 24;    // doubles of refinement state per candidate
 constexpr int REF_NACC = 28;  // accumulated J, grad (6), Gauss-Newton upper triangle (21)
-cudaError_t launch_refine_eval(const RefineDev &d, int K, const CandF *cands, double *acc_part, bool grad,
-                               float *dist_out, float *wit_out, float *nrm_out, cudaStream_t st);
+constexpr int REF_WARPS = 4;  // warps per block of the refinement evaluation (one partial sum each)
+cudaError_t launch_refine_eval(const RefineDev *Dt, const int32_t *grp, int K, int nblk, const CandF *cands,
+                               double *acc_part, bool grad, float *dist_out, float *wit_out, float *nrm_out,
+                               cudaStream_t st);
 cudaError_t launch_refine_solve(int K, int nblk, double *state, const double *acc_part, const double *prm, int mode,
                                 CandF *cands, cudaStream_t st);
 cudaError_t launch_set_xi(int B, const float *xi, double *state, cudaStream_t st);

@@ -103,19 +103,16 @@ __device__ __forceinline__ bool sdf_smooth_at(const float *x, float r, float L)
     return fabsf(dr - dz) > band && fabsf(zlo - zhi) > band && rho > band;
 }
 
-// min over v in [0, 1-u] of f(v0 + u e1 + v e2): bisection on df/dv
-__device__ float inner_min(const float *v0, const float *e1, const float *e2, float u, float r, float L, int iters,
-                           float *v_out)
+// min over v in [0, 1-u] of f(v0 + u e1 + v e2): bisection on df/dv (a
+// subgradient sign; the same steps for every call, so the lanes of a warp
+// that search together stay converged; an end minimum is approached to
+// 2^-iters of the segment)
+__device__ __noinline__ float inner_min(const float *v0, const float *e1, const float *e2, float u, float r, float L,
+                                        int iters, float *v_out)
 {
-    float vmax = 1.f - u;
+    const float vmax = fmaxf(0.f, 1.f - u);
     float x[3], g[3];
     for (int a = 0; a < 3; ++a) x[a] = fmaf(u, e1[a], v0[a]);
-    float f0 = sdf_cyl(x[0], x[1], x[2], r, L, g);
-    if (vmax <= 0.f || dot3f(g, e2) >= 0.f) { *v_out = 0.f; return f0; }
-    float xe[3];
-    for (int a = 0; a < 3; ++a) xe[a] = fmaf(vmax, e2[a], x[a]);
-    float f1 = sdf_cyl(xe[0], xe[1], xe[2], r, L, g);
-    if (dot3f(g, e2) <= 0.f) { *v_out = vmax; return f1; }
     float lo = 0.f, hi = vmax;
     for (int k = 0; k < iters; ++k) {
         float mid = 0.5f * (lo + hi);
@@ -149,19 +146,17 @@ __device__ float outer_slope(const float *v0, const float *e1, const float *e2, 
 // medial surface), then, for a minimum outside the probe (f is C^1 there), a
 // bisection on dphi/du inside a bracket that stays outside: value-based search
 // locates a smooth minimum only to ~sqrt(FP32 eps), the slope to ~eps.
-__device__ float tri_min(const float *v0, const float *v1, const float *v2, float r, float L, int iters, float *uo,
-                         float *vo)
+// First-order tests: true (with the minimum in *d and its barycentric (u, v))
+// when the minimum of f over the triangle is found at a vertex or on an edge.
+__device__ bool tri_min_shortcut(const float *v0, const float *v1, const float *v2, const float *fv, float r, float L,
+                                 float *d, float *uo, float *vo)
 {
-    float e1[3] = {v1[0] - v0[0], v1[1] - v0[1], v1[2] - v0[2]};
-    float e2[3] = {v2[0] - v0[0], v2[1] - v0[1], v2[2] - v0[2]};
     {
         // A vertex where f is differentiable and no edge from it descends is
         // the minimum (f convex: f(y) >= f(x) + g.(y - x) >= f(x) on the
         // triangle).  This settles most triangles, which are small against the
-        // probe, with three evaluations.
+        // probe; fv holds f at the three vertices.
         const float *vv[3] = {v0, v1, v2};
-        float fv[3];
-        for (int m = 0; m < 3; ++m) fv[m] = sdf_cyl(vv[m][0], vv[m][1], vv[m][2], r, L, nullptr);
         int ms = 0;
         if (fv[1] < fv[ms]) ms = 1;
         if (fv[2] < fv[ms]) ms = 2;
@@ -177,7 +172,8 @@ __device__ float tri_min(const float *v0, const float *v1, const float *v2, floa
             if (opt) {
                 *uo = ms == 1 ? 1.f : 0.f;
                 *vo = ms == 2 ? 1.f : 0.f;
-                return fv[ms];
+                *d = fv[ms];
+                return true;
             }
         }
         // An edge point that minimises f along its edge, where f is
@@ -210,9 +206,21 @@ __device__ float tri_min(const float *v0, const float *v1, const float *v2, floa
             if (k == 0) { *uo = s; *vo = 0.f; }
             else if (k == 1) { *uo = 1.f - s; *vo = s; }
             else { *uo = 0.f; *vo = 1.f - s; }
-            return fx;
+            *d = fx;
+            return true;
         }
     }
+    return false;
+}
+
+// Minimum of f over the triangle by golden-section search on the first
+// barycentric coordinate with an inner bisection (for triangles the
+// first-order tests do not settle).
+__device__ __noinline__ float tri_min_search(const float *v0, const float *v1, const float *v2, float r, float L,
+                                             int iters, float *uo, float *vo)
+{
+    float e1[3] = {v1[0] - v0[0], v1[1] - v0[1], v1[2] - v0[2]};
+    float e2[3] = {v2[0] - v0[0], v2[1] - v0[1], v2[2] - v0[2]};
     const float ig = 0.6180339887498949f;
     float a = 0.f, b = 1.f, vc, vd;
     float c = b - ig * (b - a), d = a + ig * (b - a);
@@ -220,15 +228,15 @@ __device__ float tri_min(const float *v0, const float *v1, const float *v2, floa
     float fd = inner_min(v0, e1, e2, d, r, L, iters, &vd);
     int steps = iters + iters / 2;
     for (int k = 0; k < steps; ++k) {
-        if (fc <= fd) {
-            b = d; d = c; fd = fc; vd = vc;
-            c = b - ig * (b - a);
-            fc = inner_min(v0, e1, e2, c, r, L, iters, &vc);
-        } else {
-            a = c; c = d; fc = fd; vc = vd;
-            d = a + ig * (b - a);
-            fd = inner_min(v0, e1, e2, d, r, L, iters, &vd);
-        }
+        // one evaluation per step on every path
+        const bool left = fc <= fd;
+        if (left) { b = d; d = c; fd = fc; vd = vc; }
+        else { a = c; c = d; fc = fd; vc = vd; }
+        const float xn = left ? b - ig * (b - a) : a + ig * (b - a);
+        float vn;
+        const float fn = inner_min(v0, e1, e2, xn, r, L, iters, &vn);
+        if (left) { c = xn; fc = fn; vc = vn; }
+        else { d = xn; fd = fn; vd = vn; }
     }
     float u = fc <= fd ? c : d, v = fc <= fd ? vc : vd, best = fc <= fd ? fc : fd;
     float vu0, vu1;
@@ -258,6 +266,7 @@ __device__ float tri_min(const float *v0, const float *v1, const float *v2, floa
     *vo = v;
     return best;
 }
+
 
 // Lower bound of min f over the triangle: the linearisation at the centroid
 // with a subgradient there (f is convex).
@@ -315,112 +324,171 @@ __device__ __forceinline__ float node_sdf(const RefineDev &D, const float *A, co
     return sdf_cyl(loc[0], loc[1], loc[2], D.r, D.L, nullptr);
 }
 
-// Distance query of one probe pose against the mesh for object pose (R, p).
-// Two BVH passes under the Eq. (21) test f_p(c) < r_node + eps: the first
-// takes the smallest vertex value as an upper bound UB of d*, the second
-// minimises f_p only over triangles whose linearised lower bound does not
-// exceed min(UB, best so far) (a triangle attaining d* is never skipped;
-// ties in d keep the lower triangle index).  Returns the triangle index or
-// -1; fills d*, the local witness and the local contact normal.
-__device__ int dist_query(const RefineDev &D, const float *A, const float *bvec, float *d_out, float *xw, float *nl)
+// Distance query of the warp's 32 probe poses against the mesh (one pose per
+// lane; `valid` false for lanes without a pose).  One BVH pass under the
+// Eq. (21) test f_p(c) < r_node + eps: every triangle reached lowers the
+// lane's upper bound UB of d* by its smallest vertex value, and f_p is
+// minimised only over triangles whose linearised lower bound does not exceed
+// min(UB, best so far) (a triangle attaining d* is never skipped: its lower
+// bound is at most d* <= UB; ties in d keep the lower triangle index).  The warp walks one shared traversal: a node is entered
+// when any lane needs it, the nearer child (by the smallest bound over the
+// lanes) first, and every lane applies its own tests, so the 32 nearly equal
+// poses of a trajectory run in lockstep instead of serialising their
+// traversals.  Returns the lane's triangle index or -1; fills d*, the local
+// witness and the local contact normal.
+__device__ int dist_query(const RefineDev &D, const float *A, const float *bvec, bool valid, float *d_out, float *xw,
+                          float *nl)
 {
-    // stack entries: node index and the lower bound f_p(centre) - radius of
-    // its subtree; children are pushed far first, so the nearer subtree is
-    // searched first and the bound prunes the rest early
     int sn[64];
     float sl[64];
+    constexpr int QN = 6;                        // deferred per-triangle searches per lane
+    int qt[QN];
+    float ql[QN];
+    int nq = 0;
     const float eps = D.tau_out;
-    float UB = INFINITY;
-    for (int pass = 0; pass < 2; ++pass) {
+    float UB = valid ? INFINITY : -INFINITY;     // a lane without a pose needs nothing
+    float best = INFINITY;
+    int bt = -1;
+    float bx[3] = {0.f, 0.f, 0.f};
+    {
         int sp = 0;
-        float best = INFINITY;
-        int bt = -1;
-        float bx[3] = {0.f, 0.f, 0.f};
+        const float lim0 = valid ? INFINITY : -INFINITY;
         {
             const BvhNode &rt = D.nodes[0];
             float fc = node_sdf(D, A, bvec, rt.c);
-            if (fc < rt.rad + eps) {           // Eq. (21)
-                sn[sp] = 0;
-                sl[sp++] = fc - rt.rad;
+            float lb = fc - rt.rad;
+            bool need = valid && fc < rt.rad + eps && !(lb > lim0);   // Eq. (21)
+            if (__any_sync(0xFFFFFFFFu, need)) {
+                sn[0] = 0;
+                sl[0] = -INFINITY;
+                sp = 1;
             }
         }
         while (sp > 0) {
             --sp;
             const int ni = sn[sp];
-            if (sl[sp] > fminf(UB, best)) continue;    // cannot hold the minimum
+            const float lbw = sl[sp];
+            const float lim = valid ? fminf(UB, best) : -INFINITY;
+            // the bound stored with the node is the smallest over the lanes
+            if (!__any_sync(0xFFFFFFFFu, valid && !(lbw > lim))) continue;
             const BvhNode nd = D.nodes[ni];
             if (nd.left < 0) {
                 for (int k = 0; k < nd.count; ++k) {
-                    int t = D.tri_order[nd.right + k];
+                    const int t = D.tri_order[nd.right + k];
                     const float *ts = D.tri_sphere + 4 * t;
-                    float ft = node_sdf(D, A, bvec, ts);
-                    if (!(ft < ts[3] + eps)) continue;      // Eq. (21) for the triangle's sphere
-                    if (ft - ts[3] > fminf(UB, best)) continue;
+                    const float ft = node_sdf(D, A, bvec, ts);
+                    const float limt = valid ? fminf(UB, best) : -INFINITY;
+                    bool cand = valid && ft < ts[3] + eps && !(ft - ts[3] > limt);   // Eq. (21)
+                    if (!__any_sync(0xFFFFFFFFu, cand)) continue;
                     float lv[3][3];
                     local_vertices(D, t, A, bvec, lv);
-                    if (pass == 0) {
-                        for (int m = 0; m < 3; ++m) UB = fminf(UB, sdf_cyl(lv[m][0], lv[m][1], lv[m][2], D.r, D.L, nullptr));
-                        continue;
+                    float fv[3] = {0.f, 0.f, 0.f};
+                    if (cand) {
+                        for (int m = 0; m < 3; ++m) {
+                            fv[m] = sdf_cyl(lv[m][0], lv[m][1], lv[m][2], D.r, D.L, nullptr);
+                            UB = fminf(UB, fv[m]);
+                        }
                     }
-                    if (lin_lower_bound(lv, D.r, D.L) > fminf(UB, best)) continue;
-                    float u, v;
-                    float dk = tri_min(lv[0], lv[1], lv[2], D.r, D.L, D.tri_iters, &u, &v);
-                    if (dk < best || (dk == best && t < bt)) {
-                        best = dk;
-                        bt = t;
-                        float w0 = 1.f - u - v;
-                        for (int a = 0; a < 3; ++a) bx[a] = fmaf(w0, lv[0][a], fmaf(u, lv[1][a], v * lv[2][a]));
+                    float lbt = cand ? lin_lower_bound(lv, D.r, D.L) : INFINITY;
+                    if (cand && lbt > fminf(UB, best)) cand = false;
+                    if (cand) {
+                        float u, v, dk;
+                        bool done = tri_min_shortcut(lv[0], lv[1], lv[2], fv, D.r, D.L, &dk, &u, &v);
+                        if (!done && nq < QN) {
+                            // searched later, together with the other lanes' searches
+                            qt[nq] = t;
+                            ql[nq++] = lbt;
+                        } else {
+                            if (!done) dk = tri_min_search(lv[0], lv[1], lv[2], D.r, D.L, D.tri_iters, &u, &v);
+                            if (dk < best || (dk == best && t < bt)) {
+                                best = dk;
+                                bt = t;
+                                float w0 = 1.f - u - v;
+                                for (int c = 0; c < 3; ++c) bx[c] = fmaf(w0, lv[0][c], fmaf(u, lv[1][c], v * lv[2][c]));
+                            }
+                        }
                     }
                 }
             } else if (sp + 2 <= 64) {
                 const BvhNode &cl = D.nodes[nd.left];
                 const BvhNode &cr = D.nodes[nd.right];
-                float fl = node_sdf(D, A, bvec, cl.c), fr = node_sdf(D, A, bvec, cr.c);
-                bool okl = fl < cl.rad + eps, okr = fr < cr.rad + eps;   // Eq. (21)
-                float bl = fl - cl.rad, br = fr - cr.rad;
-                if (okl && okr) {
-                    bool lfirst = bl <= br;
+                const float fl = node_sdf(D, A, bvec, cl.c), fr = node_sdf(D, A, bvec, cr.c);
+                const float bl = fl - cl.rad, br = fr - cr.rad;
+                const float limc = valid ? fminf(UB, best) : -INFINITY;
+                const bool nl_ = valid && fl < cl.rad + eps && !(bl > limc);   // Eq. (21)
+                const bool nr_ = valid && fr < cr.rad + eps && !(br > limc);
+                const bool anyl = __any_sync(0xFFFFFFFFu, nl_), anyr = __any_sync(0xFFFFFFFFu, nr_);
+                // smallest bound over the lanes that need the child
+                float wl = nl_ ? bl : INFINITY, wr = nr_ ? br : INFINITY;
+                for (int o = 16; o > 0; o >>= 1) {
+                    wl = fminf(wl, __shfl_xor_sync(0xFFFFFFFFu, wl, o));
+                    wr = fminf(wr, __shfl_xor_sync(0xFFFFFFFFu, wr, o));
+                }
+                if (anyl && anyr) {
+                    const bool lfirst = wl <= wr;
                     sn[sp] = lfirst ? nd.right : nd.left;
-                    sl[sp++] = lfirst ? br : bl;
+                    sl[sp++] = lfirst ? wr : wl;
                     sn[sp] = lfirst ? nd.left : nd.right;
-                    sl[sp++] = lfirst ? bl : br;
-                } else if (okl) {
+                    sl[sp++] = lfirst ? wl : wr;
+                } else if (anyl) {
                     sn[sp] = nd.left;
-                    sl[sp++] = bl;
-                } else if (okr) {
+                    sl[sp++] = wl;
+                } else if (anyr) {
                     sn[sp] = nd.right;
-                    sl[sp++] = br;
+                    sl[sp++] = wr;
                 }
             }
         }
-        if (pass == 1) {
-            *d_out = best;
-            if (bt >= 0) {
-                sdf_normal(bx, D.r, D.L, nl);
-                for (int a = 0; a < 3; ++a) xw[a] = bx[a];
+    }
+    // deferred searches, slot by slot across the warp; a triangle whose lower
+    // bound now exceeds the upper bound or the best minimum found cannot hold it
+    for (int s = 0; s < QN; ++s) {
+        bool has = s < nq && !(ql[s] > fminf(UB, best));
+        if (!__any_sync(0xFFFFFFFFu, has)) continue;
+        if (has) {
+            const int t = qt[s];
+            float lv[3][3];
+            local_vertices(D, t, A, bvec, lv);
+            float u, v;
+            float dk = tri_min_search(lv[0], lv[1], lv[2], D.r, D.L, D.tri_iters, &u, &v);
+            if (dk < best || (dk == best && t < bt)) {
+                best = dk;
+                bt = t;
+                float w0 = 1.f - u - v;
+                for (int c = 0; c < 3; ++c) bx[c] = fmaf(w0, lv[0][c], fmaf(u, lv[1][c], v * lv[2][c]));
             }
-            return bt;
-        }
-        if (!(UB < INFINITY)) {   // no triangle passes Eq. (21)
-            *d_out = INFINITY;
-            return -1;
         }
     }
-    return -1;
+    if (!valid || bt < 0) {
+        *d_out = INFINITY;
+        return -1;
+    }
+    *d_out = best;
+    sdf_normal(bx, D.r, D.L, nl);
+    for (int c = 0; c < 3; ++c) xw[c] = bx[c];
+    return bt;
 }
 
-// One thread per (candidate, pose).  acc_part[(c * nblk + blk) * NACC + k].
+// One thread per (candidate, pose), 128 threads (REF_WARPS warps) a block.
+// acc_part[((c * nblk + blk) * REF_WARPS + warp) * NACC + k];
+// candidate c belongs to request grp[c] (Dt[0] when grp is null); blocks past
+// a request's pose count leave zero partial sums, so a candidate's sums do not
+// depend on the other requests of the launch.
 template <bool GRAD>
-__global__ void __launch_bounds__(128)
-k_refine_eval(RefineDev D, const CandF *cands, double *acc_part, float *dist_out, float *wit_out, float *nrm_out)
+__global__ void __launch_bounds__(128, 6)
+k_refine_eval(const RefineDev *Dt, const int32_t *grp, const CandF *cands, double *acc_part, float *dist_out,
+              float *wit_out, float *nrm_out)
 {
     const int c = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;
+    // the candidate's request (object mesh, trajectory, probe, parameters)
+    const RefineDev D = Dt[grp ? grp[c] : 0];
     double acc[NACC];
 #pragma unroll
     for (int k = 0; k < NACC; ++k) acc[k] = 0.0;
-    if (i < D.P) {
+    const bool valid = i < D.P;
+    {
         const CandF &cf = cands[c];
-        const PoseRec &pr = D.poses[i];
+        const PoseRec &pr = D.poses[valid ? i : D.P - 1];
         // probe pose in the object frame: A = R^T R_i, b = R^T (t_i - p);
         // a mesh point m maps to probe-local A^T (m - b)
         float A[9], bvec[3];
@@ -430,7 +498,7 @@ k_refine_eval(RefineDev D, const CandF *cands, double *acc_part, float *dist_out
         float tp[3] = {pr.tf[0] - cf.p[0], pr.tf[1] - cf.p[1], pr.tf[2] - cf.p[2]};
         for (int a = 0; a < 3; ++a) bvec[a] = fmaf(cf.R[0 * 3 + a], tp[0], fmaf(cf.R[1 * 3 + a], tp[1], cf.R[2 * 3 + a] * tp[2]));
         float d, xl[3], nl[3];
-        int bt = dist_query(D, A, bvec, &d, xl, nl);
+        int bt = dist_query(D, A, bvec, valid, &d, xl, nl);
         float n[3] = {0.f, 0.f, 0.f}, w[3] = {0.f, 0.f, 0.f};
         if (bt >= 0) {
             for (int a = 0; a < 3; ++a) {
@@ -438,7 +506,7 @@ k_refine_eval(RefineDev D, const CandF *cands, double *acc_part, float *dist_out
                 w[a] = fmaf(pr.Rf[a * 3 + 0], xl[0], fmaf(pr.Rf[a * 3 + 1], xl[1], fmaf(pr.Rf[a * 3 + 2], xl[2], pr.tf[a])));
             }
         }
-        if (dist_out) {
+        if (dist_out && valid) {
             size_t o = (size_t)c * D.P + i;
             dist_out[o] = bt >= 0 ? d : INFINITY;
             for (int a = 0; a < 3; ++a) { wit_out[3 * o + a] = w[a]; nrm_out[3 * o + a] = n[a]; }
@@ -465,20 +533,15 @@ k_refine_eval(RefineDev D, const CandF *cands, double *acc_part, float *dist_out
             }
         }
     }
-    // block reduction in a fixed order
-    __shared__ double red[4][NACC];
+    // warp sums in a fixed order, one partial per warp (no block barrier: the
+    // warps of a block finish at different times)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double *dst = acc_part + (((size_t)c * gridDim.x + blockIdx.x) * REF_WARPS + warp) * NACC;
 #pragma unroll
     for (int k = 0; k < NACC; ++k) {
         double v = acc[k];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
-        if (lane == 0) red[warp][k] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < NACC) {
-        double v = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) v += red[q][threadIdx.x];
-        acc_part[((size_t)c * gridDim.x + blockIdx.x) * NACC + threadIdx.x] = v;
+        if (lane == 0) dst[k] = v;
     }
 }
 
@@ -628,12 +691,13 @@ __global__ void k_refine_solve(int K, int nblk, double *state, const double *acc
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-cudaError_t launch_refine_eval(const RefineDev &d, int K, const CandF *cands, double *acc_part, bool grad,
-                               float *dist_out, float *wit_out, float *nrm_out, cudaStream_t st)
+cudaError_t launch_refine_eval(const RefineDev *Dt, const int32_t *grp, int K, int nblk, const CandF *cands,
+                               double *acc_part, bool grad, float *dist_out, float *wit_out, float *nrm_out,
+                               cudaStream_t st)
 {
-    dim3 grid((d.P + 127) / 128, K);
-    if (grad) k_refine_eval<true><<<grid, 128, 0, st>>>(d, cands, acc_part, dist_out, wit_out, nrm_out);
-    else k_refine_eval<false><<<grid, 128, 0, st>>>(d, cands, acc_part, dist_out, wit_out, nrm_out);
+    dim3 grid(nblk, K);
+    if (grad) k_refine_eval<true><<<grid, 128, 0, st>>>(Dt, grp, cands, acc_part, dist_out, wit_out, nrm_out);
+    else k_refine_eval<false><<<grid, 128, 0, st>>>(Dt, grp, cands, acc_part, dist_out, wit_out, nrm_out);
     return cudaGetLastError();
 }
 

@@ -233,7 +233,8 @@ __device__ __forceinline__ void vox_row(const float *B, const float *c, int jy, 
 // along the row, short intervals, failed core ends, or cores that do not
 // overlap) classify their row voxel by voxel with vox_row.
 template <int N>
-__device__ void voxelise_slab(const Geo &g, const RotRec &rr, const PoseRec *poses, int P, int jz, uint32_t *bits)
+__device__ void voxelise_slab(const Geo &g, const RotRec &rr, const PoseRec *poses, int P, int jz, uint32_t *bits,
+                              int *next_chunk)
 {
     constexpr int NW = N / 32;
     constexpr float CORE_M = 0.1f;
@@ -245,7 +246,15 @@ __device__ void voxelise_slab(const Geo &g, const RotRec &rr, const PoseRec *pos
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const float fz = (float)jz;
     const volatile uint32_t *vb = bits;
-    for (int base = warp * 32; base < P; base += nwarp * 32) {
+    (void)warp;
+    (void)nwarp;
+    for (;;) {
+        // warps take chunks of 32 poses from a block-wide counter, so a warp
+        // that drew chunks far from this slab goes on to the next chunk
+        int base = 0;
+        if (lane == 0) base = atomicAdd(next_chunk, 32);
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (base >= P) break;
         const int i = base + lane;
         bool hit = false;
         float B[9], c[3];
@@ -292,12 +301,16 @@ __device__ void voxelise_slab(const Geo &g, const RotRec &rr, const PoseRec *pos
             const bool act = hit && jy >= y0 && jy <= y1;
             int st = 0;                      // 0: nothing on this row, 1: verified core, 2: voxel by voxel
             int ca = N, cb = -1;
+            int ea = N, eb = -1;             // a voxel beyond the estimate (reliable estimates only)
+            bool rel = true;                 // the lane's voxels on this row lie in [ea, eb]
+            bool want_core = false;
             float l0[3];
             if (act) {
                 const float dyv = (float)jy - c[1], dzv = fz - c[2], dxv = -c[0];
                 for (int k = 0; k < 3; ++k) l0[k] = fmaf(B[0 * 3 + k], dxv, fmaf(B[1 * 3 + k], dyv, B[2 * 3 + k] * dzv));
                 if (!radial_ok) {
                     st = 2;
+                    rel = false;
                 } else {
                     // nearest point of the row to the axis, then the radial chord around it
                     const float js = -fmaf(l0[0], bx[0], l0[1] * bx[1]) * iAq;
@@ -326,19 +339,41 @@ __device__ void voxelise_slab(const Geo &g, const RotRec &rr, const PoseRec *pos
                             st = 0;
                         } else if (unsure) {
                             st = 2;
+                            rel = false;
                         } else if (lo <= hi + 2.f) {
                             ca = max(0, (int)ceilf(fmaxf(lo + CORE_M, -1.f)));
                             cb = min(N - 1, (int)floorf(fminf(hi - CORE_M, (float)N)));
-                            if (ca <= cb && classify(l0, bx, ca, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz) &&
-                                classify(l0, bx, cb, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz))
-                                st = 1;
-                            else
-                                st = 2;
+                            ea = max(0, (int)floorf(fmaxf(lo, -2.f)) - 1);
+                            eb = min(N - 1, (int)ceilf(fminf(hi, (float)N + 1.f)) + 1);
+                            want_core = ca <= cb;
+                            st = 2;
                         }
                     } else if (disc > -1e-2f * (1.f + fabsf(Aq * rv2))) {
                         st = 2;                   // tangent row: decide voxel by voxel
+                        rel = false;
                     }
                 }
+            }
+            // Every voxel the warp could add on this row already set (by the
+            // warp's earlier rows or other warps)?  Then the row is done.  Bits
+            // are only ever set, so a stale read only skips less.
+            if (__all_sync(0xFFFFFFFFu, rel)) {
+                const int A0 = __reduce_min_sync(0xFFFFFFFFu, st != 0 ? ea : N);
+                const int B0 = __reduce_max_sync(0xFFFFFFFFu, st != 0 ? eb : -1);
+                bool cov = true;
+                if (lane < NW && A0 <= B0) {
+                    const int lo = max(A0, 32 * lane) - 32 * lane, hi = min(B0, 32 * lane + 31) - 32 * lane;
+                    if (lo <= hi) {
+                        const uint32_t m = (hi == 31 ? 0xFFFFFFFFu : ((1u << (hi + 1)) - 1u)) & ~((1u << lo) - 1u);
+                        cov = (vb[jy * NW + lane] & m) == m;
+                    }
+                }
+                if (__all_sync(0xFFFFFFFFu, cov)) continue;
+            }
+            if (want_core) {
+                if (classify(l0, bx, ca, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz) &&
+                    classify(l0, bx, cb, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz))
+                    st = 1;
             }
             const unsigned cm = __ballot_sync(0xFFFFFFFFu, st == 1);
             if (cm) {
@@ -402,15 +437,17 @@ k_voxelise(Geo g, const ReqDev *reqs, const RotRec *rots, uint32_t *bits_out)
 {
     constexpr int NW = N / 32;
     __shared__ uint32_t bits[N * NW];
+    __shared__ int next_chunk;
     // slabs from the lattice centre outward (the swept volume is centred, so
     // the heaviest slabs of every rotation are scheduled first)
     const int k = blockIdx.y, b = blockIdx.x;
     const int jz = N / 2 + ((k & 1) ? -((k + 1) >> 1) : (k >> 1));
     for (int i = threadIdx.x; i < N * NW; i += blockDim.x) bits[i] = 0u;
+    if (threadIdx.x == 0) next_chunk = 0;
     __syncthreads();
     const RotRec &rr = rots[b];
     const ReqDev &q = reqs[rr.req];
-    voxelise_slab<N>(req_geo(g, q), rr, q.poses, q.P, jz, bits);
+    voxelise_slab<N>(req_geo(g, q), rr, q.poses, q.P, jz, bits, &next_chunk);
     __syncthreads();
     uint32_t *o = bits_out + ((size_t)b * N + jz) * N * NW;
     for (int i = threadIdx.x; i < N * NW; i += blockDim.x) o[i] = bits[i];
@@ -588,12 +625,14 @@ __global__ void __launch_bounds__(256) k_vox_export(Geo g, const ReqDev *reqs, c
 {
     constexpr int NW = N / 32;
     __shared__ uint32_t bits[N * NW];
+    __shared__ int next_chunk;
     const int jz = blockIdx.x, b = blockIdx.y;
     for (int i = threadIdx.x; i < N * NW; i += blockDim.x) bits[i] = 0u;
+    if (threadIdx.x == 0) next_chunk = 0;
     __syncthreads();
     const RotRec &rr = rots[b];
     const ReqDev &q = reqs[rr.req];
-    voxelise_slab<N>(req_geo(g, q), rr, q.poses, q.P, jz, bits);
+    voxelise_slab<N>(req_geo(g, q), rr, q.poses, q.P, jz, bits, &next_chunk);
     __syncthreads();
     uint8_t *o = out + ((size_t)b * N + jz) * N * N;
     for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
@@ -740,12 +779,14 @@ template <int M> struct PlaneCfg {
     static constexpr int PC = H / CL;                      // packed columns per CTA
     static constexpr int PP = PC + 1;                      // odd pitch: a warp's rows hit distinct banks
     static constexpr int NT = Plan<M>::T * 32;             // threads
+    static constexpr int COLS = 32;                        // columns per round of the y transform
     static constexpr int RPR = NT / Plan<H>::T;            // rows per round of the C2R
-    static constexpr int S1 = M * 32;                      // phase-1 exchange
-    static constexpr int S2 = (M / CL) * PP;               // peer rows (cluster)
+    static constexpr int S1 = M * COLS;                    // phase-1 exchange
+    static constexpr int S2 = CL > 1 ? (M / CL) * PP : 0;  // peer rows (cluster only)
     static constexpr int S3 = H * RPR;                     // phase-2 exchange (single CTA)
     static constexpr int STG = S1 > S2 ? (S1 > S3 ? S1 : S3) : (S2 > S3 ? S2 : S3);
     static constexpr size_t SMEM = sizeof(cf) * ((size_t)M * PP + STG + 2 * M);   // + twiddles + Nyquist column
+    static_assert(SMEM <= 227 * 1024, "plane pass exceeds the shared memory of one CTA");
 };
 
 template <int M, bool EXPORT>
@@ -753,7 +794,7 @@ __device__ __forceinline__ void plane_body(const float2 *Zp, const float2 *tw_g,
                                            int zc, cf *pb, cf *stg, cf *tw, int rank)
 {
     using C = PlaneCfg<M>;
-    constexpr int H = M / 2, CL = C::CL, PC = C::PC, PP = C::PP, E = Plan<M>::E, COLS = 32;
+    constexpr int H = M / 2, CL = C::CL, PC = C::PC, PP = C::PP, E = Plan<M>::E, COLS = C::COLS;
     const int P = H + 2;
     for (int i = threadIdx.x; i < M; i += blockDim.x) { float2 w = tw_g[i]; tw[i] = cmake(w.x, w.y); }
     __syncthreads();

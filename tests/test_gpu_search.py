@@ -30,7 +30,7 @@ _OBJ = {}
 
 
 def _gpu_pair(ctx, w):
-    key = (w.name, w.seed)
+    key = (w.name, w.seed, w.N, w.h, len(w.poses_world))
     if key not in _OBJ:
         ob = ctx.object_grid(w.obj.verts, w.obj.tris, w.h, w.N)
         sw = ctx.sweep_grid(w.poses_world, w.radius, w.length, w.h, w.N, contact=w.labels)
@@ -245,3 +245,26 @@ def test_large_lattice_sampled_parity(ctx, workload):
                                                    xs.start + dk[0]:xs.stop + dk[0]]))
             c = [(d + M) % M for d in dk]
             assert abs(C[c[2], c[1], c[0]] - acc) <= 1e-9 * max(1.0, abs(acc))
+
+
+def test_n96_lattice_sampled_parity(ctx, workload):
+    # 96^3 lattice (canvas 192^3, the radix-3 plans): bits exact and peaks
+    # against the oracle's FFT field for two rotations
+    w = workload("free64", N=96, h=16.0 / 96, poses=300, n_theta=48, n_phi=96, lines=3, noncontact=0.0)
+    ob, sw = _gpu_pair(ctx, w)
+    Go, oo, _, fits = O.object_grid(w.obj.verts, w.obj.tris, w.h, w.N)
+    assert fits
+    M = O.canvas_size(w.N)
+    assert M == 192
+    quats = np.concatenate([[w.gt_q], synth.random_unit_quats(1, 23)])
+    bits, orig = sw.voxelise(quats)
+    cands, peaks = ctx.search_so3(ob, sw, len(quats), 2, sampler=3, quats=quats, want_peaks=True)
+    for i, q in enumerate(quats):
+        S, o_s = O.sweep_grid(w.poses_world, q, w.h, w.N, w.radius, w.length)
+        assert np.array_equal(bits[i], S)
+        C = O.correlate_fft(Go, S, M)
+        sc, idx = O.peak(C)
+        tol = 1e-4 * np.max(np.abs(C))
+        assert abs(peaks["score"][i] - sc) <= tol + 1e-4 * abs(sc)
+        if sc - _second_best(C, idx) > 2 * tol:
+            assert peaks["idx"][i] == idx
