@@ -299,8 +299,9 @@ __device__ void voxelise_slab(const Geo &g, const RotRec &rr, const PoseRec *pos
         const float ibz = cap_ok ? 1.f / bx[2] : 0.f;
         for (int jy = Y0; jy <= Y1; ++jy) {
             const bool act = hit && jy >= y0 && jy <= y1;
-            int st = 0;                      // 0: nothing on this row, 1: verified core, 2: voxel by voxel
+            int st = 0;                      // 0: nothing, 1: verified core, 2: walk voxel by voxel, 3: short
             int ca = N, cb = -1;
+            int qa = 0, qb = -1;             // st 3: the few candidate voxels
             int ea = N, eb = -1;             // a voxel beyond the estimate (reliable estimates only)
             bool rel = true;                 // the lane's voxels on this row lie in [ea, eb]
             bool want_core = false;
@@ -346,11 +347,21 @@ __device__ void voxelise_slab(const Geo &g, const RotRec &rr, const PoseRec *pos
                             ea = max(0, (int)floorf(fmaxf(lo, -2.f)) - 1);
                             eb = min(N - 1, (int)ceilf(fminf(hi, (float)N + 1.f)) + 1);
                             want_core = ca <= cb;
-                            st = 2;
+                            if (want_core) {
+                                st = 2;
+                            } else {
+                                // chord under ~1.2 voxels: its voxels lie in [ea, eb]
+                                st = 3;
+                                qa = ea;
+                                qb = eb;
+                            }
                         }
                     } else if (disc > -1e-2f * (1.f + fabsf(Aq * rv2))) {
-                        st = 2;                   // tangent row: decide voxel by voxel
-                        rel = false;
+                        // tangent row: the exact chord (if any) is within a quarter
+                        // voxel of js
+                        st = 3;
+                        qa = ea = max(0, (int)floorf(fmaxf(js, -2.f)) - 1);
+                        qb = eb = min(N - 1, (int)ceilf(fminf(js, (float)N + 1.f)) + 1);
                     }
                 }
             }
@@ -408,6 +419,18 @@ __device__ void voxelise_slab(const Geo &g, const RotRec &rr, const PoseRec *pos
                     }
                 } else if (st == 1) {
                     st = 2;
+                }
+            }
+            // short chords: the lanes classify their few candidate voxels together
+            if (__any_sync(0xFFFFFFFFu, st == 3)) {
+                const int len = (st == 3) ? qb - qa + 1 : 0;
+                const int maxlen = __reduce_max_sync(0xFFFFFFFFu, len);
+                for (int k = 0; k < maxlen; ++k) {
+                    const int j = qa + k;
+                    bool in = false;
+                    if (k < len && !((vb[jy * NW + (j >> 5)] >> (j & 31)) & 1u))
+                        in = classify(l0, bx, j, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz);
+                    if (in) atomicOr(&bits[jy * NW + (j >> 5)], 1u << (j & 31));
                 }
             }
             if (st == 2) vox_row<N>(B, c, jy, jz, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, bits + jy * NW);
