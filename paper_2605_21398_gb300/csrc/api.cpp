@@ -40,6 +40,29 @@ struct KStat {
 
 struct Engine;
 
+// Device buffers of one refinement launch sequence (grown on demand).
+struct RefBufs {
+    double *state = nullptr, *acc = nullptr, *prm = nullptr;
+    size_t state_n = 0, acc_n = 0, prm_n = 0;
+    void *cands = nullptr;
+    size_t cands_n = 0;
+    RefineDev *dev = nullptr;   // per-request refinement tables of a launch
+    size_t dev_n = 0;
+    int32_t *grp = nullptr;     // candidate -> request
+    size_t grp_n = 0;
+};
+
+static void free_refbufs(RefBufs &b)
+{
+    cudaFree(b.state);
+    cudaFree(b.acc);
+    cudaFree(b.prm);
+    cudaFree(b.cands);
+    cudaFree(b.dev);
+    cudaFree(b.grp);
+    b = RefBufs();
+}
+
 struct dock_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -68,14 +91,7 @@ struct dock_ctx {
     RotRec *phase = nullptr;  // rotations of several requests gathered for one pipeline pass
     size_t phase_n = 0;
     // refinement buffers
-    double *ref_state = nullptr, *ref_acc = nullptr, *ref_prm = nullptr;
-    size_t ref_state_n = 0, ref_acc_n = 0, ref_prm_n = 0;
-    void *ref_cands = nullptr;
-    size_t ref_cands_n = 0;
-    RefineDev *ref_dev = nullptr;   // per-request refinement tables of a launch
-    size_t ref_dev_n = 0;
-    int32_t *ref_grp = nullptr;     // candidate -> request
-    size_t ref_grp_n = 0;
+    RefBufs ref;
     // twiddle tables per canvas size
     std::map<int, float2 *> tw, qt;
     std::map<int, double2 *> twd;
@@ -200,13 +216,14 @@ static void dfree(dock_ctx *ctx, void *p, size_t bytes)
 struct Prof {
     dock_ctx *ctx;
     const char *name;
+    cudaStream_t st;
     cudaEvent_t a = nullptr, b = nullptr;
-    Prof(dock_ctx *c, const char *n) : ctx(c), name(n)
+    Prof(dock_ctx *c, const char *n, cudaStream_t s = nullptr) : ctx(c), name(n), st(s ? s : c->stream)
     {
         if (!ctx->prof) return;
         a = get();
         b = get();
-        cudaEventRecord(a, ctx->stream);
+        cudaEventRecord(a, st);
     }
     cudaEvent_t get()
     {
@@ -222,7 +239,7 @@ struct Prof {
     ~Prof()
     {
         if (!ctx->prof) return;
-        cudaEventRecord(b, ctx->stream);
+        cudaEventRecord(b, st);
         ctx->pending.push_back({name, a, b});
     }
 };
@@ -230,9 +247,9 @@ struct Prof {
 static void prof_resolve(dock_ctx *ctx)
 {
     if (ctx->pending.empty()) return;
-    cudaStreamSynchronize(ctx->stream);
     for (auto &p : ctx->pending) {
         float ms = 0.f;
+        cudaEventSynchronize(p.b);   // recorded on the context's or the engine's refinement stream
         cudaEventElapsedTime(&ms, p.a, p.b);
         KStat &s = ctx->stats[p.name];
         s.launches += 1;
@@ -461,12 +478,7 @@ void dock_destroy(dock_ctx *c)
     cudaFree(c->cands);
     cudaFree(c->reqs);
     cudaFree(c->phase);
-    cudaFree(c->ref_state);
-    cudaFree(c->ref_acc);
-    cudaFree(c->ref_prm);
-    cudaFree(c->ref_cands);
-    cudaFree(c->ref_dev);
-    cudaFree(c->ref_grp);
+    free_refbufs(c->ref);
     for (auto &kv : c->tw) cudaFree(kv.second);
     for (auto &kv : c->qt) cudaFree(kv.second);
     for (auto &kv : c->twd) cudaFree(kv.second);
@@ -1549,13 +1561,13 @@ static RefineDev make_refine_dev(const dock_object *ob, const dock_sweep *sw, co
     return D;
 }
 
-static dock_status ref_buffers(dock_ctx *ctx, int K, int nblk)
+static dock_status ref_buffers(dock_ctx *ctx, RefBufs &rb, int K, int nblk)
 {
     dock_status s;
-    if ((s = ensure(ctx, (void **)&ctx->ref_state, &ctx->ref_state_n, (size_t)K * REF_ST, sizeof(double))) != DOCK_OK) return s;
-    if ((s = ensure(ctx, (void **)&ctx->ref_acc, &ctx->ref_acc_n, (size_t)K * nblk * REF_NACC, sizeof(double))) != DOCK_OK) return s;
-    if ((s = ensure(ctx, (void **)&ctx->ref_prm, &ctx->ref_prm_n, 8, sizeof(double))) != DOCK_OK) return s;
-    if ((s = ensure(ctx, (void **)&ctx->ref_cands, &ctx->ref_cands_n, (size_t)K, cand_bytes())) != DOCK_OK) return s;
+    if ((s = ensure(ctx, (void **)&rb.state, &rb.state_n, (size_t)K * REF_ST, sizeof(double))) != DOCK_OK) return s;
+    if ((s = ensure(ctx, (void **)&rb.acc, &rb.acc_n, (size_t)K * nblk * REF_NACC, sizeof(double))) != DOCK_OK) return s;
+    if ((s = ensure(ctx, (void **)&rb.prm, &rb.prm_n, 8, sizeof(double))) != DOCK_OK) return s;
+    if ((s = ensure(ctx, (void **)&rb.cands, &rb.cands_n, (size_t)K, cand_bytes())) != DOCK_OK) return s;
     return DOCK_OK;
 }
 
@@ -1620,45 +1632,43 @@ static void pose_of_state(const double *st, double *R, double *p)
     for (int i = 0; i < 3; ++i) p[i] = ((p0[i] + Vu[i]) + Ra[i]) - dRRa[i];
 }
 
-// Runs `iters` projected Gauss-Newton iterations on the K states in
-// ctx->ref_state, then a final evaluation that records J at the final twist.
 // Uploads the per-request tables of one refinement launch (staged copies:
 // the host vectors may be released once the copies are issued).
-static dock_status upload_refdev(dock_ctx *ctx, const std::vector<RefineDev> &Ds, const std::vector<int32_t> &grp,
-                                 cudaStream_t st)
+static dock_status upload_refdev(dock_ctx *ctx, RefBufs &rb, const std::vector<RefineDev> &Ds,
+                                 const std::vector<int32_t> &grp, cudaStream_t st)
 {
     dock_status s;
-    if ((s = ensure(ctx, (void **)&ctx->ref_dev, &ctx->ref_dev_n, Ds.size(), sizeof(RefineDev))) != DOCK_OK) return s;
-    if ((s = ensure(ctx, (void **)&ctx->ref_grp, &ctx->ref_grp_n, std::max<size_t>(1, grp.size()), sizeof(int32_t))) !=
-        DOCK_OK)
+    if ((s = ensure(ctx, (void **)&rb.dev, &rb.dev_n, Ds.size(), sizeof(RefineDev))) != DOCK_OK) return s;
+    if ((s = ensure(ctx, (void **)&rb.grp, &rb.grp_n, std::max<size_t>(1, grp.size()), sizeof(int32_t))) != DOCK_OK)
         return s;
-    CK(ctx, cudaMemcpyAsync(ctx->ref_dev, Ds.data(), sizeof(RefineDev) * Ds.size(), cudaMemcpyHostToDevice, st));
+    CK(ctx, cudaMemcpyAsync(rb.dev, Ds.data(), sizeof(RefineDev) * Ds.size(), cudaMemcpyHostToDevice, st));
     if (!grp.empty())
-        CK(ctx, cudaMemcpyAsync(ctx->ref_grp, grp.data(), sizeof(int32_t) * grp.size(), cudaMemcpyHostToDevice, st));
+        CK(ctx, cudaMemcpyAsync(rb.grp, grp.data(), sizeof(int32_t) * grp.size(), cudaMemcpyHostToDevice, st));
     return DOCK_OK;
 }
 
-static dock_status refine_loop(dock_ctx *ctx, int K, int nblk, int iters, const dock_params *p, cudaStream_t st)
+// Runs `iters` projected Gauss-Newton iterations on the K states in
+// rb.state, then a final evaluation that records J at the final twist.
+static dock_status refine_loop(dock_ctx *ctx, RefBufs &rb, int K, int nblk, int iters, const dock_params *p,
+                               cudaStream_t st)
 {
     double prm[6] = {p->lambda, p->mu, p->step_t, p->step_r, p->b_t, p->b_r};
-    CK(ctx, cudaMemcpyAsync(ctx->ref_prm, prm, sizeof(prm), cudaMemcpyHostToDevice, st));
-    CandF *cf = (CandF *)ctx->ref_cands;
-    CK(ctx, launch_refine_solve(K, nblk * REF_WARPS, ctx->ref_state, ctx->ref_acc, ctx->ref_prm, 0, cf, st));
+    CK(ctx, cudaMemcpyAsync(rb.prm, prm, sizeof(prm), cudaMemcpyHostToDevice, st));
+    CandF *cf = (CandF *)rb.cands;
+    CK(ctx, launch_refine_solve(K, nblk * REF_WARPS, rb.state, rb.acc, rb.prm, 0, cf, st));
     for (int it = 0; it < iters; ++it) {
         {
-            Prof pr(ctx, "refine_eval");
-            CK(ctx, launch_refine_eval(ctx->ref_dev, ctx->ref_grp, K, nblk, cf, ctx->ref_acc, true, nullptr, nullptr,
-                                       nullptr, st));
+            Prof pr(ctx, "refine_eval", st);
+            CK(ctx, launch_refine_eval(rb.dev, rb.grp, K, nblk, cf, rb.acc, true, nullptr, nullptr, nullptr, st));
         }
-        Prof pr(ctx, "refine_solve");
-        CK(ctx, launch_refine_solve(K, nblk * REF_WARPS, ctx->ref_state, ctx->ref_acc, ctx->ref_prm, 1, cf, st));
+        Prof pr(ctx, "refine_solve", st);
+        CK(ctx, launch_refine_solve(K, nblk * REF_WARPS, rb.state, rb.acc, rb.prm, 1, cf, st));
     }
     {
-        Prof pr(ctx, "refine_eval");
-        CK(ctx, launch_refine_eval(ctx->ref_dev, ctx->ref_grp, K, nblk, cf, ctx->ref_acc, false, nullptr, nullptr,
-                                   nullptr, st));
+        Prof pr(ctx, "refine_eval", st);
+        CK(ctx, launch_refine_eval(rb.dev, rb.grp, K, nblk, cf, rb.acc, false, nullptr, nullptr, nullptr, st));
     }
-    CK(ctx, launch_refine_solve(K, nblk * REF_WARPS, ctx->ref_state, ctx->ref_acc, ctx->ref_prm, 2, cf, st));
+    CK(ctx, launch_refine_solve(K, nblk * REF_WARPS, rb.state, rb.acc, rb.prm, 2, cf, st));
     return DOCK_OK;
 }
 
@@ -1669,37 +1679,50 @@ struct RefGroup {
     int c0, K;
 };
 
-// Refines the candidates of several requests (same parameters) in shared
-// launches; each candidate's arithmetic is the same as refined alone.
-static dock_status refine_many(dock_ctx *ctx, const std::vector<RefGroup> &groups, const dock_candidate *in,
-                               const dock_params *p, dock_refined *out)
+static int refine_count(const std::vector<RefGroup> &groups)
 {
-    int K = 0, nblk = 1;
-    for (auto &gr : groups) {
-        K += gr.K;
-        nblk = std::max(nblk, ((int)gr.sw->P + 127) / 128);
-    }
+    int K = 0;
+    for (auto &gr : groups) K += gr.K;
+    return K;
+}
+
+// Issues the refinement of the candidates of several requests (same
+// parameters) on stream st, in shared launches; each candidate's arithmetic
+// is the same as refined alone.  The final states (REF_ST doubles per
+// candidate) are copied to host_state, which must stay valid (and, for the
+// copy to be asynchronous, be pinned) until st reaches this point.
+static dock_status refine_launch(dock_ctx *ctx, RefBufs &rb, const std::vector<RefGroup> &groups,
+                                 const dock_candidate *in, const dock_params *p, cudaStream_t st, double *host_state)
+{
+    int K = refine_count(groups), nblk = 1;
+    for (auto &gr : groups) nblk = std::max(nblk, ((int)gr.sw->P + 127) / 128);
     dock_status s;
-    if ((s = ref_buffers(ctx, K, nblk * REF_WARPS)) != DOCK_OK) return s;
-    std::vector<double> st((size_t)K * REF_ST);
+    if ((s = ref_buffers(ctx, rb, K, nblk * REF_WARPS)) != DOCK_OK) return s;
+    std::vector<double> sv((size_t)K * REF_ST);
     std::vector<RefineDev> Ds;
     std::vector<int32_t> grp(K);
     for (size_t g = 0; g < groups.size(); ++g) {
         const RefGroup &gr = groups[g];
         Ds.push_back(make_refine_dev(gr.ob, gr.sw, p));
         for (int c = gr.c0; c < gr.c0 + gr.K; ++c) {
-            state_from_pose(in[c].q, in[c].t, gr.ob->anchor, st.data() + (size_t)c * REF_ST);
+            state_from_pose(in[c].q, in[c].t, gr.ob->anchor, sv.data() + (size_t)c * REF_ST);
             grp[c] = (int32_t)g;
         }
     }
-    CK(ctx, cudaMemcpyAsync(ctx->ref_state, st.data(), sizeof(double) * st.size(), cudaMemcpyHostToDevice, ctx->stream));
-    if ((s = upload_refdev(ctx, Ds, grp, ctx->stream)) != DOCK_OK) return s;
-    if ((s = refine_loop(ctx, K, nblk, p->iters, p, ctx->stream)) != DOCK_OK) return s;
-    CK(ctx, cudaMemcpyAsync(st.data(), ctx->ref_state, sizeof(double) * st.size(), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    CK(ctx, cudaMemcpyAsync(rb.state, sv.data(), sizeof(double) * sv.size(), cudaMemcpyHostToDevice, st));
+    if ((s = upload_refdev(ctx, rb, Ds, grp, st)) != DOCK_OK) return s;
+    if ((s = refine_loop(ctx, rb, K, nblk, p->iters, p, st)) != DOCK_OK) return s;
+    CK(ctx, cudaMemcpyAsync(host_state, rb.state, sizeof(double) * sv.size(), cudaMemcpyDeviceToHost, st));
+    return DOCK_OK;
+}
+
+// Poses, twists and J of refined candidates from their final states.
+static void refine_results(const std::vector<RefGroup> &groups, const double *host_state, const dock_params *p,
+                           dock_refined *out)
+{
     for (auto &gr : groups)
         for (int c = gr.c0; c < gr.c0 + gr.K; ++c) {
-            const double *x = st.data() + (size_t)c * REF_ST;
+            const double *x = host_state + (size_t)c * REF_ST;
             double R[9], t[3];
             pose_of_state(x, R, t);
             mat_to_quat(R, out[c].q);
@@ -1709,6 +1732,17 @@ static dock_status refine_many(dock_ctx *ctx, const std::vector<RefGroup> &group
             out[c].cand = c - gr.c0;
             out[c].iters = p->iters;
         }
+}
+
+// Synchronous refinement on the context's own buffers and stream.
+static dock_status refine_many(dock_ctx *ctx, const std::vector<RefGroup> &groups, const dock_candidate *in,
+                               const dock_params *p, dock_refined *out)
+{
+    std::vector<double> hs((size_t)refine_count(groups) * REF_ST);
+    dock_status s;
+    if ((s = refine_launch(ctx, ctx->ref, groups, in, p, ctx->stream, hs.data())) != DOCK_OK) return s;
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    refine_results(groups, hs.data(), p, out);
     return DOCK_OK;
 }
 
@@ -1765,22 +1799,22 @@ static dock_status objective_impl(dock_ctx *ctx, const dock_object *ob, const do
     cudaSetDevice(ctx->device);
     cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
     int nblk = ((int)sw->P + 127) / 128;
-    if ((s = ref_buffers(ctx, B, nblk * REF_WARPS)) != DOCK_OK) return s;
+    if ((s = ref_buffers(ctx, ctx->ref, B, nblk * REF_WARPS)) != DOCK_OK) return s;
     std::vector<double> stv((size_t)B * REF_ST);
     for (int b = 0; b < B; ++b) state_from_pose(base + 7 * b, base + 7 * b + 4, ob->anchor, stv.data() + (size_t)b * REF_ST);
-    CK(ctx, cudaMemcpyAsync(ctx->ref_state, stv.data(), sizeof(double) * stv.size(), cudaMemcpyHostToDevice, st));
+    CK(ctx, cudaMemcpyAsync(ctx->ref.state, stv.data(), sizeof(double) * stv.size(), cudaMemcpyHostToDevice, st));
     std::vector<RefineDev> Ds(1, make_refine_dev(ob, sw, p));
-    if ((s = upload_refdev(ctx, Ds, std::vector<int32_t>(), st)) != DOCK_OK) return s;
+    if ((s = upload_refdev(ctx, ctx->ref, Ds, std::vector<int32_t>(), st)) != DOCK_OK) return s;
     CK(ctx, cudaStreamSynchronize(st));   // the host staging vectors are released on return
-    CK(ctx, launch_set_xi(B, xi, ctx->ref_state, st));
-    CandF *cf = (CandF *)ctx->ref_cands;
-    CK(ctx, launch_refine_solve(B, nblk * REF_WARPS, ctx->ref_state, ctx->ref_acc, ctx->ref_prm, 0, cf, st));
+    CK(ctx, launch_set_xi(B, xi, ctx->ref.state, st));
+    CandF *cf = (CandF *)ctx->ref.cands;
+    CK(ctx, launch_refine_solve(B, nblk * REF_WARPS, ctx->ref.state, ctx->ref.acc, ctx->ref.prm, 0, cf, st));
     {
         Prof pr(ctx, grad ? "objective_adjoint" : "objective_fwd");
-        CK(ctx, launch_refine_eval(ctx->ref_dev, nullptr, B, nblk, cf, ctx->ref_acc, grad != nullptr, nullptr, nullptr,
+        CK(ctx, launch_refine_eval(ctx->ref.dev, nullptr, B, nblk, cf, ctx->ref.acc, grad != nullptr, nullptr, nullptr,
                                    nullptr, st));
     }
-    CK(ctx, launch_finish_objective(B, nblk * REF_WARPS, ctx->ref_state, ctx->ref_acc, p->lambda, J, grad, gJ, st));
+    CK(ctx, launch_finish_objective(B, nblk * REF_WARPS, ctx->ref.state, ctx->ref.acc, p->lambda, J, grad, gJ, st));
     return DOCK_OK;
 }
 
@@ -1818,7 +1852,7 @@ extern "C" dock_status dock_distances(dock_ctx *ctx, const dock_object *ob, cons
     const dock_params *p = params ? params : &pd;
     cudaSetDevice(ctx->device);
     int nblk = ((int)sw->P + 127) / 128;
-    if ((s = ref_buffers(ctx, B, nblk * REF_WARPS)) != DOCK_OK) return s;
+    if ((s = ref_buffers(ctx, ctx->ref, B, nblk * REF_WARPS)) != DOCK_OK) return s;
     std::vector<double> stv((size_t)B * REF_ST);
     for (int b = 0; b < B; ++b) {
         if ((s = check_quat_pose(ctx, obj_poses + 7 * b)) != DOCK_OK) return s;
@@ -1828,16 +1862,16 @@ extern "C" dock_status dock_distances(dock_ctx *ctx, const dock_object *ob, cons
     float *buf = nullptr;
     if ((s = dalloc(ctx, (void **)&buf, sizeof(float) * 7 * n, nullptr)) != DOCK_OK) return s;
     cudaStream_t st = ctx->stream;
-    CandF *cf = (CandF *)ctx->ref_cands;
+    CandF *cf = (CandF *)ctx->ref.cands;
     std::vector<RefineDev> Ds(1, make_refine_dev(ob, sw, p));
-    if ((s = upload_refdev(ctx, Ds, std::vector<int32_t>(), st)) != DOCK_OK) {
+    if ((s = upload_refdev(ctx, ctx->ref, Ds, std::vector<int32_t>(), st)) != DOCK_OK) {
         dfree(ctx, buf, sizeof(float) * 7 * n);
         return s;
     }
-    cudaError_t e = cudaMemcpyAsync(ctx->ref_state, stv.data(), sizeof(double) * stv.size(), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = launch_refine_solve(B, nblk * REF_WARPS, ctx->ref_state, ctx->ref_acc, ctx->ref_prm, 0, cf, st);
+    cudaError_t e = cudaMemcpyAsync(ctx->ref.state, stv.data(), sizeof(double) * stv.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_refine_solve(B, nblk * REF_WARPS, ctx->ref.state, ctx->ref.acc, ctx->ref.prm, 0, cf, st);
     if (e == cudaSuccess)
-        e = launch_refine_eval(ctx->ref_dev, nullptr, B, nblk, cf, ctx->ref_acc, false, buf, buf + n, buf + 4 * n, st);
+        e = launch_refine_eval(ctx->ref.dev, nullptr, B, nblk, cf, ctx->ref.acc, false, buf, buf + n, buf + 4 * n, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d, buf, sizeof(float) * n, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(witness, buf + n, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(normal, buf + 4 * n, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, st);
@@ -1913,6 +1947,17 @@ struct Engine {
     std::vector<JobP> refine_wait;        // searches done, refinement pending
     Clock::time_point refine_since;       // when the oldest of them finished its search
     cudaEvent_t pass_ev[2] = {nullptr, nullptr};   // completion of the last two passes
+    // one refinement batch at a time runs on its own stream, beside the search
+    // passes, with its own buffers and a pinned host copy of its final states
+    cudaStream_t rstream = nullptr;
+    cudaEvent_t rdone = nullptr;
+    RefBufs rb;
+    double *rhost = nullptr;
+    size_t rhost_n = 0;
+    bool rbusy = false;
+    std::vector<JobP> rjobs;
+    std::vector<RefGroup> rgroups;
+    dock_params rparams{};
     std::thread worker;
     bool started = false, stop = false;
 };
@@ -1951,6 +1996,15 @@ static dock_status engine_init(dock_ctx *ctx)
             delete E;
             return cuda_fail(ctx, e, "cudaEventCreate");
         }
+    }
+    cudaError_t e = cudaStreamCreateWithFlags(&E->rstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&E->rdone, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        if (E->rstream) cudaStreamDestroy(E->rstream);
+        for (auto &x : E->pass_ev) if (x) cudaEventDestroy(x);
+        dfree(ctx, E->reqtab, sizeof(ReqDev) * ENGINE_SLOTS);
+        delete E;
+        return cuda_fail(ctx, e, "creating the refinement stream");
     }
     for (int i = ENGINE_SLOTS - 1; i >= 0; --i) E->free_slots.push_back(i);
     ctx->eng = E;
@@ -2098,38 +2152,30 @@ static dock_status job_advance(dock_ctx *ctx, Job &j, bool *final)
     return DOCK_OK;
 }
 
-// Refines the top-K candidates of jobs whose searches are complete, in shared
-// launches per parameter set; the lowest J wins (ties: lower candidate index).
-static void jobs_refine(dock_ctx *ctx, Engine &E, std::vector<JobP> &done)
+// Results of the refinement batch in flight once its stream has finished
+// it: the lowest J of a job's candidates wins (ties: lower candidate index).
+static void engine_refine_collect(dock_ctx *ctx, Engine &E, bool wait)
 {
-    std::vector<bool> used(done.size(), false);
-    for (size_t i = 0; i < done.size(); ++i) {
-        if (used[i]) continue;
-        std::vector<size_t> grp_jobs;
-        for (size_t k = i; k < done.size(); ++k)
-            if (!used[k] && memcmp(&done[k]->p, &done[i]->p, sizeof(dock_params)) == 0) {
-                used[k] = true;
-                grp_jobs.push_back(k);
-            }
-        std::vector<RefGroup> groups;
-        std::vector<dock_candidate> cands;
-        for (size_t k : grp_jobs) {
-            Job &j = *done[k];
-            groups.push_back(RefGroup{j.ob, j.sw, (int)cands.size(), (int)j.cands.size()});
-            cands.insert(cands.end(), j.cands.begin(), j.cands.end());
-        }
-        std::vector<dock_refined> ref(cands.size());
-        dock_status s = refine_many(ctx, groups, cands.data(), &done[i]->p, ref.data());
-        for (size_t g = 0; g < grp_jobs.size(); ++g) {
-            const JobP &jp = done[grp_jobs[g]];
-            if (s != DOCK_OK) {
-                job_finish(ctx, E, jp, s);
-                continue;
-            }
+    if (!E.rbusy) return;
+    cudaError_t e = wait ? cudaEventSynchronize(E.rdone) : cudaEventQuery(E.rdone);
+    if (e == cudaErrorNotReady) return;
+    E.rbusy = false;
+    std::vector<JobP> jobs;
+    jobs.swap(E.rjobs);
+    if (e != cudaSuccess) {
+        dock_status s = cuda_fail(ctx, e, "refinement");
+        for (auto &jp : jobs)
+            if (jp->stage != JOB_DONE) job_finish(ctx, E, jp, s);
+    } else {
+        std::vector<dock_refined> ref(refine_count(E.rgroups));
+        refine_results(E.rgroups, E.rhost, &E.rparams, ref.data());
+        for (size_t g = 0; g < jobs.size(); ++g) {
+            const JobP &jp = jobs[g];
+            if (jp->stage == JOB_DONE) continue;   // cancelled meanwhile
             Job &j = *jp;
-            const dock_refined *r = ref.data() + groups[g].c0;
+            const dock_refined *r = ref.data() + E.rgroups[g].c0;
             int bi = 0;
-            for (int c = 1; c < groups[g].K; ++c) if (r[c].J < r[bi].J) bi = c;
+            for (int c = 1; c < E.rgroups[g].K; ++c) if (r[c].J < r[bi].J) bi = c;
             memcpy(j.res.q, r[bi].q, sizeof(j.res.q));
             memcpy(j.res.t, r[bi].t, sizeof(j.res.t));
             j.res.J = r[bi].J;
@@ -2139,25 +2185,65 @@ static void jobs_refine(dock_ctx *ctx, Engine &E, std::vector<JobP> &done)
             job_finish(ctx, E, jp, DOCK_OK);
         }
     }
+    E.rgroups.clear();
+    E.active.erase(std::remove_if(E.active.begin(), E.active.end(),
+                                  [](const JobP &j) { return j->stage == JOB_DONE; }),
+                   E.active.end());
 }
 
 // Refinements of several requests share launches, which a single request's
 // few candidates cannot fill.  Finished searches wait (in admission order)
 // until 16 of them are ready, no search work is left, or the oldest has
-// waited 50 ms.
+// waited 50 ms; the batch (the waiting jobs with the first one's parameters)
+// then runs on the refinement stream while search passes go on.
 constexpr size_t ENGINE_REFINE_BATCH = 16;
 constexpr double ENGINE_REFINE_WAIT_MS = 50.0;
 
 static void engine_refine_now(dock_ctx *ctx, Engine &E)
 {
-    std::vector<JobP> batch;
-    for (auto &j : E.refine_wait)
-        if (j->stage != JOB_DONE) batch.push_back(j);   // an error may have ended some meanwhile
-    E.refine_wait.clear();
-    if (!batch.empty()) jobs_refine(ctx, E, batch);
-    E.active.erase(std::remove_if(E.active.begin(), E.active.end(),
-                                  [](const JobP &j) { return j->stage == JOB_DONE; }),
-                   E.active.end());
+    if (E.rbusy) return;
+    std::vector<JobP> batch, rest;
+    for (auto &j : E.refine_wait) {
+        if (j->stage == JOB_DONE) continue;   // an error may have ended some meanwhile
+        if (batch.empty() || memcmp(&j->p, &batch[0]->p, sizeof(dock_params)) == 0) batch.push_back(j);
+        else rest.push_back(j);
+    }
+    E.refine_wait.swap(rest);
+    if (!E.refine_wait.empty()) E.refine_since = Clock::now();
+    if (batch.empty()) return;
+    std::vector<RefGroup> groups;
+    std::vector<dock_candidate> cands;
+    for (auto &jp : batch) {
+        groups.push_back(RefGroup{jp->ob, jp->sw, (int)cands.size(), (int)jp->cands.size()});
+        cands.insert(cands.end(), jp->cands.begin(), jp->cands.end());
+    }
+    const size_t need = cands.size() * REF_ST;
+    dock_status s = DOCK_OK;
+    if (need > E.rhost_n) {
+        if (E.rhost) cudaFreeHost(E.rhost);
+        E.rhost = nullptr;
+        E.rhost_n = 0;
+        cudaError_t e = cudaMallocHost((void **)&E.rhost, need * sizeof(double));
+        if (e != cudaSuccess) s = cuda_fail(ctx, e, "pinned host buffer for the refinement");
+        else E.rhost_n = need;
+    }
+    if (s == DOCK_OK) s = refine_launch(ctx, E.rb, groups, cands.data(), &batch[0]->p, E.rstream, E.rhost);
+    if (s == DOCK_OK) {
+        cudaError_t e = cudaEventRecord(E.rdone, E.rstream);
+        if (e != cudaSuccess) s = cuda_fail(ctx, e, "recording the refinement");
+    }
+    if (s != DOCK_OK) {
+        cudaStreamSynchronize(E.rstream);
+        for (auto &jp : batch) job_finish(ctx, E, jp, s);
+        E.active.erase(std::remove_if(E.active.begin(), E.active.end(),
+                                      [](const JobP &j) { return j->stage == JOB_DONE; }),
+                       E.active.end());
+        return;
+    }
+    E.rbusy = true;
+    E.rjobs = batch;
+    E.rgroups = groups;
+    E.rparams = batch[0]->p;
 }
 
 static void engine_refine_if_due(dock_ctx *ctx, Engine &E)
@@ -2193,6 +2279,7 @@ static bool engine_step(dock_ctx *ctx)
             ++i;
         }
     }
+    engine_refine_collect(ctx, E, false);
     bool did = false;
     for (;;) {
         JobP j;
@@ -2239,7 +2326,11 @@ static bool engine_step(dock_ctx *ctx)
         for (auto &j : E.active)
             if (j->issued < j->s1 - j->s0 && (pick == 0 || j->ob->N < pick)) pick = j->ob->N;
     if (pick == 0) {
-        // no search work: refine whatever waits
+        // no search work: finish the refinement in flight, refine whatever waits
+        if (E.rbusy) {
+            engine_refine_collect(ctx, E, true);
+            return true;
+        }
         if (!E.refine_wait.empty()) {
             engine_refine_now(ctx, E);
             return true;
@@ -2363,6 +2454,7 @@ static void engine_shutdown(dock_ctx *ctx)
         E->cv_work.notify_all();
     }
     if (E->worker.joinable()) E->worker.join();
+    if (E->rbusy) cudaStreamSynchronize(E->rstream);   // its jobs end cancelled below
     fail(ctx, DOCK_E_CANCELLED, "context destroyed");
     for (auto &j : E->active) job_finish(ctx, *E, j, DOCK_E_CANCELLED);
     std::deque<JobP> q;
@@ -2373,6 +2465,13 @@ static void engine_shutdown(dock_ctx *ctx)
     for (auto &j : q) job_finish(ctx, *E, j, DOCK_E_CANCELLED);
     dfree(ctx, E->reqtab, sizeof(ReqDev) * ENGINE_SLOTS);
     for (auto &ev : E->pass_ev) if (ev) cudaEventDestroy(ev);
+    if (E->rstream) {
+        cudaStreamSynchronize(E->rstream);
+        cudaStreamDestroy(E->rstream);
+    }
+    if (E->rdone) cudaEventDestroy(E->rdone);
+    if (E->rhost) cudaFreeHost(E->rhost);
+    free_refbufs(E->rb);
     delete E;
     ctx->eng = nullptr;
 }
@@ -2383,6 +2482,7 @@ static void engine_drop_handle(dock_ctx *ctx, const dock_object *ob, const dock_
 {
     Engine *E = ctx->eng;
     if (!E) return;
+    engine_refine_collect(ctx, *E, true);   // the batch in flight may read the handle
     auto uses = [&](const JobP &j) { return (ob && j->ob == ob) || (sw && j->sw == sw); };
     std::vector<JobP> drop;
     {

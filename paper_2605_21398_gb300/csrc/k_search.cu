@@ -37,6 +37,16 @@ __device__ __forceinline__ void cp_async8(void *smem_dst, const void *gmem_src)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+// wait until at most n (0..3) of this thread's committed groups are pending
+__device__ __forceinline__ void cp_async_wait_pending(int n)
+{
+    switch (n) {
+    case 0: asm volatile("cp.async.wait_group 0;\n" ::: "memory"); break;
+    case 1: asm volatile("cp.async.wait_group 1;\n" ::: "memory"); break;
+    case 2: asm volatile("cp.async.wait_group 2;\n" ::: "memory"); break;
+    default: asm volatile("cp.async.wait_group 3;\n" ::: "memory"); break;
+    }
+}
 
 __device__ void quat_to_mat_exact(const double *q, double *R)
 {
@@ -822,30 +832,39 @@ __device__ __forceinline__ void plane_body(const float2 *Zp, const float2 *tw_g,
     for (int i = threadIdx.x; i < M; i += blockDim.x) { float2 w = tw_g[i]; tw[i] = cmake(w.x, w.y); }
     __syncthreads();
     // phase 1: this CTA's packed columns, all ky, are copied asynchronously
-    // into pb (every load in flight at once), column 0 is packed with the
-    // Nyquist column (W0 + i W_{M/2}), and each column is inverse transformed
-    // along y in place: pb[ky][col] -> pb[y][col].
+    // into pb, one copy group per round of COLS columns (all in flight at
+    // once; a round starts as soon as its own group has landed), column 0 is
+    // packed with the Nyquist column (W0 + i W_{M/2}), and each column is
+    // inverse transformed along y in place: pb[ky][col] -> pb[y][col].
     {
+        constexpr int NR = (PC + COLS - 1) / COLS;
+        static_assert(NR <= 4, "copy groups");
         cf *nyq = tw + M;
-        for (int e = threadIdx.x; e < M * PC; e += blockDim.x) {
-            int ky = e / PC, pl = e % PC;
-            cp_async8(&pb[ky * PP + pl], &Zp[ky * P + rank * PC + pl]);
-        }
-        if (rank == 0)
-            for (int ky = threadIdx.x; ky < M; ky += blockDim.x) cp_async8(&nyq[ky], &Zp[ky * P + H]);
-        cp_async_commit();
-        cp_async_wait_all();
-        __syncthreads();
-        if (rank == 0)
-            for (int ky = threadIdx.x; ky < M; ky += blockDim.x) {
-                cf a = pb[ky * PP], u = nyq[ky];
-                pb[ky * PP] = cmake(a.x - u.y, a.y + u.x);   // + i * Z[ky][M/2]
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const int p0 = r * COLS, nc = (PC - p0) < COLS ? (PC - p0) : COLS;
+            for (int e = threadIdx.x; e < M * nc; e += blockDim.x) {
+                int ky = e / nc, pl = p0 + e % nc;
+                cp_async8(&pb[ky * PP + pl], &Zp[ky * P + rank * PC + pl]);
             }
-        __syncthreads();
+            if (r == 0 && rank == 0)
+                for (int ky = threadIdx.x; ky < M; ky += blockDim.x) cp_async8(&nyq[ky], &Zp[ky * P + H]);
+            cp_async_commit();
+        }
         const int c = threadIdx.x % COLS, j = threadIdx.x / COLS;
-        for (int p0 = 0; p0 < PC; p0 += COLS) {
-            int pl = p0 + c;                   // local packed column
-            bool act = pl < PC;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            cp_async_wait_pending(NR - 1 - r);
+            __syncthreads();
+            if (r == 0 && rank == 0) {
+                for (int ky = threadIdx.x; ky < M; ky += blockDim.x) {
+                    cf a = pb[ky * PP], u = nyq[ky];
+                    pb[ky * PP] = cmake(a.x - u.y, a.y + u.x);   // + i * Z[ky][M/2]
+                }
+                __syncthreads();
+            }
+            const int pl = r * COLS + c;       // local packed column
+            const bool act = pl < PC;
             cf v[E];
 #pragma unroll
             for (int s = 0; s < E; ++s) v[s] = act ? pb[in_index<M>(j, s) * PP + pl] : cmake(0.f, 0.f);
@@ -866,9 +885,20 @@ __device__ __forceinline__ void plane_body(const float2 *Zp, const float2 *tw_g,
         cg::cluster_group cl = cg::this_cluster();
         cl.sync();
         const cf *peer = cl.map_shared_rank(pb, rank ^ 1);
-        for (int e = threadIdx.x; e < rows * PC; e += blockDim.x) {
-            int r = e / PC, col = e % PC;
-            stg[r * PP + col] = peer[(row0 + r) * PP + col];
+        // every thread's loads in flight at once, then the stores (a load ->
+        // store chain per element would wait one remote latency each)
+        constexpr int PER = (M / CL) * PC / C::NT;
+        static_assert((M / CL) * PC % C::NT == 0, "peer copy split");
+        cf tmp[PER];
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int e = threadIdx.x + k * C::NT, r = e / PC, col = e % PC;
+            tmp[k] = peer[(row0 + r) * PP + col];
+        }
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int e = threadIdx.x + k * C::NT, r = e / PC, col = e % PC;
+            stg[r * PP + col] = tmp[k];
         }
         cl.sync();
         xb2 = pb + (rank ^ 1) * rows * PP;
