@@ -885,20 +885,24 @@ __device__ __forceinline__ void plane_body(const float2 *Zp, const float2 *tw_g,
         cg::cluster_group cl = cg::this_cluster();
         cl.sync();
         const cf *peer = cl.map_shared_rank(pb, rank ^ 1);
-        // every thread's loads in flight at once, then the stores (a load ->
-        // store chain per element would wait one remote latency each)
-        constexpr int PER = (M / CL) * PC / C::NT;
-        static_assert((M / CL) * PC % C::NT == 0, "peer copy split");
-        cf tmp[PER];
+        // the peer's rows [row0, row0 + rows) are one contiguous, 16-byte
+        // aligned block of its pb (padding included): copy it verbatim into
+        // stg with 16-byte loads, every thread's loads in flight at once
+        constexpr int NV = (M / CL) * PP * (int)sizeof(cf) / 16;
+        constexpr int PER = (NV + C::NT - 1) / C::NT;
+        static_assert((M / CL) * PP * sizeof(cf) % 16 == 0 && (M * PP * sizeof(cf)) % 16 == 0, "16-byte copy");
+        const float4 *src4 = reinterpret_cast<const float4 *>(peer + row0 * PP);
+        float4 *dst4 = reinterpret_cast<float4 *>(stg);
+        float4 tmp[PER];
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
-            const int e = threadIdx.x + k * C::NT, r = e / PC, col = e % PC;
-            tmp[k] = peer[(row0 + r) * PP + col];
+            const int v = threadIdx.x + k * C::NT;
+            if (v < NV) tmp[k] = src4[v];
         }
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
-            const int e = threadIdx.x + k * C::NT, r = e / PC, col = e % PC;
-            stg[r * PP + col] = tmp[k];
+            const int v = threadIdx.x + k * C::NT;
+            if (v < NV) dst4[v] = tmp[k];
         }
         cl.sync();
         xb2 = pb + (rank ^ 1) * rows * PP;
