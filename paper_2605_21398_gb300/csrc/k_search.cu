@@ -948,17 +948,31 @@ __device__ __forceinline__ void plane_body(const float2 *Zp, const float2 *tw_g,
             }
             fft_column<H, true, 2>(v, j, xb2, rowl, RPR, tw);
             if (act) {
+                const uint32_t rowbase = ((uint32_t)zc * M + (uint32_t)y) * M;
+                if (EXPORT) {
 #pragma unroll
-                for (int s = 0; s < EH; ++s) {
-                    int n = out_index<H>(j, s);
-                    uint32_t base = ((uint32_t)zc * M + (uint32_t)y) * M + 2u * n;
-                    if (EXPORT) {
+                    for (int s = 0; s < EH; ++s) {
+                        const uint32_t base = rowbase + 2u * out_index<H>(j, s);
                         Cout[base] = v[s].x;
                         Cout[base + 1] = v[s].y;
                     }
-                    float a0 = v[s].x, a1 = v[s].y;
-                    if (a0 > best || (a0 == best && base < bidx)) { best = a0; bidx = base; }
-                    if (a1 > best || (a1 == best && base + 1 < bidx)) { best = a1; bidx = base + 1; }
+                }
+                // the thread's maximum first; the canvas index (lowest among
+                // equal values) only for the values that reach it
+                float m = v[0].x;
+#pragma unroll
+                for (int s = 0; s < EH; ++s) m = fmaxf(m, fmaxf(v[s].x, v[s].y));
+                if (m >= best) {
+                    uint32_t bi = 0xFFFFFFFFu;
+#pragma unroll
+                    for (int s = 0; s < EH; ++s) {
+                        if (v[s].x == m || v[s].y == m) {
+                            const uint32_t base = rowbase + 2u * out_index<H>(j, s);
+                            if (v[s].x == m) bi = min(bi, base);
+                            if (v[s].y == m) bi = min(bi, base + 1u);
+                        }
+                    }
+                    if (m > best || bi < bidx) { best = m; bidx = bi; }
                 }
             }
             __syncthreads();
