@@ -239,6 +239,17 @@ __device__ __forceinline__ int out_index(int t, int slot)
     return (j / NS) * NS * R + (j % NS) + r * NS;
 }
 
+// True when register slot s of the first stage reads an index in [0, M/2):
+// with one butterfly per thread (E = R0) and M / R0 = T, slot s reads
+// j + T s, which is below M/2 exactly when s < R0/2, whatever the thread j.
+// Zero-padded inputs (the upper half) then need no load.
+template <int M>
+__device__ __forceinline__ constexpr bool slot_in_lower_half(int s)
+{
+    static_assert(Plan<M>::E == Plan<M>::R(0) && M / Plan<M>::R(0) == Plan<M>::T, "first-stage layout");
+    return s < Plan<M>::R(0) / 2;
+}
+
 // Input index of register slot (b, r) for the first stage.
 template <int M>
 __device__ __forceinline__ int in_index(int t, int slot)

@@ -598,7 +598,7 @@ k_fwd2d(int P, const uint32_t *bits_g, float2 *Y, const float2 *tw_g, const floa
 #pragma unroll
         for (int s = 0; s < E; ++s) {
             int yy = in_index<M>(j, s);
-            v[s] = (yy < N) ? X[yy * H + p0 + c] : cmake(0.f, 0.f);
+            v[s] = slot_in_lower_half<M>(s) ? X[yy * H + p0 + c] : cmake(0.f, 0.f);   // yy < N
         }
         fft_column<M, false>(v, j, xb, c, COLS, tw);
         const int kx = p0 + c;
@@ -746,7 +746,7 @@ k_zpass(int P, int B, int group, const float2 *Y, const RotRec *rots, const ReqD
 #pragma unroll
         for (int s = 0; s < E; ++s) {
             int z = in_index<M>(j, s);
-            v[s] = (z < N) ? src[z * COLS + c] : cmake(0.f, 0.f);
+            v[s] = slot_in_lower_half<M>(s) ? src[z * COLS + c] : cmake(0.f, 0.f);   // z < N
         }
         fft_column<M, false>(v, j, xb, c, COLS, tw);
         // forward output slot (bb, r) holds kz = j + (M/E)(bb + (E/R_LAST) r)
