@@ -252,7 +252,9 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": "large128: 128^3 lattice at 0.15 mm, 5000 probe poses, 65k-triangle star object",
+            "config": {"workload": "large128: 128^3 lattice at 0.15 mm (canvas 256^3), 5000 probe poses on 3 raster "
+                                   "segments (20% labels flipped, 0.02 mm noise), 65k-triangle star object; the oracle's "
+                                   "per-rotation search (sweep + FP64 FFT correlation + argmax) on sampled rotations",
                        "sample": "%d rotations per step" % per_step},
             "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle",
                              "sample": "%d random rotations per step, sweep + FFT correlation + argmax" % per_step},
