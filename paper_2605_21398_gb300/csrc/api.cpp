@@ -48,6 +48,8 @@ struct RefBufs {
     size_t cands_n = 0;
     RefineDev *dev = nullptr;   // per-request refinement tables of a launch
     size_t dev_n = 0;
+    int32_t *hint = nullptr;    // per-query witness triangle of the previous evaluation
+    size_t hint_n = 0;
     int32_t *grp = nullptr;     // candidate -> request
     size_t grp_n = 0;
 };
@@ -60,6 +62,7 @@ static void free_refbufs(RefBufs &b)
     cudaFree(b.cands);
     cudaFree(b.dev);
     cudaFree(b.grp);
+    cudaFree(b.hint);
     b = RefBufs();
 }
 
@@ -1655,18 +1658,23 @@ static dock_status refine_loop(dock_ctx *ctx, RefBufs &rb, int K, int nblk, int 
     double prm[6] = {p->lambda, p->mu, p->step_t, p->step_r, p->b_t, p->b_r};
     CK(ctx, cudaMemcpyAsync(rb.prm, prm, sizeof(prm), cudaMemcpyHostToDevice, st));
     CandF *cf = (CandF *)rb.cands;
+    dock_status s;
+    if ((s = ensure(ctx, (void **)&rb.hint, &rb.hint_n, (size_t)K * nblk * 128, sizeof(int32_t))) != DOCK_OK) return s;
+    CK(ctx, cudaMemsetAsync(rb.hint, 0xFF, sizeof(int32_t) * (size_t)K * nblk * 128, st));   // -1: no hint yet
     CK(ctx, launch_refine_solve(K, nblk * REF_WARPS, rb.state, rb.acc, rb.prm, 0, cf, st));
     for (int it = 0; it < iters; ++it) {
         {
             Prof pr(ctx, "refine_eval", st);
-            CK(ctx, launch_refine_eval(rb.dev, rb.grp, K, nblk, cf, rb.acc, true, nullptr, nullptr, nullptr, st));
+            CK(ctx, launch_refine_eval(rb.dev, rb.grp, K, nblk, cf, rb.acc, true, nullptr, nullptr, nullptr, st,
+                                       rb.hint));
         }
         Prof pr(ctx, "refine_solve", st);
         CK(ctx, launch_refine_solve(K, nblk * REF_WARPS, rb.state, rb.acc, rb.prm, 1, cf, st));
     }
     {
         Prof pr(ctx, "refine_eval", st);
-        CK(ctx, launch_refine_eval(rb.dev, rb.grp, K, nblk, cf, rb.acc, false, nullptr, nullptr, nullptr, st));
+        CK(ctx, launch_refine_eval(rb.dev, rb.grp, K, nblk, cf, rb.acc, false, nullptr, nullptr, nullptr, st,
+                                   rb.hint));
     }
     CK(ctx, launch_refine_solve(K, nblk * REF_WARPS, rb.state, rb.acc, rb.prm, 2, cf, st));
     return DOCK_OK;

@@ -112,9 +112,11 @@ size_t cand_bytes();
 constexpr int REF_ST = 24;    // doubles of refinement state per candidate
 constexpr int REF_NACC = 28;  // accumulated J, grad (6), Gauss-Newton upper triangle (21)
 constexpr int REF_WARPS = 4;  // warps per block of the refinement evaluation (one partial sum each)
+// hints (optional, K x nblk x 128): each query's witness triangle, read as a
+// starting bound and overwritten; -1 = none.
 cudaError_t launch_refine_eval(const RefineDev *Dt, const int32_t *grp, int K, int nblk, const CandF *cands,
                                double *acc_part, bool grad, float *dist_out, float *wit_out, float *nrm_out,
-                               cudaStream_t st);
+                               cudaStream_t st, int32_t *hints = nullptr);
 cudaError_t launch_refine_solve(int K, int nblk, double *state, const double *acc_part, const double *prm, int mode,
                                 CandF *cands, cudaStream_t st);
 cudaError_t launch_set_xi(int B, const float *xi, double *state, cudaStream_t st);

@@ -336,8 +336,8 @@ __device__ __forceinline__ float node_sdf(const RefineDev &D, const float *A, co
 // poses of a trajectory run in lockstep instead of serialising their
 // traversals.  Returns the lane's triangle index or -1; fills d*, the local
 // witness and the local contact normal.
-__device__ int dist_query(const RefineDev &D, const float *A, const float *bvec, bool valid, float *d_out, float *xw,
-                          float *nl)
+__device__ int dist_query(const RefineDev &D, const float *A, const float *bvec, bool valid, int hint, float *d_out,
+                          float *xw, float *nl)
 {
     int sn[64];
     float sl[64];
@@ -350,6 +350,29 @@ __device__ int dist_query(const RefineDev &D, const float *A, const float *bvec,
     float best = INFINITY;
     int bt = -1;
     float bx[3] = {0.f, 0.f, 0.f};
+    // Start from the hint (the triangle that held this query's minimum at the
+    // previous evaluation, if it still passes Eq. (21)): its minimum bounds
+    // d* from the first node on.  The result does not depend on the order in
+    // which triangles are met, so the hint changes only the work.
+    int seeded = -1;
+    if (valid && hint >= 0) {
+        const float *ts = D.tri_sphere + 4 * hint;
+        if (node_sdf(D, A, bvec, ts) < ts[3] + eps) {
+            float lv[3][3], fv[3];
+            local_vertices(D, hint, A, bvec, lv);
+            for (int m = 0; m < 3; ++m) {
+                fv[m] = sdf_cyl(lv[m][0], lv[m][1], lv[m][2], D.r, D.L, nullptr);
+                UB = fminf(UB, fv[m]);
+            }
+            float u, v, dk;
+            if (!tri_min_shortcut(lv[0], lv[1], lv[2], fv, D.r, D.L, &dk, &u, &v))
+                dk = tri_min_search(lv[0], lv[1], lv[2], D.r, D.L, D.tri_iters, &u, &v);
+            best = dk;
+            bt = seeded = hint;
+            const float w0 = 1.f - u - v;
+            for (int c = 0; c < 3; ++c) bx[c] = fmaf(w0, lv[0][c], fmaf(u, lv[1][c], v * lv[2][c]));
+        }
+    }
     {
         int sp = 0;
         const float lim0 = valid ? INFINITY : -INFINITY;
@@ -378,7 +401,7 @@ __device__ int dist_query(const RefineDev &D, const float *A, const float *bvec,
                     const float *ts = D.tri_sphere + 4 * t;
                     const float ft = node_sdf(D, A, bvec, ts);
                     const float limt = valid ? fminf(UB, best) : -INFINITY;
-                    bool cand = valid && ft < ts[3] + eps && !(ft - ts[3] > limt);   // Eq. (21)
+                    bool cand = valid && t != seeded && ft < ts[3] + eps && !(ft - ts[3] > limt);   // Eq. (21)
                     if (!__any_sync(0xFFFFFFFFu, cand)) continue;
                     float lv[3][3];
                     local_vertices(D, t, A, bvec, lv);
@@ -477,7 +500,7 @@ __device__ int dist_query(const RefineDev &D, const float *A, const float *bvec,
 template <bool GRAD>
 __global__ void __launch_bounds__(128, 6)
 k_refine_eval(const RefineDev *Dt, const int32_t *grp, const CandF *cands, double *acc_part, float *dist_out,
-              float *wit_out, float *nrm_out)
+              float *wit_out, float *nrm_out, int32_t *hints)
 {
     const int c = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;
     // the candidate's request (object mesh, trajectory, probe, parameters)
@@ -498,7 +521,11 @@ k_refine_eval(const RefineDev *Dt, const int32_t *grp, const CandF *cands, doubl
         float tp[3] = {pr.tf[0] - cf.p[0], pr.tf[1] - cf.p[1], pr.tf[2] - cf.p[2]};
         for (int a = 0; a < 3; ++a) bvec[a] = fmaf(cf.R[0 * 3 + a], tp[0], fmaf(cf.R[1 * 3 + a], tp[1], cf.R[2 * 3 + a] * tp[2]));
         float d, xl[3], nl[3];
-        int bt = dist_query(D, A, bvec, valid, &d, xl, nl);
+        // hints[c][i]: the query's witness triangle of the previous evaluation (-1: none)
+        int32_t *hp = hints ? hints + (size_t)c * gridDim.x * blockDim.x + i : nullptr;
+        const int hint = (hp && valid) ? *hp : -1;
+        int bt = dist_query(D, A, bvec, valid, hint, &d, xl, nl);
+        if (hp && valid) *hp = bt;
         float n[3] = {0.f, 0.f, 0.f}, w[3] = {0.f, 0.f, 0.f};
         if (bt >= 0) {
             for (int a = 0; a < 3; ++a) {
@@ -693,11 +720,11 @@ __global__ void k_refine_solve(int K, int nblk, double *state, const double *acc
 // ---------------------------------------------------------------------------
 cudaError_t launch_refine_eval(const RefineDev *Dt, const int32_t *grp, int K, int nblk, const CandF *cands,
                                double *acc_part, bool grad, float *dist_out, float *wit_out, float *nrm_out,
-                               cudaStream_t st)
+                               cudaStream_t st, int32_t *hints)
 {
     dim3 grid(nblk, K);
-    if (grad) k_refine_eval<true><<<grid, 128, 0, st>>>(Dt, grp, cands, acc_part, dist_out, wit_out, nrm_out);
-    else k_refine_eval<false><<<grid, 128, 0, st>>>(Dt, grp, cands, acc_part, dist_out, wit_out, nrm_out);
+    if (grad) k_refine_eval<true><<<grid, 128, 0, st>>>(Dt, grp, cands, acc_part, dist_out, wit_out, nrm_out, hints);
+    else k_refine_eval<false><<<grid, 128, 0, st>>>(Dt, grp, cands, acc_part, dist_out, wit_out, nrm_out, hints);
     return cudaGetLastError();
 }
 
