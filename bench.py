@@ -324,6 +324,10 @@ def main():
     ob = ctx.object_grid(w.obj.verts, w.obj.tris, w.h, w.N)
     obj_setup_ms = 1000 * (time.perf_counter() - t0)
     sw = ctx.sweep_grid(w.poses_world, w.radius, w.length, w.h, w.N, contact=w.labels)
+    # launch shape of the search kernels for this lattice side, picked by the
+    # autotuner (once per lattice side, before the warm-up; results do not
+    # depend on it)
+    tuning = ctx.autotune(ob, sw, n_rot=512)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
 
     def step():
@@ -438,7 +442,8 @@ def main():
                                    % (args.n_global, args.n_local, TOP_K),
                        "l2": "inputs larger than L2 (per-batch FFT intermediates ~4 GB) and a 256 MB L2 flush "
                              "before every step",
-                       "parallelism": "replicas" if ws > 1 else "single"},
+                       "parallelism": "replicas" if ws > 1 else "single",
+                       "search_launch_shape": {k: tuning[k] for k in ("batch", "group", "vox_blocks")}},
             "roofline": roofline, "model_roofline_frac": round(model_frac, 4),
             "model_bytes_per_eval": model_bytes_per_eval(w.N),
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "kernels": kernels,
