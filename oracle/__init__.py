@@ -14,7 +14,10 @@ adds the steps that are plain definitions or textbook library primitives:
 * translation from the peak, Eq. (8), composed with the sampled rotation;
 * orientation samplers, Sec. IV-C: Super-Fibonacci, a Hopf-coordinate map of a
   Halton sequence, and GeoBall-SF (Algorithm 1, Eq. (10)-(12));
-* the per-rotation argmax and the global top-K.
+* the per-rotation argmax and the global top-K;
+* the label-aware score (Sec. I and IV-A: trajectories hold contact and
+  non-contact evidence): voxels swept by a contact pose score O, voxels swept
+  only by non-contact poses score min(O, 0), the penetration part alone.
 
 Parity unpinned: the Super-Fibonacci constants beyond the paper's
 nearest-neighbour statistic (Sec. VI: 8.0 deg at n = 20000), and the
@@ -137,15 +140,34 @@ def sweep_origin(poses, q, h, N):
     return o
 
 
-def sweep_grid(poses, q, h, N, r, L):
-    """S_R[jz, jy, jx] (uint8) and its origin o_s,R for rotation q."""
+def sweep_grid(poses, q, h, N, r, L, use=None):
+    """S_R[jz, jy, jx] (uint8) and its origin o_s,R for rotation q.  With
+    `use` (one flag per pose) only the flagged poses are swept; the origin
+    still follows all poses."""
     P = _c64(poses)
     q = _c64(q)
     S = np.empty((N, N, N), dtype=np.uint8)
     o = np.empty(3)
-    lib().orc_sweep_grid(_p(P), ctypes.c_int64(len(P)), _p(q), ctypes.c_double(h), ctypes.c_int32(N),
-                         ctypes.c_double(r), ctypes.c_double(L), _p(o), _p(S, _u8p))
+    u = None
+    if use is not None:
+        u = np.ascontiguousarray(use, dtype=np.uint8)
+        assert u.shape == (len(P),)
+    lib().orc_sweep_grid_sel(_p(P), ctypes.c_int64(len(P)), None if u is None else _p(u, _u8p), _p(q),
+                             ctypes.c_double(h), ctypes.c_int32(N), ctypes.c_double(r), ctypes.c_double(L),
+                             _p(o), _p(S, _u8p))
     return S, o
+
+
+def sweep_grids_by_label(poses, labels, q, h, N, r, L):
+    """Label-aware split of the sweep (Sec. I and IV-A: trajectories carry
+    contact and non-contact evidence).  S_c: voxels swept by a contact pose;
+    S_n: voxels swept only by non-contact poses (S_n and S_c are disjoint,
+    their union is the plain S_R).  Both on the lattice of all poses."""
+    lab = np.asarray(labels).astype(bool)
+    S_c, o = sweep_grid(poses, q, h, N, r, L, use=lab)
+    S_any, _ = sweep_grid(poses, q, h, N, r, L, use=~lab)
+    S_n = (S_any & (1 - S_c)).astype(np.uint8)
+    return S_c, S_n, o
 
 
 # ----------------------------------------------------------------------------
@@ -215,6 +237,33 @@ def top_k(scores, k):
     scores = np.asarray(scores)
     order = np.lexsort((np.arange(len(scores)), -scores))
     return order[:k]
+
+
+def penetration_part(O):
+    """min(O, 0): the interior penalty of Eq. (1)-(4) without the near-surface
+    reward.  A pose that did not touch the object may not overlap it, but its
+    approach to the surface earns nothing."""
+    return np.minimum(O, 0.0)
+
+
+def correlate_label_aware(O, S_c, S_n, M, fft=True):
+    """C = corr(O, S_c) + corr(min(O, 0), S_n): voxels reached by a contact
+    pose score O (Eq. (7)), voxels reached only by non-contact poses score the
+    penetration part alone."""
+    f = correlate_fft if fft else correlate_direct
+    return f(O, S_c, M) + f(penetration_part(O), S_n, M)
+
+
+def search_label_aware(O, o_o, poses, labels, quats, h, N, r, L, fft=True):
+    """`search` with the label-aware score (`correlate_label_aware`)."""
+    M = canvas_size(N)
+    out = []
+    for q in quats:
+        S_c, S_n, o_s = sweep_grids_by_label(poses, labels, q, h, N, r, L)
+        C = correlate_label_aware(O, S_c, S_n, M, fft=fft)
+        sc, idx = peak(C)
+        out.append(dict(score=sc, idx=idx, dk=canvas_shift(idx, M, N), o_s=o_s, C=C, S_c=S_c, S_n=S_n))
+    return out
 
 
 def search(O, o_o, poses, quats, h, N, r, L, fft=True):

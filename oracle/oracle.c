@@ -16,6 +16,8 @@
  *                        distance, sign = parity of +x ray crossings.
  *   orc_sweep_grid       Sec. IV-A.2, Eq. (5)-(6): binary swept occupancy of the
  *                        probe along the trajectory, on a lattice rotated by R.
+ *   orc_sweep_grid_sel   the same over a subset of the poses (contact or
+ *                        non-contact labels), on the lattice of all poses.
  *   orc_probe_sdf        Sec. V-B: flat-ended cylinder SDF f_p and its gradient.
  *   orc_tri_min          Sec. V-B: minimum of f_p over a triangle (bisection
  *                        inside golden-section search; see the function).
@@ -328,8 +330,14 @@ ORC_API void orc_sweep_origin(const double *poses, int64_t P, const double *q, d
     }
 }
 
-ORC_API void orc_sweep_grid(const double *poses, int64_t P, const double *q, double h, int32_t N,
-                            double r, double L, double *origin, uint8_t *S)
+/*
+ * Eq. (5)-(6) over the poses i with use[i] != 0 (all poses when use is NULL);
+ * the lattice origin always follows the mean tip of ALL P poses, so the grids
+ * of two pose subsets share one lattice (the label-aware score splits the
+ * sweep by contact label this way).
+ */
+ORC_API void orc_sweep_grid_sel(const double *poses, int64_t P, const uint8_t *use, const double *q, double h,
+                                int32_t N, double r, double L, double *origin, uint8_t *S)
 {
     double R[9];
     orc_quat_to_mat(q, R);
@@ -337,6 +345,7 @@ ORC_API void orc_sweep_grid(const double *poses, int64_t P, const double *q, dou
     memset(S, 0, (size_t)N * N * N);
     double r2 = r * r;
     for (int64_t i = 0; i < P; ++i) {
+        if (use && !use[i]) continue;
         double Ri[9];
         orc_quat_to_mat(poses + 7 * i, Ri);
         const double *t = poses + 7 * i + 4;
@@ -367,6 +376,12 @@ ORC_API void orc_sweep_grid(const double *poses, int64_t P, const double *q, dou
                     if (l0 * l0 + l1 * l1 <= r2 && 0.0 <= l2 && l2 <= L) S[idx] = 1;
                 }
     }
+}
+
+ORC_API void orc_sweep_grid(const double *poses, int64_t P, const double *q, double h, int32_t N,
+                            double r, double L, double *origin, uint8_t *S)
+{
+    orc_sweep_grid_sel(poses, P, NULL, q, h, N, r, L, origin, S);
 }
 
 /* ------------------------------------------------------------------ */

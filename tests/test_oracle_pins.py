@@ -257,6 +257,87 @@ def test_planted_lattice_pose_is_recovered_within_a_voxel(workload):
 
 
 # --------------------------------------------------------------------------
+# Label-aware score: contact poses score O, non-contact poses min(O, 0)
+# --------------------------------------------------------------------------
+
+def test_label_aware_with_all_contact_labels_is_the_plain_search(workload):
+    w = workload("tiny32")
+    Og, o_o, _, _ = O.object_grid(w.obj.verts, w.obj.tris, w.h, w.N)
+    qs = [w.gt_q, synth.random_quat(np.random.default_rng(3))]
+    ones = np.ones(len(w.poses_world), dtype=np.uint8)
+    la = O.search_label_aware(Og, o_o, w.poses_world, ones, qs, w.h, w.N, w.radius, w.length)
+    pl = O.search(Og, o_o, w.poses_world, qs, w.h, w.N, w.radius, w.length)
+    for a, b in zip(la, pl):
+        assert not a["S_n"].any() and np.array_equal(a["S_c"], b["S"])
+        assert np.array_equal(a["C"], b["C"]) and a["idx"] == b["idx"]
+
+
+def test_label_split_partitions_the_plain_sweep(workload):
+    w = workload("tiny32")
+    rng = np.random.default_rng(11)
+    lab = (rng.random(len(w.poses_world)) < 0.6).astype(np.uint8)
+    for q in synth.random_quat(rng, 2):
+        S, o = O.sweep_grid(w.poses_world, q, w.h, w.N, w.radius, w.length)
+        S_c, S_n, o2 = O.sweep_grids_by_label(w.poses_world, lab, q, w.h, w.N, w.radius, w.length)
+        assert np.array_equal(o, o2)
+        assert not (S_c & S_n).any() and np.array_equal(S_c | S_n, S)
+        assert S_c.any() and S_n.any()
+
+
+def test_label_aware_score_is_the_per_voxel_best_over_covering_poses():
+    # Brute force from the definition: a voxel j of the swept lattice, placed
+    # over object voxel k = j - dk, earns O[k] if some contact pose covers it,
+    # else min(O[k], 0) if some non-contact pose covers it, else nothing; i.e.
+    # the largest value any covering pose allows.  Each pose is swept alone.
+    rng = np.random.default_rng(21)
+    N, h, r, L = 6, 1.0, 0.9, 2.5
+    M = O.canvas_size(N)
+    P = 5
+    poses = np.zeros((P, 7))
+    poses[:, :4] = synth.random_quat(rng, P)
+    poses[:, 4:] = rng.uniform(-1.5, 1.5, size=(P, 3))
+    lab = np.array([1, 0, 0, 1, 0], dtype=np.uint8)
+    Og = rng.uniform(-50, 1, size=(N, N, N)) * (rng.random((N, N, N)) < 0.7)
+    q = synth.random_quat(rng)
+    cover = np.stack([O.sweep_grid(poses, q, h, N, r, L, use=(np.arange(P) == i).astype(np.uint8))[0]
+                      for i in range(P)]).astype(bool)
+    assert cover[lab == 1].any() and (cover[lab == 0].any(0) & ~cover[lab == 1].any(0)).any()
+    Opad = np.zeros((M, M, M))
+    Opad[:N, :N, :N] = Og
+    jz, jy, jx = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
+    C = np.zeros((M, M, M))
+    for cz in range(M):
+        for cy in range(M):
+            for cx in range(M):
+                ok = Opad[(jz - cz) % M, (jy - cy) % M, (jx - cx) % M]
+                vals = np.where(lab[:, None, None, None] == 1, ok[None], np.minimum(ok, 0.0)[None])
+                best = np.where(cover, vals, -np.inf).max(0)
+                C[cz, cy, cx] = best[np.isfinite(best)].sum()
+    S_c, S_n, _ = O.sweep_grids_by_label(poses, lab, q, h, N, r, L)
+    Cf = O.correlate_label_aware(Og, S_c, S_n, M)
+    assert np.max(np.abs(Cf - C)) <= 1e-12 * max(1.0, np.max(np.abs(C)))
+    Cd = O.correlate_label_aware(Og, S_c, S_n, M, fft=False)      # summation order differs
+    assert np.max(np.abs(Cd - C)) <= 1e-12 * max(1.0, np.max(np.abs(C)))
+
+
+def test_label_aware_score_bounds(workload):
+    # min(O, 0) <= O: relabelling a pose non-contact can only lower a score;
+    # with every pose non-contact nothing is rewarded (C <= 0).
+    w = workload("tiny32")
+    Og, o_o, _, _ = O.object_grid(w.obj.verts, w.obj.tris, w.h, w.N)
+    rng = np.random.default_rng(13)
+    lab = (rng.random(len(w.poses_world)) < 0.5).astype(np.uint8)
+    zeros = np.zeros_like(lab)
+    pl = O.search(Og, o_o, w.poses_world, [w.gt_q], w.h, w.N, w.radius, w.length)[0]
+    la = O.search_label_aware(Og, o_o, w.poses_world, lab, [w.gt_q], w.h, w.N, w.radius, w.length)[0]
+    nc = O.search_label_aware(Og, o_o, w.poses_world, zeros, [w.gt_q], w.h, w.N, w.radius, w.length)[0]
+    tol = 1e-9 * np.abs(pl["C"]).max()
+    assert (la["C"] <= pl["C"] + tol).all() and (nc["C"] <= la["C"] + tol).all()
+    assert nc["C"].max() <= tol and nc["C"].min() < -1.0
+    assert la["score"] < pl["score"]
+
+
+# --------------------------------------------------------------------------
 # Sec. IV-C: samplers
 # --------------------------------------------------------------------------
 
