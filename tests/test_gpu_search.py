@@ -58,6 +58,27 @@ def test_object_grid_matches_oracle(ctx, workload, name):
     assert d.max() <= 1, (d.max(), np.argwhere(d > 1)[:5])
 
 
+def test_object_grid_with_touchable_sub_mesh_matches_oracle(ctx, workload):
+    # Eq. (2) with a touchable sub-mesh: the triangles facing +z (upper
+    # cap of the object) are touchable, the rest only bound the inside
+    w = workload("tiny32")
+    V, T = w.obj.verts, w.obj.tris
+    nz = np.cross(V[T[:, 1]] - V[T[:, 0]], V[T[:, 2]] - V[T[:, 0]])[:, 2]
+    touch = (nz > 0).astype(np.uint8)
+    assert 0 < touch.sum() < len(T)
+    ob = ctx.object_grid(V, T, w.h, w.N, touchable=touch)
+    try:
+        G, o = ob.export_grid()
+        Go, oo, _, fits = O.object_grid(V, T, w.h, w.N, touch=touch)
+        assert fits and np.array_equal(o, oo)
+        d = _ulp_diff(G, Go.astype(np.float32))
+        assert d.max() <= 1, (d.max(), np.argwhere(d > 1)[:5])
+        Gall, _, _, _ = O.object_grid(V, T, w.h, w.N)
+        assert np.count_nonzero(Go != Gall) > 0      # the mask changes the grid
+    finally:
+        ob.close()
+
+
 @pytest.mark.parametrize("name,nrot", [("tiny32", 6), ("free64", 3)])
 def test_voxelised_swept_grid_is_bit_exact(ctx, workload, name, nrot):
     w = workload(name)
