@@ -187,8 +187,9 @@ DOCK_API dock_status dock_object_export_grid(dock_ctx *ctx, const dock_object *o
 /*
  * Probe + trajectory of Sec. IV-A.2 (Eq. (5)-(6)), resident on the device.
  *   poses    P x 7 doubles, probe -> world; quaternions must be unit (1e-6).
- *   contact  P labels (1 = contact, 0 = non-contact) or NULL.  Eq. (5) takes
- *            the max over all poses, so the labels do not change the search.
+ *   contact  P labels (1 = contact, 0 = non-contact) or NULL (all contact).
+ *            Eq. (5) takes the max over all poses, so the labels do not change
+ *            the search unless dock_sweep_set_label_aware switches it on.
  *   h, N     must equal the object's when used together.
  * The swept lattice for an orientation sample R has origin
  * o_s,R = h round(R^T c_s / h) - (N/2) h, c_s = mean tip position.
@@ -200,6 +201,28 @@ DOCK_API void dock_sweep_free(dock_sweep *sw);
  * (n x N^3 bytes, 0/1) and their origins (n x 3 doubles).  Test hook. */
 DOCK_API dock_status dock_sweep_voxelise(dock_ctx *ctx, const dock_sweep *sw, const double *quats, int32_t n,
                                 uint8_t *bits, double *origins);
+
+/*
+ * Label-aware score (a use of the trajectory's contact labels; Sec. I and
+ * Sec. IV-A: a trajectory holds contact and non-contact evidence).  With
+ * on = 1, searches and registrations of this sweep that start after the call
+ * (a submitted request keeps the mode it was submitted with) correlate
+ *     C[dk] = sum_k O[k] S_c[k + dk] + sum_k min(O[k], 0) S_n[k + dk],
+ * S_c = the voxels swept by contact poses, S_n = the voxels swept only by
+ * non-contact poses (S_c + S_n = the plain S of Eq. (5)-(6), on the same
+ * lattice o_s,R of all poses): a pose that did not touch the object may not
+ * overlap its interior but earns nothing near its surface.  A sweep whose
+ * poses are all contact scores as before.  The refinement (Sec. V) is
+ * unchanged.  The first label-aware search of an object computes and keeps
+ * conj(F(min(O, 0))) beside its spectrum (the same size).  Default 0 (Eq. (7)
+ * over all poses).  dock_search_peaks_noalloc rejects a label-aware sweep
+ * (DOCK_E_INVALID).  Returns DOCK_E_INVALID for on outside {0, 1}.
+ */
+DOCK_API dock_status dock_sweep_set_label_aware(dock_ctx *ctx, dock_sweep *sw, int32_t on);
+/* S_c and S_n above for `n` quaternions into host bits_c, bits_n (n x N^3
+ * bytes each, 0/1) and the origins (n x 3 doubles, nullable).  Test hook. */
+DOCK_API dock_status dock_sweep_voxelise_labels(dock_ctx *ctx, const dock_sweep *sw, const double *quats, int32_t n,
+                                                uint8_t *bits_c, uint8_t *bits_n, double *origins);
 
 /* ----------------------------------------------------------------- search */
 
@@ -216,7 +239,8 @@ DOCK_API dock_status dock_sweep_voxelise(dock_ctx *ctx, const dock_sweep *sw, co
 DOCK_API dock_status dock_search_so3(dock_ctx *ctx, const dock_object *obj, const dock_sweep *sw,
                             const dock_search_desc *desc, dock_candidate *out, dock_peak *per_rot);
 
-/* Full correlation field C (M^3 floats, host) for one quaternion.  Test hook. */
+/* Full correlation field C (M^3 floats, host) for one quaternion (the
+ * label-aware field when the sweep is label-aware).  Test hook. */
 DOCK_API dock_status dock_search_scores(dock_ctx *ctx, const dock_object *obj, const dock_sweep *sw, const double *quat,
                                float *C);
 

@@ -135,6 +135,7 @@ struct dock_object {
     double anchor[3];
     float *O = nullptr;       // N^3
     float2 *spec = nullptr;   // tiled conj(F(O)) / M^3
+    float2 *spec_pen = nullptr;   // tiled conj(F(min(O, 0))) / M^3, made by the first label-aware use
     double *o_dev = nullptr;
     // mesh for the refinement
     int64_t nv = 0, nt = 0;
@@ -158,6 +159,11 @@ struct dock_sweep {
     uint8_t *labels = nullptr;
     std::vector<double> host_poses;
     size_t bytes = 0;
+    // label-aware score: the poses again, contact ones first (P_c of them),
+    // each group in trajectory order; nullptr when every pose is contact
+    PoseRec *poses_lab = nullptr;
+    int64_t P_c = 0;
+    std::atomic<bool> label_aware{false};
 };
 
 static dock_status fail(dock_ctx *ctx, dock_status st, const char *fmt, ...)
@@ -902,6 +908,7 @@ extern "C" void dock_object_free(dock_object *ob)
     cudaStreamSynchronize(ctx->stream);
     cudaFree(ob->O);
     cudaFree(ob->spec);
+    cudaFree(ob->spec_pen);
     cudaFree(ob->o_dev);
     cudaFree(ob->Vf);
     cudaFree(ob->T);
@@ -975,6 +982,21 @@ extern "C" dock_status dock_sweep_grid(dock_ctx *ctx, const dock_probe *probe, c
     std::vector<uint8_t> lab(P, 1);
     if (contact) for (int64_t i = 0; i < P; ++i) lab[i] = contact[i] ? 1 : 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(sw->labels, lab.data(), (size_t)P, cudaMemcpyHostToDevice, ctx->stream);
+    std::vector<PoseRec> prl;
+    prl.reserve(P);
+    for (int64_t i = 0; i < P; ++i)
+        if (lab[i]) prl.push_back(pr[i]);
+    sw->P_c = (int64_t)prl.size();
+    for (int64_t i = 0; i < P; ++i)
+        if (!lab[i]) prl.push_back(pr[i]);
+    if (e == cudaSuccess && sw->P_c < P) {
+        if ((s = dalloc(ctx, (void **)&sw->poses_lab, sizeof(PoseRec) * P, &sw->bytes)) != DOCK_OK) {
+            cudaStreamSynchronize(ctx->stream);
+            dock_sweep_free(sw);
+            return s;
+        }
+        e = cudaMemcpyAsync(sw->poses_lab, prl.data(), sizeof(PoseRec) * P, cudaMemcpyHostToDevice, ctx->stream);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
         dock_sweep_free(sw);
@@ -995,6 +1017,7 @@ extern "C" void dock_sweep_free(dock_sweep *sw)
     cudaFree(sw->poses);
     cudaFree(sw->cs_dev);
     cudaFree(sw->labels);
+    cudaFree(sw->poses_lab);
     ctx->held = ctx->held >= sw->bytes ? ctx->held - sw->bytes : 0;
     delete sw;
 }
@@ -1046,11 +1069,25 @@ static dock_status upload_rots(dock_ctx *ctx, const dock_sweep *sw, const double
     return DOCK_OK;
 }
 
-static ReqDev make_reqdev(const dock_object *ob, const dock_sweep *sw, unsigned long long *keys)
+// la: the label-aware score (contact poses as pose set 0, non-contact poses
+// as pose set 1); a sweep whose poses are all contact has no set 1 and
+// scores as a plain one.  For a search, ob->spec_pen must exist
+// (ensure_spec_pen) before a label-aware table is used.
+static ReqDev make_reqdev(const dock_object *ob, const dock_sweep *sw, unsigned long long *keys, bool la)
 {
     ReqDev q;
     q.poses = sw->poses;
     q.P = (int)sw->P;
+    q.poses_nc = nullptr;
+    q.P_nc = 0;
+    q.spec_pen = nullptr;
+    if (la && sw->poses_lab) {
+        q.poses = sw->poses_lab;
+        q.P = (int)sw->P_c;
+        q.poses_nc = sw->poses_lab + sw->P_c;
+        q.P_nc = (int)(sw->P - sw->P_c);
+        q.spec_pen = ob ? ob->spec_pen : nullptr;
+    }
     q.h = sw->h;
     q.r = sw->r;
     q.L = sw->L;
@@ -1085,7 +1122,7 @@ extern "C" dock_status dock_sweep_voxelise(dock_ctx *ctx, const dock_sweep *sw, 
     dock_status s;
     if ((s = gen_samples(ctx, &d, q)) != DOCK_OK) return s;
     if ((s = upload_rots(ctx, sw, q.data(), n, 0, n, 0, 0)) != DOCK_OK) return s;
-    std::vector<ReqDev> rq(1, make_reqdev(nullptr, sw, nullptr));
+    std::vector<ReqDev> rq(1, make_reqdev(nullptr, sw, nullptr, false));
     if ((s = upload_reqs(ctx, rq)) != DOCK_OK) return s;
     Geo g = make_geo(sw);
     size_t per = (size_t)g.N * g.N * g.N;
@@ -1102,6 +1139,58 @@ extern "C" dock_status dock_sweep_voxelise(dock_ctx *ctx, const dock_sweep *sw, 
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     dfree(ctx, dbits, per * n);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "voxelise");
+    if (origins)
+        for (int i = 0; i < n; ++i) memcpy(origins + 3 * i, rr[i].o, sizeof(double) * 3);
+    return DOCK_OK;
+}
+
+extern "C" dock_status dock_sweep_set_label_aware(dock_ctx *ctx, dock_sweep *sw, int32_t on)
+{
+    if (!ctx || !sw || sw->ctx != ctx) return DOCK_E_INVALID;
+    if (on != 0 && on != 1) return fail(ctx, DOCK_E_INVALID, "label_aware must be 0 or 1");
+    sw->label_aware.store(on != 0);
+    return DOCK_OK;
+}
+
+extern "C" dock_status dock_sweep_voxelise_labels(dock_ctx *ctx, const dock_sweep *sw, const double *quats, int32_t n,
+                                                  uint8_t *bits_c, uint8_t *bits_n, double *origins)
+{
+    if (!ctx || !sw || !quats || n <= 0 || !bits_c || !bits_n) return DOCK_E_INVALID;
+    DevLock dev_lock_(ctx);
+    if (ctx->dead) return fail(ctx, DOCK_E_CUDA_FATAL, "context is dead after a sticky CUDA error");
+    cudaSetDevice(ctx->device);
+    dock_search_desc d = {};
+    d.sampler = DOCK_SAMPLER_EXPLICIT;
+    d.n = n;
+    d.quats = quats;
+    std::vector<double> q;
+    dock_status s;
+    if ((s = gen_samples(ctx, &d, q)) != DOCK_OK) return s;
+    if ((s = upload_rots(ctx, sw, q.data(), n, 0, n, 0, 0)) != DOCK_OK) return s;
+    std::vector<ReqDev> rq(1, make_reqdev(nullptr, sw, nullptr, true));
+    if ((s = upload_reqs(ctx, rq)) != DOCK_OK) return s;
+    Geo g = make_geo(sw);
+    const size_t per = (size_t)g.N * g.N * g.N;
+    uint8_t *dbits = nullptr;
+    if ((s = dalloc(ctx, (void **)&dbits, 2 * per * n, nullptr)) != DOCK_OK) return s;
+    cudaError_t e;
+    {
+        Prof pr(ctx, "vox_export");
+        e = launch_vox_export(g, ctx->reqs, ctx->rots, n, dbits, ctx->stream, 0);
+        if (e == cudaSuccess && sw->poses_lab)
+            e = launch_vox_export(g, ctx->reqs, ctx->rots, n, dbits + per * n, ctx->stream, 1);
+        else if (e == cudaSuccess)
+            e = cudaMemsetAsync(dbits + per * n, 0, per * n, ctx->stream);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bits_c, dbits, per * n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bits_n, dbits + per * n, per * n, cudaMemcpyDeviceToHost, ctx->stream);
+    std::vector<RotRec> rr(n);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rr.data(), ctx->rots, sizeof(RotRec) * n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dfree(ctx, dbits, 2 * per * n);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "voxelise_labels");
+    // the scored non-contact grid is the part that no contact pose covers
+    for (size_t i = 0; i < per * n; ++i) bits_n[i] = bits_n[i] && !bits_c[i];
     if (origins)
         for (int i = 0; i < n; ++i) memcpy(origins + 3 * i, rr[i].o, sizeof(double) * 3);
     return DOCK_OK;
@@ -1144,9 +1233,12 @@ static dock_tuning tuning_for(dock_ctx *ctx, const Geo &g)
 
 // Runs records [r0, r1) of rots through the search pipeline; every
 // rotation's peak key lands in its request's key array (reqs[rot.req]).  All
-// requests of the call share the lattice side of g.
+// requests of the call share the lattice side of g.  dual: some request of
+// the table is label-aware; each batch then also voxelises pose set 1, takes
+// the voxels that set 0 leaves uncovered and adds their correlation with
+// min(O, 0) in the z pass (requests without a set 1 are unaffected).
 static dock_status run_pipeline_rots(dock_ctx *ctx, const Geo &g, const ReqDev *reqs, const RotRec *rots, size_t r0,
-                                     size_t r1, int batch)
+                                     size_t r1, int batch, bool dual = false)
 {
     float2 *tw, *qt;
     double2 *twd;
@@ -1155,7 +1247,7 @@ static dock_status run_pipeline_rots(dock_ctx *ctx, const Geo &g, const ReqDev *
     const dock_tuning tc = tuning_for(ctx, g);
     int B = batch > 0 ? batch : tc.batch;
     size_t ysz = (size_t)B * g.N * g.M * g.P, zsz = (size_t)B * g.M * g.M * g.P;
-    size_t need = ysz + zsz;
+    size_t need = ysz + zsz + (dual ? ysz : 0);
     if (ctx->yz_bytes < need) {
         if (ctx->Y) {
             cudaStreamSynchronize(ctx->stream);
@@ -1166,9 +1258,11 @@ static dock_status run_pipeline_rots(dock_ctx *ctx, const Geo &g, const ReqDev *
         if ((s = dalloc(ctx, (void **)&ctx->Y, need * sizeof(float2), nullptr)) != DOCK_OK) return s;
         ctx->yz_bytes = need;
     }
-    float2 *Y = ctx->Y, *Z = ctx->Y + ysz;
-    if ((s = ensure(ctx, (void **)&ctx->bits, &ctx->bits_n, (size_t)B * g.N * g.N * (g.N / 32), sizeof(uint32_t))) != DOCK_OK)
+    float2 *Y = ctx->Y, *Z = ctx->Y + ysz, *Y2 = dual ? ctx->Y + ysz + zsz : nullptr;
+    const size_t bsz = (size_t)B * g.N * g.N * (g.N / 32);
+    if ((s = ensure(ctx, (void **)&ctx->bits, &ctx->bits_n, dual ? 2 * bsz : bsz, sizeof(uint32_t))) != DOCK_OK)
         return s;
+    uint32_t *bits2 = dual ? ctx->bits + bsz : nullptr;
     int chunks = g.M * g.P / 32;
     for (size_t b0 = r0; b0 < r1; b0 += B) {
         int nb = (int)std::min<size_t>(B, r1 - b0);
@@ -1179,13 +1273,21 @@ static dock_status run_pipeline_rots(dock_ctx *ctx, const Geo &g, const ReqDev *
             Prof pr(ctx, "voxelise");
             CK(ctx, launch_voxelise(g, reqs, rb, nb, ctx->bits, ctx->stream, tc.vox_blocks));
         }
+        if (dual) {
+            Prof pr(ctx, "voxelise_nc");
+            CK(ctx, launch_voxelise(g, reqs, rb, nb, bits2, ctx->stream, tc.vox_blocks, 1));
+        }
         {
             Prof pr(ctx, "fwd2d");
             CK(ctx, launch_fwd2d(g, nb, ctx->bits, Y, tw, qt, ctx->stream));
         }
+        if (dual) {
+            Prof pr(ctx, "fwd2d_nc");
+            CK(ctx, launch_fwd2d(g, nb, bits2, Y2, tw, qt, ctx->stream, ctx->bits));
+        }
         {
-            Prof pr(ctx, "zpass");
-            CK(ctx, launch_zpass(g, nb, group, Y, rb, reqs, Z, tw, ctx->stream));
+            Prof pr(ctx, dual ? "zpass_dual" : "zpass");
+            CK(ctx, launch_zpass(g, nb, group, Y, rb, reqs, Z, tw, ctx->stream, Y2));
         }
         {
             Prof pr(ctx, "plane");
@@ -1195,9 +1297,51 @@ static dock_status run_pipeline_rots(dock_ctx *ctx, const Geo &g, const ReqDev *
     return DOCK_OK;
 }
 
-static dock_status run_pipeline(dock_ctx *ctx, const Geo &g, size_t r0, size_t r1, int batch)
+static dock_status run_pipeline(dock_ctx *ctx, const Geo &g, size_t r0, size_t r1, int batch, bool dual)
 {
-    return run_pipeline_rots(ctx, g, ctx->reqs, ctx->rots, r0, r1, batch);
+    return run_pipeline_rots(ctx, g, ctx->reqs, ctx->rots, r0, r1, batch, dual);
+}
+
+// The label-aware score of this sweep is in force and differs from the plain one.
+static bool dual_scoring(const dock_sweep *sw) { return sw->label_aware.load() && sw->poses_lab != nullptr; }
+
+// conj(F(min(O, 0))) / M^3 of the object, made on first use and kept with it.
+static dock_status ensure_spec_pen(dock_ctx *ctx, const dock_object *obc)
+{
+    dock_object *ob = const_cast<dock_object *>(obc);
+    if (ob->spec_pen) return DOCK_OK;
+    const int N = ob->N, M = ob->M, P = ob->P;
+    float2 *tw, *qt;
+    double2 *twd;
+    dock_status s;
+    if ((s = tables(ctx, M, &tw, &qt, &twd)) != DOCK_OK) return s;
+    const size_t spec_n = (size_t)M * P / 32 * M * 32;
+    const size_t b1 = sizeof(double2) * (size_t)N * N * (N + 1), b2 = sizeof(double2) * (size_t)N * M * (N + 1);
+    float2 *sp = nullptr;
+    double2 *w1 = nullptr, *w2 = nullptr;
+    size_t held = 0;
+    if ((s = dalloc(ctx, (void **)&sp, sizeof(float2) * spec_n, &held)) != DOCK_OK) return s;
+    if ((s = dalloc(ctx, (void **)&w1, b1, nullptr)) != DOCK_OK) { dfree(ctx, sp, sizeof(float2) * spec_n); return s; }
+    if ((s = dalloc(ctx, (void **)&w2, b2, nullptr)) != DOCK_OK) {
+        dfree(ctx, sp, sizeof(float2) * spec_n);
+        dfree(ctx, w1, b1);
+        return s;
+    }
+    cudaError_t e;
+    {
+        Prof pr(ctx, "object_spectrum_pen");
+        e = launch_spectrum(ob->O, N, M, P, w1, w2, twd, sp, ctx->stream, true);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dfree(ctx, w1, b1);
+    dfree(ctx, w2, b2);
+    if (e != cudaSuccess) {
+        dfree(ctx, sp, sizeof(float2) * spec_n);
+        return cuda_fail(ctx, e, "penetration spectrum");
+    }
+    ob->spec_pen = sp;
+    ob->bytes += held;
+    return DOCK_OK;
 }
 
 static dock_status search_impl(dock_ctx *ctx, const dock_object *ob, const dock_sweep *sw, const dock_search_desc *d,
@@ -1209,9 +1353,11 @@ static dock_status search_impl(dock_ctx *ctx, const dock_object *ob, const dock_
     if ((s = ensure(ctx, (void **)&ctx->keys, &ctx->keys_n, (size_t)n, sizeof(unsigned long long))) != DOCK_OK) return s;
     CK(ctx, cudaMemsetAsync(ctx->keys, 0, sizeof(unsigned long long) * n, ctx->stream));
     CK(ctx, cudaMemsetAsync(ctx->errflag, 0, sizeof(int), ctx->stream));
-    std::vector<ReqDev> rq(1, make_reqdev(ob, sw, ctx->keys));
+    const bool dual = dual_scoring(sw);
+    if (dual && (s = ensure_spec_pen(ctx, ob)) != DOCK_OK) return s;
+    std::vector<ReqDev> rq(1, make_reqdev(ob, sw, ctx->keys, dual));
     if ((s = upload_reqs(ctx, rq)) != DOCK_OK) return s;
-    if ((s = run_pipeline(ctx, make_geo(sw), r0, r1, d->batch)) != DOCK_OK) return s;
+    if ((s = run_pipeline(ctx, make_geo(sw), r0, r1, d->batch, dual)) != DOCK_OK) return s;
     if ((s = ensure(ctx, (void **)&ctx->cands, &ctx->cands_n, (size_t)d->top_k, sizeof(dock_candidate))) != DOCK_OK) return s;
     {
         Prof pr(ctx, "topk");
@@ -1273,6 +1419,8 @@ extern "C" dock_status dock_search_peaks_noalloc(dock_ctx *ctx, const dock_objec
     if (n < 1 || n > NOALLOC_MAX_ROT)
         return fail(ctx, DOCK_E_INVALID, "rotation count %d outside [1, %d] of dock_search_peaks_noalloc", n,
                     NOALLOC_MAX_ROT);
+    if (dual_scoring(sw))
+        return fail(ctx, DOCK_E_INVALID, "dock_search_peaks_noalloc scores plainly; the sweep is label-aware");
     for (int i = 0; i < n; ++i) {
         const double *a = quats + 4 * (size_t)i;
         double nq = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);
@@ -1286,7 +1434,7 @@ extern "C" dock_status dock_search_peaks_noalloc(dock_ctx *ctx, const dock_objec
     NoallocJob j;
     j.device = ctx->device;
     j.g = make_geo(sw);
-    j.req = make_reqdev(ob, sw, nullptr);
+    j.req = make_reqdev(ob, sw, nullptr, false);
     j.c_s = sw->cs_dev;
     j.quats = quats;
     j.n = n;
@@ -1374,7 +1522,7 @@ extern "C" dock_status dock_autotune(dock_ctx *ctx, const dock_object *ob, const
     if ((s = ensure(ctx, (void **)&ctx->keys, &ctx->keys_n, (size_t)n_rot, sizeof(unsigned long long))) != DOCK_OK)
         return s;
     CK(ctx, cudaMemsetAsync(ctx->keys, 0, sizeof(unsigned long long) * n_rot, ctx->stream));
-    std::vector<ReqDev> rq(1, make_reqdev(ob, sw, ctx->keys));
+    std::vector<ReqDev> rq(1, make_reqdev(ob, sw, ctx->keys, false));   // plain score: its launch shape
     if ((s = upload_reqs(ctx, rq)) != DOCK_OK) return s;
     const Geo g = make_geo(sw);
     const bool had = ctx->tune.count(g.N) != 0;
@@ -1500,27 +1648,33 @@ extern "C" dock_status dock_search_scores(dock_ctx *ctx, const dock_object *ob, 
     std::vector<double> q;
     if ((s = gen_samples(ctx, &d, q)) != DOCK_OK) return s;
     if ((s = upload_rots(ctx, sw, q.data(), 1, 0, 1, 0, 0)) != DOCK_OK) return s;
-    std::vector<ReqDev> rq(1, make_reqdev(ob, sw, nullptr));
+    const bool dual = dual_scoring(sw);
+    if (dual && (s = ensure_spec_pen(ctx, ob)) != DOCK_OK) return s;
+    std::vector<ReqDev> rq(1, make_reqdev(ob, sw, nullptr, dual));
     if ((s = upload_reqs(ctx, rq)) != DOCK_OK) return s;
     Geo g = make_geo(sw);
     float2 *tw, *qt;
     double2 *twd;
     if ((s = tables(ctx, g.M, &tw, &qt, &twd)) != DOCK_OK) return s;
     size_t ysz = (size_t)g.N * g.M * g.P, zsz = (size_t)g.M * g.M * g.P, csz = (size_t)g.M * g.M * g.M;
+    const size_t ybytes = (ysz + zsz + (dual ? ysz : 0)) * sizeof(float2);
+    const size_t bsz = (size_t)g.N * g.N * (g.N / 32);
     float2 *Y = nullptr;
     float *dC = nullptr;
-    if ((s = ensure(ctx, (void **)&ctx->bits, &ctx->bits_n, (size_t)g.N * g.N * (g.N / 32), sizeof(uint32_t))) != DOCK_OK)
-        return s;
-    if ((s = dalloc(ctx, (void **)&Y, (ysz + zsz) * sizeof(float2), nullptr)) != DOCK_OK) return s;
-    if ((s = dalloc(ctx, (void **)&dC, csz * sizeof(float), nullptr)) != DOCK_OK) { dfree(ctx, Y, (ysz + zsz) * sizeof(float2)); return s; }
+    if ((s = ensure(ctx, (void **)&ctx->bits, &ctx->bits_n, 2 * bsz, sizeof(uint32_t))) != DOCK_OK) return s;
+    if ((s = dalloc(ctx, (void **)&Y, ybytes, nullptr)) != DOCK_OK) return s;
+    if ((s = dalloc(ctx, (void **)&dC, csz * sizeof(float), nullptr)) != DOCK_OK) { dfree(ctx, Y, ybytes); return s; }
+    float2 *Y2 = dual ? Y + ysz + zsz : nullptr;
     cudaError_t e = cudaMemsetAsync(ctx->errflag, 0, sizeof(int), ctx->stream);
     if (e == cudaSuccess) e = launch_voxelise(g, ctx->reqs, ctx->rots, 1, ctx->bits, ctx->stream);
     if (e == cudaSuccess) e = launch_fwd2d(g, 1, ctx->bits, Y, tw, qt, ctx->stream);
-    if (e == cudaSuccess) e = launch_zpass(g, 1, 1, Y, ctx->rots, ctx->reqs, Y + ysz, tw, ctx->stream);
+    if (dual && e == cudaSuccess) e = launch_voxelise(g, ctx->reqs, ctx->rots, 1, ctx->bits + bsz, ctx->stream, 4, 1);
+    if (dual && e == cudaSuccess) e = launch_fwd2d(g, 1, ctx->bits + bsz, Y2, tw, qt, ctx->stream, ctx->bits);
+    if (e == cudaSuccess) e = launch_zpass(g, 1, 1, Y, ctx->rots, ctx->reqs, Y + ysz, tw, ctx->stream, Y2);
     if (e == cudaSuccess) e = launch_plane_export(g, Y + ysz, tw, dC, ctx->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(C, dC, csz * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    dfree(ctx, Y, (ysz + zsz) * sizeof(float2));
+    dfree(ctx, Y, ybytes);
     dfree(ctx, dC, csz * sizeof(float));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "search_scores");
     return DOCK_OK;
@@ -1937,6 +2091,7 @@ struct Job {
     std::string err;
     bool cancel = false;
     bool async = false;                   // submitted by dock_submit (kept until polled)
+    bool la = false;                      // label-aware score (the sweep's mode at submission)
     Clock::time_point t_submit;
 };
 using JobP = std::shared_ptr<Job>;
@@ -2027,10 +2182,10 @@ static size_t job_bytes(const Job &j)
 }
 
 // Device bytes the Y/Z scratch must grow by for a pass at lattice side N.
-static size_t yz_growth(dock_ctx *ctx, const dock_sweep *sw)
+static size_t yz_growth(dock_ctx *ctx, const dock_sweep *sw, bool la)
 {
     Geo g = make_geo(sw);
-    size_t need = (size_t)tuning_for(ctx, g).batch * (g.N + g.M) * g.M * g.P;
+    size_t need = (size_t)tuning_for(ctx, g).batch * (g.N + g.M + (la ? g.N : 0)) * g.M * g.P;
     return need > ctx->yz_bytes ? (need - ctx->yz_bytes) * sizeof(float2) : 0;
 }
 
@@ -2066,7 +2221,9 @@ static dock_status job_admit(dock_ctx *ctx, Engine &E, Job &j, int *wait)
 {
     *wait = ADMIT_OK;
     const size_t bytes = job_bytes(j);
-    if (ctx->budget && ctx->held + bytes + yz_growth(ctx, j.sw) > ctx->budget) {
+    const bool la = j.la && j.sw->poses_lab;
+    size_t pen_bytes = la && !j.ob->spec_pen ? sizeof(float2) * (size_t)j.ob->M * j.ob->P * j.ob->M : 0;
+    if (ctx->budget && ctx->held + bytes + pen_bytes + yz_growth(ctx, j.sw, la) > ctx->budget) {
         if (!E.active.empty()) {
             *wait = ADMIT_WAIT;
             return DOCK_OK;
@@ -2074,6 +2231,7 @@ static dock_status job_admit(dock_ctx *ctx, Engine &E, Job &j, int *wait)
         return fail(ctx, DOCK_E_TOO_LARGE, "request needs %zu bytes beyond the HBM budget", bytes);
     }
     dock_status s;
+    if (la && (s = ensure_spec_pen(ctx, j.ob)) != DOCK_OK) return s;
     if ((s = dalloc(ctx, &j.dev, bytes, nullptr)) != DOCK_OK) return s;
     j.dev_bytes = bytes;
     const size_t n = (size_t)j.d.n_global + j.d.n_local;
@@ -2098,7 +2256,7 @@ static dock_status job_admit(dock_ctx *ctx, Engine &E, Job &j, int *wait)
     CK(ctx, cudaMemcpyAsync(j.dq, j.q.data(), sizeof(double) * 4 * j.d.n_global, cudaMemcpyHostToDevice, ctx->stream));
     CK(ctx, launch_rot_setup(j.dq, j.d.n_global, 0, j.slot, j.sw->cs_dev, j.sw->h, j.sw->N, j.drot, ctx->stream));
     CK(ctx, cudaMemsetAsync(j.dkey, 0, sizeof(unsigned long long) * n, ctx->stream));
-    ReqDev r = make_reqdev(j.ob, j.sw, j.dkey);
+    ReqDev r = make_reqdev(j.ob, j.sw, j.dkey, la);
     CK(ctx, cudaMemcpyAsync(E.reqtab + j.slot, &r, sizeof(ReqDev), cudaMemcpyHostToDevice, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));   // r and j.q are host staging of this call
     j.stage = JOB_GLOBAL;
@@ -2394,8 +2552,10 @@ static bool engine_step(dock_ctx *ctx)
             if (std::find(in_pass.begin(), in_pass.end(), jp) == in_pass.end()) in_pass.push_back(jp);
             if (taken == B) break;
         }
+    bool dual = false;
+    for (auto *jp : in_pass) dual = dual || (jp->la && jp->sw->poses_lab);
     if (ce != cudaSuccess) s = cuda_fail(ctx, ce, "gather of rotation records");
-    else s = run_pipeline_rots(ctx, g, E.reqtab, ctx->phase, 0, taken, B);
+    else s = run_pipeline_rots(ctx, g, E.reqtab, ctx->phase, 0, taken, B, dual);
     if (s == DOCK_OK) {
         cudaError_t e = cudaEventRecord(E.pass_ev[E.passes % 2], ctx->stream);
         if (e != cudaSuccess) s = cuda_fail(ctx, e, "recording a search pass");
@@ -2577,6 +2737,7 @@ static JobP make_job(const dock_object *ob, const dock_sweep *sw, const dock_reg
     j->res.last_pass = -1;
     j->ob = ob;
     j->sw = sw;
+    j->la = sw && sw->label_aware.load();
     j->d = *rd;
     if (params) j->p = *params;
     else dock_params_default(&j->p);

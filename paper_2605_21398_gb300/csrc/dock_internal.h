@@ -43,6 +43,10 @@ struct Geo {
 
 // Per-request data of a search launch: the rotations of one launch may come
 // from several registrations that share the lattice side N.
+// Pose set 0 is (poses, P): every pose of a plain request, the contact poses
+// of a label-aware one.  Pose set 1 is (poses_nc, P_nc): the non-contact
+// poses of a label-aware request (P_nc = 0 otherwise), whose voxels scored
+// against spec_pen count only where set 0 leaves them uncovered.
 struct ReqDev {
     const PoseRec *poses;
     int P;
@@ -50,23 +54,30 @@ struct ReqDev {
     float inv_h, rv, lv;      // FP32 copies; rv, lv in voxels
     const float2 *spec;       // tiled conj(F(O)) / M^3 of the request's object
     unsigned long long *keys; // per-rotation peak keys, indexed by RotRec::rot
+    const PoseRec *poses_nc;  // label-aware: non-contact poses (else nullptr)
+    int P_nc;
+    const float2 *spec_pen;   // label-aware: tiled conj(F(min(O, 0))) / M^3 (else nullptr)
 };
 
 // Kernel launchers (k_search.cu)
 cudaError_t launch_rot_setup(const double *quats, int n, int rot0, int req, const double *c_s, double h, int N,
                              RotRec *out, cudaStream_t st);
+// pose_set: 0 = (poses, P), 1 = (poses_nc, P_nc) of each rotation's request.
 cudaError_t launch_voxelise(const Geo &g, const ReqDev *reqs, const RotRec *rots, int B, uint32_t *bits,
-                            cudaStream_t st, int minb = 4);
+                            cudaStream_t st, int minb = 4, int pose_set = 0);
+// mask (nullable, the layout of bits): bits & ~mask is transformed.
 cudaError_t launch_fwd2d(const Geo &g, int B, const uint32_t *bits, float2 *Y, const float2 *tw, const float2 *q,
-                         cudaStream_t st);
+                         cudaStream_t st, const uint32_t *mask = nullptr);
+// Y2 (nullable): transforms of the label-aware second grids; when given, the
+// product with each request's spec_pen is added before the inverse FFT.
 cudaError_t launch_zpass(const Geo &g, int B, int group, const float2 *Y, const RotRec *rots, const ReqDev *reqs,
-                         float2 *Z, const float2 *tw, cudaStream_t st);
+                         float2 *Z, const float2 *tw, cudaStream_t st, const float2 *Y2 = nullptr);
 cudaError_t launch_plane(const Geo &g, int B, const float2 *Z, const float2 *tw, const RotRec *rots,
                          const ReqDev *reqs, cudaStream_t st);
 cudaError_t launch_topk(const unsigned long long *keys, int n, int K, int N, int M, double h, const double *o_o,
                         const double *quats, const RotRec *rots_all, dock_candidate *out, cudaStream_t st);
 cudaError_t launch_vox_export(const Geo &g, const ReqDev *reqs, const RotRec *rots, int B, uint8_t *bits,
-                              cudaStream_t st);
+                              cudaStream_t st, int pose_set = 0);
 cudaError_t launch_plane_export(const Geo &g, const float2 *Z, const float2 *tw, float *C, cudaStream_t st);
 
 // Object grid kernels (k_object.cu)
@@ -82,8 +93,9 @@ struct ObjBins {
 cudaError_t launch_object_grid(const double *V, const int32_t *T, const uint8_t *touch, const ObjBins &bins,
                                int N, double h, const double *o, double tau_out, double tau_in, double deep,
                                float *O, float *f_out, int *err, cudaStream_t st);
+// pen: transform min(O, 0) instead of O (the label-aware penetration part).
 cudaError_t launch_spectrum(const float *O, int N, int M, int P, double2 *work1, double2 *work2,
-                            const double2 *twd, float2 *spec, cudaStream_t st);
+                            const double2 *twd, float2 *spec, cudaStream_t st, bool pen = false);
 
 // Refinement kernels (k_refine.cu)
 struct BvhNode {

@@ -162,8 +162,8 @@ __device__ __forceinline__ double2 cmuld(double2 a, double2 b)
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// A[z][y][kx] = sum_x O[z][y][x] w^(kx x), kx in [0, H]
-__global__ void k_spec_x(const float *O, int N, int M, const double2 *tw, double2 *A)
+// A[z][y][kx] = sum_x O[z][y][x] w^(kx x), kx in [0, H]  (min(O, 0) when pen)
+__global__ void k_spec_x(const float *O, int N, int M, const double2 *tw, double2 *A, bool pen)
 {
     const int H = M / 2;
     const int row = blockIdx.x;   // z * N + y
@@ -172,6 +172,7 @@ __global__ void k_spec_x(const float *O, int N, int M, const double2 *tw, double
         double2 acc = make_double2(0.0, 0.0);
         for (int x = 0; x < N; ++x) {
             double v = (double)o[x];
+            if (pen) v = fmin(v, 0.0);
             if (v != 0.0) {
                 double2 w = tw[(kx * x) % M];
                 acc.x += v * w.x;
@@ -221,9 +222,9 @@ __global__ void k_spec_z(const double2 *Bi, int N, int M, int P, const double2 *
 }
 
 cudaError_t launch_spectrum(const float *O, int N, int M, int P, double2 *work1, double2 *work2, const double2 *twd,
-                            float2 *spec, cudaStream_t st)
+                            float2 *spec, cudaStream_t st, bool pen)
 {
-    k_spec_x<<<N * N, 160, 0, st>>>(O, N, M, twd, work1);
+    k_spec_x<<<N * N, 160, 0, st>>>(O, N, M, twd, work1, pen);
     k_spec_y<<<dim3(M, N), 160, 0, st>>>(work1, N, M, twd, work2);
     k_spec_z<<<dim3(M, M), 160, 0, st>>>(work2, N, M, P, twd, spec);
     return cudaGetLastError();

@@ -466,7 +466,7 @@ __device__ __forceinline__ Geo req_geo(const Geo &g, const ReqDev &q)
 // to 80 registers; 4: 64 registers, a few spills); the autotuner picks one.
 template <int N, int MINB>
 __global__ void __launch_bounds__(256, MINB)
-k_voxelise(Geo g, const ReqDev *reqs, const RotRec *rots, uint32_t *bits_out)
+k_voxelise(Geo g, const ReqDev *reqs, const RotRec *rots, uint32_t *bits_out, int pose_set)
 {
     constexpr int NW = N / 32;
     __shared__ uint32_t bits[N * NW];
@@ -480,7 +480,8 @@ k_voxelise(Geo g, const ReqDev *reqs, const RotRec *rots, uint32_t *bits_out)
     __syncthreads();
     const RotRec &rr = rots[b];
     const ReqDev &q = reqs[rr.req];
-    voxelise_slab<N>(req_geo(g, q), rr, q.poses, q.P, jz, bits, &next_chunk);
+    voxelise_slab<N>(req_geo(g, q), rr, pose_set ? q.poses_nc : q.poses, pose_set ? q.P_nc : q.P, jz, bits,
+                     &next_chunk);
     __syncthreads();
     uint32_t *o = bits_out + ((size_t)b * N + jz) * N * NW;
     for (int i = threadIdx.x; i < N * NW; i += blockDim.x) o[i] = bits[i];
@@ -488,26 +489,26 @@ k_voxelise(Geo g, const ReqDev *reqs, const RotRec *rots, uint32_t *bits_out)
 
 template <int MINB>
 static cudaError_t launch_voxelise_t(const Geo &g, const ReqDev *reqs, const RotRec *rots, int B, uint32_t *bits,
-                                     cudaStream_t st)
+                                     cudaStream_t st, int ps)
 {
     dim3 grid(B, g.N);
     switch (g.N) {
-    case 32: k_voxelise<32, MINB><<<grid, 256, 0, st>>>(g, reqs, rots, bits); break;
-    case 64: k_voxelise<64, MINB><<<grid, 256, 0, st>>>(g, reqs, rots, bits); break;
-    case 96: k_voxelise<96, MINB><<<grid, 256, 0, st>>>(g, reqs, rots, bits); break;
-    case 128: k_voxelise<128, MINB><<<grid, 256, 0, st>>>(g, reqs, rots, bits); break;
+    case 32: k_voxelise<32, MINB><<<grid, 256, 0, st>>>(g, reqs, rots, bits, ps); break;
+    case 64: k_voxelise<64, MINB><<<grid, 256, 0, st>>>(g, reqs, rots, bits, ps); break;
+    case 96: k_voxelise<96, MINB><<<grid, 256, 0, st>>>(g, reqs, rots, bits, ps); break;
+    case 128: k_voxelise<128, MINB><<<grid, 256, 0, st>>>(g, reqs, rots, bits, ps); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_voxelise(const Geo &g, const ReqDev *reqs, const RotRec *rots, int B, uint32_t *bits,
-                            cudaStream_t st, int minb)
+                            cudaStream_t st, int minb, int pose_set)
 {
-    if (B < 1 || B > 65535) return cudaErrorInvalidValue;
+    if (B < 1 || B > 65535 || (pose_set != 0 && pose_set != 1)) return cudaErrorInvalidValue;
     switch (minb) {
-    case 3: return launch_voxelise_t<3>(g, reqs, rots, B, bits, st);
-    case 4: return launch_voxelise_t<4>(g, reqs, rots, B, bits, st);
+    case 3: return launch_voxelise_t<3>(g, reqs, rots, B, bits, st, pose_set);
+    case 4: return launch_voxelise_t<4>(g, reqs, rots, B, bits, st, pose_set);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -518,7 +519,7 @@ cudaError_t launch_voxelise(const Geo &g, const ReqDev *reqs, const RotRec *rots
 // ---------------------------------------------------------------------------
 template <int M>
 __global__ void __launch_bounds__(Plan<M>::T * 32)
-k_fwd2d(int P, const uint32_t *bits_g, float2 *Y, const float2 *tw_g, const float2 *q_g)
+k_fwd2d(int P, const uint32_t *bits_g, float2 *Y, const float2 *tw_g, const float2 *q_g, const uint32_t *mask_g)
 {
     constexpr int N = M / 2, H = M / 2, NW = N / 32, COLS = 32, E = Plan<M>::E;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -531,7 +532,12 @@ k_fwd2d(int P, const uint32_t *bits_g, float2 *Y, const float2 *tw_g, const floa
     const int jz = blockIdx.x, b = blockIdx.y;
     const uint32_t *bg = bits_g + ((size_t)b * N + jz) * N * NW;
     for (int i = threadIdx.x; i < M; i += blockDim.x) { float2 w = tw_g[i]; tw[i] = cmake(w.x, w.y); }
-    for (int i = threadIdx.x; i < N * NW; i += blockDim.x) bits[i] = bg[i];
+    if (mask_g) {
+        const uint32_t *mg = mask_g + ((size_t)b * N + jz) * N * NW;
+        for (int i = threadIdx.x; i < N * NW; i += blockDim.x) bits[i] = bg[i] & ~mg[i];
+    } else {
+        for (int i = threadIdx.x; i < N * NW; i += blockDim.x) bits[i] = bg[i];
+    }
     __syncthreads();
 
     // x: X[y][kx] = sum over runs [a, a+len) of sum_x exp(-2 pi i kx x / M)
@@ -630,23 +636,23 @@ static size_t fwd2d_smem()
 
 template <int M>
 static cudaError_t launch_fwd2d_t(const Geo &g, int B, const uint32_t *bits, float2 *Y, const float2 *tw,
-                                  const float2 *q, cudaStream_t st)
+                                  const float2 *q, cudaStream_t st, const uint32_t *mask)
 {
     size_t sm = fwd2d_smem<M>();
     cudaError_t e = cudaFuncSetAttribute(k_fwd2d<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_fwd2d<M><<<dim3(M / 2, B), Plan<M>::T * 32, sm, st>>>(g.P, bits, Y, tw, q);
+    k_fwd2d<M><<<dim3(M / 2, B), Plan<M>::T * 32, sm, st>>>(g.P, bits, Y, tw, q, mask);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fwd2d(const Geo &g, int B, const uint32_t *bits, float2 *Y, const float2 *tw, const float2 *q,
-                         cudaStream_t st)
+                         cudaStream_t st, const uint32_t *mask)
 {
     switch (g.M) {
-    case 64: return launch_fwd2d_t<64>(g, B, bits, Y, tw, q, st);
-    case 128: return launch_fwd2d_t<128>(g, B, bits, Y, tw, q, st);
-    case 192: return launch_fwd2d_t<192>(g, B, bits, Y, tw, q, st);
-    case 256: return launch_fwd2d_t<256>(g, B, bits, Y, tw, q, st);
+    case 64: return launch_fwd2d_t<64>(g, B, bits, Y, tw, q, st, mask);
+    case 128: return launch_fwd2d_t<128>(g, B, bits, Y, tw, q, st, mask);
+    case 192: return launch_fwd2d_t<192>(g, B, bits, Y, tw, q, st, mask);
+    case 256: return launch_fwd2d_t<256>(g, B, bits, Y, tw, q, st, mask);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -654,7 +660,8 @@ cudaError_t launch_fwd2d(const Geo &g, int B, const uint32_t *bits, float2 *Y, c
 // Bits of S_b to a byte array (test hook): the production voxeliser, then
 // one byte per voxel.
 template <int N>
-__global__ void __launch_bounds__(256) k_vox_export(Geo g, const ReqDev *reqs, const RotRec *rots, uint8_t *out)
+__global__ void __launch_bounds__(256) k_vox_export(Geo g, const ReqDev *reqs, const RotRec *rots, uint8_t *out,
+                                                    int pose_set)
 {
     constexpr int NW = N / 32;
     __shared__ uint32_t bits[N * NW];
@@ -665,7 +672,8 @@ __global__ void __launch_bounds__(256) k_vox_export(Geo g, const ReqDev *reqs, c
     __syncthreads();
     const RotRec &rr = rots[b];
     const ReqDev &q = reqs[rr.req];
-    voxelise_slab<N>(req_geo(g, q), rr, q.poses, q.P, jz, bits, &next_chunk);
+    voxelise_slab<N>(req_geo(g, q), rr, pose_set ? q.poses_nc : q.poses, pose_set ? q.P_nc : q.P, jz, bits,
+                     &next_chunk);
     __syncthreads();
     uint8_t *o = out + ((size_t)b * N + jz) * N * N;
     for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
@@ -675,14 +683,15 @@ __global__ void __launch_bounds__(256) k_vox_export(Geo g, const ReqDev *reqs, c
 }
 
 cudaError_t launch_vox_export(const Geo &g, const ReqDev *reqs, const RotRec *rots, int B, uint8_t *bits,
-                              cudaStream_t st)
+                              cudaStream_t st, int ps)
 {
     dim3 grid(g.N, B);
+    if (ps != 0 && ps != 1) return cudaErrorInvalidValue;
     switch (g.N) {
-    case 32: k_vox_export<32><<<grid, 256, 0, st>>>(g, reqs, rots, bits); break;
-    case 64: k_vox_export<64><<<grid, 256, 0, st>>>(g, reqs, rots, bits); break;
-    case 96: k_vox_export<96><<<grid, 256, 0, st>>>(g, reqs, rots, bits); break;
-    case 128: k_vox_export<128><<<grid, 256, 0, st>>>(g, reqs, rots, bits); break;
+    case 32: k_vox_export<32><<<grid, 256, 0, st>>>(g, reqs, rots, bits, ps); break;
+    case 64: k_vox_export<64><<<grid, 256, 0, st>>>(g, reqs, rots, bits, ps); break;
+    case 96: k_vox_export<96><<<grid, 256, 0, st>>>(g, reqs, rots, bits, ps); break;
+    case 128: k_vox_export<128><<<grid, 256, 0, st>>>(g, reqs, rots, bits, ps); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -692,13 +701,20 @@ cudaError_t launch_vox_export(const Geo &g, const ReqDev *reqs, const RotRec *ro
 // K_B: per chunk of 32 columns f = ky P + kx: forward FFT along z (N non-zero
 // inputs), multiply by conj(F(O)) / M^3, inverse FFT along z.  The spectrum
 // of the chunk stays in registers across the `group` rotations of the block.
+// DUAL (label-aware score): each rotation has a second tile, Y2, the
+// transform of the voxels reached only by non-contact poses; its product
+// with conj(F(min(O, 0))) / M^3 is added before the inverse FFT, so one
+// inverse transform yields the sum of both correlations.  Requests without
+// non-contact poses skip the addition and keep the plain result bit for bit.
 // ---------------------------------------------------------------------------
-template <int M>
+template <int M, bool DUAL>
 __global__ void __launch_bounds__(Plan<M>::T * 32)
-k_zpass(int P, int B, int group, const float2 *Y, const RotRec *rots, const ReqDev *reqs, float2 *Z, const float2 *tw_g)
+k_zpass(int P, int B, int group, const float2 *Y, const float2 *Y2, const RotRec *rots, const ReqDev *reqs, float2 *Z,
+        const float2 *tw_g)
 {
     constexpr int N = M / 2, E = Plan<M>::E, COLS = 32;
     constexpr int R_LAST = Plan<M>::R(Plan<M>::S - 1);
+    constexpr int TPR = DUAL ? 2 : 1;        // tiles per rotation
     extern __shared__ __align__(16) unsigned char smem[];
     cf *xb = reinterpret_cast<cf *>(smem);   // [M][COLS]
     cf *tw = xb + M * COLS;                  // [M]
@@ -710,38 +726,43 @@ k_zpass(int P, int B, int group, const float2 *Y, const RotRec *rots, const ReqD
     const size_t f0 = (size_t)chunk * COLS;
     const int b0 = blockIdx.y * group;
     const int nb = min(group, B - b0);
+    const int nt = nb * TPR;
     // spectrum values in input-slot order of the inverse transform: slot
     // s <-> kz = j + (M/E) s; held in registers across the block's rotations
     // and reloaded when the request (object) changes
     cf sp[E];
     int sp_req = -1;
-    // asynchronous copy of rotation b's non-zero z rows of this chunk (coalesced 256-byte rows)
-    auto prefetch = [&](int bi) {
-        const float2 *Yb = Y + (size_t)(b0 + bi) * N * plane + f0;
-        cf *dst = yt + (bi & 1) * N * COLS;
+    // asynchronous copy of tile t's non-zero z rows of this chunk (coalesced 256-byte rows)
+    auto prefetch = [&](int t) {
+        const float2 *src = (DUAL && (t & 1)) ? Y2 : Y;
+        const float2 *Yb = src + (size_t)(b0 + t / TPR) * N * plane + f0;
+        cf *dst = yt + (t & 1) * N * COLS;
         for (int e = threadIdx.x; e < N * COLS; e += blockDim.x) cp_async8(&dst[e], &Yb[(size_t)(e / COLS) * plane + e % COLS]);
         cp_async_commit();
     };
-    if (nb > 0) prefetch(0);
-    for (int bi = 0; bi < nb; ++bi) {
-        if (bi + 1 < nb) {
-            prefetch(bi + 1);
+    if (nt > 0) prefetch(0);
+    cf w[E];
+    for (int t = 0; t < nt; ++t) {
+        if (t + 1 < nt) {
+            prefetch(t + 1);
             cp_async_wait_one();
         } else {
             cp_async_wait_all();
         }
         __syncthreads();
+        const int bi = t / TPR;
+        const bool second = DUAL && (t & 1);
         const int req = rots[b0 + bi].req;
-        if (req != sp_req) {
+        if (!second && req != sp_req) {
             const float2 *spec = reqs[req].spec;
 #pragma unroll
             for (int s = 0; s < E; ++s) {
-                float2 t = spec[((size_t)chunk * M + (j + (M / E) * s)) * COLS + c];
-                sp[s] = cmake(t.x, t.y);
+                float2 v = spec[((size_t)chunk * M + (j + (M / E) * s)) * COLS + c];
+                sp[s] = cmake(v.x, v.y);
             }
             sp_req = req;
         }
-        const cf *src = yt + (bi & 1) * N * COLS;
+        const cf *src = yt + (t & 1) * N * COLS;
         cf v[E];
 #pragma unroll
         for (int s = 0; s < E; ++s) {
@@ -750,45 +771,64 @@ k_zpass(int P, int B, int group, const float2 *Y, const RotRec *rots, const ReqD
         }
         fft_column<M, false>(v, j, xb, c, COLS, tw);
         // forward output slot (bb, r) holds kz = j + (M/E)(bb + (E/R_LAST) r)
-        cf w[E];
+        if (!second) {
 #pragma unroll
-        for (int bb = 0; bb < E / R_LAST; ++bb)
+            for (int bb = 0; bb < E / R_LAST; ++bb)
 #pragma unroll
-            for (int r = 0; r < R_LAST; ++r) {
-                int k = bb + (E / R_LAST) * r;
-                w[k] = cmul(v[bb * R_LAST + r], sp[k]);
+                for (int r = 0; r < R_LAST; ++r) {
+                    int k = bb + (E / R_LAST) * r;
+                    w[k] = cmul(v[bb * R_LAST + r], sp[k]);
+                }
+        } else if (reqs[req].P_nc > 0) {
+            const float2 *pen = reqs[req].spec_pen;
+#pragma unroll
+            for (int bb = 0; bb < E / R_LAST; ++bb)
+#pragma unroll
+                for (int r = 0; r < R_LAST; ++r) {
+                    int k = bb + (E / R_LAST) * r;
+                    float2 q = pen[((size_t)chunk * M + (j + (M / E) * k)) * COLS + c];
+                    w[k] = cadd(w[k], cmul(v[bb * R_LAST + r], cmake(q.x, q.y)));
+                }
+        }
+        if (!DUAL || second) {
+            __syncthreads();
+            fft_column<M, true>(w, j, xb, c, COLS, tw);
+            float2 *Zb = Z + (size_t)(b0 + bi) * M * plane + f0 + c;
+#pragma unroll
+            for (int s = 0; s < E; ++s) {
+                int z = out_index<M>(j, s);
+                Zb[(size_t)z * plane] = make_float2(w[s].x, w[s].y);
             }
-        __syncthreads();
-        fft_column<M, true>(w, j, xb, c, COLS, tw);
-        float2 *Zb = Z + (size_t)(b0 + bi) * M * plane + f0 + c;
-#pragma unroll
-        for (int s = 0; s < E; ++s) {
-            int z = out_index<M>(j, s);
-            Zb[(size_t)z * plane] = make_float2(w[s].x, w[s].y);
         }
         __syncthreads();
     }
 }
 
+template <int MM, bool DUAL>
+static cudaError_t launch_zpass_t(const Geo &g, dim3 grid, int B, int group, const float2 *Y, const float2 *Y2,
+                                  const RotRec *rots, const ReqDev *reqs, float2 *Z, const float2 *tw, cudaStream_t st)
+{
+    size_t sm = sizeof(cf) * ((size_t)MM * 32 + MM + (size_t)MM * 32);
+    cudaError_t e = cudaFuncSetAttribute(k_zpass<MM, DUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_zpass<MM, DUAL><<<grid, Plan<MM>::T * 32, sm, st>>>(g.P, B, group, Y, Y2, rots, reqs, Z, tw);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_zpass(const Geo &g, int B, int group, const float2 *Y, const RotRec *rots, const ReqDev *reqs,
-                         float2 *Z, const float2 *tw, cudaStream_t st)
+                         float2 *Z, const float2 *tw, cudaStream_t st, const float2 *Y2)
 {
     int chunks = g.M * g.P / 32;
     dim3 grid(chunks, (B + group - 1) / group);
     switch (g.M) {
-#define ZCASE(MM)                                                                                            \
-    case MM: {                                                                                               \
-        size_t sm = sizeof(cf) * ((size_t)MM * 32 + MM + (size_t)MM * 32);                                   \
-        cudaError_t e = cudaFuncSetAttribute(k_zpass<MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-        if (e != cudaSuccess) return e;                                                                      \
-        k_zpass<MM><<<grid, Plan<MM>::T * 32, sm, st>>>(g.P, B, group, Y, rots, reqs, Z, tw);                \
-        break;                                                                                               \
-    }
+#define ZCASE(MM)                                                                                    \
+    case MM:                                                                                         \
+        return Y2 ? launch_zpass_t<MM, true>(g, grid, B, group, Y, Y2, rots, reqs, Z, tw, st)        \
+                  : launch_zpass_t<MM, false>(g, grid, B, group, Y, nullptr, rots, reqs, Z, tw, st);
         ZCASE(64) ZCASE(128) ZCASE(192) ZCASE(256)
 #undef ZCASE
     default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

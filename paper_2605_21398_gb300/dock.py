@@ -108,6 +108,8 @@ SIGNATURES = [
                               ctypes.POINTER(_vp)]),
     ("dock_sweep_free", None, [_vp]),
     ("dock_sweep_voxelise", _st, [_vp, _vp, _dp, ctypes.c_int32, _u8p, _dp]),
+    ("dock_sweep_set_label_aware", _st, [_vp, _vp, ctypes.c_int32]),
+    ("dock_sweep_voxelise_labels", _st, [_vp, _vp, _dp, ctypes.c_int32, _u8p, _u8p, _dp]),
     ("dock_search_so3", _st, [_vp, _vp, _vp, ctypes.POINTER(SearchDesc), ctypes.POINTER(Candidate),
                               ctypes.POINTER(Peak)]),
     ("dock_search_scores", _st, [_vp, _vp, _vp, _dp, _fp]),
@@ -454,6 +456,24 @@ class DockSweep:
         self.ctx.check(lib().dock_sweep_voxelise(self.ctx.h, self.h, qp, n, bits.ctypes.data_as(_u8p),
                                                  orig.ctypes.data_as(_dp)))
         return bits, orig
+
+    def set_label_aware(self, on=True):
+        """Score contact poses with O and non-contact poses with min(O, 0)."""
+        self.ctx.check(lib().dock_sweep_set_label_aware(self.ctx.h, self.h, int(bool(on))))
+
+    def voxelise_labels(self, quats):
+        """(S_c, S_n, origins): voxels swept by contact poses, voxels swept
+        only by non-contact poses."""
+        q, qp = _d(quats)
+        q = q.reshape(-1, 4)
+        n = len(q)
+        N = self.N
+        bc = np.empty((n, N, N, N), dtype=np.uint8)
+        bn = np.empty((n, N, N, N), dtype=np.uint8)
+        orig = np.empty((n, 3))
+        self.ctx.check(lib().dock_sweep_voxelise_labels(self.ctx.h, self.h, qp, n, bc.ctypes.data_as(_u8p),
+                                                        bn.ctypes.data_as(_u8p), orig.ctypes.data_as(_dp)))
+        return bc, bn, orig
 
     def close(self):
         if self.h and self.ctx.h:
