@@ -18,6 +18,9 @@ adds the steps that are plain definitions or textbook library primitives:
 * the label-aware score (Sec. I and IV-A: trajectories hold contact and
   non-contact evidence): voxels swept by a contact pose score O, voxels swept
   only by non-contact poses score min(O, 0), the penetration part alone.
+* the rotation mechanism Sec. IV-D prints: the object grid rotated and
+  resampled by trilinear interpolation per sample, correlated with the fixed
+  swept grid (`search_rotate_object`).
 
 Parity unpinned: the Super-Fibonacci constants beyond the paper's
 nearest-neighbour statistic (Sec. VI: 8.0 deg at n = 20000), and the
@@ -276,6 +279,48 @@ def search(O, o_o, poses, quats, h, N, r, L, fft=True):
         C = correlate_fft(O, S, M) if fft else correlate_direct(O, S, M)
         sc, idx = peak(C)
         out.append(dict(score=sc, idx=idx, dk=canvas_shift(idx, M, N), o_s=o_s, C=C, S=S))
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Sec. IV-D as printed: rotate the object grid, keep the swept grid fixed
+# ----------------------------------------------------------------------------
+
+IDENTITY_Q = np.array([1.0, 0.0, 0.0, 0.0])
+
+
+def rotate_object(O, o_o, q, h):
+    """(O_R, o_R): O rotated by R(q) and resampled by trilinear interpolation
+    (zero outside O's lattice) onto the lattice h k + o_R, with
+    o_R = h round(R c_o / h) - (N/2) h, c_o = o_o + (N/2) h."""
+    N = O.shape[0]
+    Oc = _c64(O)
+    OR = np.empty((N, N, N))
+    oR = np.empty(3)
+    lib().orc_rotate_object(_p(Oc), ctypes.c_int32(N), _p(_c64(o_o)), _p(_c64(q)), ctypes.c_double(h), _p(OR),
+                            _p(oR))
+    return OR, oR
+
+
+def pose_from_peak_rotated_object(q, dk, h, o_s, o_R):
+    """Object voxel k of O_R (world point h k + o_R for the pose (R, 0)) meets
+    swept voxel k + dk (world point h (k + dk) + o_s): T = (R, h dk + o_s - o_R)."""
+    return quat_to_mat(q), h * np.asarray(dk, dtype=np.float64) + o_s - o_R
+
+
+def search_rotate_object(O, o_o, poses, quats, h, N, r, L, fft=True):
+    """Sec. IV-D as printed: S on the world-aligned lattice of the mean tip,
+    fixed; per rotation O_R and C = Eq. (7) of O_R with S; the peak and its pose."""
+    M = canvas_size(N)
+    S, o_s = sweep_grid(poses, IDENTITY_Q, h, N, r, L)
+    out = []
+    for q in quats:
+        OR, oR = rotate_object(O, o_o, q, h)
+        C = correlate_fft(OR, S, M) if fft else correlate_direct(OR, S, M)
+        sc, idx = peak(C)
+        dk = canvas_shift(idx, M, N)
+        R, t = pose_from_peak_rotated_object(q, dk, h, o_s, oR)
+        out.append(dict(score=sc, idx=idx, dk=dk, o_s=o_s, o_R=oR, C=C, t=t))
     return out
 
 

@@ -18,6 +18,8 @@
  *                        probe along the trajectory, on a lattice rotated by R.
  *   orc_sweep_grid_sel   the same over a subset of the poses (contact or
  *                        non-contact labels), on the lattice of all poses.
+ *   orc_rotate_object    Sec. IV-D: O rotated by R and resampled by trilinear
+ *                        interpolation (the paper's own rotation mechanism).
  *   orc_probe_sdf        Sec. V-B: flat-ended cylinder SDF f_p and its gradient.
  *   orc_tri_min          Sec. V-B: minimum of f_p over a triangle (bisection
  *                        inside golden-section search; see the function).
@@ -382,6 +384,52 @@ ORC_API void orc_sweep_grid(const double *poses, int64_t P, const double *q, dou
                             double r, double L, double *origin, uint8_t *S)
 {
     orc_sweep_grid_sel(poses, P, NULL, q, h, N, r, L, origin, S);
+}
+
+/*
+ * Sec. IV-D, the paper's rotation mechanism: the object grid rotated by R and
+ * resampled by trilinear interpolation onto a lattice of spacing h.
+ *   o_R = h round(R c_o / h) - (N/2) h with c_o = o_o + (N/2) h, so the
+ *         rotated lattice follows the rotated lattice centre (the rule of
+ *         o_s,R with R in place of R^T);
+ *   O_R[k] = O~(R^T (h k + o_R)), O~ the trilinear interpolant of O on its
+ *         lattice (h k + o_o), zero at lattice points outside [0, N)^3.
+ */
+ORC_API void orc_rotate_object(const double *O, int32_t N, const double *o_o, const double *q, double h,
+                               double *O_R, double *o_R)
+{
+    double R[9];
+    orc_quat_to_mat(q, R);
+    double c[3];
+    for (int a = 0; a < 3; ++a) c[a] = o_o[a] + (double)(N / 2) * h;
+    for (int a = 0; a < 3; ++a) {
+        double u = (R[a * 3 + 0] * c[0] + R[a * 3 + 1] * c[1]) + R[a * 3 + 2] * c[2];
+        o_R[a] = lattice_origin(u, h, N);
+    }
+    for (int64_t kz = 0; kz < N; ++kz)
+        for (int64_t ky = 0; ky < N; ++ky)
+            for (int64_t kx = 0; kx < N; ++kx) {
+                double x[3] = {h * (double)kx + o_R[0], h * (double)ky + o_R[1], h * (double)kz + o_R[2]};
+                double v[3];
+                int64_t i0[3];
+                double f[3];
+                for (int a = 0; a < 3; ++a) {
+                    double y = (R[0 * 3 + a] * x[0] + R[1 * 3 + a] * x[1]) + R[2 * 3 + a] * x[2];
+                    v[a] = (y - o_o[a]) / h;
+                    i0[a] = (int64_t)floor(v[a]);
+                    f[a] = v[a] - (double)i0[a];
+                }
+                double acc = 0.0;
+                for (int dz = 0; dz < 2; ++dz)
+                    for (int dy = 0; dy < 2; ++dy)
+                        for (int dx = 0; dx < 2; ++dx) {
+                            int64_t jx = i0[0] + dx, jy = i0[1] + dy, jz = i0[2] + dz;
+                            if (jx < 0 || jy < 0 || jz < 0 || jx >= N || jy >= N || jz >= N) continue;
+                            double w = (dx ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
+                            acc += w * O[(jz * N + jy) * N + jx];
+                        }
+                O_R[(kz * N + ky) * N + kx] = acc;
+            }
 }
 
 /* ------------------------------------------------------------------ */

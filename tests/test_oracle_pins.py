@@ -338,6 +338,93 @@ def test_label_aware_score_bounds(workload):
 
 
 # --------------------------------------------------------------------------
+# Sec. IV-D as printed: the object grid rotated by trilinear resampling
+# --------------------------------------------------------------------------
+
+def test_rotated_object_at_identity_is_the_object_and_the_plain_search(workload):
+    w = workload("tiny32")
+    Og, o_o, _, _ = O.object_grid(w.obj.verts, w.obj.tris, w.h, w.N)
+    OR, oR = O.rotate_object(Og, o_o, O.IDENTITY_Q, w.h)
+    assert np.array_equal(OR, Og) and np.array_equal(oR, o_o)
+    a = O.search_rotate_object(Og, o_o, w.poses_world, [O.IDENTITY_Q], w.h, w.N, w.radius, w.length)[0]
+    b = O.search(Og, o_o, w.poses_world, [O.IDENTITY_Q], w.h, w.N, w.radius, w.length)[0]
+    assert np.array_equal(a["C"], b["C"]) and a["idx"] == b["idx"]
+    _, tb = O.pose_from_peak(O.IDENTITY_Q, b["dk"], w.h, b["o_s"], o_o)
+    assert np.allclose(a["t"], tb, atol=1e-12)
+
+
+def test_trilinear_resampling_reproduces_a_linear_field():
+    # trilinear interpolation is exact on a field linear in position, so O_R
+    # must equal that linear function at the object-frame point R^T x its
+    # voxel x samples (pins R^T against R, the origin o_R and the weights),
+    # and read zero where the preimage is more than a voxel off the lattice
+    rng = np.random.default_rng(31)
+    N, h = 12, 0.7
+    o_o = np.array([-4.2, -3.5, -4.9])
+    a, b = np.array([0.3, -1.1, 0.7]), 2.5
+    kz, ky, kx = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
+    pts = np.stack([h * kx + o_o[0], h * ky + o_o[1], h * kz + o_o[2]], -1)
+    Olin = pts @ a + b
+    for q in synth.random_quat(rng, 4):
+        OR, oR = O.rotate_object(Olin, o_o, q, h)
+        R = O.quat_to_mat(q)
+        c_o = o_o + (N // 2) * h
+        assert np.all(np.abs(oR + (N // 2) * h - R @ c_o) <= 0.5 * h + 1e-12)
+        n = (oR + (N // 2) * h) / h
+        assert np.allclose(n, np.round(n), atol=1e-9)
+        x = np.stack([h * kx + oR[0], h * ky + oR[1], h * kz + oR[2]], -1)
+        y = x @ R                                   # each row is R^T x
+        u = (y - o_o) / h
+        inside = np.all((u >= 0) & (u <= N - 1), axis=-1)
+        assert inside.sum() > N ** 3 // 10
+        assert np.max(np.abs(OR[inside] - (y @ a + b)[inside])) <= 1e-12 * np.abs(Olin).max() * 100
+        far = np.any((u <= -1) | (u >= N), axis=-1)
+        assert far.sum() > 0 and np.all(OR[far] == 0.0)
+
+
+def test_quarter_turns_permute_the_object_grid(workload):
+    # a rotation that maps the lattice onto itself moves every value to one
+    # lattice point: the multiset of values is kept (no blending, no loss)
+    w = workload("tiny32")
+    Og, o_o, _, _ = O.object_grid(w.obj.verts, w.obj.tris, w.h, w.N)
+    s2 = math.sqrt(0.5)
+    for q in [(s2, 0, 0, s2), (s2, s2, 0, 0), (0, 0, 1, 0), (0.5, 0.5, 0.5, 0.5)]:
+        OR, _ = O.rotate_object(Og, o_o, np.array(q), w.h)
+        assert np.allclose(np.sort(OR.ravel()), np.sort(Og.ravel()), atol=1e-9)
+    q = synth.random_quat(np.random.default_rng(4))
+    OR, _ = O.rotate_object(Og, o_o, q, w.h)       # a generic rotation blends values
+    assert not np.allclose(np.sort(OR.ravel()), np.sort(Og.ravel()), atol=1e-3)
+    assert abs(OR.sum() - Og.sum()) <= 0.02 * np.abs(Og).sum()   # the integral is nearly kept
+
+
+@pytest.mark.parametrize("name", ["tiny32", "free64"])
+def test_rotating_the_object_equals_rotating_the_sweep_at_quarter_turns(workload, name):
+    # where no interpolation is involved (rotations mapping the lattice onto
+    # itself) the two mechanisms describe the same configurations: equal peak
+    # scores and equal poses (pins Eq. (8) of both forms against each other)
+    w = workload(name)
+    Og, o_o, _, _ = O.object_grid(w.obj.verts, w.obj.tris, w.h, w.N)
+    s2 = math.sqrt(0.5)
+    for q in [(s2, 0, 0, s2), (s2, s2, 0, 0), (0.5, 0.5, 0.5, 0.5)]:
+        q = np.array(q)
+        a = O.search_rotate_object(Og, o_o, w.poses_world, [q], w.h, w.N, w.radius, w.length)[0]
+        b = O.search(Og, o_o, w.poses_world, [q], w.h, w.N, w.radius, w.length)[0]
+        assert abs(a["score"] - b["score"]) <= 1e-9 * abs(b["score"])
+        _, tb = O.pose_from_peak(q, b["dk"], w.h, b["o_s"], o_o)
+        assert np.allclose(a["t"], tb, atol=1e-9)
+
+
+def test_rotated_object_search_recovers_the_planted_pose(workload):
+    # at 64^3 / 0.25 mm; at 32^3 / 0.5 mm the inner band (0.2 mm) is narrower
+    # than a voxel and interpolation blends it into the -50 interior
+    w = workload("free64")
+    Og, o_o, _, fits = O.object_grid(w.obj.verts, w.obj.tris, w.h, w.N)
+    assert fits
+    res = O.search_rotate_object(Og, o_o, w.poses_world, [w.gt_q], w.h, w.N, w.radius, w.length)[0]
+    assert np.linalg.norm(res["t"] - w.gt_t) <= 2 * math.sqrt(3) * w.h
+
+
+# --------------------------------------------------------------------------
 # Sec. IV-C: samplers
 # --------------------------------------------------------------------------
 
