@@ -216,9 +216,35 @@ DOCK_API dock_status dock_sweep_voxelise(dock_ctx *ctx, const dock_sweep *sw, co
  * unchanged.  The first label-aware search of an object computes and keeps
  * conj(F(min(O, 0))) beside its spectrum (the same size).  Default 0 (Eq. (7)
  * over all poses).  dock_search_peaks_noalloc rejects a label-aware sweep
- * (DOCK_E_INVALID).  Returns DOCK_E_INVALID for on outside {0, 1}.
+ * (DOCK_E_INVALID).  Returns DOCK_E_INVALID for on outside {0, 1} and for
+ * on = 1 while dock_sweep_set_rotate_object is on.
  */
 DOCK_API dock_status dock_sweep_set_label_aware(dock_ctx *ctx, dock_sweep *sw, int32_t on);
+
+/*
+ * The rotation mechanism as Sec. IV-D prints it.  With on = 1, searches and
+ * registrations of this sweep that start after the call rotate the object
+ * grid instead of the swept volume: S is voxelised once, on the
+ * world-aligned lattice o_s = h round(c_s / h) - (N/2) h, and for each
+ * orientation sample R
+ *     O_R[k] = trilinear interpolant of O at R^T (h k + o_R) (zero outside
+ *              O's lattice), o_R = h round(R c_o / h) - (N/2) h,
+ *              c_o = o_o + (N/2) h;
+ *     C[dk] = sum_k O_R[k] S[k + dk]  (Eq. (7));
+ *     pose T = (R, h dk + o_s - o_R).
+ * The first such search of a sweep computes and keeps F(S) / M^3 (the size
+ * of an object spectrum).  Interpolation blends the -50 interior into the
+ * contact band by up to a voxel, so scores differ from the default (which
+ * voxelises the rotated sweep exactly); at rotations that map the lattice
+ * onto itself the two agree.  Default 0.  Excludes the label-aware score
+ * (DOCK_E_INVALID while it is on); dock_search_peaks_noalloc rejects such a
+ * sweep.  Returns DOCK_E_INVALID for on outside {0, 1}.
+ */
+DOCK_API dock_status dock_sweep_set_rotate_object(dock_ctx *ctx, dock_sweep *sw, int32_t on);
+/* O_R and o_R above for `n` quaternions into host grids (n x N^3 floats) and
+ * origins (n x 3 doubles, nullable).  Test hook. */
+DOCK_API dock_status dock_object_rotated(dock_ctx *ctx, const dock_object *obj, const double *quats, int32_t n,
+                                         float *grids, double *origins);
 /* S_c and S_n above for `n` quaternions into host bits_c, bits_n (n x N^3
  * bytes each, 0/1) and the origins (n x 3 doubles, nullable).  Test hook. */
 DOCK_API dock_status dock_sweep_voxelise_labels(dock_ctx *ctx, const dock_sweep *sw, const double *quats, int32_t n,

@@ -164,6 +164,12 @@ struct dock_sweep {
     PoseRec *poses_lab = nullptr;
     int64_t P_c = 0;
     std::atomic<bool> label_aware{false};
+    // rotating the object (Sec. IV-D as printed): S on the world-aligned
+    // lattice of the mean tip, its spectrum F(S) / M^3 and origin o_s, made
+    // on first use
+    std::atomic<bool> rotate_object{false};
+    float2 *spec_S = nullptr;
+    double *os_dev = nullptr;
 };
 
 static dock_status fail(dock_ctx *ctx, dock_status st, const char *fmt, ...)
@@ -1018,6 +1024,8 @@ extern "C" void dock_sweep_free(dock_sweep *sw)
     cudaFree(sw->cs_dev);
     cudaFree(sw->labels);
     cudaFree(sw->poses_lab);
+    cudaFree(sw->spec_S);
+    cudaFree(sw->os_dev);
     ctx->held = ctx->held >= sw->bytes ? ctx->held - sw->bytes : 0;
     delete sw;
 }
@@ -1055,8 +1063,9 @@ static dock_status ensure(dock_ctx *ctx, void **p, size_t *have, size_t need, si
 // Upload `count` quaternions (host q) to slots [base, base + count) of the
 // context's rotation arrays (capacity `cap`) and build their lattice set-up
 // records: sample indices rot0.., request index `req`.
+// o_o (nullable, device): rotate the object instead of the sweep.
 static dock_status upload_rots(dock_ctx *ctx, const dock_sweep *sw, const double *q, size_t cap, size_t base, int count,
-                               int rot0, int req)
+                               int rot0, int req, const double *o_o = nullptr)
 {
     dock_status s;
     if ((s = ensure(ctx, (void **)&ctx->quats, &ctx->quats_n, cap * 4, sizeof(double))) != DOCK_OK) return s;
@@ -1065,7 +1074,7 @@ static dock_status upload_rots(dock_ctx *ctx, const dock_sweep *sw, const double
     CK(ctx, cudaMemcpyAsync(ctx->quats + 4 * base, q, sizeof(double) * 4 * count, cudaMemcpyHostToDevice, ctx->stream));
     Prof pr(ctx, "rot_setup");
     CK(ctx, launch_rot_setup(ctx->quats + 4 * base, count, rot0, req, sw->cs_dev, sw->h, sw->N, ctx->rots + base,
-                             ctx->stream));
+                             ctx->stream, o_o));
     return DOCK_OK;
 }
 
@@ -1073,7 +1082,10 @@ static dock_status upload_rots(dock_ctx *ctx, const dock_sweep *sw, const double
 // as pose set 1); a sweep whose poses are all contact has no set 1 and
 // scores as a plain one.  For a search, ob->spec_pen must exist
 // (ensure_spec_pen) before a label-aware table is used.
-static ReqDev make_reqdev(const dock_object *ob, const dock_sweep *sw, unsigned long long *keys, bool la)
+// ro: rotate the object; spec is then the sweep's F(S) / M^3 (ensure_spec_S
+// first) and Og the object grid.
+static ReqDev make_reqdev(const dock_object *ob, const dock_sweep *sw, unsigned long long *keys, bool la,
+                          bool ro = false)
 {
     ReqDev q;
     q.poses = sw->poses;
@@ -1096,6 +1108,13 @@ static ReqDev make_reqdev(const dock_object *ob, const dock_sweep *sw, unsigned 
     q.lv = (float)(sw->L / sw->h);
     q.spec = ob ? ob->spec : nullptr;
     q.keys = keys;
+    q.Og = nullptr;
+    q.rotate_object = 0;
+    if (ro) {
+        q.spec = sw->spec_S;
+        q.Og = ob ? ob->O : nullptr;
+        q.rotate_object = 1;
+    }
     return q;
 }
 
@@ -1148,7 +1167,19 @@ extern "C" dock_status dock_sweep_set_label_aware(dock_ctx *ctx, dock_sweep *sw,
 {
     if (!ctx || !sw || sw->ctx != ctx) return DOCK_E_INVALID;
     if (on != 0 && on != 1) return fail(ctx, DOCK_E_INVALID, "label_aware must be 0 or 1");
+    if (on && sw->rotate_object.load())
+        return fail(ctx, DOCK_E_INVALID, "the label-aware score needs the rotated sweep (rotate_object is on)");
     sw->label_aware.store(on != 0);
+    return DOCK_OK;
+}
+
+extern "C" dock_status dock_sweep_set_rotate_object(dock_ctx *ctx, dock_sweep *sw, int32_t on)
+{
+    if (!ctx || !sw || sw->ctx != ctx) return DOCK_E_INVALID;
+    if (on != 0 && on != 1) return fail(ctx, DOCK_E_INVALID, "rotate_object must be 0 or 1");
+    if (on && sw->label_aware.load())
+        return fail(ctx, DOCK_E_INVALID, "rotating the object excludes the label-aware score (label_aware is on)");
+    sw->rotate_object.store(on != 0);
     return DOCK_OK;
 }
 
@@ -1191,6 +1222,54 @@ extern "C" dock_status dock_sweep_voxelise_labels(dock_ctx *ctx, const dock_swee
     if (e != cudaSuccess) return cuda_fail(ctx, e, "voxelise_labels");
     // the scored non-contact grid is the part that no contact pose covers
     for (size_t i = 0; i < per * n; ++i) bits_n[i] = bits_n[i] && !bits_c[i];
+    if (origins)
+        for (int i = 0; i < n; ++i) memcpy(origins + 3 * i, rr[i].o, sizeof(double) * 3);
+    return DOCK_OK;
+}
+
+extern "C" dock_status dock_object_rotated(dock_ctx *ctx, const dock_object *ob, const double *quats, int32_t n,
+                                           float *grids, double *origins)
+{
+    if (!ctx || !ob || !quats || n <= 0 || !grids) return DOCK_E_INVALID;
+    DevLock dev_lock_(ctx);
+    if (ctx->dead) return fail(ctx, DOCK_E_CUDA_FATAL, "context is dead after a sticky CUDA error");
+    cudaSetDevice(ctx->device);
+    dock_search_desc d = {};
+    d.sampler = DOCK_SAMPLER_EXPLICIT;
+    d.n = n;
+    d.quats = quats;
+    std::vector<double> q;
+    dock_status s;
+    if ((s = gen_samples(ctx, &d, q)) != DOCK_OK) return s;
+    if ((s = ensure(ctx, (void **)&ctx->quats, &ctx->quats_n, (size_t)n * 4, sizeof(double))) != DOCK_OK) return s;
+    if ((s = ensure(ctx, (void **)&ctx->rots, &ctx->rots_n, (size_t)n, sizeof(RotRec))) != DOCK_OK) return s;
+    CK(ctx, cudaMemcpyAsync(ctx->quats, q.data(), sizeof(double) * 4 * n, cudaMemcpyHostToDevice, ctx->stream));
+    // the object's origin drives the set-up (no sweep mean is read)
+    CK(ctx, launch_rot_setup(ctx->quats, n, 0, 0, nullptr, ob->h, ob->N, ctx->rots, ctx->stream, ob->o_dev));
+    ReqDev r = {};
+    r.Og = ob->O;
+    r.rotate_object = 1;
+    std::vector<ReqDev> rq(1, r);
+    if ((s = upload_reqs(ctx, rq)) != DOCK_OK) return s;
+    Geo g = {};
+    g.N = ob->N;
+    g.M = ob->M;
+    g.P = ob->P;
+    g.h = ob->h;
+    const size_t per = (size_t)g.N * g.N * g.N;
+    float *dg = nullptr;
+    if ((s = dalloc(ctx, (void **)&dg, sizeof(float) * per * n, nullptr)) != DOCK_OK) return s;
+    cudaError_t e;
+    {
+        Prof pr(ctx, "rot_export");
+        e = launch_rot_export(g, ctx->reqs, ctx->rots, n, dg, ctx->stream);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(grids, dg, sizeof(float) * per * n, cudaMemcpyDeviceToHost, ctx->stream);
+    std::vector<RotRec> rr(n);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rr.data(), ctx->rots, sizeof(RotRec) * n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dfree(ctx, dg, sizeof(float) * per * n);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "object_rotated");
     if (origins)
         for (int i = 0; i < n; ++i) memcpy(origins + 3 * i, rr[i].o, sizeof(double) * 3);
     return DOCK_OK;
@@ -1279,11 +1358,11 @@ static dock_status run_pipeline_rots(dock_ctx *ctx, const Geo &g, const ReqDev *
         }
         {
             Prof pr(ctx, "fwd2d");
-            CK(ctx, launch_fwd2d(g, nb, ctx->bits, Y, tw, qt, ctx->stream));
+            CK(ctx, launch_fwd2d(g, nb, ctx->bits, Y, tw, qt, ctx->stream, nullptr, rb, reqs));
         }
         if (dual) {
             Prof pr(ctx, "fwd2d_nc");
-            CK(ctx, launch_fwd2d(g, nb, bits2, Y2, tw, qt, ctx->stream, ctx->bits));
+            CK(ctx, launch_fwd2d(g, nb, bits2, Y2, tw, qt, ctx->stream, ctx->bits, rb, reqs));
         }
         {
             Prof pr(ctx, dual ? "zpass_dual" : "zpass");
@@ -1344,25 +1423,90 @@ static dock_status ensure_spec_pen(dock_ctx *ctx, const dock_object *obc)
     return DOCK_OK;
 }
 
+// The fixed swept grid of the rotated-object search: S voxelised on the
+// lattice of the identity rotation (origin o_s = h round(c_s / h) - (N/2) h),
+// its spectrum F(S) / M^3 and o_s, made on first use and kept with the sweep.
+static dock_status ensure_spec_S(dock_ctx *ctx, const dock_sweep *swc)
+{
+    dock_sweep *sw = const_cast<dock_sweep *>(swc);
+    if (sw->spec_S) return DOCK_OK;
+    const Geo g = make_geo(sw);
+    const int N = g.N, M = g.M, P = g.P;
+    float2 *tw, *qt;
+    double2 *twd;
+    dock_status s;
+    if ((s = tables(ctx, M, &tw, &qt, &twd)) != DOCK_OK) return s;
+    const double qi[4] = {1.0, 0.0, 0.0, 0.0};
+    if ((s = upload_rots(ctx, sw, qi, 1, 0, 1, 0, 0)) != DOCK_OK) return s;
+    std::vector<ReqDev> rq(1, make_reqdev(nullptr, sw, nullptr, false));
+    if ((s = upload_reqs(ctx, rq)) != DOCK_OK) return s;
+    const size_t spec_n = (size_t)M * P / 32 * M * 32;
+    const size_t bS = sizeof(float) * (size_t)N * N * N;
+    const size_t b1 = sizeof(double2) * (size_t)N * N * (N + 1), b2 = sizeof(double2) * (size_t)N * M * (N + 1);
+    float2 *sp = nullptr;
+    double *os = nullptr;
+    float *Sg = nullptr;
+    double2 *w1 = nullptr, *w2 = nullptr;
+    size_t held = 0;
+    auto release = [&](bool keep) {
+        dfree(ctx, Sg, bS);
+        dfree(ctx, w1, b1);
+        dfree(ctx, w2, b2);
+        if (!keep) {
+            dfree(ctx, sp, sizeof(float2) * spec_n);
+            dfree(ctx, os, sizeof(double) * 3);
+        }
+    };
+    if ((s = dalloc(ctx, (void **)&sp, sizeof(float2) * spec_n, &held)) != DOCK_OK) return s;
+    if ((s = dalloc(ctx, (void **)&os, sizeof(double) * 3, &held)) != DOCK_OK) { release(false); return s; }
+    if ((s = dalloc(ctx, (void **)&Sg, bS, nullptr)) != DOCK_OK) { release(false); return s; }
+    if ((s = dalloc(ctx, (void **)&w1, b1, nullptr)) != DOCK_OK) { release(false); return s; }
+    if ((s = dalloc(ctx, (void **)&w2, b2, nullptr)) != DOCK_OK) { release(false); return s; }
+    cudaError_t e;
+    {
+        Prof pr(ctx, "sweep_spectrum");
+        e = launch_vox_float(g, ctx->reqs, ctx->rots, Sg, ctx->stream);
+        if (e == cudaSuccess) e = launch_spectrum(Sg, N, M, P, w1, w2, twd, sp, ctx->stream, false, false);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(os, reinterpret_cast<const char *>(ctx->rots) + offsetof(RotRec, o), sizeof(double) * 3,
+                            cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        release(false);
+        return cuda_fail(ctx, e, "swept-grid spectrum");
+    }
+    release(true);
+    sw->spec_S = sp;
+    sw->os_dev = os;
+    sw->bytes += held;
+    return DOCK_OK;
+}
+
+// The search of this sweep rotates the object grid.
+static bool rotates_object(const dock_sweep *sw) { return sw->rotate_object.load(); }
+
 static dock_status search_impl(dock_ctx *ctx, const dock_object *ob, const dock_sweep *sw, const dock_search_desc *d,
                                const std::vector<double> &q, int r0, int r1, dock_candidate *out, dock_peak *per_rot)
 {
     const int n = d->n;
     dock_status s;
-    if ((s = upload_rots(ctx, sw, q.data(), n, 0, n, 0, 0)) != DOCK_OK) return s;
+    const bool ro = rotates_object(sw);
+    if (ro && (s = ensure_spec_S(ctx, sw)) != DOCK_OK) return s;
+    if ((s = upload_rots(ctx, sw, q.data(), n, 0, n, 0, 0, ro ? ob->o_dev : nullptr)) != DOCK_OK) return s;
     if ((s = ensure(ctx, (void **)&ctx->keys, &ctx->keys_n, (size_t)n, sizeof(unsigned long long))) != DOCK_OK) return s;
     CK(ctx, cudaMemsetAsync(ctx->keys, 0, sizeof(unsigned long long) * n, ctx->stream));
     CK(ctx, cudaMemsetAsync(ctx->errflag, 0, sizeof(int), ctx->stream));
     const bool dual = dual_scoring(sw);
     if (dual && (s = ensure_spec_pen(ctx, ob)) != DOCK_OK) return s;
-    std::vector<ReqDev> rq(1, make_reqdev(ob, sw, ctx->keys, dual));
+    std::vector<ReqDev> rq(1, make_reqdev(ob, sw, ctx->keys, dual, ro));
     if ((s = upload_reqs(ctx, rq)) != DOCK_OK) return s;
     if ((s = run_pipeline(ctx, make_geo(sw), r0, r1, d->batch, dual)) != DOCK_OK) return s;
     if ((s = ensure(ctx, (void **)&ctx->cands, &ctx->cands_n, (size_t)d->top_k, sizeof(dock_candidate))) != DOCK_OK) return s;
     {
         Prof pr(ctx, "topk");
         CK(ctx, launch_topk(ctx->keys, n, d->top_k, ob->N, ob->M, ob->h, ob->o_dev, ctx->quats, ctx->rots, ctx->cands,
-                            ctx->stream));
+                            ctx->stream, ro ? sw->os_dev : nullptr));
     }
     CK(ctx, cudaMemcpyAsync(out, ctx->cands, sizeof(dock_candidate) * d->top_k, cudaMemcpyDeviceToHost, ctx->stream));
     std::vector<unsigned long long> keys;
@@ -1419,8 +1563,9 @@ extern "C" dock_status dock_search_peaks_noalloc(dock_ctx *ctx, const dock_objec
     if (n < 1 || n > NOALLOC_MAX_ROT)
         return fail(ctx, DOCK_E_INVALID, "rotation count %d outside [1, %d] of dock_search_peaks_noalloc", n,
                     NOALLOC_MAX_ROT);
-    if (dual_scoring(sw))
-        return fail(ctx, DOCK_E_INVALID, "dock_search_peaks_noalloc scores plainly; the sweep is label-aware");
+    if (dual_scoring(sw) || rotates_object(sw))
+        return fail(ctx, DOCK_E_INVALID,
+                    "dock_search_peaks_noalloc rotates the sweep and scores plainly; the sweep asks otherwise");
     for (int i = 0; i < n; ++i) {
         const double *a = quats + 4 * (size_t)i;
         double nq = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);
@@ -1647,10 +1792,12 @@ extern "C" dock_status dock_search_scores(dock_ctx *ctx, const dock_object *ob, 
     d.quats = quat;
     std::vector<double> q;
     if ((s = gen_samples(ctx, &d, q)) != DOCK_OK) return s;
-    if ((s = upload_rots(ctx, sw, q.data(), 1, 0, 1, 0, 0)) != DOCK_OK) return s;
+    const bool ro = rotates_object(sw);
+    if (ro && (s = ensure_spec_S(ctx, sw)) != DOCK_OK) return s;
+    if ((s = upload_rots(ctx, sw, q.data(), 1, 0, 1, 0, 0, ro ? ob->o_dev : nullptr)) != DOCK_OK) return s;
     const bool dual = dual_scoring(sw);
     if (dual && (s = ensure_spec_pen(ctx, ob)) != DOCK_OK) return s;
-    std::vector<ReqDev> rq(1, make_reqdev(ob, sw, nullptr, dual));
+    std::vector<ReqDev> rq(1, make_reqdev(ob, sw, nullptr, dual, ro));
     if ((s = upload_reqs(ctx, rq)) != DOCK_OK) return s;
     Geo g = make_geo(sw);
     float2 *tw, *qt;
@@ -1667,9 +1814,10 @@ extern "C" dock_status dock_search_scores(dock_ctx *ctx, const dock_object *ob, 
     float2 *Y2 = dual ? Y + ysz + zsz : nullptr;
     cudaError_t e = cudaMemsetAsync(ctx->errflag, 0, sizeof(int), ctx->stream);
     if (e == cudaSuccess) e = launch_voxelise(g, ctx->reqs, ctx->rots, 1, ctx->bits, ctx->stream);
-    if (e == cudaSuccess) e = launch_fwd2d(g, 1, ctx->bits, Y, tw, qt, ctx->stream);
+    if (e == cudaSuccess) e = launch_fwd2d(g, 1, ctx->bits, Y, tw, qt, ctx->stream, nullptr, ctx->rots, ctx->reqs);
     if (dual && e == cudaSuccess) e = launch_voxelise(g, ctx->reqs, ctx->rots, 1, ctx->bits + bsz, ctx->stream, 4, 1);
-    if (dual && e == cudaSuccess) e = launch_fwd2d(g, 1, ctx->bits + bsz, Y2, tw, qt, ctx->stream, ctx->bits);
+    if (dual && e == cudaSuccess)
+        e = launch_fwd2d(g, 1, ctx->bits + bsz, Y2, tw, qt, ctx->stream, ctx->bits, ctx->rots, ctx->reqs);
     if (e == cudaSuccess) e = launch_zpass(g, 1, 1, Y, ctx->rots, ctx->reqs, Y + ysz, tw, ctx->stream, Y2);
     if (e == cudaSuccess) e = launch_plane_export(g, Y + ysz, tw, dC, ctx->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(C, dC, csz * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
@@ -2092,6 +2240,7 @@ struct Job {
     bool cancel = false;
     bool async = false;                   // submitted by dock_submit (kept until polled)
     bool la = false;                      // label-aware score (the sweep's mode at submission)
+    bool ro = false;                      // rotate the object (the sweep's mode at submission)
     Clock::time_point t_submit;
 };
 using JobP = std::shared_ptr<Job>;
@@ -2223,6 +2372,7 @@ static dock_status job_admit(dock_ctx *ctx, Engine &E, Job &j, int *wait)
     const size_t bytes = job_bytes(j);
     const bool la = j.la && j.sw->poses_lab;
     size_t pen_bytes = la && !j.ob->spec_pen ? sizeof(float2) * (size_t)j.ob->M * j.ob->P * j.ob->M : 0;
+    if (j.ro && !j.sw->spec_S) pen_bytes += sizeof(float2) * (size_t)j.ob->M * j.ob->P * j.ob->M;
     if (ctx->budget && ctx->held + bytes + pen_bytes + yz_growth(ctx, j.sw, la) > ctx->budget) {
         if (!E.active.empty()) {
             *wait = ADMIT_WAIT;
@@ -2232,6 +2382,7 @@ static dock_status job_admit(dock_ctx *ctx, Engine &E, Job &j, int *wait)
     }
     dock_status s;
     if (la && (s = ensure_spec_pen(ctx, j.ob)) != DOCK_OK) return s;
+    if (j.ro && (s = ensure_spec_S(ctx, j.sw)) != DOCK_OK) return s;
     if ((s = dalloc(ctx, &j.dev, bytes, nullptr)) != DOCK_OK) return s;
     j.dev_bytes = bytes;
     const size_t n = (size_t)j.d.n_global + j.d.n_local;
@@ -2254,9 +2405,10 @@ static dock_status job_admit(dock_ctx *ctx, Engine &E, Job &j, int *wait)
     j.q.assign(4 * n, 0.0);
     memcpy(j.q.data(), qg.data(), sizeof(double) * qg.size());
     CK(ctx, cudaMemcpyAsync(j.dq, j.q.data(), sizeof(double) * 4 * j.d.n_global, cudaMemcpyHostToDevice, ctx->stream));
-    CK(ctx, launch_rot_setup(j.dq, j.d.n_global, 0, j.slot, j.sw->cs_dev, j.sw->h, j.sw->N, j.drot, ctx->stream));
+    CK(ctx, launch_rot_setup(j.dq, j.d.n_global, 0, j.slot, j.sw->cs_dev, j.sw->h, j.sw->N, j.drot, ctx->stream,
+                             j.ro ? j.ob->o_dev : nullptr));
     CK(ctx, cudaMemsetAsync(j.dkey, 0, sizeof(unsigned long long) * n, ctx->stream));
-    ReqDev r = make_reqdev(j.ob, j.sw, j.dkey, la);
+    ReqDev r = make_reqdev(j.ob, j.sw, j.dkey, la, j.ro);
     CK(ctx, cudaMemcpyAsync(E.reqtab + j.slot, &r, sizeof(ReqDev), cudaMemcpyHostToDevice, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));   // r and j.q are host staging of this call
     j.stage = JOB_GLOBAL;
@@ -2279,7 +2431,8 @@ static dock_status job_advance(dock_ctx *ctx, Job &j, bool *final)
     if (j.stage == JOB_GLOBAL && nl > 0) {
         {
             Prof pr(ctx, "topk");
-            CK(ctx, launch_topk(j.dkey, ng, 1, ob->N, ob->M, ob->h, ob->o_dev, j.dq, j.drot, j.dcand, ctx->stream));
+            CK(ctx, launch_topk(j.dkey, ng, 1, ob->N, ob->M, ob->h, ob->o_dev, j.dq, j.drot, j.dcand, ctx->stream,
+                                j.ro ? j.sw->os_dev : nullptr));
         }
         dock_candidate best;
         CK(ctx, cudaMemcpyAsync(&best, j.dcand, sizeof(best), cudaMemcpyDeviceToHost, ctx->stream));
@@ -2295,7 +2448,7 @@ static dock_status job_advance(dock_ctx *ctx, Job &j, bool *final)
         CK(ctx, cudaMemcpyAsync(j.dq + 4 * (size_t)ng, j.q.data() + 4 * (size_t)ng, sizeof(double) * 4 * nl,
                                 cudaMemcpyHostToDevice, ctx->stream));
         CK(ctx, launch_rot_setup(j.dq + 4 * (size_t)ng, nl, ng, j.slot, j.sw->cs_dev, j.sw->h, j.sw->N, j.drot + ng,
-                                 ctx->stream));
+                                 ctx->stream, j.ro ? ob->o_dev : nullptr));
         j.stage = JOB_LOCAL;
         j.s0 = ng;
         j.s1 = ng + nl;
@@ -2305,7 +2458,8 @@ static dock_status job_advance(dock_ctx *ctx, Job &j, bool *final)
     const int n = ng + nl, K = j.d.top_k;
     {
         Prof pr(ctx, "topk");
-        CK(ctx, launch_topk(j.dkey, n, K, ob->N, ob->M, ob->h, ob->o_dev, j.dq, j.drot, j.dcand, ctx->stream));
+        CK(ctx, launch_topk(j.dkey, n, K, ob->N, ob->M, ob->h, ob->o_dev, j.dq, j.drot, j.dcand, ctx->stream,
+                            j.ro ? j.sw->os_dev : nullptr));
     }
     j.cands.assign(K, dock_candidate());
     CK(ctx, cudaMemcpyAsync(j.cands.data(), j.dcand, sizeof(dock_candidate) * K, cudaMemcpyDeviceToHost, ctx->stream));
@@ -2738,6 +2892,7 @@ static JobP make_job(const dock_object *ob, const dock_sweep *sw, const dock_reg
     j->ob = ob;
     j->sw = sw;
     j->la = sw && sw->label_aware.load();
+    j->ro = sw && sw->rotate_object.load();
     j->d = *rd;
     if (params) j->p = *params;
     else dock_params_default(&j->p);

@@ -12,11 +12,16 @@
 namespace dock {
 
 // Per-rotation lattice set-up, FP64 (exact operation order) and FP32 copies.
+// Rotating the sweep (default): o = the swept-lattice origin o_s,R.
+// Rotating the object (Sec. IV-D as printed): o = o_R, the rotated object
+// lattice's origin, and ub = (R^T o_R - o_o) / h, so that voxel k of the
+// rotated object samples O at the continuous index R^T k + ub.
 struct RotRec {
     double R[9];   // rotation of the sample (row-major)
-    double o[3];   // swept-lattice origin o_s,R
+    double o[3];
     float Rf[9];
     float of[3];
+    float ub[3];
     int32_t rot;   // sample index within its request
     int32_t req;   // request index in the launch's request table
 };
@@ -57,28 +62,44 @@ struct ReqDev {
     const PoseRec *poses_nc;  // label-aware: non-contact poses (else nullptr)
     int P_nc;
     const float2 *spec_pen;   // label-aware: tiled conj(F(min(O, 0))) / M^3 (else nullptr)
+    // rotate_object: the object grid is rotated and resampled per rotation
+    // (from Og, N^3 floats) and spec holds F(S) / M^3 of the fixed swept grid
+    const float *Og;
+    int rotate_object;
 };
 
 // Kernel launchers (k_search.cu)
+// o_o (nullable, device): rotate the object about its lattice instead of the
+// sweep (o = o_R, ub set); c_s is then unused.
 cudaError_t launch_rot_setup(const double *quats, int n, int rot0, int req, const double *c_s, double h, int N,
-                             RotRec *out, cudaStream_t st);
+                             RotRec *out, cudaStream_t st, const double *o_o = nullptr);
 // pose_set: 0 = (poses, P), 1 = (poses_nc, P_nc) of each rotation's request.
 cudaError_t launch_voxelise(const Geo &g, const ReqDev *reqs, const RotRec *rots, int B, uint32_t *bits,
                             cudaStream_t st, int minb = 4, int pose_set = 0);
-// mask (nullable, the layout of bits): bits & ~mask is transformed.
+// mask (nullable, the layout of bits): bits & ~mask is transformed.  With
+// rots/reqs given, rotations of rotate_object requests transform their
+// resampled object grid instead of bits (and are skipped when mask is set).
 cudaError_t launch_fwd2d(const Geo &g, int B, const uint32_t *bits, float2 *Y, const float2 *tw, const float2 *q,
-                         cudaStream_t st, const uint32_t *mask = nullptr);
+                         cudaStream_t st, const uint32_t *mask = nullptr, const RotRec *rots = nullptr,
+                         const ReqDev *reqs = nullptr);
 // Y2 (nullable): transforms of the label-aware second grids; when given, the
 // product with each request's spec_pen is added before the inverse FFT.
 cudaError_t launch_zpass(const Geo &g, int B, int group, const float2 *Y, const RotRec *rots, const ReqDev *reqs,
                          float2 *Z, const float2 *tw, cudaStream_t st, const float2 *Y2 = nullptr);
 cudaError_t launch_plane(const Geo &g, int B, const float2 *Z, const float2 *tw, const RotRec *rots,
                          const ReqDev *reqs, cudaStream_t st);
+// o_s (nullable, device): the rotate_object pose T = (R, h dk + o_s - o_R);
+// else T = (R, R (h dk + o_s,R - o_o)).
 cudaError_t launch_topk(const unsigned long long *keys, int n, int K, int N, int M, double h, const double *o_o,
-                        const double *quats, const RotRec *rots_all, dock_candidate *out, cudaStream_t st);
+                        const double *quats, const RotRec *rots_all, dock_candidate *out, cudaStream_t st,
+                        const double *o_s = nullptr);
 cudaError_t launch_vox_export(const Geo &g, const ReqDev *reqs, const RotRec *rots, int B, uint8_t *bits,
                               cudaStream_t st, int pose_set = 0);
 cudaError_t launch_plane_export(const Geo &g, const float2 *Z, const float2 *tw, float *C, cudaStream_t st);
+// S of rotation 0 (pose set 0) as N^3 floats 0/1.
+cudaError_t launch_vox_float(const Geo &g, const ReqDev *reqs, const RotRec *rots, float *out, cudaStream_t st);
+// The resampled object grid of each of B rotate_object rotations (B x N^3 floats; test hook).
+cudaError_t launch_rot_export(const Geo &g, const ReqDev *reqs, const RotRec *rots, int B, float *out, cudaStream_t st);
 
 // Object grid kernels (k_object.cu)
 struct ObjBins {
@@ -94,8 +115,9 @@ cudaError_t launch_object_grid(const double *V, const int32_t *T, const uint8_t 
                                int N, double h, const double *o, double tau_out, double tau_in, double deep,
                                float *O, float *f_out, int *err, cudaStream_t st);
 // pen: transform min(O, 0) instead of O (the label-aware penetration part).
+// conj = false stores F(O) / M^3 (the fixed swept grid of rotate_object).
 cudaError_t launch_spectrum(const float *O, int N, int M, int P, double2 *work1, double2 *work2,
-                            const double2 *twd, float2 *spec, cudaStream_t st, bool pen = false);
+                            const double2 *twd, float2 *spec, cudaStream_t st, bool pen = false, bool conj = true);
 
 // Refinement kernels (k_refine.cu)
 struct BvhNode {

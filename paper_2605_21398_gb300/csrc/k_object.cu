@@ -200,8 +200,8 @@ __global__ void k_spec_y(const double2 *A, int N, int M, const double2 *tw, doub
     }
 }
 
-// spec tile: conj(sum_z B[z][ky][kx] w^(kz z)) / M^3 at f = ky P + kx
-__global__ void k_spec_z(const double2 *Bi, int N, int M, int P, const double2 *tw, float2 *spec)
+// spec tile: conj(sum_z B[z][ky][kx] w^(kz z)) / M^3 at f = ky P + kx (no conj when !cj)
+__global__ void k_spec_z(const double2 *Bi, int N, int M, int P, const double2 *tw, float2 *spec, bool cj)
 {
     const int H = M / 2;
     const int ky = blockIdx.y, kz = blockIdx.x;
@@ -217,16 +217,16 @@ __global__ void k_spec_z(const double2 *Bi, int N, int M, int P, const double2 *
         }
         size_t f = (size_t)ky * P + kx;
         size_t chunk = f / 32, lane = f % 32;
-        spec[(chunk * M + kz) * 32 + lane] = make_float2((float)(acc.x * sc), (float)(-acc.y * sc));
+        spec[(chunk * M + kz) * 32 + lane] = make_float2((float)(acc.x * sc), (float)((cj ? -acc.y : acc.y) * sc));
     }
 }
 
 cudaError_t launch_spectrum(const float *O, int N, int M, int P, double2 *work1, double2 *work2, const double2 *twd,
-                            float2 *spec, cudaStream_t st, bool pen)
+                            float2 *spec, cudaStream_t st, bool pen, bool conj)
 {
     k_spec_x<<<N * N, 160, 0, st>>>(O, N, M, twd, work1, pen);
     k_spec_y<<<dim3(M, N), 160, 0, st>>>(work1, N, M, twd, work2);
-    k_spec_z<<<dim3(M, M), 160, 0, st>>>(work2, N, M, P, twd, spec);
+    k_spec_z<<<dim3(M, M), 160, 0, st>>>(work2, N, M, P, twd, spec, conj);
     return cudaGetLastError();
 }
 

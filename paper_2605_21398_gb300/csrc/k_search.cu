@@ -62,18 +62,36 @@ __device__ void quat_to_mat_exact(const double *q, double *R)
     R[8] = ds(1.0, dm(2.0, da(dm(x, x), dm(y, y))));
 }
 
-// R = R(q), o = h round(R^T c_s / h) - (N/2) h   (Sec. IV-A: lattice origin)
-__global__ void k_rot_setup(const double *quats, int n, int rot0, int req, const double *c_s, double h, int N, RotRec *out)
+// R = R(q), o = h round(R^T c_s / h) - (N/2) h   (Sec. IV-A: lattice origin).
+// With o_o (the object rotated, Sec. IV-D): c = o_o + (N/2) h,
+// o = o_R = h round(R c / h) - (N/2) h and ub = (R^T o_R - o_o) / h.
+__global__ void k_rot_setup(const double *quats, int n, int rot0, int req, const double *c_s, double h, int N,
+                            RotRec *out, const double *o_o)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     RotRec rr;
     double q[4] = {quats[4 * i], quats[4 * i + 1], quats[4 * i + 2], quats[4 * i + 3]};
     quat_to_mat_exact(q, rr.R);
-    double c0 = c_s[0], c1 = c_s[1], c2 = c_s[2];
-    for (int a = 0; a < 3; ++a) {
-        double u = da(da(dm(rr.R[0 * 3 + a], c0), dm(rr.R[1 * 3 + a], c1)), dm(rr.R[2 * 3 + a], c2));
-        rr.o[a] = ds(dm(h, round(__ddiv_rn(u, h))), dm((double)(N / 2), h));
+    const double half = dm((double)(N / 2), h);
+    if (o_o) {
+        double c[3];
+        for (int a = 0; a < 3; ++a) c[a] = da(o_o[a], half);
+        for (int a = 0; a < 3; ++a) {
+            double u = da(da(dm(rr.R[a * 3 + 0], c[0]), dm(rr.R[a * 3 + 1], c[1])), dm(rr.R[a * 3 + 2], c[2]));
+            rr.o[a] = ds(dm(h, round(__ddiv_rn(u, h))), half);
+        }
+        for (int a = 0; a < 3; ++a) {
+            double y = da(da(dm(rr.R[0 * 3 + a], rr.o[0]), dm(rr.R[1 * 3 + a], rr.o[1])), dm(rr.R[2 * 3 + a], rr.o[2]));
+            rr.ub[a] = (float)__ddiv_rn(ds(y, o_o[a]), h);
+        }
+    } else {
+        double c0 = c_s[0], c1 = c_s[1], c2 = c_s[2];
+        for (int a = 0; a < 3; ++a) {
+            double u = da(da(dm(rr.R[0 * 3 + a], c0), dm(rr.R[1 * 3 + a], c1)), dm(rr.R[2 * 3 + a], c2));
+            rr.o[a] = ds(dm(h, round(__ddiv_rn(u, h))), half);
+            rr.ub[a] = 0.f;
+        }
     }
     for (int k = 0; k < 9; ++k) rr.Rf[k] = (float)rr.R[k];
     for (int a = 0; a < 3; ++a) rr.of[a] = (float)rr.o[a];
@@ -83,11 +101,50 @@ __global__ void k_rot_setup(const double *quats, int n, int rot0, int req, const
 }
 
 cudaError_t launch_rot_setup(const double *quats, int n, int rot0, int req, const double *c_s, double h, int N,
-                             RotRec *out, cudaStream_t st)
+                             RotRec *out, cudaStream_t st, const double *o_o)
 {
     if (n <= 0) return cudaSuccess;
-    k_rot_setup<<<(n + 127) / 128, 128, 0, st>>>(quats, n, rot0, req, c_s, h, N, out);
+    k_rot_setup<<<(n + 127) / 128, 128, 0, st>>>(quats, n, rot0, req, c_s, h, N, out, o_o);
     return cudaGetLastError();
+}
+
+// Trilinear interpolant of the N^3 grid O at continuous index (ux, uy, uz);
+// lattice points outside [0, N)^3 count as zero (Sec. IV-D resampling).
+__device__ __forceinline__ float trilerp(const float *__restrict__ O, int N, float ux, float uy, float uz)
+{
+    const float fx = floorf(ux), fy = floorf(uy), fz = floorf(uz);
+    const int ix = (int)fx, iy = (int)fy, iz = (int)fz;
+    if (ix < -1 || iy < -1 || iz < -1 || ix >= N || iy >= N || iz >= N) return 0.f;
+    const float ax = ux - fx, ay = uy - fy, az = uz - fz;
+    float c[2][2][2];
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+                const int jx = ix + dx, jy = iy + dy, jz = iz + dz;
+                const bool in = (unsigned)jx < (unsigned)N && (unsigned)jy < (unsigned)N && (unsigned)jz < (unsigned)N;
+                c[dz][dy][dx] = in ? __ldg(&O[((size_t)jz * N + jy) * N + jx]) : 0.f;
+            }
+    float e[2][2];
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) e[dz][dy] = fmaf(ax, c[dz][dy][1] - c[dz][dy][0], c[dz][dy][0]);
+    const float f0 = fmaf(ay, e[0][1] - e[0][0], e[0][0]);
+    const float f1 = fmaf(ay, e[1][1] - e[1][0], e[1][0]);
+    return fmaf(az, f1 - f0, f0);
+}
+
+// Voxel (x, y, z) of the rotated object grid of rotation rr.
+__device__ __forceinline__ float rotated_object_voxel(const RotRec &rr, const float *O, int N, int x, int y, int z)
+{
+    const float fx = (float)x, fy = (float)y, fz = (float)z;
+    const float ux = fmaf(rr.Rf[0], fx, fmaf(rr.Rf[3], fy, fmaf(rr.Rf[6], fz, rr.ub[0])));
+    const float uy = fmaf(rr.Rf[1], fx, fmaf(rr.Rf[4], fy, fmaf(rr.Rf[7], fz, rr.ub[1])));
+    const float uz = fmaf(rr.Rf[2], fx, fmaf(rr.Rf[5], fy, fmaf(rr.Rf[8], fz, rr.ub[2])));
+    return trilerp(O, N, ux, uy, uz);
 }
 
 // ---------------------------------------------------------------------------
@@ -480,6 +537,7 @@ k_voxelise(Geo g, const ReqDev *reqs, const RotRec *rots, uint32_t *bits_out, in
     __syncthreads();
     const RotRec &rr = rots[b];
     const ReqDev &q = reqs[rr.req];
+    if (q.rotate_object) return;   // its grid is the resampled object, made in k_fwd2d
     voxelise_slab<N>(req_geo(g, q), rr, pose_set ? q.poses_nc : q.poses, pose_set ? q.P_nc : q.P, jz, bits,
                      &next_chunk);
     __syncthreads();
@@ -517,21 +575,88 @@ cudaError_t launch_voxelise(const Geo &g, const ReqDev *reqs, const RotRec *rots
 // K_A: forward transform of slab z of S_b along x (R2C in closed form per run
 // of set bits) and y (radix FFT, N non-zero inputs of M); writes Y[b][z].
 // ---------------------------------------------------------------------------
-template <int M>
-__global__ void __launch_bounds__(Plan<M>::T * 32)
-k_fwd2d(int P, const uint32_t *bits_g, float2 *Y, const float2 *tw_g, const float2 *q_g, const uint32_t *mask_g)
-{
-    constexpr int N = M / 2, H = M / 2, NW = N / 32, COLS = 32, E = Plan<M>::E;
-    extern __shared__ __align__(16) unsigned char smem[];
-    cf *X = reinterpret_cast<cf *>(smem);                       // [N][H] packed columns
-    cf *xb = X + N * H;                                          // [M][COLS] exchange
-    cf *tw = xb + M * COLS;                                      // [M]
-    cf *c0 = tw + M;                                             // [M] packed column 0 after the y FFT
-    uint32_t *bits = reinterpret_cast<uint32_t *>(c0 + M);       // [N][NW]
+// Shared-memory layout of k_fwd2d (complex elements unless noted): X [N][H]
+// plus 4N bytes of slack (the resampled slab's row pairs overhang X by that
+// much), the exchange buffer (the FFT's [M][32], or [32][M + 1] for the
+// resampled rows), twiddles [M], column 0 after the y FFT [M], bits [N][N/32].
+template <int M> struct Fwd2dSmem {
+    static constexpr int N = M / 2, H = M / 2;
+    static constexpr size_t X_BYTES = (size_t)N * H * 8 + ((4 * N + 15) / 16) * 16;
+    static constexpr size_t XB_ELEMS = (size_t)32 * (M + 1);
+    static constexpr size_t BYTES = X_BYTES + 8 * (XB_ELEMS + 2 * M) + 4 * (size_t)N * (N / 32);
+    static_assert(BYTES <= 227 * 1024, "fwd2d shared memory");
+};
 
-    const int jz = blockIdx.x, b = blockIdx.y;
+// Sec. IV-D as printed, x stage: slab z of the rotated object grid (trilinear
+// resampling of O, lanes along x so that neighbouring lanes read neighbouring
+// corners) is transformed along x two rows at a time, rows 2p and 2p+1 as the
+// real and imaginary parts of one complex FFT, and unpacked into X[y][kx]
+// (kx in [0, H); column 0 holds the real kx = 0 and kx = H values as one
+// complex number, as the closed-form path stores them).  The row pairs sit in
+// the upper half of X's bytes as float2 [N/2][N + 1]: the pairs a round reads
+// are loaded into registers before its outputs overwrite that memory, and
+// later rounds' pairs lie above what a round writes.
+template <int M>
+__device__ __forceinline__ void resampled_x_stage(const RotRec &rr, const ReqDev &q, int jz, cf *X, cf *xbt, cf *xb,
+                                                  const cf *tw)
+{
+    constexpr int N = M / 2, H = M / 2, COLS = 32, E = Plan<M>::E, NP = N / 2, PP = N + 1;
+    float2 *pairs = reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(X) + (size_t)N * H * 4);
+    const float *O = q.Og;
+    for (int i = threadIdx.x; i < NP * N; i += blockDim.x) {
+        const int x = i % N, p = i / N;
+        pairs[p * PP + x] = make_float2(rotated_object_voxel(rr, O, N, x, 2 * p, jz),
+                                        rotated_object_voxel(rr, O, N, x, 2 * p + 1, jz));
+    }
+    __syncthreads();
+    const int c = threadIdx.x % COLS, j = threadIdx.x / COLS;
+    for (int p0 = 0; p0 < NP; p0 += COLS) {
+        const int p = p0 + c;
+        cf v[E];
+#pragma unroll
+        for (int s = 0; s < E; ++s) {
+            const int x = in_index<M>(j, s);
+            float2 t = make_float2(0.f, 0.f);
+            if (slot_in_lower_half<M>(s) && p < NP) t = pairs[p * PP + x];   // x < N
+            v[s] = cmake(t.x, t.y);
+        }
+        fft_column<M, false>(v, j, xb, c, COLS, tw);
+        __syncthreads();   // every pair of this round is in registers before X is written
+#pragma unroll
+        for (int s = 0; s < E; ++s) xbt[c * (M + 1) + out_index<M>(j, s)] = v[s];
+        __syncthreads();
+        for (int e = threadIdx.x; e < COLS * H; e += blockDim.x) {
+            const int kx = e % H, cc = e / H, pp = p0 + cc;
+            if (pp >= NP) continue;
+            const cf *V = xbt + cc * (M + 1);
+            const cf a = V[kx];
+            cf A, B;
+            if (kx == 0) {
+                const cf hq = V[H];
+                A = cmake(a.x, hq.x);
+                B = cmake(a.y, hq.y);
+            } else {
+                const cf r = V[M - kx];
+                A = cmake(0.5f * (a.x + r.x), 0.5f * (a.y - r.y));
+                B = cmake(0.5f * (a.y + r.y), -0.5f * (a.x - r.x));
+            }
+            X[(2 * pp) * H + kx] = A;
+            X[(2 * pp + 1) * H + kx] = B;
+        }
+        __syncthreads();
+    }
+}
+
+// Closed-form x stage on binary data: X[y][kx] = sum over runs [a, a+len) of
+// set bits of sum_x w^(kx x) = (w^(kx a) - w^(kx (a+len))) / (1 - w^kx)
+// (kx != 0), the Nyquist column packed into column 0 (bits & ~mask when a
+// mask is given).
+template <int M>
+__device__ __forceinline__ void bits_x_stage(const uint32_t *bits_g, const uint32_t *mask_g, int b, int jz, cf *X,
+                                             uint32_t *bits, const cf *tw, const float2 *q_g)
+{
+    constexpr int N = M / 2, H = M / 2, NW = N / 32;
     const uint32_t *bg = bits_g + ((size_t)b * N + jz) * N * NW;
-    for (int i = threadIdx.x; i < M; i += blockDim.x) { float2 w = tw_g[i]; tw[i] = cmake(w.x, w.y); }
     if (mask_g) {
         const uint32_t *mg = mask_g + ((size_t)b * N + jz) * N * NW;
         for (int i = threadIdx.x; i < N * NW; i += blockDim.x) bits[i] = bg[i] & ~mg[i];
@@ -591,6 +716,32 @@ k_fwd2d(int P, const uint32_t *bits_g, float2 *Y, const float2 *tw_g, const floa
             X[y * H + kx] = val;
         }
     }
+}
+
+template <int M>
+__global__ void __launch_bounds__(Plan<M>::T * 32)
+k_fwd2d(int P, const uint32_t *bits_g, float2 *Y, const float2 *tw_g, const float2 *q_g, const uint32_t *mask_g,
+        const RotRec *rots, const ReqDev *reqs)
+{
+    constexpr int N = M / 2, H = M / 2, COLS = 32, E = Plan<M>::E;
+    using L = Fwd2dSmem<M>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    cf *X = reinterpret_cast<cf *>(smem);                       // [N][H] packed columns
+    cf *xb = reinterpret_cast<cf *>(smem + L::X_BYTES);         // [M][COLS] exchange (or [COLS][M + 1])
+    cf *tw = xb + L::XB_ELEMS;                                   // [M]
+    cf *c0 = tw + M;                                             // [M] packed column 0 after the y FFT
+    uint32_t *bits = reinterpret_cast<uint32_t *>(c0 + M);       // [N][NW]
+
+    const int jz = blockIdx.x, b = blockIdx.y;
+    const bool resample = rots && reqs[rots[b].req].rotate_object;
+    if (resample && mask_g) return;   // no second (non-contact) grid for a rotated object
+    for (int i = threadIdx.x; i < M; i += blockDim.x) { float2 w = tw_g[i]; tw[i] = cmake(w.x, w.y); }
+    if (resample) {
+        __syncthreads();
+        resampled_x_stage<M>(rots[b], reqs[rots[b].req], jz, X, xb, xb, tw);
+    } else {
+        bits_x_stage<M>(bits_g, mask_g, b, jz, X, bits, tw, q_g);
+    }
     __syncthreads();
 
     // y: FFT of each packed column; thread (c, j) of a round of 32 columns
@@ -628,31 +779,26 @@ k_fwd2d(int P, const uint32_t *bits_g, float2 *Y, const float2 *tw_g, const floa
 }
 
 template <int M>
-static size_t fwd2d_smem()
-{
-    constexpr int N = M / 2, H = M / 2, NW = N / 32;
-    return sizeof(cf) * ((size_t)N * H + (size_t)M * 32 + 2 * M) + sizeof(uint32_t) * N * NW;
-}
-
-template <int M>
 static cudaError_t launch_fwd2d_t(const Geo &g, int B, const uint32_t *bits, float2 *Y, const float2 *tw,
-                                  const float2 *q, cudaStream_t st, const uint32_t *mask)
+                                  const float2 *q, cudaStream_t st, const uint32_t *mask, const RotRec *rots,
+                                  const ReqDev *reqs)
 {
-    size_t sm = fwd2d_smem<M>();
+    size_t sm = Fwd2dSmem<M>::BYTES;
     cudaError_t e = cudaFuncSetAttribute(k_fwd2d<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_fwd2d<M><<<dim3(M / 2, B), Plan<M>::T * 32, sm, st>>>(g.P, bits, Y, tw, q, mask);
+    k_fwd2d<M><<<dim3(M / 2, B), Plan<M>::T * 32, sm, st>>>(g.P, bits, Y, tw, q, mask, rots, reqs);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fwd2d(const Geo &g, int B, const uint32_t *bits, float2 *Y, const float2 *tw, const float2 *q,
-                         cudaStream_t st, const uint32_t *mask)
+                         cudaStream_t st, const uint32_t *mask, const RotRec *rots, const ReqDev *reqs)
 {
+    if ((rots == nullptr) != (reqs == nullptr)) return cudaErrorInvalidValue;
     switch (g.M) {
-    case 64: return launch_fwd2d_t<64>(g, B, bits, Y, tw, q, st, mask);
-    case 128: return launch_fwd2d_t<128>(g, B, bits, Y, tw, q, st, mask);
-    case 192: return launch_fwd2d_t<192>(g, B, bits, Y, tw, q, st, mask);
-    case 256: return launch_fwd2d_t<256>(g, B, bits, Y, tw, q, st, mask);
+    case 64: return launch_fwd2d_t<64>(g, B, bits, Y, tw, q, st, mask, rots, reqs);
+    case 128: return launch_fwd2d_t<128>(g, B, bits, Y, tw, q, st, mask, rots, reqs);
+    case 192: return launch_fwd2d_t<192>(g, B, bits, Y, tw, q, st, mask, rots, reqs);
+    case 256: return launch_fwd2d_t<256>(g, B, bits, Y, tw, q, st, mask, rots, reqs);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -697,9 +843,63 @@ cudaError_t launch_vox_export(const Geo &g, const ReqDev *reqs, const RotRec *ro
     return cudaGetLastError();
 }
 
+// S of rotation 0 as floats (the fixed swept grid whose spectrum a rotated
+// object is correlated with).
+template <int N>
+__global__ void __launch_bounds__(256) k_vox_float(Geo g, const ReqDev *reqs, const RotRec *rots, float *out)
+{
+    constexpr int NW = N / 32;
+    __shared__ uint32_t bits[N * NW];
+    __shared__ int next_chunk;
+    const int jz = blockIdx.x;
+    for (int i = threadIdx.x; i < N * NW; i += blockDim.x) bits[i] = 0u;
+    if (threadIdx.x == 0) next_chunk = 0;
+    __syncthreads();
+    const RotRec &rr = rots[0];
+    const ReqDev &q = reqs[rr.req];
+    voxelise_slab<N>(req_geo(g, q), rr, q.poses, q.P, jz, bits, &next_chunk);
+    __syncthreads();
+    float *o = out + (size_t)jz * N * N;
+    for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
+        int y = i / N, x = i % N;
+        o[i] = (float)((bits[y * NW + (x >> 5)] >> (x & 31)) & 1u);
+    }
+}
+
+cudaError_t launch_vox_float(const Geo &g, const ReqDev *reqs, const RotRec *rots, float *out, cudaStream_t st)
+{
+    switch (g.N) {
+    case 32: k_vox_float<32><<<g.N, 256, 0, st>>>(g, reqs, rots, out); break;
+    case 64: k_vox_float<64><<<g.N, 256, 0, st>>>(g, reqs, rots, out); break;
+    case 96: k_vox_float<96><<<g.N, 256, 0, st>>>(g, reqs, rots, out); break;
+    case 128: k_vox_float<128><<<g.N, 256, 0, st>>>(g, reqs, rots, out); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// The resampled object grid of rotation b, slab z (test hook; the same voxel
+// function as the fused x stage).
+__global__ void __launch_bounds__(256) k_rot_export(int N, const ReqDev *reqs, const RotRec *rots, float *out)
+{
+    const int jz = blockIdx.x, b = blockIdx.y;
+    const RotRec &rr = rots[b];
+    const ReqDev &q = reqs[rr.req];
+    float *o = out + ((size_t)b * N + jz) * N * N;
+    for (int i = threadIdx.x; i < N * N; i += blockDim.x) o[i] = rotated_object_voxel(rr, q.Og, N, i % N, i / N, jz);
+}
+
+cudaError_t launch_rot_export(const Geo &g, const ReqDev *reqs, const RotRec *rots, int B, float *out, cudaStream_t st)
+{
+    if (B < 1 || B > 65535) return cudaErrorInvalidValue;
+    k_rot_export<<<dim3(g.N, B), 256, 0, st>>>(g.N, reqs, rots, out);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // K_B: per chunk of 32 columns f = ky P + kx: forward FFT along z (N non-zero
-// inputs), multiply by conj(F(O)) / M^3, inverse FFT along z.  The spectrum
+// inputs), multiply by conj(F(O)) / M^3 (for a rotated object: conjugate the
+// tile, multiply by F(S) / M^3), inverse FFT along z.  The spectrum
 // of the chunk stays in registers across the `group` rotations of the block.
 // DUAL (label-aware score): each rotation has a second tile, Y2, the
 // transform of the voxels reached only by non-contact poses; its product
@@ -772,12 +972,17 @@ k_zpass(int P, int B, int group, const float2 *Y, const float2 *Y2, const RotRec
         fft_column<M, false>(v, j, xb, c, COLS, tw);
         // forward output slot (bb, r) holds kz = j + (M/E)(bb + (E/R_LAST) r)
         if (!second) {
+            // a rotated object: this tile is F(O_R) and spec is F(S) / M^3,
+            // so the product is conj(F(O_R)) F(S) / M^3 (Eq. (9) read as Eq. (7))
+            const float cj = reqs[req].rotate_object ? -1.f : 1.f;
 #pragma unroll
             for (int bb = 0; bb < E / R_LAST; ++bb)
 #pragma unroll
                 for (int r = 0; r < R_LAST; ++r) {
                     int k = bb + (E / R_LAST) * r;
-                    w[k] = cmul(v[bb * R_LAST + r], sp[k]);
+                    cf a = v[bb * R_LAST + r];
+                    a.y *= cj;
+                    w[k] = cmul(a, sp[k]);
                 }
         } else if (reqs[req].P_nc > 0) {
             const float2 *pen = reqs[req].spec_pen;
@@ -1135,7 +1340,7 @@ cudaError_t launch_plane_export(const Geo &g, const float2 *Z, const float2 *tw,
 // candidate poses T = (R, R (h dk + o_s - o_o)) (Eq. (8)).
 // ---------------------------------------------------------------------------
 __global__ void k_topk(const unsigned long long *keys, int n, int K, int N, int M, double h, const double *o_o,
-                       const double *quats, const RotRec *rots_all, dock_candidate *out)
+                       const double *quats, const RotRec *rots_all, dock_candidate *out, const double *o_s)
 {
     __shared__ unsigned long long red[32];
     __shared__ unsigned long long prev;
@@ -1183,10 +1388,15 @@ __global__ void k_topk(const unsigned long long *keys, int n, int K, int N, int 
                     cd.rot = rot;
                     for (int a = 0; a < 4; ++a) cd.q[a] = quats[4 * rot + a];
                     const RotRec &rr = rots_all[rot];
-                    double v[3];
-                    for (int a = 0; a < 3; ++a) v[a] = ds(da(dm(h, (double)cd.dk[a]), rr.o[a]), o_o[a]);
-                    for (int a = 0; a < 3; ++a)
-                        cd.t[a] = da(da(dm(rr.R[3 * a], v[0]), dm(rr.R[3 * a + 1], v[1])), dm(rr.R[3 * a + 2], v[2]));
+                    if (o_s) {
+                        // rotated object: T = (R, h dk + o_s - o_R)
+                        for (int a = 0; a < 3; ++a) cd.t[a] = ds(da(dm(h, (double)cd.dk[a]), o_s[a]), rr.o[a]);
+                    } else {
+                        double v[3];
+                        for (int a = 0; a < 3; ++a) v[a] = ds(da(dm(h, (double)cd.dk[a]), rr.o[a]), o_o[a]);
+                        for (int a = 0; a < 3; ++a)
+                            cd.t[a] = da(da(dm(rr.R[3 * a], v[0]), dm(rr.R[3 * a + 1], v[1])), dm(rr.R[3 * a + 2], v[2]));
+                    }
                 } else {
                     cd.score = -INFINITY;
                     cd.canvas_idx = -1;
@@ -1202,10 +1412,11 @@ __global__ void k_topk(const unsigned long long *keys, int n, int K, int N, int 
 }
 
 cudaError_t launch_topk(const unsigned long long *keys, int n, int K, int N, int M, double h, const double *o_o,
-                        const double *quats, const RotRec *rots_all, dock_candidate *out, cudaStream_t st)
+                        const double *quats, const RotRec *rots_all, dock_candidate *out, cudaStream_t st,
+                        const double *o_s)
 {
     if (K > 1024) return cudaErrorInvalidValue;
-    k_topk<<<1, 1024, 0, st>>>(keys, n, K, N, M, h, o_o, quats, rots_all, out);
+    k_topk<<<1, 1024, 0, st>>>(keys, n, K, N, M, h, o_o, quats, rots_all, out, o_s);
     return cudaGetLastError();
 }
 

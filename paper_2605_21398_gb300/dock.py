@@ -109,6 +109,8 @@ SIGNATURES = [
     ("dock_sweep_free", None, [_vp]),
     ("dock_sweep_voxelise", _st, [_vp, _vp, _dp, ctypes.c_int32, _u8p, _dp]),
     ("dock_sweep_set_label_aware", _st, [_vp, _vp, ctypes.c_int32]),
+    ("dock_sweep_set_rotate_object", _st, [_vp, _vp, ctypes.c_int32]),
+    ("dock_object_rotated", _st, [_vp, _vp, _dp, ctypes.c_int32, _fp, _dp]),
     ("dock_sweep_voxelise_labels", _st, [_vp, _vp, _dp, ctypes.c_int32, _u8p, _u8p, _dp]),
     ("dock_search_so3", _st, [_vp, _vp, _vp, ctypes.POINTER(SearchDesc), ctypes.POINTER(Candidate),
                               ctypes.POINTER(Peak)]),
@@ -416,6 +418,18 @@ class DockObject:
         self.ctx.check(lib().dock_object_export_grid(self.ctx.h, self.h, G.ctypes.data_as(_fp), o.ctypes.data_as(_dp)))
         return G, o
 
+    def rotated(self, quats):
+        """(O_R, o_R) per quaternion: the grid rotated and resampled by trilinear
+        interpolation, as the rotated-object search builds it."""
+        q, qp = _d(quats)
+        q = q.reshape(-1, 4)
+        n, N = len(q), self.N
+        G = np.empty((n, N, N, N), dtype=np.float32)
+        o = np.empty((n, 3))
+        self.ctx.check(lib().dock_object_rotated(self.ctx.h, self.h, qp, n, G.ctypes.data_as(_fp),
+                                                 o.ctypes.data_as(_dp)))
+        return G, o
+
     def close(self):
         # a handle is freed before its context (Context.close frees it first)
         if self.h and self.ctx.h:
@@ -460,6 +474,11 @@ class DockSweep:
     def set_label_aware(self, on=True):
         """Score contact poses with O and non-contact poses with min(O, 0)."""
         self.ctx.check(lib().dock_sweep_set_label_aware(self.ctx.h, self.h, int(bool(on))))
+
+    def set_rotate_object(self, on=True):
+        """Rotate and resample the object grid per sample (S fixed) instead of
+        voxelising the rotated sweep."""
+        self.ctx.check(lib().dock_sweep_set_rotate_object(self.ctx.h, self.h, int(bool(on))))
 
     def voxelise_labels(self, quats):
         """(S_c, S_n, origins): voxels swept by contact poses, voxels swept
