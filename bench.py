@@ -299,7 +299,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--no-label-aware", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--ncu-case", action="store_true",
                     help="small fixed case for ncu captures: one search of 8 rotations (batch 8) of the bench workload")
     args = ap.parse_args()
@@ -413,13 +413,13 @@ def main():
         e2e = {"value": evals_per_step * len(t_e) / sum(t_e), "unit": "evals/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": d2h}
 
-    # the label-aware score on the same registration (contact poses score O,
-    # the 20 % non-contact-labelled poses min(O, 0)): one warm-up, one timed step
-    label_aware = None
-    if rank == 0 and not args.no_label_aware:
-        sw_la = ctx.sweep_grid(w.poses_world, w.radius, w.length, w.h, w.N, contact=w.labels)
-        sw_la.set_label_aware(True)
-        ctx.register(ob, sw_la, args.n_global, args.n_local, THETA, TOP_K)
+    # variants of the search on the same registration (one warm-up, one
+    # timed step each): the label-aware score (the 20 % non-contact-labelled
+    # poses score min(O, 0)) and the rotated-object mechanism of Sec. IV-D
+    def variant(switch, kernel_names):
+        sw_v = ctx.sweep_grid(w.poses_world, w.radius, w.length, w.h, w.N, contact=w.labels)
+        switch(sw_v)
+        ctx.register(ob, sw_v, args.n_global, args.n_local, THETA, TOP_K)
         torch.cuda.synchronize()
         ctx.reset_kernel_stats()
         ctx.set_profiling(True)
@@ -428,20 +428,27 @@ def main():
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        r_la = ctx.register(ob, sw_la, args.n_global, args.n_local, THETA, TOP_K)
+        r_v = ctx.register(ob, sw_v, args.n_global, args.n_local, THETA, TOP_K)
         ev1.record(stream)
         ev1.synchronize()
-        ms_la = ev0.elapsed_time(ev1)
+        ms_v = ev0.elapsed_time(ev1)
         ctx.set_profiling(False)
-        st_la = ctx.kernel_stats()
-        sw_la.close()
-        search_k = ("voxelise", "voxelise_nc", "fwd2d", "fwd2d_nc", "zpass_dual", "plane")
-        label_aware = {
-            "value": evals_per_step / (ms_la / 1000.0), "unit": "evals/s", "ms_per_step": round(ms_la, 2),
-            "non_contact_poses": int((w.labels == 0).sum()),
-            "ms_per_eval_search": round(sum(st_la[k][1] for k in search_k if k in st_la) / evals_per_step * 1000.0, 3),
-            "kernels_ms": {k: round(st_la[k][1], 2) for k in search_k if k in st_la},
-            "best_search_rot": int(r_la["best_search"]["rot"]), "J": r_la["J"]}
+        st_v = ctx.kernel_stats()
+        sw_v.close()
+        out = {"value": evals_per_step / (ms_v / 1000.0), "unit": "evals/s", "ms_per_step": round(ms_v, 2),
+               "ms_per_eval_search": round(sum(st_v[k][1] for k in kernel_names if k in st_v) / evals_per_step
+                                           * 1000.0, 3),
+               "kernels_ms": {k: round(st_v[k][1], 2) for k in kernel_names if k in st_v},
+               "best_search_rot": int(r_v["best_search"]["rot"]), "J": r_v["J"]}
+        return out, r_v
+
+    label_aware = rotate_object = None
+    r_la = r_ro = None
+    if rank == 0 and not args.no_variants:
+        label_aware, r_la = variant(lambda sv: sv.set_label_aware(True),
+                                    ("voxelise", "voxelise_nc", "fwd2d", "fwd2d_nc", "zpass_dual", "plane"))
+        label_aware["non_contact_poses"] = int((w.labels == 0).sum())
+        rotate_object, r_ro = variant(lambda sv: sv.set_rotate_object(True), ("voxelise", "fwd2d", "zpass", "plane"))
 
     serving = None
     if rank == 0 and not args.no_serving:
@@ -463,10 +470,11 @@ def main():
     Rr, Rg = synth.quat_to_mat(res["q"]), synth.quat_to_mat(w.gt_q)
     err_t = float(np.linalg.norm(Rr @ a + res["t"] - (Rg @ a + w.gt_t)))
     err_r = math.degrees(math.acos(max(-1.0, min(1.0, (np.trace(Rr @ Rg.T) - 1) / 2))))
-    if label_aware is not None:
-        Rl = synth.quat_to_mat(r_la["q"])
-        label_aware["trans_err_mm"] = round(float(np.linalg.norm(Rl @ a + r_la["t"] - (Rg @ a + w.gt_t))), 4)
-        label_aware["rot_err_deg"] = round(math.degrees(math.acos(max(-1.0, min(1.0, (np.trace(Rl @ Rg.T) - 1) / 2)))), 4)
+    for vd, rv in ((label_aware, r_la), (rotate_object, r_ro)):
+        if vd is not None:
+            Rl = synth.quat_to_mat(rv["q"])
+            vd["trans_err_mm"] = round(float(np.linalg.norm(Rl @ a + rv["t"] - (Rg @ a + w.gt_t))), 4)
+            vd["rot_err_deg"] = round(math.degrees(math.acos(max(-1.0, min(1.0, (np.trace(Rl @ Rg.T) - 1) / 2)))), 4)
     launches = int(sum(v[0] for v in stats.values()))
     line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
@@ -485,7 +493,7 @@ def main():
             "ms_per_eval_search": round(sum(stats[k][1] for k in ("voxelise", "fwd2d", "zpass", "plane") if k in stats)
                                         / rot_total * 1000.0, 3),
             "clocks": clk, "object_setup_ms": round(obj_setup_ms, 2), "serving": serving,
-            "label_aware": label_aware,
+            "label_aware": label_aware, "rotate_object": rotate_object,
             "accuracy": {"trans_err_mm": round(err_t, 4), "rot_err_deg": round(err_r, 4), "J": res["J"]}}
     if rank == 0:
         print(json.dumps(line))

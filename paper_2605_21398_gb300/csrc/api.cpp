@@ -136,6 +136,7 @@ struct dock_object {
     float *O = nullptr;       // N^3
     float2 *spec = nullptr;   // tiled conj(F(O)) / M^3
     float2 *spec_pen = nullptr;   // tiled conj(F(min(O, 0))) / M^3, made by the first label-aware use
+    float4 *cells = nullptr;      // corner cells of O for the rotated-object search, made on first use
     double *o_dev = nullptr;
     // mesh for the refinement
     int64_t nv = 0, nt = 0;
@@ -915,6 +916,7 @@ extern "C" void dock_object_free(dock_object *ob)
     cudaFree(ob->O);
     cudaFree(ob->spec);
     cudaFree(ob->spec_pen);
+    cudaFree(ob->cells);
     cudaFree(ob->o_dev);
     cudaFree(ob->Vf);
     cudaFree(ob->T);
@@ -1108,11 +1110,11 @@ static ReqDev make_reqdev(const dock_object *ob, const dock_sweep *sw, unsigned 
     q.lv = (float)(sw->L / sw->h);
     q.spec = ob ? ob->spec : nullptr;
     q.keys = keys;
-    q.Og = nullptr;
+    q.Og4 = nullptr;
     q.rotate_object = 0;
     if (ro) {
         q.spec = sw->spec_S;
-        q.Og = ob ? ob->O : nullptr;
+        q.Og4 = ob ? ob->cells : nullptr;
         q.rotate_object = 1;
     }
     return q;
@@ -1227,6 +1229,8 @@ extern "C" dock_status dock_sweep_voxelise_labels(dock_ctx *ctx, const dock_swee
     return DOCK_OK;
 }
 
+static dock_status ensure_cells(dock_ctx *ctx, const dock_object *obc);
+
 extern "C" dock_status dock_object_rotated(dock_ctx *ctx, const dock_object *ob, const double *quats, int32_t n,
                                            float *grids, double *origins)
 {
@@ -1246,8 +1250,9 @@ extern "C" dock_status dock_object_rotated(dock_ctx *ctx, const dock_object *ob,
     CK(ctx, cudaMemcpyAsync(ctx->quats, q.data(), sizeof(double) * 4 * n, cudaMemcpyHostToDevice, ctx->stream));
     // the object's origin drives the set-up (no sweep mean is read)
     CK(ctx, launch_rot_setup(ctx->quats, n, 0, 0, nullptr, ob->h, ob->N, ctx->rots, ctx->stream, ob->o_dev));
+    if ((s = ensure_cells(ctx, ob)) != DOCK_OK) return s;
     ReqDev r = {};
-    r.Og = ob->O;
+    r.Og4 = ob->cells;
     r.rotate_object = 1;
     std::vector<ReqDev> rq(1, r);
     if ((s = upload_reqs(ctx, rq)) != DOCK_OK) return s;
@@ -1423,6 +1428,28 @@ static dock_status ensure_spec_pen(dock_ctx *ctx, const dock_object *obc)
     return DOCK_OK;
 }
 
+// Corner cells of the object grid for the rotated-object search (4 (N+1)^3
+// floats), made on first use and kept with the object.
+static dock_status ensure_cells(dock_ctx *ctx, const dock_object *obc)
+{
+    dock_object *ob = const_cast<dock_object *>(obc);
+    if (ob->cells) return DOCK_OK;
+    const size_t n = (size_t)(ob->N + 1) * (ob->N + 1) * (ob->N + 1);
+    float4 *c = nullptr;
+    size_t held = 0;
+    dock_status s;
+    if ((s = dalloc(ctx, (void **)&c, sizeof(float4) * n, &held)) != DOCK_OK) return s;
+    cudaError_t e = launch_corner_cells(ob->O, ob->N, c, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        dfree(ctx, c, sizeof(float4) * n);
+        return cuda_fail(ctx, e, "corner cells");
+    }
+    ob->cells = c;
+    ob->bytes += held;
+    return DOCK_OK;
+}
+
 // The fixed swept grid of the rotated-object search: S voxelised on the
 // lattice of the identity rotation (origin o_s = h round(c_s / h) - (N/2) h),
 // its spectrum F(S) / M^3 and o_s, made on first use and kept with the sweep.
@@ -1492,7 +1519,7 @@ static dock_status search_impl(dock_ctx *ctx, const dock_object *ob, const dock_
     const int n = d->n;
     dock_status s;
     const bool ro = rotates_object(sw);
-    if (ro && (s = ensure_spec_S(ctx, sw)) != DOCK_OK) return s;
+    if (ro && ((s = ensure_spec_S(ctx, sw)) != DOCK_OK || (s = ensure_cells(ctx, ob)) != DOCK_OK)) return s;
     if ((s = upload_rots(ctx, sw, q.data(), n, 0, n, 0, 0, ro ? ob->o_dev : nullptr)) != DOCK_OK) return s;
     if ((s = ensure(ctx, (void **)&ctx->keys, &ctx->keys_n, (size_t)n, sizeof(unsigned long long))) != DOCK_OK) return s;
     CK(ctx, cudaMemsetAsync(ctx->keys, 0, sizeof(unsigned long long) * n, ctx->stream));
@@ -1793,7 +1820,7 @@ extern "C" dock_status dock_search_scores(dock_ctx *ctx, const dock_object *ob, 
     std::vector<double> q;
     if ((s = gen_samples(ctx, &d, q)) != DOCK_OK) return s;
     const bool ro = rotates_object(sw);
-    if (ro && (s = ensure_spec_S(ctx, sw)) != DOCK_OK) return s;
+    if (ro && ((s = ensure_spec_S(ctx, sw)) != DOCK_OK || (s = ensure_cells(ctx, ob)) != DOCK_OK)) return s;
     if ((s = upload_rots(ctx, sw, q.data(), 1, 0, 1, 0, 0, ro ? ob->o_dev : nullptr)) != DOCK_OK) return s;
     const bool dual = dual_scoring(sw);
     if (dual && (s = ensure_spec_pen(ctx, ob)) != DOCK_OK) return s;
@@ -2373,6 +2400,7 @@ static dock_status job_admit(dock_ctx *ctx, Engine &E, Job &j, int *wait)
     const bool la = j.la && j.sw->poses_lab;
     size_t pen_bytes = la && !j.ob->spec_pen ? sizeof(float2) * (size_t)j.ob->M * j.ob->P * j.ob->M : 0;
     if (j.ro && !j.sw->spec_S) pen_bytes += sizeof(float2) * (size_t)j.ob->M * j.ob->P * j.ob->M;
+    if (j.ro && !j.ob->cells) pen_bytes += sizeof(float4) * (size_t)(j.ob->N + 1) * (j.ob->N + 1) * (j.ob->N + 1);
     if (ctx->budget && ctx->held + bytes + pen_bytes + yz_growth(ctx, j.sw, la) > ctx->budget) {
         if (!E.active.empty()) {
             *wait = ADMIT_WAIT;
@@ -2382,7 +2410,7 @@ static dock_status job_admit(dock_ctx *ctx, Engine &E, Job &j, int *wait)
     }
     dock_status s;
     if (la && (s = ensure_spec_pen(ctx, j.ob)) != DOCK_OK) return s;
-    if (j.ro && (s = ensure_spec_S(ctx, j.sw)) != DOCK_OK) return s;
+    if (j.ro && ((s = ensure_spec_S(ctx, j.sw)) != DOCK_OK || (s = ensure_cells(ctx, j.ob)) != DOCK_OK)) return s;
     if ((s = dalloc(ctx, &j.dev, bytes, nullptr)) != DOCK_OK) return s;
     j.dev_bytes = bytes;
     const size_t n = (size_t)j.d.n_global + j.d.n_local;

@@ -63,8 +63,9 @@ struct ReqDev {
     int P_nc;
     const float2 *spec_pen;   // label-aware: tiled conj(F(min(O, 0))) / M^3 (else nullptr)
     // rotate_object: the object grid is rotated and resampled per rotation
-    // (from Og, N^3 floats) and spec holds F(S) / M^3 of the fixed swept grid
-    const float *Og;
+    // (from its corner cells Og4, (N+1)^3) and spec holds F(S) / M^3 of the
+    // fixed swept grid
+    const float4 *Og4;
     int rotate_object;
 };
 
@@ -96,6 +97,8 @@ cudaError_t launch_topk(const unsigned long long *keys, int n, int K, int N, int
 cudaError_t launch_vox_export(const Geo &g, const ReqDev *reqs, const RotRec *rots, int B, uint8_t *bits,
                               cudaStream_t st, int pose_set = 0);
 cudaError_t launch_plane_export(const Geo &g, const float2 *Z, const float2 *tw, float *C, cudaStream_t st);
+// Corner cells of O for trilinear interpolation ((N+1)^3 float4).
+cudaError_t launch_corner_cells(const float *O, int N, float4 *cells, cudaStream_t st);
 // S of rotation 0 (pose set 0) as N^3 floats 0/1.
 cudaError_t launch_vox_float(const Geo &g, const ReqDev *reqs, const RotRec *rots, float *out, cudaStream_t st);
 // The resampled object grid of each of B rotate_object rotations (B x N^3 floats; test hook).

@@ -108,43 +108,62 @@ cudaError_t launch_rot_setup(const double *quats, int n, int rot0, int req, cons
     return cudaGetLastError();
 }
 
-// Trilinear interpolant of the N^3 grid O at continuous index (ux, uy, uz);
-// lattice points outside [0, N)^3 count as zero (Sec. IV-D resampling).
-__device__ __forceinline__ float trilerp(const float *__restrict__ O, int N, float ux, float uy, float uz)
+// Corner cells of the object grid for trilinear interpolation: cell
+// (cx, cy, cz), c in [-1, N) per axis, holds O at (cx, cy), (cx+1, cy),
+// (cx, cy+1), (cx+1, cy+1) of plane cz (zero off the lattice), stored at
+// ((cz+1) (N+1) + cy+1) (N+1) + cx+1.  An interpolation then reads two
+// 16-byte cells (planes cz and cz+1) instead of eight scattered floats.
+__global__ void k_corner_cells(const float *__restrict__ O, int N, float4 *cells)
+{
+    const int N1 = N + 1;
+    const size_t n = (size_t)N1 * N1 * N1;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int cx = (int)(i % N1) - 1, cy = (int)((i / N1) % N1) - 1, cz = (int)(i / ((size_t)N1 * N1)) - 1;
+        float v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int x = cx + (k & 1), y = cy + (k >> 1);
+            const bool in = (unsigned)x < (unsigned)N && (unsigned)y < (unsigned)N && (unsigned)cz < (unsigned)N;
+            v[k] = in ? O[((size_t)cz * N + y) * N + x] : 0.f;
+        }
+        cells[i] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+}
+
+cudaError_t launch_corner_cells(const float *O, int N, float4 *cells, cudaStream_t st)
+{
+    k_corner_cells<<<152 * 4, 256, 0, st>>>(O, N, cells);
+    return cudaGetLastError();
+}
+
+// Trilinear interpolant of the N^3 grid O (as corner cells) at continuous
+// index (ux, uy, uz); lattice points outside [0, N)^3 count as zero (Sec.
+// IV-D resampling).  Interpolates along x, then y, then z.
+__device__ __forceinline__ float trilerp(const float4 *__restrict__ cells, int N, float ux, float uy, float uz)
 {
     const float fx = floorf(ux), fy = floorf(uy), fz = floorf(uz);
     const int ix = (int)fx, iy = (int)fy, iz = (int)fz;
     if (ix < -1 || iy < -1 || iz < -1 || ix >= N || iy >= N || iz >= N) return 0.f;
     const float ax = ux - fx, ay = uy - fy, az = uz - fz;
-    float c[2][2][2];
-#pragma unroll
-    for (int dz = 0; dz < 2; ++dz)
-#pragma unroll
-        for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < 2; ++dx) {
-                const int jx = ix + dx, jy = iy + dy, jz = iz + dz;
-                const bool in = (unsigned)jx < (unsigned)N && (unsigned)jy < (unsigned)N && (unsigned)jz < (unsigned)N;
-                c[dz][dy][dx] = in ? __ldg(&O[((size_t)jz * N + jy) * N + jx]) : 0.f;
-            }
-    float e[2][2];
-#pragma unroll
-    for (int dz = 0; dz < 2; ++dz)
-#pragma unroll
-        for (int dy = 0; dy < 2; ++dy) e[dz][dy] = fmaf(ax, c[dz][dy][1] - c[dz][dy][0], c[dz][dy][0]);
-    const float f0 = fmaf(ay, e[0][1] - e[0][0], e[0][0]);
-    const float f1 = fmaf(ay, e[1][1] - e[1][0], e[1][0]);
+    const int N1 = N + 1;
+    const size_t c = ((size_t)(iz + 1) * N1 + (iy + 1)) * N1 + (ix + 1);
+    const float4 p = __ldg(&cells[c]);
+    const float4 q = iz + 1 < N ? __ldg(&cells[c + (size_t)N1 * N1]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float e00 = fmaf(ax, p.y - p.x, p.x), e01 = fmaf(ax, p.w - p.z, p.z);
+    const float e10 = fmaf(ax, q.y - q.x, q.x), e11 = fmaf(ax, q.w - q.z, q.z);
+    const float f0 = fmaf(ay, e01 - e00, e00);
+    const float f1 = fmaf(ay, e11 - e10, e10);
     return fmaf(az, f1 - f0, f0);
 }
 
 // Voxel (x, y, z) of the rotated object grid of rotation rr.
-__device__ __forceinline__ float rotated_object_voxel(const RotRec &rr, const float *O, int N, int x, int y, int z)
+__device__ __forceinline__ float rotated_object_voxel(const RotRec &rr, const float4 *cells, int N, int x, int y, int z)
 {
     const float fx = (float)x, fy = (float)y, fz = (float)z;
     const float ux = fmaf(rr.Rf[0], fx, fmaf(rr.Rf[3], fy, fmaf(rr.Rf[6], fz, rr.ub[0])));
     const float uy = fmaf(rr.Rf[1], fx, fmaf(rr.Rf[4], fy, fmaf(rr.Rf[7], fz, rr.ub[1])));
     const float uz = fmaf(rr.Rf[2], fx, fmaf(rr.Rf[5], fy, fmaf(rr.Rf[8], fz, rr.ub[2])));
-    return trilerp(O, N, ux, uy, uz);
+    return trilerp(cells, N, ux, uy, uz);
 }
 
 // ---------------------------------------------------------------------------
@@ -602,7 +621,8 @@ __device__ __forceinline__ void resampled_x_stage(const RotRec &rr, const ReqDev
 {
     constexpr int N = M / 2, H = M / 2, COLS = 32, E = Plan<M>::E, NP = N / 2, PP = N + 1;
     float2 *pairs = reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(X) + (size_t)N * H * 4);
-    const float *O = q.Og;
+    const float4 *O = q.Og4;
+#pragma unroll 4
     for (int i = threadIdx.x; i < NP * N; i += blockDim.x) {
         const int x = i % N, p = i / N;
         pairs[p * PP + x] = make_float2(rotated_object_voxel(rr, O, N, x, 2 * p, jz),
@@ -886,7 +906,7 @@ __global__ void __launch_bounds__(256) k_rot_export(int N, const ReqDev *reqs, c
     const RotRec &rr = rots[b];
     const ReqDev &q = reqs[rr.req];
     float *o = out + ((size_t)b * N + jz) * N * N;
-    for (int i = threadIdx.x; i < N * N; i += blockDim.x) o[i] = rotated_object_voxel(rr, q.Og, N, i % N, i / N, jz);
+    for (int i = threadIdx.x; i < N * N; i += blockDim.x) o[i] = rotated_object_voxel(rr, q.Og4, N, i % N, i / N, jz);
 }
 
 cudaError_t launch_rot_export(const Geo &g, const ReqDev *reqs, const RotRec *rots, int B, float *out, cudaStream_t st)
