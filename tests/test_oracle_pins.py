@@ -629,6 +629,43 @@ def test_gradient_matches_central_differences(workload):
     assert checked >= 1
 
 
+def _lbfgsb_case(w, dr_deg, dt_mm, every=2):
+    a = O.mesh_anchor(w.obj.verts)
+    prm = O.refine_params(w.radius, w.length)
+    q0 = synth.quat_mul(synth.axis_angle_quat(np.radians(dr_deg)), w.gt_q)
+    return a, prm, O.quat_to_mat(q0), w.gt_t + np.array(dt_mm), w.poses_world[::every]
+
+
+def test_lbfgsb_refinement_recovers_the_planted_pose(workload):
+    # Sec. V-C as printed (L-BFGS-B from xi_0 = 0 under the box): on
+    # noise-free contacts the minimiser is the planted pose (every d_i = 0,
+    # J = -N); the run must end near it with J close to -N
+    w = workload("tiny32")
+    a, prm, R0, p0, poses = _lbfgsb_case(w, [0.3, 0.2, -0.1], [0.05, 0.03, -0.04])
+    J0 = O.objective(w.obj.verts, w.obj.tris, poses, R0, p0, a, np.zeros(6), prm)[0]
+    res = O.refine_lbfgsb(w.obj.verts, w.obj.tris, poses, R0, p0, a, prm)
+    Rg = O.quat_to_mat(w.gt_q)
+    e0 = np.linalg.norm(R0 @ a + p0 - (Rg @ a + w.gt_t))
+    e1 = np.linalg.norm(res["R"] @ a + res["p"] - (Rg @ a + w.gt_t))
+    assert res["J"] < J0 and res["J"] <= -0.995 * len(poses)
+    assert e1 <= 0.02 and e1 < 0.2 * e0, (e0, e1)
+
+
+def test_lbfgsb_refinement_stops_on_the_box_with_outward_gradients(workload):
+    # a translation bound tighter than the start's error: the minimiser lies
+    # on the box, and each translation component held there has the
+    # gradient pushing outward (the KKT sign condition of Eq. (20))
+    w = workload("tiny32")
+    a, prm, R0, p0, poses = _lbfgsb_case(w, [0.0, 0.0, 0.0], [0.08, -0.06, 0.05])
+    bt = 0.02
+    res = O.refine_lbfgsb(w.obj.verts, w.obj.tris, poses, R0, p0, a, prm, b_t=bt)
+    u, G = res["xi"][:3], res["G"][:3]
+    assert np.all(np.abs(u) <= bt + 1e-12)
+    held = np.abs(np.abs(u) - bt) <= 1e-12
+    assert held.any()
+    assert np.all(G[held] * np.sign(u[held]) <= 1e-6)
+
+
 def test_refinement_reduces_J_and_moves_toward_the_planted_pose(workload):
     w = workload("tiny32")
     a = O.mesh_anchor(w.obj.verts)
