@@ -507,6 +507,64 @@ static void comb(const double *v0, const double *v1, const double *v2, const dou
 }
 
 /*
+ * The subgradient of f_p at the witness x that gives the derivative of
+ * d = min over the triangle of f_p (Sec. V-B, Eq. (22)-(24)).  Where f_p is
+ * differentiable it is the gradient.  On the medial surface inside the
+ * probe (|dr - dz| <= KINK_BAND) the subdifferential is the segment between
+ * the radial gradient a and the cap gradient b, and the minimum over the
+ * triangle selects the element whose component along the face holding x
+ * (the triangle's plane, or the edge when a barycentric weight is zero)
+ * vanishes (the optimality condition of the convex minimum; the value then
+ * moves with the pose as that subgradient says, by Danskin's theorem):
+ * n = lam a + (1 - lam) b with lam minimising |P (lam a + (1 - lam) b)|,
+ * P the projection onto the face.  At a vertex witness the condition leaves
+ * lam free and the blend of orc_probe_normal is kept.  n is not normalised.
+ */
+static void witness_subgradient(const double *x, const double loc[3][3], const double *lam, double r, double L,
+                                double *n)
+{
+    double rho = sqrt(x[0] * x[0] + x[1] * x[1]);
+    double dr = rho - r, zlo = -x[2], zhi = x[2] - L;
+    double dz = zlo >= zhi ? zlo : zhi;
+    int nz = 0, zi = -1;
+    for (int k = 0; k < 3; ++k)
+        if (lam[k] <= 1e-9) { ++nz; zi = k; }
+    if (!(dr <= 0.0 && dz <= 0.0 && fabs(dr - dz) <= KINK_BAND && rho > 0.0) || nz >= 2) {
+        orc_probe_normal(x, r, L, n);
+        return;
+    }
+    double a[3] = {x[0] / rho, x[1] / rho, 0.0}, b[3] = {0.0, 0.0, zlo >= zhi ? -1.0 : 1.0};
+    double Pa[3], Pb[3];
+    if (nz == 0) {
+        double e1[3], e2[3], nu[3];
+        for (int i = 0; i < 3; ++i) { e1[i] = loc[1][i] - loc[0][i]; e2[i] = loc[2][i] - loc[0][i]; }
+        nu[0] = e1[1] * e2[2] - e1[2] * e2[1];
+        nu[1] = e1[2] * e2[0] - e1[0] * e2[2];
+        nu[2] = e1[0] * e2[1] - e1[1] * e2[0];
+        double nn = (nu[0] * nu[0] + nu[1] * nu[1]) + nu[2] * nu[2];
+        double an = ((a[0] * nu[0] + a[1] * nu[1]) + a[2] * nu[2]) / nn;
+        double bn = ((b[0] * nu[0] + b[1] * nu[1]) + b[2] * nu[2]) / nn;
+        for (int i = 0; i < 3; ++i) { Pa[i] = a[i] - an * nu[i]; Pb[i] = b[i] - bn * nu[i]; }
+    } else {
+        const double *p = loc[(zi + 1) % 3], *q = loc[(zi + 2) % 3];
+        double e[3] = {q[0] - p[0], q[1] - p[1], q[2] - p[2]};
+        double ee = (e[0] * e[0] + e[1] * e[1]) + e[2] * e[2];
+        double ae = ((a[0] * e[0] + a[1] * e[1]) + a[2] * e[2]) / ee;
+        double be = ((b[0] * e[0] + b[1] * e[1]) + b[2] * e[2]) / ee;
+        for (int i = 0; i < 3; ++i) { Pa[i] = ae * e[i]; Pb[i] = be * e[i]; }
+    }
+    double df[3] = {Pa[0] - Pb[0], Pa[1] - Pb[1], Pa[2] - Pb[2]};
+    double dd = (df[0] * df[0] + df[1] * df[1]) + df[2] * df[2];
+    double lm = 0.5;
+    if (dd > 0.0) {
+        lm = -((Pb[0] * df[0] + Pb[1] * df[1]) + Pb[2] * df[2]) / dd;
+        if (lm < 0.0) lm = 0.0;
+        if (lm > 1.0) lm = 1.0;
+    }
+    for (int i = 0; i < 3; ++i) n[i] = lm * a[i] + (1.0 - lm) * b[i];
+}
+
+/*
  * min over the triangle conv{v0,v1,v2} (probe-local coordinates) of f_p, the
  * per-triangle minimisation of Sec. V-B.  f_p is convex (the signed distance
  * of a convex body), so with x(u,v) = v0 + u (v1 - v0) + v (v2 - v0) the
@@ -728,7 +786,7 @@ static int64_t dist_query(const query_t *Q, const double *V, const int32_t *T, i
 {
     double best = INFINITY;
     int64_t bt = -1;
-    double bx[3] = {0, 0, 0};
+    double bx[3] = {0, 0, 0}, blam[3] = {0, 0, 0}, bloc[3][3];
     for (int64_t t = 0; t < nt; ++t) {
         double loc[3][3];
         for (int k = 0; k < 3; ++k) {
@@ -756,12 +814,14 @@ static int64_t dist_query(const query_t *Q, const double *V, const int32_t *T, i
         if (dk < best) {
             best = dk; bt = t;
             comb(loc[0], loc[1], loc[2], lam, bx);
+            memcpy(blam, lam, sizeof(blam));
+            memcpy(bloc, loc, sizeof(bloc));
         }
     }
     *d_out = best;
     if (bt >= 0) {
         double g[3];
-        orc_probe_normal(bx, Q->r, Q->L, g);
+        witness_subgradient(bx, (const double(*)[3])bloc, blam, Q->r, Q->L, g);
         for (int i = 0; i < 3; ++i) {
             n_out[i] = (Ri[3 * i] * g[0] + Ri[3 * i + 1] * g[1]) + Ri[3 * i + 2] * g[2];
             w_out[i] = ((Ri[3 * i] * bx[0] + Ri[3 * i + 1] * bx[1]) + Ri[3 * i + 2] * bx[2]) + ti[i];
