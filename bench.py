@@ -416,10 +416,10 @@ def main():
     # variants of the search on the same registration (one warm-up, one
     # timed step each): the label-aware score (the 20 % non-contact-labelled
     # poses score min(O, 0)) and the rotated-object mechanism of Sec. IV-D
-    def variant(switch, kernel_names):
+    def variant(switch, kernel_names, params=None):
         sw_v = ctx.sweep_grid(w.poses_world, w.radius, w.length, w.h, w.N, contact=w.labels)
         switch(sw_v)
-        ctx.register(ob, sw_v, args.n_global, args.n_local, THETA, TOP_K)
+        ctx.register(ob, sw_v, args.n_global, args.n_local, THETA, TOP_K, params=params)
         torch.cuda.synchronize()
         ctx.reset_kernel_stats()
         ctx.set_profiling(True)
@@ -428,7 +428,7 @@ def main():
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        r_v = ctx.register(ob, sw_v, args.n_global, args.n_local, THETA, TOP_K)
+        r_v = ctx.register(ob, sw_v, args.n_global, args.n_local, THETA, TOP_K, params=params)
         ev1.record(stream)
         ev1.synchronize()
         ms_v = ev0.elapsed_time(ev1)
@@ -442,13 +442,20 @@ def main():
                "best_search_rot": int(r_v["best_search"]["rot"]), "J": r_v["J"]}
         return out, r_v
 
-    label_aware = rotate_object = None
-    r_la = r_ro = None
+    label_aware = rotate_object = lbfgsb = None
+    r_la = r_ro = r_lb = None
     if rank == 0 and not args.no_variants:
         label_aware, r_la = variant(lambda sv: sv.set_label_aware(True),
                                     ("voxelise", "voxelise_nc", "fwd2d", "fwd2d_nc", "zpass_dual", "plane"))
         label_aware["non_contact_poses"] = int((w.labels == 0).sum())
         rotate_object, r_ro = variant(lambda sv: sv.set_rotate_object(True), ("voxelise", "fwd2d", "zpass", "plane"))
+        # the refinement by L-BFGS-B (Sec. V-C as printed) instead of Gauss-Newton
+        p_lb = dock.default_params()
+        p_lb.solver = dock.SOLVER_LBFGSB
+        p_lb.iters = 200
+        lbfgsb, r_lb = variant(lambda sv: None, ("refine_eval", "refine_lbfgs", "refine_solve"), params=p_lb)
+        lbfgsb["refine_ms"] = round(sum(lbfgsb["kernels_ms"].values()), 2)
+        del lbfgsb["ms_per_eval_search"]
 
     serving = None
     if rank == 0 and not args.no_serving:
@@ -470,7 +477,7 @@ def main():
     Rr, Rg = synth.quat_to_mat(res["q"]), synth.quat_to_mat(w.gt_q)
     err_t = float(np.linalg.norm(Rr @ a + res["t"] - (Rg @ a + w.gt_t)))
     err_r = math.degrees(math.acos(max(-1.0, min(1.0, (np.trace(Rr @ Rg.T) - 1) / 2))))
-    for vd, rv in ((label_aware, r_la), (rotate_object, r_ro)):
+    for vd, rv in ((label_aware, r_la), (rotate_object, r_ro), (lbfgsb, r_lb)):
         if vd is not None:
             Rl = synth.quat_to_mat(rv["q"])
             vd["trans_err_mm"] = round(float(np.linalg.norm(Rl @ a + rv["t"] - (Rg @ a + w.gt_t))), 4)
@@ -493,7 +500,7 @@ def main():
             "ms_per_eval_search": round(sum(stats[k][1] for k in ("voxelise", "fwd2d", "zpass", "plane") if k in stats)
                                         / rot_total * 1000.0, 3),
             "clocks": clk, "object_setup_ms": round(obj_setup_ms, 2), "serving": serving,
-            "label_aware": label_aware, "rotate_object": rotate_object,
+            "label_aware": label_aware, "rotate_object": rotate_object, "lbfgsb_refinement": lbfgsb,
             "accuracy": {"trans_err_mm": round(err_t, 4), "rot_err_deg": round(err_r, 4), "J": res["J"]}}
     if rank == 0:
         print(json.dumps(line))

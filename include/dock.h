@@ -75,10 +75,28 @@ typedef struct dock_params {
     double mu;           /* Gauss-Newton damping added to the normal matrix, mm^-2 (1e-6) */
     double b_t, b_r;     /* Eq. (20) box bounds: |u|_inf <= b_t mm, |w|_inf <= b_r rad (1.0, 5 deg) */
     double step_t, step_r; /* per-iteration trust region on the Gauss-Newton step (0.05 mm, 0.5 deg) */
-    int32_t iters;       /* refinement iterations (20) */
+    int32_t iters;       /* refinement iterations (20); with L-BFGS-B the most accepted steps */
     int32_t tri_iters;   /* inner bisection steps of the per-triangle search (outer golden steps: 1.5x);
                             default 20: u and v to ~1e-6 of the triangle */
+    int32_t solver;      /* DOCK_SOLVER_GAUSS_NEWTON (default) or DOCK_SOLVER_LBFGSB (Sec. V-C as printed) */
+    int32_t lbfgs_evals; /* L-BFGS-B: most evaluations of J and grad J per candidate (100) */
+    double lbfgs_pgtol;  /* L-BFGS-B: stop when the largest projected-gradient component is below (1e-5) */
+    double lbfgs_ftol;   /* L-BFGS-B: stop when the relative decrease of J is below (2.2e-9) */
 } dock_params;
+
+/*
+ * Refinement solvers.  GAUSS_NEWTON: `iters` projected Gauss-Newton steps
+ * (FP64 6x6 Cholesky, trust region step_t / step_r, the box of Eq. (20)).
+ * LBFGSB: limited-memory BFGS with the box of Eq. (20), from xi_0 = 0 with
+ * the analytic gradient of Eq. (28) (Sec. V-C): 8 stored pairs, two-loop
+ * direction on the variables not held at a bound, projected Armijo
+ * backtracking (safeguarded quadratic interpolation); a candidate stops on lbfgs_pgtol, lbfgs_ftol, `iters`
+ * accepted steps, lbfgs_evals evaluations or a failed line search (the
+ * objective has kinks where the witness triangle changes), keeping its last
+ * accepted twist.  dock_refined.iters reports the accepted steps.
+ */
+#define DOCK_SOLVER_GAUSS_NEWTON 0
+#define DOCK_SOLVER_LBFGSB 1
 
 typedef struct dock_probe {
     int32_t kind;        /* 0 = flat-ended cylinder (the paper's bur, Sec. VI) */

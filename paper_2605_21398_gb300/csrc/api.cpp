@@ -52,6 +52,10 @@ struct RefBufs {
     size_t hint_n = 0;
     int32_t *grp = nullptr;     // candidate -> request
     size_t grp_n = 0;
+    double *lb = nullptr;       // L-BFGS-B state per candidate (LB_ST doubles)
+    size_t lb_n = 0;
+    int32_t *active = nullptr;  // L-BFGS-B: candidates still iterating
+    size_t active_n = 0;
 };
 
 static void free_refbufs(RefBufs &b)
@@ -63,6 +67,8 @@ static void free_refbufs(RefBufs &b)
     cudaFree(b.dev);
     cudaFree(b.grp);
     cudaFree(b.hint);
+    cudaFree(b.lb);
+    cudaFree(b.active);
     b = RefBufs();
 }
 
@@ -443,6 +449,10 @@ void dock_params_default(dock_params *p)
     p->step_r = 0.5 * M_PI / 180.0;
     p->iters = 20;
     p->tri_iters = 20;
+    p->solver = DOCK_SOLVER_GAUSS_NEWTON;
+    p->lbfgs_evals = 100;
+    p->lbfgs_pgtol = 1e-5;
+    p->lbfgs_ftol = 2.220446049250313e-09;
 }
 
 dock_status dock_create(dock_ctx **out, int device, size_t hbm_budget_bytes, void *cuda_stream)
@@ -1898,7 +1908,7 @@ static dock_status ref_buffers(dock_ctx *ctx, RefBufs &rb, int K, int nblk)
     dock_status s;
     if ((s = ensure(ctx, (void **)&rb.state, &rb.state_n, (size_t)K * REF_ST, sizeof(double))) != DOCK_OK) return s;
     if ((s = ensure(ctx, (void **)&rb.acc, &rb.acc_n, (size_t)K * nblk * REF_NACC, sizeof(double))) != DOCK_OK) return s;
-    if ((s = ensure(ctx, (void **)&rb.prm, &rb.prm_n, 8, sizeof(double))) != DOCK_OK) return s;
+    if ((s = ensure(ctx, (void **)&rb.prm, &rb.prm_n, 16, sizeof(double))) != DOCK_OK) return s;
     if ((s = ensure(ctx, (void **)&rb.cands, &rb.cands_n, (size_t)K, cand_bytes())) != DOCK_OK) return s;
     return DOCK_OK;
 }
@@ -1984,12 +1994,32 @@ static dock_status upload_refdev(dock_ctx *ctx, RefBufs &rb, const std::vector<R
 static dock_status refine_loop(dock_ctx *ctx, RefBufs &rb, int K, int nblk, int iters, const dock_params *p,
                                cudaStream_t st)
 {
-    double prm[6] = {p->lambda, p->mu, p->step_t, p->step_r, p->b_t, p->b_r};
+    double prm[9] = {p->lambda, p->mu, p->step_t, p->step_r, p->b_t, p->b_r, p->lbfgs_pgtol, p->lbfgs_ftol,
+                     (double)iters};
     CK(ctx, cudaMemcpyAsync(rb.prm, prm, sizeof(prm), cudaMemcpyHostToDevice, st));
     CandF *cf = (CandF *)rb.cands;
     dock_status s;
     if ((s = ensure(ctx, (void **)&rb.hint, &rb.hint_n, (size_t)K * nblk * 128, sizeof(int32_t))) != DOCK_OK) return s;
     CK(ctx, cudaMemsetAsync(rb.hint, 0xFF, sizeof(int32_t) * (size_t)K * nblk * 128, st));   // -1: no hint yet
+    if (p->solver == DOCK_SOLVER_LBFGSB) {
+        // L-BFGS-B (Sec. V-C as printed): rounds of one evaluation (J and
+        // grad J at every active candidate's trial twist) and one solver
+        // step; finished candidates skip the evaluation
+        if ((s = ensure(ctx, (void **)&rb.lb, &rb.lb_n, (size_t)K * LB_ST, sizeof(double))) != DOCK_OK) return s;
+        if ((s = ensure(ctx, (void **)&rb.active, &rb.active_n, (size_t)K, sizeof(int32_t))) != DOCK_OK) return s;
+        CK(ctx, launch_lbfgs(K, nblk * REF_WARPS, rb.state, rb.acc, rb.prm, rb.lb, rb.active, cf, 0, st));
+        for (int r = 0; r < p->lbfgs_evals; ++r) {
+            {
+                Prof pr(ctx, "refine_eval", st);
+                CK(ctx, launch_refine_eval(rb.dev, rb.grp, K, nblk, cf, rb.acc, true, nullptr, nullptr, nullptr, st,
+                                           rb.hint, rb.active));
+            }
+            Prof pr(ctx, "refine_lbfgs", st);
+            CK(ctx, launch_lbfgs(K, nblk * REF_WARPS, rb.state, rb.acc, rb.prm, rb.lb, rb.active, cf, 1, st));
+        }
+        CK(ctx, launch_lbfgs(K, nblk * REF_WARPS, rb.state, rb.acc, rb.prm, rb.lb, rb.active, cf, 2, st));
+        return DOCK_OK;
+    }
     CK(ctx, launch_refine_solve(K, nblk * REF_WARPS, rb.state, rb.acc, rb.prm, 0, cf, st));
     for (int it = 0; it < iters; ++it) {
         {
@@ -2048,7 +2078,7 @@ static dock_status refine_launch(dock_ctx *ctx, RefBufs &rb, const std::vector<R
     }
     CK(ctx, cudaMemcpyAsync(rb.state, sv.data(), sizeof(double) * sv.size(), cudaMemcpyHostToDevice, st));
     if ((s = upload_refdev(ctx, rb, Ds, grp, st)) != DOCK_OK) return s;
-    if ((s = refine_loop(ctx, rb, K, nblk, p->iters, p, st)) != DOCK_OK) return s;
+    if ((s = refine_loop(ctx, rb, K, nblk, p->iters, p, st)) != DOCK_OK) return s;   // iters: the most L-BFGS-B steps
     CK(ctx, cudaMemcpyAsync(host_state, rb.state, sizeof(double) * sv.size(), cudaMemcpyDeviceToHost, st));
     return DOCK_OK;
 }
@@ -2067,7 +2097,7 @@ static void refine_results(const std::vector<RefGroup> &groups, const double *ho
             memcpy(out[c].xi, x + 15, sizeof(double) * 6);
             out[c].J = x[21];
             out[c].cand = c - gr.c0;
-            out[c].iters = p->iters;
+            out[c].iters = p->solver == DOCK_SOLVER_LBFGSB ? (int32_t)x[22] : p->iters;
         }
 }
 
@@ -2098,6 +2128,17 @@ static dock_status check_quat_pose(dock_ctx *ctx, const double *q)
     return DOCK_OK;
 }
 
+static dock_status check_params(dock_ctx *ctx, const dock_params *p)
+{
+    if (p->iters < 0 || p->iters > 10000) return fail(ctx, DOCK_E_INVALID, "iters out of range");
+    if (p->solver != DOCK_SOLVER_GAUSS_NEWTON && p->solver != DOCK_SOLVER_LBFGSB)
+        return fail(ctx, DOCK_E_INVALID, "unknown solver %d", p->solver);
+    if (p->solver == DOCK_SOLVER_LBFGSB &&
+        (p->lbfgs_evals < 1 || p->lbfgs_evals > 10000 || !(p->lbfgs_pgtol >= 0.0) || !(p->lbfgs_ftol >= 0.0)))
+        return fail(ctx, DOCK_E_INVALID, "L-BFGS-B limits out of range");
+    return DOCK_OK;
+}
+
 extern "C" dock_status dock_refine_se3(dock_ctx *ctx, const dock_object *ob, const dock_sweep *sw,
                                        const dock_candidate *in, int32_t K, const dock_params *params,
                                        dock_refined *out)
@@ -2111,7 +2152,7 @@ extern "C" dock_status dock_refine_se3(dock_ctx *ctx, const dock_object *ob, con
     dock_params pd;
     dock_params_default(&pd);
     const dock_params *p = params ? params : &pd;
-    if (p->iters < 0 || p->iters > 10000) return fail(ctx, DOCK_E_INVALID, "iters out of range");
+    if ((s = check_params(ctx, p)) != DOCK_OK) return s;
     for (int c = 0; c < K; ++c) {
         double pose[7] = {in[c].q[0], in[c].q[1], in[c].q[2], in[c].q[3], in[c].t[0], in[c].t[1], in[c].t[2]};
         if ((s = check_quat_pose(ctx, pose)) != DOCK_OK) return s;
@@ -2314,7 +2355,7 @@ static dock_status check_job(dock_ctx *ctx, const Job &j)
     if (d.sampler != DOCK_SAMPLER_SF && d.sampler != DOCK_SAMPLER_HOPF)
         return fail(ctx, DOCK_E_INVALID, "global sampler must be SF or HOPF");
     if (d.n_local > 0 && !(d.theta > 0.0 && d.theta < M_PI / 2)) return fail(ctx, DOCK_E_INVALID, "theta out of range");
-    return DOCK_OK;
+    return check_params(ctx, &j.p);
 }
 
 static dock_status engine_init(dock_ctx *ctx)

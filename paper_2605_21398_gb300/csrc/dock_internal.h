@@ -151,9 +151,15 @@ constexpr int REF_NACC = 28;  // accumulated J, grad (6), Gauss-Newton upper tri
 constexpr int REF_WARPS = 4;  // warps per block of the refinement evaluation (one partial sum each)
 // hints (optional, K x nblk x 128): each query's witness triangle, read as a
 // starting bound and overwritten; -1 = none.
+// active (optional, K): candidates whose flag is 0 are skipped.
 cudaError_t launch_refine_eval(const RefineDev *Dt, const int32_t *grp, int K, int nblk, const CandF *cands,
                                double *acc_part, bool grad, float *dist_out, float *wit_out, float *nrm_out,
-                               cudaStream_t st, int32_t *hints = nullptr);
+                               cudaStream_t st, int32_t *hints = nullptr, const int32_t *active = nullptr);
+// L-BFGS-B refinement (Sec. V-C): LB_ST doubles of solver state per candidate.
+constexpr int LB_M = 8;                  // stored (s, y) pairs
+constexpr int LB_ST = 32 + 13 * LB_M;
+cudaError_t launch_lbfgs(int K, int nblk, double *state, const double *acc_part, const double *prm, double *lbs,
+                         int32_t *active, CandF *cands, int phase, cudaStream_t st);
 cudaError_t launch_refine_solve(int K, int nblk, double *state, const double *acc_part, const double *prm, int mode,
                                 CandF *cands, cudaStream_t st);
 cudaError_t launch_set_xi(int B, const float *xi, double *state, cudaStream_t st);

@@ -67,7 +67,9 @@ __device__ __forceinline__ float sdf_cyl(float x, float y, float z, float r, flo
 }
 
 // Contact normal n* (Eq. (23)): the unit gradient; inside, within KINK_BAND
-// of the medial surface, a continuous blend of the two branch gradients.
+// of the medial surface, a continuous blend of the two branch gradients (used
+// where the witness alone does not select a subgradient: see
+// witness_subgradient).
 __device__ __forceinline__ void sdf_normal(const float *x, float r, float L, float *n)
 {
     float rho = sqrtf(fmaf(x[0], x[0], x[1] * x[1]));
@@ -89,6 +91,56 @@ __device__ __forceinline__ void sdf_normal(const float *x, float r, float L, flo
 }
 
 __device__ __forceinline__ float dot3f(const float *a, const float *b) { return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2])); }
+
+// The subgradient of f_p at the witness x (probe frame) of triangle lv that
+// gives the derivative of d = min over the triangle of f_p (Sec. V-B,
+// Eq. (22)-(24)): the gradient where f_p is differentiable; on the medial
+// surface inside the probe, the combination lam a + (1 - lam) b of the
+// radial and cap gradients whose component along the witness's face (the
+// triangle's plane, or its edge when a barycentric weight is ~0) vanishes,
+// the element the minimum over the triangle selects (Danskin); at a vertex
+// witness the blend of sdf_normal.  Not normalised.
+__device__ __noinline__ void witness_subgradient(const float *x, const float lv[3][3], float r, float L, float *n)
+{
+    const float rho = sqrtf(fmaf(x[0], x[0], x[1] * x[1]));
+    const float dr = rho - r, zlo = -x[2], zhi = x[2] - L;
+    const float dz = zlo >= zhi ? zlo : zhi;
+    if (!(dr <= 0.f && dz <= 0.f && fabsf(dr - dz) <= KINK_BAND && rho > 0.f)) {
+        sdf_normal(x, r, L, n);
+        return;
+    }
+    float e1[3], e2[3], p[3];
+    for (int i = 0; i < 3; ++i) { e1[i] = lv[1][i] - lv[0][i]; e2[i] = lv[2][i] - lv[0][i]; p[i] = x[i] - lv[0][i]; }
+    const float d00 = dot3f(e1, e1), d01 = dot3f(e1, e2), d11 = dot3f(e2, e2), d20 = dot3f(p, e1), d21 = dot3f(p, e2);
+    const float den = fmaf(d00, d11, -d01 * d01);
+    float w[3];
+    w[1] = den != 0.f ? fmaf(d11, d20, -d01 * d21) / den : 0.f;
+    w[2] = den != 0.f ? fmaf(d00, d21, -d01 * d20) / den : 0.f;
+    w[0] = 1.f - w[1] - w[2];
+    int nz = 0, zi = -1;
+    for (int k = 0; k < 3; ++k)
+        if (w[k] <= 1e-4f) { ++nz; zi = k; }
+    if (nz >= 2 || den == 0.f) {
+        sdf_normal(x, r, L, n);
+        return;
+    }
+    const float a[3] = {x[0] / rho, x[1] / rho, 0.f}, b[3] = {0.f, 0.f, zlo >= zhi ? -1.f : 1.f};
+    float Pa[3], Pb[3];
+    if (nz == 0) {
+        const float nu[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        const float nn = dot3f(nu, nu), an = dot3f(a, nu) / nn, bn = dot3f(b, nu) / nn;
+        for (int i = 0; i < 3; ++i) { Pa[i] = a[i] - an * nu[i]; Pb[i] = b[i] - bn * nu[i]; }
+    } else {
+        const float *pp = lv[(zi + 1) % 3], *qq = lv[(zi + 2) % 3];
+        const float e[3] = {qq[0] - pp[0], qq[1] - pp[1], qq[2] - pp[2]};
+        const float ee = dot3f(e, e), ae = dot3f(a, e) / ee, be = dot3f(b, e) / ee;
+        for (int i = 0; i < 3; ++i) { Pa[i] = ae * e[i]; Pb[i] = be * e[i]; }
+    }
+    const float df[3] = {Pa[0] - Pb[0], Pa[1] - Pb[1], Pa[2] - Pb[2]};
+    const float dd = dot3f(df, df);
+    const float lm = dd > 0.f ? fminf(1.f, fmaxf(0.f, -dot3f(Pb, df) / dd)) : 0.5f;
+    for (int i = 0; i < 3; ++i) n[i] = fmaf(lm, a[i], (1.f - lm) * b[i]);
+}
 
 // f_p is differentiable at x: everywhere outside the probe; inside, away
 // (by more than 1e-3 mm) from the medial surfaces where two branches meet
@@ -487,7 +539,11 @@ __device__ int dist_query(const RefineDev &D, const float *A, const float *bvec,
         return -1;
     }
     *d_out = best;
-    sdf_normal(bx, D.r, D.L, nl);
+    {
+        float lv[3][3];
+        local_vertices(D, bt, A, bvec, lv);
+        witness_subgradient(bx, lv, D.r, D.L, nl);
+    }
     for (int c = 0; c < 3; ++c) xw[c] = bx[c];
     return bt;
 }
@@ -500,9 +556,10 @@ __device__ int dist_query(const RefineDev &D, const float *A, const float *bvec,
 template <bool GRAD>
 __global__ void __launch_bounds__(128, 6)
 k_refine_eval(const RefineDev *Dt, const int32_t *grp, const CandF *cands, double *acc_part, float *dist_out,
-              float *wit_out, float *nrm_out, int32_t *hints)
+              float *wit_out, float *nrm_out, int32_t *hints, const int32_t *active)
 {
     const int c = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (active && !active[c]) return;   // a finished candidate (its partials are not read)
     // the candidate's request (object mesh, trajectory, probe, parameters)
     const RefineDev D = Dt[grp ? grp[c] : 0];
     double acc[NACC];
@@ -716,15 +773,214 @@ __global__ void k_refine_solve(int K, int nblk, double *state, const double *acc
 }
 
 // ---------------------------------------------------------------------------
+// L-BFGS-B (Sec. V-C as printed): one thread per candidate, FP64.  A round
+// evaluates J and grad J (Eq. (19), (28)) at every active candidate's trial
+// twist; this kernel then accepts or backtracks the step (Armijo), updates the
+// limited-memory pairs (s, y) and builds the next trial.  The direction is the
+// two-loop recursion on the variables that are not held at a bound of
+// Eq. (20) (a variable is held when it sits on its bound and the gradient
+// pushes it outward), steps are projected onto the box and backtracked by
+// safeguarded quadratic interpolation (first step of unit length, as in
+// L-BFGS-B; later ones start at alpha = 1), and a candidate stops
+// when the projected gradient or the relative decrease of J is below its
+// tolerance, after max_iter accepted steps, or when backtracking fails.
+// ---------------------------------------------------------------------------
+enum {
+    LB_X = 0, LB_F = 6, LB_G = 7, LB_D = 13, LB_ALPHA = 19, LB_GTD = 20, LB_ITER = 21, LB_NBACK = 22,
+    LB_NH = 23, LB_HEAD = 24, LB_STATUS = 25, LB_NEV = 26, LB_HIST = 32
+};
+constexpr int LB_S = LB_HIST, LB_Y = LB_HIST + 6 * LB_M, LB_RHO = LB_HIST + 12 * LB_M;
+static_assert(LB_RHO + LB_M <= LB_ST, "L-BFGS state");
+
+__device__ __forceinline__ double lb_hi(int j, const double *prm) { return j < 3 ? prm[4] : prm[5]; }
+
+__device__ __forceinline__ double lb_clamp(double v, double hi) { return v > hi ? hi : (v < -hi ? -hi : v); }
+
+__device__ __forceinline__ bool lb_held(const double *x, const double *g, int j, const double *prm)
+{
+    const double hi = lb_hi(j, prm);
+    return (x[j] <= -hi && g[j] > 0.0) || (x[j] >= hi && g[j] < 0.0);
+}
+
+// d = -H g on the free variables (two-loop recursion over the stored pairs)
+__device__ void lb_direction(double *L, const double *prm)
+{
+    const double *x = L + LB_X, *g = L + LB_G;
+    double *d = L + LB_D;
+    const int nh = (int)L[LB_NH], head = (int)L[LB_HEAD];
+    double q[6], al[LB_M];
+    for (int j = 0; j < 6; ++j) q[j] = lb_held(x, g, j, prm) ? 0.0 : g[j];
+    for (int k = 0; k < nh; ++k) {
+        const int i = (head - 1 - k + 2 * LB_M) % LB_M;
+        const double *S = L + LB_S + 6 * i, *Y = L + LB_Y + 6 * i;
+        double a = 0.0;
+        for (int j = 0; j < 6; ++j) a += S[j] * q[j];
+        a *= L[LB_RHO + i];
+        al[k] = a;
+        for (int j = 0; j < 6; ++j) q[j] -= a * Y[j];
+    }
+    double gam = 1.0;
+    if (nh > 0) {
+        const int i = (head - 1 + LB_M) % LB_M;
+        const double *S = L + LB_S + 6 * i, *Y = L + LB_Y + 6 * i;
+        double sy = 0.0, yy = 0.0;
+        for (int j = 0; j < 6; ++j) { sy += S[j] * Y[j]; yy += Y[j] * Y[j]; }
+        gam = sy / yy;
+    }
+    for (int j = 0; j < 6; ++j) q[j] *= gam;
+    for (int k = nh - 1; k >= 0; --k) {
+        const int i = (head - 1 - k + 2 * LB_M) % LB_M;
+        const double *S = L + LB_S + 6 * i, *Y = L + LB_Y + 6 * i;
+        double b = 0.0;
+        for (int j = 0; j < 6; ++j) b += Y[j] * q[j];
+        b *= L[LB_RHO + i];
+        for (int j = 0; j < 6; ++j) q[j] += S[j] * (al[k] - b);
+    }
+    double gd = 0.0;
+    for (int j = 0; j < 6; ++j) {
+        d[j] = lb_held(x, g, j, prm) ? 0.0 : -q[j];
+        gd += g[j] * d[j];
+    }
+    if (!(gd < 0.0)) {   // not a descent direction: forget the pairs, steepest descent
+        L[LB_NH] = 0.0;
+        for (int j = 0; j < 6; ++j) d[j] = lb_held(x, g, j, prm) ? 0.0 : -g[j];
+    }
+}
+
+// trial twist x + alpha d projected onto the box; false when it does not move
+__device__ bool lb_trial(double *L, double *xi, const double *prm)
+{
+    const double *x = L + LB_X, *g = L + LB_G, *d = L + LB_D;
+    double gtd = 0.0, mv = 0.0;
+    for (int j = 0; j < 6; ++j) {
+        xi[j] = lb_clamp(x[j] + L[LB_ALPHA] * d[j], lb_hi(j, prm));
+        gtd += g[j] * (xi[j] - x[j]);
+        mv = fmax(mv, fabs(xi[j] - x[j]));
+    }
+    L[LB_GTD] = gtd;
+    return mv > 0.0 && gtd < 0.0;
+}
+
+__device__ void lb_new_step(double *L, double *xi, const double *prm)
+{
+    lb_direction(L, prm);
+    double dn = 0.0;
+    for (int j = 0; j < 6; ++j) dn += L[LB_D + j] * L[LB_D + j];
+    dn = sqrt(dn);
+    L[LB_ALPHA] = (L[LB_NH] == 0.0 && dn > 1.0) ? 1.0 / dn : 1.0;
+    L[LB_NBACK] = 0.0;
+    if (!lb_trial(L, xi, prm)) L[LB_STATUS] = 1.0;
+}
+
+// prm: lambda, mu, step_t, step_r, b_t, b_r, pgtol, ftol, max_iter
+// phase 0: start at xi = 0; phase 1: take the round's evaluation; phase 2:
+// leave every candidate at its last accepted twist (J, iterations and
+// evaluations in the state's slots 21, 22, 23)
+__global__ void k_lbfgs(int K, int nblk, double *state, const double *acc_part, const double *prm, double *lbs,
+                        int32_t *active, CandF *cands, int phase)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= K) return;
+    double *st = state + (size_t)c * ST, *xi = st + 15, *L = lbs + (size_t)c * LB_ST;
+    if (phase == 0) {
+        for (int k = 0; k < LB_ST; ++k) L[k] = 0.0;
+        L[LB_ITER] = -1.0;
+        for (int j = 0; j < 6; ++j) xi[j] = 0.0;
+        active[c] = 1;
+    } else if (phase == 1) {
+        if (L[LB_STATUS] != 0.0) {
+            active[c] = 0;
+            return;
+        }
+        double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int q = 0; q < nblk; ++q)
+            for (int k = 0; k < 7; ++k) acc[k] += acc_part[((size_t)c * nblk + q) * NACC + k];
+        const double lam = prm[0];
+        double xx = 0.0;
+        for (int j = 0; j < 6; ++j) xx += xi[j] * xi[j];
+        const double ft = acc[0] + lam * xx;
+        double gt[6];
+        for (int j = 0; j < 6; ++j) gt[j] = acc[1 + j] + 2.0 * lam * xi[j];
+        L[LB_NEV] += 1.0;
+        bool take = false;
+        if (L[LB_ITER] < 0.0) {
+            take = true;   // the starting point
+        } else if (isfinite(ft) && ft <= L[LB_F] + 1e-4 * L[LB_GTD]) {
+            take = true;
+        }
+        if (take) {
+            const bool first = L[LB_ITER] < 0.0;
+            const double fold = L[LB_F];
+            if (!first) {
+                double s[6], y[6], sy = 0.0, yy = 0.0;
+                for (int j = 0; j < 6; ++j) {
+                    s[j] = xi[j] - L[LB_X + j];
+                    y[j] = gt[j] - L[LB_G + j];
+                    sy += s[j] * y[j];
+                    yy += y[j] * y[j];
+                }
+                if (sy > 1e-12 * yy) {
+                    const int i = (int)L[LB_HEAD];
+                    for (int j = 0; j < 6; ++j) { L[LB_S + 6 * i + j] = s[j]; L[LB_Y + 6 * i + j] = y[j]; }
+                    L[LB_RHO + i] = 1.0 / sy;
+                    L[LB_HEAD] = (double)((i + 1) % LB_M);
+                    L[LB_NH] = fmin((double)LB_M, L[LB_NH] + 1.0);
+                }
+            }
+            for (int j = 0; j < 6; ++j) { L[LB_X + j] = xi[j]; L[LB_G + j] = gt[j]; }
+            L[LB_F] = ft;
+            L[LB_ITER] = first ? 0.0 : L[LB_ITER] + 1.0;
+            double pg = 0.0;
+            for (int j = 0; j < 6; ++j) pg = fmax(pg, fabs(lb_clamp(xi[j] - gt[j], lb_hi(j, prm)) - xi[j]));
+            const bool conv = pg <= prm[6] ||
+                              (!first && fold - ft <= prm[7] * fmax(fmax(fabs(fold), fabs(ft)), 1.0)) ||
+                              L[LB_ITER] >= prm[8];
+            if (conv) L[LB_STATUS] = 1.0;
+            else lb_new_step(L, xi, prm);
+        } else {
+            // backtrack to the minimiser of the quadratic through f, the
+            // slope gtd and the trial value, kept within [0.1, 0.5] of the step
+            const double gtd = L[LB_GTD], dphi = ft - L[LB_F];
+            double t = (isfinite(ft) && dphi - gtd > 0.0) ? -gtd / (2.0 * (dphi - gtd)) : 0.1;
+            t = fmin(fmax(t, 0.1), 0.5);
+            L[LB_NBACK] += 1.0;
+            L[LB_ALPHA] *= t;
+            if (L[LB_NBACK] > 30.0 || !lb_trial(L, xi, prm)) L[LB_STATUS] = 1.0;
+        }
+        if (L[LB_STATUS] != 0.0) {
+            for (int j = 0; j < 6; ++j) xi[j] = L[LB_X + j];
+            active[c] = 0;
+        }
+    } else {
+        if (L[LB_ITER] >= 0.0)
+            for (int j = 0; j < 6; ++j) xi[j] = L[LB_X + j];
+        st[21] = L[LB_F];
+        st[22] = fmax(L[LB_ITER], 0.0);
+        st[23] = L[LB_NEV];
+        active[c] = 0;
+    }
+    cand_from_state(st, &cands[c]);
+}
+
+cudaError_t launch_lbfgs(int K, int nblk, double *state, const double *acc_part, const double *prm, double *lbs,
+                         int32_t *active, CandF *cands, int phase, cudaStream_t st)
+{
+    k_lbfgs<<<(K + 63) / 64, 64, 0, st>>>(K, nblk, state, acc_part, prm, lbs, active, cands, phase);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 cudaError_t launch_refine_eval(const RefineDev *Dt, const int32_t *grp, int K, int nblk, const CandF *cands,
                                double *acc_part, bool grad, float *dist_out, float *wit_out, float *nrm_out,
-                               cudaStream_t st, int32_t *hints)
+                               cudaStream_t st, int32_t *hints, const int32_t *active)
 {
     dim3 grid(nblk, K);
-    if (grad) k_refine_eval<true><<<grid, 128, 0, st>>>(Dt, grp, cands, acc_part, dist_out, wit_out, nrm_out, hints);
-    else k_refine_eval<false><<<grid, 128, 0, st>>>(Dt, grp, cands, acc_part, dist_out, wit_out, nrm_out, hints);
+    if (grad)
+        k_refine_eval<true><<<grid, 128, 0, st>>>(Dt, grp, cands, acc_part, dist_out, wit_out, nrm_out, hints, active);
+    else
+        k_refine_eval<false><<<grid, 128, 0, st>>>(Dt, grp, cands, acc_part, dist_out, wit_out, nrm_out, hints, active);
     return cudaGetLastError();
 }
 

@@ -20,6 +20,7 @@ OK, PENDING = 0, 1
 E_INVALID, E_NOMEM, E_TOO_LARGE, E_CUDA, E_CUDA_FATAL, E_TIMEOUT, E_CANCELLED, E_BUSY, E_OVERFLOW = \
     -1, -2, -3, -4, -5, -6, -7, -8, -9
 SAMPLER_SF, SAMPLER_HOPF, SAMPLER_GEOBALL, SAMPLER_EXPLICIT = 0, 1, 2, 3
+SOLVER_GAUSS_NEWTON, SOLVER_LBFGSB = 0, 1
 
 
 class DockError(RuntimeError):
@@ -33,7 +34,8 @@ class Params(ctypes.Structure):
                 ("tau_out2", ctypes.c_double), ("tau_in2", ctypes.c_double), ("k_slope", ctypes.c_double),
                 ("lambda_", ctypes.c_double), ("mu", ctypes.c_double), ("b_t", ctypes.c_double),
                 ("b_r", ctypes.c_double), ("step_t", ctypes.c_double), ("step_r", ctypes.c_double),
-                ("iters", ctypes.c_int32), ("tri_iters", ctypes.c_int32)]
+                ("iters", ctypes.c_int32), ("tri_iters", ctypes.c_int32), ("solver", ctypes.c_int32),
+                ("lbfgs_evals", ctypes.c_int32), ("lbfgs_pgtol", ctypes.c_double), ("lbfgs_ftol", ctypes.c_double)]
 
 
 class Probe(ctypes.Structure):

@@ -38,6 +38,8 @@ def test_params_default_is_table_I():
     p = dock.default_params()
     assert (p.tau_out1, p.tau_in1, p.deep_value, p.tau_out2, p.tau_in2) == (0.5, 0.2, -50.0, 0.2, 0.03)
     assert p.k_slope == 15.0 and p.iters == 20
+    assert p.solver == dock.SOLVER_GAUSS_NEWTON and p.lbfgs_evals == 100 and p.lbfgs_pgtol == 1e-5
+    assert ctypes.sizeof(dock.Params) == 128     # 12 doubles, 4 int32, 2 doubles: no padding
 
 
 def test_binding_fails_loudly_without_the_library(monkeypatch):
