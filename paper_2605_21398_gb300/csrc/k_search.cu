@@ -1266,7 +1266,7 @@ __device__ __forceinline__ void plane_body(const float2 *Zp, const float2 *tw_g,
 
 template <int M>
 __global__ void __launch_bounds__(PlaneCfg<M>::NT)
-k_plane(int B, const float2 *Z, const float2 *tw_g, const RotRec *rots, const ReqDev *reqs)
+k_plane(int B, const float2 *Z, const float2 *tw_g, const RotRec *rots, const ReqDev *reqs, int ahead)
 {
     using C = PlaneCfg<M>;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1278,6 +1278,27 @@ k_plane(int B, const float2 *Z, const float2 *tw_g, const RotRec *rots, const Re
     if constexpr (C::CL > 1) rank = (int)cg::this_cluster().block_rank();
     const size_t plane = (size_t)M * (M / 2 + 2);
     const float2 *Zp = Z + ((size_t)b * M + zc) * plane;
+    // One CTA fits an SM, so its column loads cannot overlap another CTA's
+    // compute.  Ask L2 for the same half of the plane `ahead` planes on (the
+    // one the CTA that next runs on this SM is likely to take): every line
+    // of each row's half (kx in [rank PC, rank PC + PC), plus the Nyquist
+    // column for rank 0), all addresses inside that row.
+    const size_t nxt = (size_t)b * M + zc + (size_t)ahead;
+    if (ahead > 0 && nxt < (size_t)B * M) {
+        constexpr int HB = C::PC * (int)sizeof(float2);   // bytes of a half row
+        constexpr int NL = (HB + 127) / 128 + 1;           // prefetches per half row (the last at its end)
+        const char *rows = reinterpret_cast<const char *>(Z + nxt * plane);
+        for (int i = threadIdx.x; i < M * (NL + 1); i += blockDim.x) {
+            const int ky = i / (NL + 1), k = i % (NL + 1);
+            const char *row = rows + (size_t)ky * (M / 2 + 2) * sizeof(float2);
+            int off;
+            if (k < NL - 1) off = rank * HB + 128 * k;
+            else if (k == NL - 1) off = rank * HB + HB - 1;
+            else off = (M / 2) * (int)sizeof(float2);   // the Nyquist column
+            if (k == NL && rank != 0) continue;
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(row + off));
+        }
+    }
     plane_body<M, false>(Zp, tw_g, &reqs[rots[b].req].keys[rots[b].rot], nullptr, zc, pb, stg, tw, rank);
 }
 
@@ -1326,7 +1347,12 @@ static cudaError_t launch_plane_t(int B, const float2 *Z, const float2 *tw, cons
     } else {
         e = cudaFuncSetAttribute(k_plane<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        e = cudaLaunchKernelEx(&cfg, k_plane<M>, B, Z, tw, rots, reqs);
+        // planes in flight at one CTA per SM: the next CTA on an SM takes
+        // roughly the plane this many further on
+        int dev = 0, sms = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        e = cudaLaunchKernelEx(&cfg, k_plane<M>, B, Z, tw, rots, reqs, sms / CL);
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
