@@ -263,16 +263,24 @@ def run_reference(args):
     return 0
 
 
-def run_ncu_case():
+def run_ncu_case(variant="plain"):
     """One search of 8 SF rotations in one batch on the bench workload (every
     search kernel launches once with 8 rotations, a few GB on the device), then
-    a refinement of 8 candidates near the planted pose."""
+    a refinement of 8 candidates near the planted pose.  variant: "plain", or
+    the search with the rotated object ("rotate_object") or the label-aware
+    score ("label_aware")."""
     from paper_2605_21398_gb300 import build, dock, synth
     build.build()
     w = synth.make_workload(WORKLOAD)
     ctx = dock.Context(0)
     ob = ctx.object_grid(w.obj.verts, w.obj.tris, w.h, w.N)
     sw = ctx.sweep_grid(w.poses_world, w.radius, w.length, w.h, w.N, contact=w.labels)
+    if variant == "rotate_object":
+        sw.set_rotate_object(True)
+    elif variant == "label_aware":
+        sw.set_label_aware(True)
+    elif variant != "plain":
+        raise ValueError("unknown ncu variant %r" % variant)
     c = ctx.search_so3(ob, sw, 8, 4, batch=8)
     # refinement of 8 candidates near the planted pose (every refinement kernel launches)
     rng = np.random.default_rng(3)
@@ -281,7 +289,8 @@ def run_ncu_case():
         dq = synth.axis_angle_quat(np.radians(rng.normal(0.0, 1.0, 3)))
         cands.append(dict(q=synth.quat_mul(dq, w.gt_q), t=w.gt_t + rng.normal(0.0, 0.05, 3)))
     r = ctx.refine_se3(ob, sw, cands)
-    print(json.dumps({"ncu_case": WORKLOAD, "rotations": 8, "best_score": c[0]["score"], "refined": len(r)}))
+    print(json.dumps({"ncu_case": WORKLOAD, "variant": variant, "rotations": 8, "best_score": c[0]["score"],
+                      "refined": len(r)}))
     ob.close()
     sw.close()
     ctx.close()
@@ -300,13 +309,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--ncu-variant", default="plain", choices=["plain", "rotate_object", "label_aware"])
     ap.add_argument("--ncu-case", action="store_true",
                     help="small fixed case for ncu captures: one search of 8 rotations (batch 8) of the bench workload")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.ncu_case:
-        return run_ncu_case()
+        return run_ncu_case(args.ncu_variant)
 
     import torch
     rank, ws = _dist()
