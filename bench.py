@@ -63,6 +63,52 @@ def serving_mix(synth, n_req=24, seed=11):
     return works, reqs
 
 
+def cufft_comparison(ctx, ob, sw, w, stream, n_rot=16, batch=8):
+    """The correlation of the search done with cuFFT (through torch.fft) for
+    comparison only: S_R from the library's voxeliser (bit-identical), then
+    R2C, the product with conj(F(O)), C2R and the argmax over the M^3 canvas,
+    batch rotations at a time.  Returns the cuFFT device time per rotation
+    (CUDA events; the voxeliser excluded, as in the kernels it is set against)
+    and the largest score difference to the library's peaks."""
+    import torch
+    N, M = w.N, 2 * w.N
+    quats = synth_rotations(n_rot)
+    bits, _ = sw.voxelise(quats)
+    G, _ = ob.export_grid()
+    with torch.cuda.stream(stream):
+        Og = torch.zeros((M, M, M), dtype=torch.float32, device="cuda")
+        Og[:N, :N, :N] = torch.from_numpy(G).cuda()
+        FOc = torch.conj(torch.fft.rfftn(Og))
+        del Og
+        Sd = torch.from_numpy(bits).cuda()
+        best = torch.empty(n_rot, dtype=torch.float32, device="cuda")
+
+        def run():
+            for b0 in range(0, n_rot, batch):
+                Sp = torch.zeros((batch, M, M, M), dtype=torch.float32, device="cuda")
+                Sp[:, :N, :N, :N] = Sd[b0:b0 + batch].float()
+                C = torch.fft.irfftn(torch.fft.rfftn(Sp, dim=(1, 2, 3)) * FOc, s=(M, M, M), dim=(1, 2, 3))
+                best[b0:b0 + batch] = C.reshape(batch, -1).max(dim=1).values
+        run()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        run()
+        ev1.record(stream)
+    ev1.synchronize()
+    us = ev0.elapsed_time(ev1) * 1000.0 / n_rot
+    _, pk = ctx.search_so3(ob, sw, n_rot, 1, sampler=3, quats=quats, want_peaks=True)
+    diff = float(np.max(np.abs(best.cpu().numpy() - pk["score"])))
+    torch.cuda.empty_cache()
+    return {"us_per_rotation": round(us, 1), "rotations": n_rot, "batch": batch,
+            "path": "torch.fft (cuFFT) R2C + conj(F(O)) product + C2R + argmax, S_R from the library's voxeliser",
+            "max_peak_score_diff": round(diff, 4)}
+
+
+def synth_rotations(n, seed=5):
+    from paper_2605_21398_gb300 import synth
+    return synth.random_unit_quats(n, seed)
+
+
 def serving_experiment(ctx, synth):
     """Plain loop (dock_register one request at a time) against the serving
     engine (dock_submit/dock_poll): a burst of all requests for throughput,
@@ -467,6 +513,15 @@ def main():
         lbfgsb["refine_ms"] = round(sum(lbfgsb["kernels_ms"].values()), 2)
         del lbfgsb["ms_per_eval_search"]
 
+    cufft = None
+    if rank == 0 and not args.no_variants:
+        try:
+            cufft = cufft_comparison(ctx, ob, sw, w, stream)
+            ours = sum(stats[k][1] for k in ("fwd2d", "zpass", "plane") if k in stats) / rot_total * 1000.0
+            cufft["ours_fwd2d_zpass_plane_us_per_rotation"] = round(ours, 1)
+        except Exception as exc:   # reported, not fatal to the throughput line
+            cufft = {"error": "%s: %s" % (type(exc).__name__, exc)}
+
     serving = None
     if rank == 0 and not args.no_serving:
         try:
@@ -511,6 +566,7 @@ def main():
                                         / rot_total * 1000.0, 3),
             "clocks": clk, "object_setup_ms": round(obj_setup_ms, 2), "serving": serving,
             "label_aware": label_aware, "rotate_object": rotate_object, "lbfgsb_refinement": lbfgsb,
+            "cufft_comparison": cufft,
             "accuracy": {"trans_err_mm": round(err_t, 4), "rot_err_deg": round(err_r, 4), "J": res["J"]}}
     if rank == 0:
         print(json.dumps(line))
