@@ -43,9 +43,9 @@ def _labels(w):
 
 
 def _pair(ctx, w, labels, label_aware=True):
-    if w.name not in _OBJ:
-        _OBJ[w.name] = ctx.object_grid(w.obj.verts, w.obj.tris, w.h, w.N)
-    ob = _OBJ[w.name]
+    if id(w) not in _OBJ:
+        _OBJ[id(w)] = ctx.object_grid(w.obj.verts, w.obj.tris, w.h, w.N)
+    ob = _OBJ[id(w)]
     sw = ctx.sweep_grid(w.poses_world, w.radius, w.length, w.h, w.N, contact=labels)
     if label_aware:
         sw.set_label_aware(True)
@@ -200,3 +200,32 @@ def test_bad_label_aware_flag_is_rejected(ctx, workload):
     assert dock.lib().dock_sweep_set_label_aware(ctx.h, sw.h, 2) != 0
     sw.set_label_aware(True)
     sw.set_label_aware(False)
+
+
+@pytest.mark.parametrize("N", [96, 128])
+def test_label_aware_parity_on_the_192_and_256_canvases(ctx, workload, N):
+    # the dual z pass on the radix-3 (192) and 256 canvases: split grids,
+    # field and peaks against the oracle (30 % retreat poses non-contact)
+    w = workload("free64", N=N, h=16.0 / N, poses=300, n_theta=48, n_phi=96, lines=3, noncontact=0.3)
+    lab = w.labels
+    assert 0 < int((lab == 0).sum()) < len(lab)
+    ob, sw = _pair(ctx, w, lab)
+    Go, oo, _, fits = O.object_grid(w.obj.verts, w.obj.tris, w.h, w.N)
+    assert fits
+    M = O.canvas_size(N)
+    quats = np.concatenate([[w.gt_q], synth.random_unit_quats(2, 32)])
+    bc, bn, _ = sw.voxelise_labels(quats)
+    _, peaks = ctx.search_so3(ob, sw, len(quats), 2, sampler=3, quats=quats, want_peaks=True)
+    for i, q in enumerate(quats):
+        S_c, S_n, _ = O.sweep_grids_by_label(w.poses_world, lab, q, w.h, w.N, w.radius, w.length)
+        assert np.array_equal(bc[i], S_c) and np.array_equal(bn[i], S_n)
+        Co = O.correlate_label_aware(Go, S_c, S_n, M)
+        sc, idx = O.peak(Co)
+        tol = 1e-4 * np.max(np.abs(Co))
+        assert abs(peaks["score"][i] - sc) <= tol + 1e-4 * abs(sc), i
+        if sc - _second_best(Co, idx) > 2 * tol:
+            assert peaks["idx"][i] == idx, i
+    C = ctx.search_scores(ob, sw, quats[0])
+    S_c, S_n, _ = O.sweep_grids_by_label(w.poses_world, lab, quats[0], w.h, w.N, w.radius, w.length)
+    Co = O.correlate_label_aware(Go, S_c, S_n, M)
+    assert np.max(np.abs(C - Co)) <= 1e-4 * np.max(np.abs(Co))

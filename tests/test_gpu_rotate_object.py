@@ -36,13 +36,13 @@ _OBJ = {}
 
 
 def _pair(ctx, w, rotate_object=True):
-    if w.name not in _OBJ:
-        _OBJ[w.name] = ctx.object_grid(w.obj.verts, w.obj.tris, w.h, w.N)
+    if id(w) not in _OBJ:
+        _OBJ[id(w)] = ctx.object_grid(w.obj.verts, w.obj.tris, w.h, w.N)
     sw = ctx.sweep_grid(w.poses_world, w.radius, w.length, w.h, w.N, contact=w.labels)
     if rotate_object:
         sw.set_rotate_object(True)
     _KEEP.append(sw)
-    return _OBJ[w.name], sw
+    return _OBJ[id(w)], sw
 
 
 def _second_best(C, idx):
@@ -167,3 +167,32 @@ def test_rotate_object_and_label_aware_exclude_each_other(ctx, workload):
     sw.set_label_aware(True)
     with pytest.raises(dock.DockError):
         sw.set_rotate_object(True)
+
+
+@pytest.mark.parametrize("N", [96, 128])
+def test_rotated_object_parity_on_the_192_and_256_canvases(ctx, workload, N):
+    # the radix-3 (192) and 2-CTA-cluster (256) canvases of the resampled x
+    # stage: grids, field and peaks against the oracle
+    w = workload("free64", N=N, h=16.0 / N, poses=300, n_theta=48, n_phi=96, lines=3, noncontact=0.0)
+    ob, sw = _pair(ctx, w)
+    Go, oo, _, fits = O.object_grid(w.obj.verts, w.obj.tris, w.h, w.N)
+    assert fits
+    M = O.canvas_size(N)
+    S, _ = O.sweep_grid(w.poses_world, O.IDENTITY_Q, w.h, w.N, w.radius, w.length)
+    quats = np.concatenate([[w.gt_q], synth.random_unit_quats(2, 31)])
+    G, orig = ob.rotated(quats)
+    _, peaks = ctx.search_so3(ob, sw, len(quats), 2, sampler=3, quats=quats, want_peaks=True)
+    for i, q in enumerate(quats):
+        OR, oR = O.rotate_object(Go, oo, q, w.h)
+        assert np.array_equal(orig[i], oR)
+        assert np.max(np.abs(G[i] - OR)) <= 5e-3
+        Co = O.correlate_fft(OR, S, M)
+        sc, idx = O.peak(Co)
+        tol = 1e-4 * np.max(np.abs(Co))
+        assert abs(peaks["score"][i] - sc) <= tol + 1e-4 * abs(sc), i
+        if sc - _second_best(Co, idx) > 2 * tol:
+            assert peaks["idx"][i] == idx, i
+    C = ctx.search_scores(ob, sw, quats[0])
+    OR, _ = O.rotate_object(Go, oo, quats[0], w.h)
+    Co = O.correlate_fft(OR, S, M)
+    assert np.max(np.abs(C - Co)) <= 1e-4 * np.max(np.abs(Co))
