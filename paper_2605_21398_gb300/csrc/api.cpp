@@ -170,11 +170,12 @@ struct dock_sweep {
     // each group in trajectory order; nullptr when every pose is contact
     PoseRec *poses_lab = nullptr;
     int64_t P_c = 0;
-    std::atomic<bool> label_aware{false};
+    // scoring mode bits, read and changed as one word so that the two
+    // exclusive options can never both be on: SCORE_LABEL_AWARE, SCORE_ROTATE_OBJECT
+    std::atomic<int> mode{0};
     // rotating the object (Sec. IV-D as printed): S on the world-aligned
     // lattice of the mean tip, its spectrum F(S) / M^3 and origin o_s, made
     // on first use
-    std::atomic<bool> rotate_object{false};
     float2 *spec_S = nullptr;
     double *os_dev = nullptr;
 };
@@ -1175,13 +1176,25 @@ extern "C" dock_status dock_sweep_voxelise(dock_ctx *ctx, const dock_sweep *sw, 
     return DOCK_OK;
 }
 
+enum { SCORE_LABEL_AWARE = 1, SCORE_ROTATE_OBJECT = 2 };
+
+// Sets or clears `bit` of the sweep's mode; setting fails while `other` is set.
+static bool set_mode_bit(dock_sweep *sw, int bit, int other, bool on)
+{
+    int cur = sw->mode.load();
+    for (;;) {
+        if (on && (cur & other)) return false;
+        const int want = on ? (cur | bit) : (cur & ~bit);
+        if (sw->mode.compare_exchange_weak(cur, want)) return true;
+    }
+}
+
 extern "C" dock_status dock_sweep_set_label_aware(dock_ctx *ctx, dock_sweep *sw, int32_t on)
 {
     if (!ctx || !sw || sw->ctx != ctx) return DOCK_E_INVALID;
     if (on != 0 && on != 1) return fail(ctx, DOCK_E_INVALID, "label_aware must be 0 or 1");
-    if (on && sw->rotate_object.load())
+    if (!set_mode_bit(sw, SCORE_LABEL_AWARE, SCORE_ROTATE_OBJECT, on != 0))
         return fail(ctx, DOCK_E_INVALID, "the label-aware score needs the rotated sweep (rotate_object is on)");
-    sw->label_aware.store(on != 0);
     return DOCK_OK;
 }
 
@@ -1189,9 +1202,8 @@ extern "C" dock_status dock_sweep_set_rotate_object(dock_ctx *ctx, dock_sweep *s
 {
     if (!ctx || !sw || sw->ctx != ctx) return DOCK_E_INVALID;
     if (on != 0 && on != 1) return fail(ctx, DOCK_E_INVALID, "rotate_object must be 0 or 1");
-    if (on && sw->label_aware.load())
+    if (!set_mode_bit(sw, SCORE_ROTATE_OBJECT, SCORE_LABEL_AWARE, on != 0))
         return fail(ctx, DOCK_E_INVALID, "rotating the object excludes the label-aware score (label_aware is on)");
-    sw->rotate_object.store(on != 0);
     return DOCK_OK;
 }
 
@@ -1396,8 +1408,9 @@ static dock_status run_pipeline(dock_ctx *ctx, const Geo &g, size_t r0, size_t r
     return run_pipeline_rots(ctx, g, ctx->reqs, ctx->rots, r0, r1, batch, dual);
 }
 
-// The label-aware score of this sweep is in force and differs from the plain one.
-static bool dual_scoring(const dock_sweep *sw) { return sw->label_aware.load() && sw->poses_lab != nullptr; }
+// The label-aware score of a sweep in `mode` (one read of dock_sweep::mode)
+// is in force and differs from the plain one.
+static bool dual_scoring(const dock_sweep *sw, int mode) { return (mode & SCORE_LABEL_AWARE) && sw->poses_lab != nullptr; }
 
 // conj(F(min(O, 0))) / M^3 of the object, made on first use and kept with it.
 static dock_status ensure_spec_pen(dock_ctx *ctx, const dock_object *obc)
@@ -1521,20 +1534,21 @@ static dock_status ensure_spec_S(dock_ctx *ctx, const dock_sweep *swc)
 }
 
 // The search of this sweep rotates the object grid.
-static bool rotates_object(const dock_sweep *sw) { return sw->rotate_object.load(); }
+static bool rotates_object(int mode) { return (mode & SCORE_ROTATE_OBJECT) != 0; }
 
 static dock_status search_impl(dock_ctx *ctx, const dock_object *ob, const dock_sweep *sw, const dock_search_desc *d,
                                const std::vector<double> &q, int r0, int r1, dock_candidate *out, dock_peak *per_rot)
 {
     const int n = d->n;
     dock_status s;
-    const bool ro = rotates_object(sw);
+    const int mode = sw->mode.load();   // one read: the two options are exclusive
+    const bool ro = rotates_object(mode);
     if (ro && ((s = ensure_spec_S(ctx, sw)) != DOCK_OK || (s = ensure_cells(ctx, ob)) != DOCK_OK)) return s;
     if ((s = upload_rots(ctx, sw, q.data(), n, 0, n, 0, 0, ro ? ob->o_dev : nullptr)) != DOCK_OK) return s;
     if ((s = ensure(ctx, (void **)&ctx->keys, &ctx->keys_n, (size_t)n, sizeof(unsigned long long))) != DOCK_OK) return s;
     CK(ctx, cudaMemsetAsync(ctx->keys, 0, sizeof(unsigned long long) * n, ctx->stream));
     CK(ctx, cudaMemsetAsync(ctx->errflag, 0, sizeof(int), ctx->stream));
-    const bool dual = dual_scoring(sw);
+    const bool dual = dual_scoring(sw, mode);
     if (dual && (s = ensure_spec_pen(ctx, ob)) != DOCK_OK) return s;
     std::vector<ReqDev> rq(1, make_reqdev(ob, sw, ctx->keys, dual, ro));
     if ((s = upload_reqs(ctx, rq)) != DOCK_OK) return s;
@@ -1600,7 +1614,7 @@ extern "C" dock_status dock_search_peaks_noalloc(dock_ctx *ctx, const dock_objec
     if (n < 1 || n > NOALLOC_MAX_ROT)
         return fail(ctx, DOCK_E_INVALID, "rotation count %d outside [1, %d] of dock_search_peaks_noalloc", n,
                     NOALLOC_MAX_ROT);
-    if (dual_scoring(sw) || rotates_object(sw))
+    if (sw->mode.load() != 0)
         return fail(ctx, DOCK_E_INVALID,
                     "dock_search_peaks_noalloc rotates the sweep and scores plainly; the sweep asks otherwise");
     for (int i = 0; i < n; ++i) {
@@ -1829,10 +1843,11 @@ extern "C" dock_status dock_search_scores(dock_ctx *ctx, const dock_object *ob, 
     d.quats = quat;
     std::vector<double> q;
     if ((s = gen_samples(ctx, &d, q)) != DOCK_OK) return s;
-    const bool ro = rotates_object(sw);
+    const int mode = sw->mode.load();   // one read: the two options are exclusive
+    const bool ro = rotates_object(mode);
     if (ro && ((s = ensure_spec_S(ctx, sw)) != DOCK_OK || (s = ensure_cells(ctx, ob)) != DOCK_OK)) return s;
     if ((s = upload_rots(ctx, sw, q.data(), 1, 0, 1, 0, 0, ro ? ob->o_dev : nullptr)) != DOCK_OK) return s;
-    const bool dual = dual_scoring(sw);
+    const bool dual = dual_scoring(sw, mode);
     if (dual && (s = ensure_spec_pen(ctx, ob)) != DOCK_OK) return s;
     std::vector<ReqDev> rq(1, make_reqdev(ob, sw, nullptr, dual, ro));
     if ((s = upload_reqs(ctx, rq)) != DOCK_OK) return s;
@@ -2960,8 +2975,9 @@ static JobP make_job(const dock_object *ob, const dock_sweep *sw, const dock_reg
     j->res.last_pass = -1;
     j->ob = ob;
     j->sw = sw;
-    j->la = sw && sw->label_aware.load();
-    j->ro = sw && sw->rotate_object.load();
+    const int mode = sw ? sw->mode.load() : 0;   // one read: the two options are exclusive
+    j->la = (mode & SCORE_LABEL_AWARE) != 0;
+    j->ro = (mode & SCORE_ROTATE_OBJECT) != 0;
     j->d = *rd;
     if (params) j->p = *params;
     else dock_params_default(&j->p);
