@@ -196,3 +196,22 @@ def test_rotated_object_parity_on_the_192_and_256_canvases(ctx, workload, N):
     OR, _ = O.rotate_object(Go, oo, quats[0], w.h)
     Co = O.correlate_fft(OR, S, M)
     assert np.max(np.abs(C - Co)) <= 1e-4 * np.max(np.abs(Co))
+
+
+def test_a_pass_mixing_all_three_scorings_gives_each_request_its_result_alone(ctx, workload):
+    # rotated sweep, rotated object and label-aware requests of one lattice
+    # side share the search passes (the two-grid pipeline runs for all)
+    w = workload("free64")
+    ob, sw_ro = _pair(ctx, w)
+    _, sw_pl = _pair(ctx, w, rotate_object=False)
+    _, sw_la = _pair(ctx, w, rotate_object=False)
+    sw_la.set_label_aware(True)
+    th = math.radians(5)
+    reqs = [(ob, sw_ro, 512, 128, th, 2), (ob, sw_la, 512, 128, th, 2), (ob, sw_pl, 512, 128, th, 2)]
+    batch = ctx.register_batch(reqs)
+    for rq, got in zip(reqs, batch):
+        ref = ctx.register(*rq)
+        assert got["best_search"]["rot"] == ref["best_search"]["rot"]
+        assert got["best_search"]["score"] == ref["best_search"]["score"]
+        np.testing.assert_array_equal(got["q"], ref["q"])
+        np.testing.assert_array_equal(got["t"], ref["t"])
