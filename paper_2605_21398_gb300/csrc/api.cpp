@@ -86,6 +86,8 @@ struct dock_ctx {
     size_t yz_bytes = 0;
     uint32_t *bits = nullptr;
     size_t bits_n = 0;
+    float *ogr = nullptr;     // rotated object grids of a launch's rotate_object rotations
+    size_t ogr_n = 0;
     unsigned long long *keys = nullptr;
     size_t keys_n = 0;
     RotRec *rots = nullptr;
@@ -498,6 +500,7 @@ void dock_destroy(dock_ctx *c)
     cudaStreamSynchronize(c->stream);
     cudaFree(c->Y);
     cudaFree(c->bits);
+    cudaFree(c->ogr);
     cudaFree(c->keys);
     cudaFree(c->rots);
     cudaFree(c->quats);
@@ -1344,7 +1347,7 @@ static dock_tuning tuning_for(dock_ctx *ctx, const Geo &g)
 // the voxels that set 0 leaves uncovered and adds their correlation with
 // min(O, 0) in the z pass (requests without a set 1 are unaffected).
 static dock_status run_pipeline_rots(dock_ctx *ctx, const Geo &g, const ReqDev *reqs, const RotRec *rots, size_t r0,
-                                     size_t r1, int batch, bool dual = false)
+                                     size_t r1, int batch, bool dual = false, bool ro_any = false)
 {
     float2 *tw, *qt;
     double2 *twd;
@@ -1369,6 +1372,9 @@ static dock_status run_pipeline_rots(dock_ctx *ctx, const Geo &g, const ReqDev *
     if ((s = ensure(ctx, (void **)&ctx->bits, &ctx->bits_n, dual ? 2 * bsz : bsz, sizeof(uint32_t))) != DOCK_OK)
         return s;
     uint32_t *bits2 = dual ? ctx->bits + bsz : nullptr;
+    if (ro_any &&
+        (s = ensure(ctx, (void **)&ctx->ogr, &ctx->ogr_n, (size_t)B * g.N * g.N * g.N, sizeof(float))) != DOCK_OK)
+        return s;
     int chunks = g.M * g.P / 32;
     for (size_t b0 = r0; b0 < r1; b0 += B) {
         int nb = (int)std::min<size_t>(B, r1 - b0);
@@ -1383,9 +1389,14 @@ static dock_status run_pipeline_rots(dock_ctx *ctx, const Geo &g, const ReqDev *
             Prof pr(ctx, "voxelise_nc");
             CK(ctx, launch_voxelise(g, reqs, rb, nb, bits2, ctx->stream, tc.vox_blocks, 1));
         }
+        if (ro_any) {
+            Prof pr(ctx, "resample");
+            CK(ctx, launch_resample(g, reqs, rb, nb, ctx->ogr, ctx->stream));
+        }
         {
             Prof pr(ctx, "fwd2d");
-            CK(ctx, launch_fwd2d(g, nb, ctx->bits, Y, tw, qt, ctx->stream, nullptr, rb, reqs));
+            CK(ctx, launch_fwd2d(g, nb, ctx->bits, Y, tw, qt, ctx->stream, nullptr, rb, reqs,
+                                 ro_any ? ctx->ogr : nullptr));
         }
         if (dual) {
             Prof pr(ctx, "fwd2d_nc");
@@ -1403,9 +1414,9 @@ static dock_status run_pipeline_rots(dock_ctx *ctx, const Geo &g, const ReqDev *
     return DOCK_OK;
 }
 
-static dock_status run_pipeline(dock_ctx *ctx, const Geo &g, size_t r0, size_t r1, int batch, bool dual)
+static dock_status run_pipeline(dock_ctx *ctx, const Geo &g, size_t r0, size_t r1, int batch, bool dual, bool ro)
 {
-    return run_pipeline_rots(ctx, g, ctx->reqs, ctx->rots, r0, r1, batch, dual);
+    return run_pipeline_rots(ctx, g, ctx->reqs, ctx->rots, r0, r1, batch, dual, ro);
 }
 
 // The label-aware score of a sweep in `mode` (one read of dock_sweep::mode)
@@ -1552,7 +1563,7 @@ static dock_status search_impl(dock_ctx *ctx, const dock_object *ob, const dock_
     if (dual && (s = ensure_spec_pen(ctx, ob)) != DOCK_OK) return s;
     std::vector<ReqDev> rq(1, make_reqdev(ob, sw, ctx->keys, dual, ro));
     if ((s = upload_reqs(ctx, rq)) != DOCK_OK) return s;
-    if ((s = run_pipeline(ctx, make_geo(sw), r0, r1, d->batch, dual)) != DOCK_OK) return s;
+    if ((s = run_pipeline(ctx, make_geo(sw), r0, r1, d->batch, dual, ro)) != DOCK_OK) return s;
     if ((s = ensure(ctx, (void **)&ctx->cands, &ctx->cands_n, (size_t)d->top_k, sizeof(dock_candidate))) != DOCK_OK) return s;
     {
         Prof pr(ctx, "topk");
@@ -2457,6 +2468,11 @@ static dock_status job_admit(dock_ctx *ctx, Engine &E, Job &j, int *wait)
     size_t pen_bytes = la && !j.ob->spec_pen ? sizeof(float2) * (size_t)j.ob->M * j.ob->P * j.ob->M : 0;
     if (j.ro && !j.sw->spec_S) pen_bytes += sizeof(float2) * (size_t)j.ob->M * j.ob->P * j.ob->M;
     if (j.ro && !j.ob->cells) pen_bytes += sizeof(float4) * (size_t)(j.ob->N + 1) * (j.ob->N + 1) * (j.ob->N + 1);
+    if (j.ro) {   // the rotated object grids of a launch, if not held yet
+        const Geo gj = make_geo(j.sw);
+        const size_t need = (size_t)tuning_for(ctx, gj).batch * gj.N * gj.N * gj.N;
+        if (need > ctx->ogr_n) pen_bytes += sizeof(float) * need;
+    }
     if (ctx->budget && ctx->held + bytes + pen_bytes + yz_growth(ctx, j.sw, la) > ctx->budget) {
         if (!E.active.empty()) {
             *wait = ADMIT_WAIT;
@@ -2790,10 +2806,13 @@ static bool engine_step(dock_ctx *ctx)
             if (std::find(in_pass.begin(), in_pass.end(), jp) == in_pass.end()) in_pass.push_back(jp);
             if (taken == B) break;
         }
-    bool dual = false;
-    for (auto *jp : in_pass) dual = dual || (jp->la && jp->sw->poses_lab);
+    bool dual = false, ro_any = false;
+    for (auto *jp : in_pass) {
+        dual = dual || (jp->la && jp->sw->poses_lab);
+        ro_any = ro_any || jp->ro;
+    }
     if (ce != cudaSuccess) s = cuda_fail(ctx, ce, "gather of rotation records");
-    else s = run_pipeline_rots(ctx, g, E.reqtab, ctx->phase, 0, taken, B, dual);
+    else s = run_pipeline_rots(ctx, g, E.reqtab, ctx->phase, 0, taken, B, dual, ro_any);
     if (s == DOCK_OK) {
         cudaError_t e = cudaEventRecord(E.pass_ev[E.passes % 2], ctx->stream);
         if (e != cudaSuccess) s = cuda_fail(ctx, e, "recording a search pass");

@@ -80,9 +80,13 @@ cudaError_t launch_voxelise(const Geo &g, const ReqDev *reqs, const RotRec *rots
 // mask (nullable, the layout of bits): bits & ~mask is transformed.  With
 // rots/reqs given, rotations of rotate_object requests transform their
 // resampled object grid instead of bits (and are skipped when mask is set).
+// ogrids (nullable, B x N^3 floats): the rotated object grids made by
+// launch_resample, read instead of resampling inside the x stage.
 cudaError_t launch_fwd2d(const Geo &g, int B, const uint32_t *bits, float2 *Y, const float2 *tw, const float2 *q,
                          cudaStream_t st, const uint32_t *mask = nullptr, const RotRec *rots = nullptr,
-                         const ReqDev *reqs = nullptr);
+                         const ReqDev *reqs = nullptr, const float *ogrids = nullptr);
+// The rotated object grids of the rotate_object rotations of a launch into out (B x N^3 floats).
+cudaError_t launch_resample(const Geo &g, const ReqDev *reqs, const RotRec *rots, int B, float *out, cudaStream_t st);
 // Y2 (nullable): transforms of the label-aware second grids; when given, the
 // product with each request's spec_pen is added before the inverse FFT.
 cudaError_t launch_zpass(const Geo &g, int B, int group, const float2 *Y, const RotRec *rots, const ReqDev *reqs,

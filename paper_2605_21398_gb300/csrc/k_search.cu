@@ -621,16 +621,24 @@ template <int M> struct Fwd2dSmem {
 // later rounds' pairs lie above what a round writes.
 template <int M>
 __device__ __forceinline__ void resampled_x_stage(const RotRec &rr, const ReqDev &q, int jz, cf *X, cf *xbt, cf *xb,
-                                                  const cf *tw)
+                                                  const cf *tw, const float *slab)
 {
     constexpr int N = M / 2, H = M / 2, COLS = 32, E = Plan<M>::E, NP = N / 2, PP = N + 1;
     float2 *pairs = reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(X) + (size_t)N * H * 4);
-    const float4 *O = q.Og4;
+    if (slab) {
+        // the slab resampled beforehand by k_resample (N x N floats)
+        for (int i = threadIdx.x; i < NP * N; i += blockDim.x) {
+            const int x = i % N, p = i / N;
+            pairs[p * PP + x] = make_float2(slab[(2 * p) * N + x], slab[(2 * p + 1) * N + x]);
+        }
+    } else {
+        const float4 *O = q.Og4;
 #pragma unroll 4
-    for (int i = threadIdx.x; i < NP * N; i += blockDim.x) {
-        const int x = i % N, p = i / N;
-        pairs[p * PP + x] = make_float2(rotated_object_voxel(rr, O, N, x, 2 * p, jz),
-                                        rotated_object_voxel(rr, O, N, x, 2 * p + 1, jz));
+        for (int i = threadIdx.x; i < NP * N; i += blockDim.x) {
+            const int x = i % N, p = i / N;
+            pairs[p * PP + x] = make_float2(rotated_object_voxel(rr, O, N, x, 2 * p, jz),
+                                            rotated_object_voxel(rr, O, N, x, 2 * p + 1, jz));
+        }
     }
     __syncthreads();
     const int c = threadIdx.x % COLS, j = threadIdx.x / COLS;
@@ -745,7 +753,7 @@ __device__ __forceinline__ void bits_x_stage(const uint32_t *bits_g, const uint3
 template <int M>
 __global__ void __launch_bounds__(Plan<M>::T * 32)
 k_fwd2d(int P, const uint32_t *bits_g, float2 *Y, const float2 *tw_g, const float2 *q_g, const uint32_t *mask_g,
-        const RotRec *rots, const ReqDev *reqs)
+        const RotRec *rots, const ReqDev *reqs, const float *ogrids)
 {
     constexpr int N = M / 2, H = M / 2, COLS = 32, E = Plan<M>::E;
     using L = Fwd2dSmem<M>;
@@ -762,7 +770,8 @@ k_fwd2d(int P, const uint32_t *bits_g, float2 *Y, const float2 *tw_g, const floa
     for (int i = threadIdx.x; i < M; i += blockDim.x) { float2 w = tw_g[i]; tw[i] = cmake(w.x, w.y); }
     if (resample) {
         __syncthreads();
-        resampled_x_stage<M>(rots[b], reqs[rots[b].req], jz, X, xb, xb, tw);
+        resampled_x_stage<M>(rots[b], reqs[rots[b].req], jz, X, xb, xb, tw,
+                             ogrids ? ogrids + ((size_t)b * (M / 2) + jz) * (M / 2) * (M / 2) : nullptr);
     } else {
         bits_x_stage<M>(bits_g, mask_g, b, jz, X, bits, tw, q_g);
     }
@@ -805,24 +814,25 @@ k_fwd2d(int P, const uint32_t *bits_g, float2 *Y, const float2 *tw_g, const floa
 template <int M>
 static cudaError_t launch_fwd2d_t(const Geo &g, int B, const uint32_t *bits, float2 *Y, const float2 *tw,
                                   const float2 *q, cudaStream_t st, const uint32_t *mask, const RotRec *rots,
-                                  const ReqDev *reqs)
+                                  const ReqDev *reqs, const float *ogrids)
 {
     size_t sm = Fwd2dSmem<M>::BYTES;
     cudaError_t e = cudaFuncSetAttribute(k_fwd2d<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_fwd2d<M><<<dim3(M / 2, B), Plan<M>::T * 32, sm, st>>>(g.P, bits, Y, tw, q, mask, rots, reqs);
+    k_fwd2d<M><<<dim3(M / 2, B), Plan<M>::T * 32, sm, st>>>(g.P, bits, Y, tw, q, mask, rots, reqs, ogrids);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fwd2d(const Geo &g, int B, const uint32_t *bits, float2 *Y, const float2 *tw, const float2 *q,
-                         cudaStream_t st, const uint32_t *mask, const RotRec *rots, const ReqDev *reqs)
+                         cudaStream_t st, const uint32_t *mask, const RotRec *rots, const ReqDev *reqs,
+                         const float *ogrids)
 {
     if ((rots == nullptr) != (reqs == nullptr)) return cudaErrorInvalidValue;
     switch (g.M) {
-    case 64: return launch_fwd2d_t<64>(g, B, bits, Y, tw, q, st, mask, rots, reqs);
-    case 128: return launch_fwd2d_t<128>(g, B, bits, Y, tw, q, st, mask, rots, reqs);
-    case 192: return launch_fwd2d_t<192>(g, B, bits, Y, tw, q, st, mask, rots, reqs);
-    case 256: return launch_fwd2d_t<256>(g, B, bits, Y, tw, q, st, mask, rots, reqs);
+    case 64: return launch_fwd2d_t<64>(g, B, bits, Y, tw, q, st, mask, rots, reqs, ogrids);
+    case 128: return launch_fwd2d_t<128>(g, B, bits, Y, tw, q, st, mask, rots, reqs, ogrids);
+    case 192: return launch_fwd2d_t<192>(g, B, bits, Y, tw, q, st, mask, rots, reqs, ogrids);
+    case 256: return launch_fwd2d_t<256>(g, B, bits, Y, tw, q, st, mask, rots, reqs, ogrids);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -911,6 +921,34 @@ __global__ void __launch_bounds__(256) k_rot_export(int N, const ReqDev *reqs, c
     const ReqDev &q = reqs[rr.req];
     float *o = out + ((size_t)b * N + jz) * N * N;
     for (int i = threadIdx.x; i < N * N; i += blockDim.x) o[i] = rotated_object_voxel(rr, q.Og4, N, i % N, i / N, jz);
+}
+
+// The rotated object grids of a launch's rotate_object rotations, slab by
+// slab at full occupancy (the fused x stage of k_fwd2d runs one CTA per SM,
+// too few warps to hide the corner-cell loads); other rotations are skipped.
+template <int N>
+__global__ void __launch_bounds__(256) k_resample(const ReqDev *reqs, const RotRec *rots, float *out)
+{
+    const int jz = blockIdx.x, b = blockIdx.y;
+    const RotRec &rr = rots[b];
+    const ReqDev &q = reqs[rr.req];
+    if (!q.rotate_object) return;
+    float *o = out + ((size_t)b * N + jz) * N * N;
+    for (int i = threadIdx.x; i < N * N; i += blockDim.x) o[i] = rotated_object_voxel(rr, q.Og4, N, i % N, i / N, jz);
+}
+
+cudaError_t launch_resample(const Geo &g, const ReqDev *reqs, const RotRec *rots, int B, float *out, cudaStream_t st)
+{
+    if (B < 1 || B > 65535) return cudaErrorInvalidValue;
+    dim3 grid(g.N, B);
+    switch (g.N) {
+    case 32: k_resample<32><<<grid, 256, 0, st>>>(reqs, rots, out); break;
+    case 64: k_resample<64><<<grid, 256, 0, st>>>(reqs, rots, out); break;
+    case 96: k_resample<96><<<grid, 256, 0, st>>>(reqs, rots, out); break;
+    case 128: k_resample<128><<<grid, 256, 0, st>>>(reqs, rots, out); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_rot_export(const Geo &g, const ReqDev *reqs, const RotRec *rots, int B, float *out, cudaStream_t st)
