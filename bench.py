@@ -509,7 +509,8 @@ def main():
         label_aware, r_la = variant(lambda sv: sv.set_label_aware(True),
                                     ("voxelise", "voxelise_nc", "fwd2d", "fwd2d_nc", "zpass_dual", "plane"))
         label_aware["non_contact_poses"] = int((w.labels == 0).sum())
-        rotate_object, r_ro = variant(lambda sv: sv.set_rotate_object(True), ("voxelise", "fwd2d", "zpass", "plane"))
+        rotate_object, r_ro = variant(lambda sv: sv.set_rotate_object(True),
+                                      ("voxelise", "resample", "fwd2d", "zpass", "plane"))
         # the refinement by L-BFGS-B (Sec. V-C as printed) instead of Gauss-Newton
         p_lb = dock.default_params()
         p_lb.solver = dock.SOLVER_LBFGSB
