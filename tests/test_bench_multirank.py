@@ -52,3 +52,24 @@ def test_single_rank_passes_through():
     import bench
     assert bench.max_over_ranks(42.0, 1, "cpu") == 42.0
     assert bench.whole_job_rate(1, 10, 1000.0) == 10.0
+
+
+def test_reference_arm_prints_one_contract_line():
+    # the reference arm (the FP64 oracle on the host cores) needs no GPU: one
+    # JSON line with the GPU arm's metric and unit, impl "reference" and the
+    # cpu_baseline and e2e objects
+    import json
+    import subprocess
+    env = dict(os.environ)
+    env.pop("RANK", None)
+    env.pop("WORLD_SIZE", None)
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"], capture_output=True, text=True, cwd=ROOT, env=env, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "evals/s" and d["higher_is_better"] is True
+    assert d["metric"].startswith("docking evals/s") and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
