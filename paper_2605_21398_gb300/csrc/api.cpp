@@ -1328,6 +1328,9 @@ static dock_status check_pair(dock_ctx *ctx, const dock_object *ob, const dock_s
 
 // The launch shape of the search kernels for lattice side N: the tuned one
 // when the autotuner (or its cache) has one, else the defaults.
+// CTAs per plane of the inverse plane pass at canvas 256 when untuned.
+static const int PLANE_CL_DEFAULT = 4;
+
 static dock_tuning tuning_for(dock_ctx *ctx, const Geo &g)
 {
     auto it = ctx->tune.find(g.N);
@@ -1337,7 +1340,15 @@ static dock_tuning tuning_for(dock_ctx *ctx, const Geo &g)
     t.batch = auto_batch(g);
     t.group = 0;
     t.vox_blocks = 4;
+    t.plane_cl = g.M == 256 ? PLANE_CL_DEFAULT : 0;
     return t;
+}
+
+static bool valid_tuning(const dock_tuning &t)
+{
+    return valid_N(t.N) && t.batch >= 1 && t.batch <= 256 && t.group >= 0 && t.group <= 256 &&
+           (t.vox_blocks == 3 || t.vox_blocks == 4) &&
+           (t.plane_cl == 0 || t.plane_cl == 2 || t.plane_cl == 4 || t.plane_cl == 8);
 }
 
 // Runs records [r0, r1) of rots through the search pipeline; every
@@ -1408,7 +1419,7 @@ static dock_status run_pipeline_rots(dock_ctx *ctx, const Geo &g, const ReqDev *
         }
         {
             Prof pr(ctx, "plane");
-            CK(ctx, launch_plane(g, nb, Z, tw, rb, reqs, ctx->stream));
+            CK(ctx, launch_plane(g, nb, Z, tw, rb, reqs, ctx->stream, tc.plane_cl, ctx->errflag));
         }
     }
     return DOCK_OK;
@@ -1700,8 +1711,10 @@ static dock_status write_tuning(dock_ctx *ctx, const char *path)
     bool first = true;
     for (auto &kv : ctx->tune) {
         const dock_tuning &t = kv.second;
-        fprintf(f, "%s\n  {\"N\": %d, \"batch\": %d, \"group\": %d, \"vox_blocks\": %d, \"us_per_rotation\": %.3f}",
-                first ? "" : ",", t.N, t.batch, t.group, t.vox_blocks, t.us_per_rotation);
+        fprintf(f,
+                "%s\n  {\"N\": %d, \"batch\": %d, \"group\": %d, \"vox_blocks\": %d, \"plane_cl\": %d, "
+                "\"us_per_rotation\": %.3f}",
+                first ? "" : ",", t.N, t.batch, t.group, t.vox_blocks, t.plane_cl, t.us_per_rotation);
         first = false;
     }
     fprintf(f, "\n]}\n");
@@ -1771,6 +1784,13 @@ extern "C" dock_status dock_autotune(dock_ctx *ctx, const dock_object *ob, const
         t.group = gr;
         if ((s = trial(t)) != DOCK_OK) { restore(); return s; }
     }
+    if (g.M == 256)
+        for (int cl : {2, 4, 8}) {
+            if (cl == best.plane_cl) continue;
+            dock_tuning t = best;
+            t.plane_cl = cl;
+            if ((s = trial(t)) != DOCK_OK) { restore(); return s; }
+        }
     best.us_per_rotation = best_us;
     ctx->tune[g.N] = best;
     if (out) *out = best;
@@ -1806,15 +1826,21 @@ extern "C" dock_status dock_load_tuning(dock_ctx *ctx, const char *path, int32_t
         size_t end = txt.find('}', pos);
         if (end == std::string::npos) break;
         std::string e = txt.substr(pos, end - pos);
-        long N, b, gr, vb;
+        long N, b, gr, vb, pc = -1;
         if (json_int(e.c_str(), "\"N\"", &N) && json_int(e.c_str(), "\"batch\"", &b) &&
-            json_int(e.c_str(), "\"group\"", &gr) && json_int(e.c_str(), "\"vox_blocks\"", &vb) && valid_N((int)N) &&
-            b >= 1 && b <= 256 && gr >= 0 && gr <= 256 && (vb == 3 || vb == 4)) {
+            json_int(e.c_str(), "\"group\"", &gr) && json_int(e.c_str(), "\"vox_blocks\"", &vb)) {
             dock_tuning t = {};
             t.N = (int)N;
             t.batch = (int)b;
             t.group = (int)gr;
             t.vox_blocks = (int)vb;
+            Geo gt = {};
+            gt.M = 2 * t.N;
+            t.plane_cl = json_int(e.c_str(), "\"plane_cl\"", &pc) ? (int)pc : (gt.M == 256 ? PLANE_CL_DEFAULT : 0);
+            if (!valid_tuning(t)) {
+                pos = end;
+                continue;
+            }
             const char *u = strstr(e.c_str(), "\"us_per_rotation\"");
             if (u && (u = strchr(u, ':'))) t.us_per_rotation = atof(u + 1);
             ctx->tune[t.N] = t;
@@ -1836,6 +1862,15 @@ extern "C" dock_status dock_get_tuning(dock_ctx *ctx, int32_t N, dock_tuning *ou
     g.M = 2 * N;
     g.P = N + 2;
     *out = tuning_for(ctx, g);
+    return DOCK_OK;
+}
+
+extern "C" dock_status dock_set_tuning(dock_ctx *ctx, const dock_tuning *t)
+{
+    if (!ctx || !t) return DOCK_E_INVALID;
+    if (!valid_tuning(*t)) return fail(ctx, DOCK_E_INVALID, "tuning out of range");
+    DevLock dev_lock_(ctx);
+    ctx->tune[t->N] = *t;
     return DOCK_OK;
 }
 
@@ -1882,12 +1917,16 @@ extern "C" dock_status dock_search_scores(dock_ctx *ctx, const dock_object *ob, 
     if (dual && e == cudaSuccess)
         e = launch_fwd2d(g, 1, ctx->bits + bsz, Y2, tw, qt, ctx->stream, ctx->bits, ctx->rots, ctx->reqs);
     if (e == cudaSuccess) e = launch_zpass(g, 1, 1, Y, ctx->rots, ctx->reqs, Y + ysz, tw, ctx->stream, Y2);
-    if (e == cudaSuccess) e = launch_plane_export(g, Y + ysz, tw, dC, ctx->stream);
+    if (e == cudaSuccess)
+        e = launch_plane_export(g, Y + ysz, tw, dC, ctx->stream, tuning_for(ctx, g).plane_cl, ctx->errflag);
     if (e == cudaSuccess) e = cudaMemcpyAsync(C, dC, csz * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, ctx->errflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     dfree(ctx, Y, ybytes);
     dfree(ctx, dC, csz * sizeof(float));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "search_scores");
+    if (herr) return fail(ctx, herr, "device reported error %d during the search", herr);
     return DOCK_OK;
 }
 
@@ -2522,6 +2561,18 @@ static dock_status job_admit(dock_ctx *ctx, Engine &E, Job &j, int *wait)
 // global orientation, or take its top-K candidates (*final set; the
 // refinement runs afterwards, batched with other jobs finishing in the same
 // pass).
+// Synchronises the context stream and reads (and clears) the device error
+// word that kernels set when they give up (e.g. a bounded wait that ran out).
+static dock_status take_device_error(dock_ctx *ctx)
+{
+    int herr = 0;
+    CK(ctx, cudaMemcpyAsync(&herr, ctx->errflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (!herr) return DOCK_OK;
+    CK(ctx, cudaMemsetAsync(ctx->errflag, 0, sizeof(int), ctx->stream));
+    return fail(ctx, herr, "device reported error %d during a search pass", herr);
+}
+
 static dock_status job_advance(dock_ctx *ctx, Job &j, bool *final)
 {
     *final = false;
@@ -2536,7 +2587,7 @@ static dock_status job_advance(dock_ctx *ctx, Job &j, bool *final)
         }
         dock_candidate best;
         CK(ctx, cudaMemcpyAsync(&best, j.dcand, sizeof(best), cudaMemcpyDeviceToHost, ctx->stream));
-        CK(ctx, cudaStreamSynchronize(ctx->stream));
+        if ((s = take_device_error(ctx)) != DOCK_OK) return s;
         dock_search_desc dl = {};
         dl.sampler = DOCK_SAMPLER_GEOBALL;
         dl.n = nl;
@@ -2563,7 +2614,7 @@ static dock_status job_advance(dock_ctx *ctx, Job &j, bool *final)
     }
     j.cands.assign(K, dock_candidate());
     CK(ctx, cudaMemcpyAsync(j.cands.data(), j.dcand, sizeof(dock_candidate) * K, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if ((s = take_device_error(ctx)) != DOCK_OK) return s;
     int Kv = 0;
     while (Kv < K && j.cands[Kv].rot >= 0) ++Kv;
     if (Kv == 0) return fail(ctx, DOCK_E_INVALID, "the search produced no candidate");

@@ -91,8 +91,17 @@ cudaError_t launch_resample(const Geo &g, const ReqDev *reqs, const RotRec *rots
 // product with each request's spec_pen is added before the inverse FFT.
 cudaError_t launch_zpass(const Geo &g, int B, int group, const float2 *Y, const RotRec *rots, const ReqDev *reqs,
                          float2 *Z, const float2 *tw, cudaStream_t st, const float2 *Y2 = nullptr);
+// plane_cl: CTAs per plane at M = 256 (4 or 8: the cluster kernel of
+// k_plane.cu; anything else: the 2-CTA kernel).  err (nullable, device):
+// set to DOCK_E_TIMEOUT if a cluster kernel gave up waiting for its peers.
 cudaError_t launch_plane(const Geo &g, int B, const float2 *Z, const float2 *tw, const RotRec *rots,
-                         const ReqDev *reqs, cudaStream_t st);
+                         const ReqDev *reqs, cudaStream_t st, int plane_cl = 0, int *err = nullptr);
+// The cluster plane pass (k_plane.cu): M = 256, cl = 4 or 8.
+bool plane_cl_supported(int M, int cl);
+cudaError_t launch_plane_cl(const Geo &g, int cl, int B, const float2 *Z, const float2 *tw, const RotRec *rots,
+                            const ReqDev *reqs, int *err, cudaStream_t st);
+cudaError_t launch_plane_cl_export(const Geo &g, int cl, const float2 *Z, const float2 *tw, float *C, int *err,
+                                   cudaStream_t st);
 // o_s (nullable, device): the rotate_object pose T = (R, h dk + o_s - o_R);
 // else T = (R, R (h dk + o_s,R - o_o)).
 cudaError_t launch_topk(const unsigned long long *keys, int n, int K, int N, int M, double h, const double *o_o,
@@ -100,7 +109,8 @@ cudaError_t launch_topk(const unsigned long long *keys, int n, int K, int N, int
                         const double *o_s = nullptr);
 cudaError_t launch_vox_export(const Geo &g, const ReqDev *reqs, const RotRec *rots, int B, uint8_t *bits,
                               cudaStream_t st, int pose_set = 0);
-cudaError_t launch_plane_export(const Geo &g, const float2 *Z, const float2 *tw, float *C, cudaStream_t st);
+cudaError_t launch_plane_export(const Geo &g, const float2 *Z, const float2 *tw, float *C, cudaStream_t st,
+                                int plane_cl = 0, int *err = nullptr);
 // Corner cells of O for trilinear interpolation ((N+1)^3 float4).
 cudaError_t launch_corner_cells(const float *O, int N, float4 *cells, cudaStream_t st);
 // S of rotation 0 (pose set 0) as N^3 floats 0/1.

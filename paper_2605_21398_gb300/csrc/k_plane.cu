@@ -1,0 +1,412 @@
+// Inverse plane pass at canvas side M = 256 over a cluster of CL = 4 or 8
+// CTAs per plane (Eq. (7), (9): the last two inverse transforms of
+// C = F^-1(conj(F(O)) . F(S)) and the per-rotation argmax).
+//
+// Plane z of rotation b holds Z[ky][kx], ky < 256, kx <= 128 (row pitch 130).
+// CTA `rank` of the cluster owns the packed columns kx in [rank CPC,
+// (rank + 1) CPC) (CPC = 128 / CL; packed column 0 carries kx = 0 plus i
+// times the Nyquist column kx = 128):
+//   phase 1  loads its columns straight from global memory into registers
+//            (half-warp lanes on 16 consecutive kx: 128-byte rows) and
+//            inverse transforms them along y (radix 16 x 16, the exchange
+//            between the two stages in place in shared memory);
+//   push     the rows of its columns that another CTA needs are one
+//            contiguous block per destination, copied into that CTA's
+//            shared memory by the bulk-copy engine (cp.async.bulk, completion
+//            counted in bytes on the receiver's mbarrier);
+//   phase 2  C2R along x of its RPC = 256 / CL rows (half-length complex
+//            inverse FFT, radix 16 x 8, exchange in place) and the argmax
+//            with the lowest canvas index on ties.
+// Shared memory (complex elements): A [CL][CPC][RPC] holds phase 2's rows of
+// every source CTA at kx RPC (A[rank] is also phase 1's block of its own
+// rows), X [CL - 1][CPC][RPC] phase 1's blocks for the other CTAs.  Element
+// (local column c, row y) sits at offset (y mod RPC) ^ ((c + y / 16) mod 16)
+// of its column in the block: half-warps that read 16 columns at one row and
+// warps that read 32 rows of one column both hit distinct banks.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "dock_internal.h"
+#include "fft.cuh"
+#include "peak_key.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace dock {
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *m, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *m, uint32_t bytes)
+{
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(smem_u32(m)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *m, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(m)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// shared::cluster address of the same shared-memory offset in CTA `rank`
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t a, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void bulk_push(uint32_t dst, uint32_t src, uint32_t bytes, uint32_t mbar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     dst),
+                 "r"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// exp(-2 pi i m / 256), FP64 values rounded to FP32, in the constant bank
+// (per-thread twiddles are read once, through the constant cache, and kept in
+// registers; set per device before the first launch)
+__constant__ float2 c_tw256[256];
+
+// exp(+2 pi i m / 256)
+__device__ __forceinline__ cf twc_inv(int m)
+{
+    const float2 w = c_tw256[m & 255];
+    return cmake(w.x, -w.y);
+}
+
+}  // namespace
+
+template <int CL> struct PlaneClCfg {
+    static constexpr int M = 256, H = 128, P = H + 2;
+    static constexpr int NT = 256;                 // threads per CTA
+    static constexpr int CPC = H / CL;             // packed columns per CTA
+    static constexpr int RPC = M / CL;             // rows per CTA in phase 2
+    static constexpr int LR = RPC == 64 ? 6 : 5;   // log2 RPC
+    static constexpr int BLK = CPC * RPC;          // elements of one (row block, column block)
+    static constexpr int MINB = CL == 4 ? 2 : 3;   // resident CTAs per SM
+    static constexpr size_t A_OFF = 0;
+    static constexpr size_t X_OFF = (size_t)CL * BLK * 8;
+    static constexpr uint32_t PUSH_BYTES = (uint32_t)BLK * 8;
+    static constexpr uint32_t RECV_BYTES = (uint32_t)(CL - 1) * BLK * 8;
+    static constexpr size_t MB_OFF = X_OFF + (size_t)(CL - 1) * BLK * 8;
+    static constexpr size_t SMEM = MB_OFF + 16 + 8 * (NT / 32);
+    static_assert(CPC % 16 == 0 && RPC % 32 == 0 && (1 << LR) == RPC, "tile shape");
+    static_assert((SMEM + 1024) * MINB <= 228 * 1024, "resident CTAs per SM");
+    static_assert(PUSH_BYTES % 16 == 0 && X_OFF % 16 == 0, "bulk copies move 16-byte multiples");
+};
+
+// Upper bound on the wait for the peers' blocks (clock cycles, about a second).
+constexpr long long PLANE_WAIT_CYCLES = 1ll << 31;
+
+template <int CL, bool EXPORT>
+__global__ void __launch_bounds__(PlaneClCfg<CL>::NT, PlaneClCfg<CL>::MINB)
+k_plane_cl(const float2 *__restrict__ Z, const float2 *__restrict__ tw, const RotRec *rots, const ReqDev *reqs,
+           float *Cout, int *err)
+{
+    using C = PlaneClCfg<CL>;
+    constexpr int M = C::M, H = C::H, P = C::P, CPC = C::CPC, RPC = C::RPC, LR = C::LR, BLK = C::BLK;
+    extern __shared__ __align__(128) unsigned char smem[];
+    cf *A = reinterpret_cast<cf *>(smem + C::A_OFF);
+    cf *X = reinterpret_cast<cf *>(smem + C::X_OFF);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + C::MB_OFF);
+    unsigned long long *wk = reinterpret_cast<unsigned long long *>(smem + C::MB_OFF + 16);
+    const int tid = threadIdx.x;
+    const int rank = (int)cg::this_cluster().block_rank();
+    const int zc = blockIdx.x / CL, b = blockIdx.y;
+    const float2 *Zp = Z + ((size_t)b * M + zc) * ((size_t)M * P);
+    if (tid == 0) {
+        mbar_init(mbar, 1);
+        fence_mbar_init();
+        mbar_arrive_expect_tx(mbar, C::RECV_BYTES);
+    }
+    // element offset of phase-1 row block q (rows [q RPC, (q + 1) RPC)) of my columns
+    auto blk = [&](int q) -> int { return q == rank ? rank * BLK : (CL + (q < rank ? q : q - 1)) * BLK; };
+
+    // ---- phase 1: inverse FFT along y of my packed columns ----------------
+    {
+        const int c = tid & 15, j = tid >> 4;
+        cf t1[16];   // exp(+2 pi i j r / 256), r < 16: the stage-1 twiddles of this thread
+#pragma unroll
+        for (int r = 1; r < 16; ++r) t1[r] = twc_inv(j * r);
+        int boff[CL];   // indexed by compile-time row blocks only
+#pragma unroll
+        for (int q = 0; q < CL; ++q) boff[q] = blk(q);
+        // the columns of round rr: ky = j + 16 s of packed column rank CPC + 16 rr + c
+        auto load_round = [&](int rr, cf *v) {
+            const int kx = rank * CPC + rr * 16 + c;
+#pragma unroll
+            for (int s = 0; s < 16; ++s) {
+                const float2 a = __ldcs(&Zp[(j + 16 * s) * P + kx]);
+                v[s] = cmake(a.x, a.y);
+            }
+            if (kx == 0) {   // + i * Z[ky][M/2]
+#pragma unroll
+                for (int s = 0; s < 16; ++s) {
+                    const float2 u = __ldcs(&Zp[(j + 16 * s) * P + H]);
+                    v[s] = cmake(v[s].x - u.y, v[s].y + u.x);
+                }
+            }
+        };
+        constexpr int NR = CPC / 16;
+        cf v[16], nxt[16];
+        load_round(0, v);
+#pragma unroll
+        for (int rr = 0; rr < NR; ++rr) {
+            const int col = rr * 16 + c;
+            if (rr + 1 < NR) load_round(rr + 1, nxt);   // in flight during this round
+            // stage 0: DFT over ky = j + 16 s; output r is index 16 j + r
+            DFT<16, true>::run(v);
+            {
+                cf *bq = A + blk((16 * j) >> LR) + col * RPC + ((16 * j) & (RPC - 1));
+                const int u = (col + j) & 15;
+#pragma unroll
+                for (int r = 0; r < 16; ++r) bq[r ^ u] = v[r];
+            }
+            __syncthreads();
+            // stage 1: inputs j + 16 r, twiddles exp(+2 pi i j r / 256), DFT;
+            // output r is row y = j + 16 r, stored where it was read
+            auto at1 = [&](int r) -> cf * {
+                return A + boff[(16 * r) >> LR] + col * RPC + ((16 * r) & (RPC - 1)) + (j ^ ((col + r) & 15));
+            };
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = *at1(r);
+#pragma unroll
+            for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], t1[r]);
+            DFT<16, true>::run(v);
+#pragma unroll
+            for (int r = 0; r < 16; ++r) *at1(r) = v[r];
+            if (rr + 1 < NR) {
+#pragma unroll
+                for (int s = 0; s < 16; ++s) v[s] = nxt[s];
+            }
+        }
+    }
+    // ---- push: X[q] -> CTA q's A[rank] -------------------------------------
+    fence_proxy_async();
+    cg::this_cluster().sync();
+    if (tid == 0) {
+        const uint32_t mb = smem_u32(mbar);
+        const uint32_t dst = smem_u32(A + (size_t)rank * BLK);
+#pragma unroll 1
+        for (int q = 0; q < CL; ++q) {
+            if (q == rank) continue;
+            bulk_push(cluster_addr(dst, (uint32_t)q), smem_u32(X + (size_t)(q < rank ? q : q - 1) * BLK),
+                      C::PUSH_BYTES, cluster_addr(mb, (uint32_t)q));
+        }
+        bulk_commit();
+    }
+    bool ok = true;
+    {
+        const long long t0 = clock64();
+        while (!mbar_try_wait(mbar, 0)) {
+            if (clock64() - t0 > PLANE_WAIT_CYCLES) {
+                ok = false;
+                break;
+            }
+        }
+    }
+    if (__syncthreads_or(!ok)) {
+        if (tid == 0) {
+            if (err) atomicExch(err, DOCK_E_TIMEOUT);
+            bulk_wait_read();
+        }
+        return;
+    }
+
+    // ---- phase 2: C2R along x of my rows, argmax ---------------------------
+    // element (kx, row y) of A: kx RPC + (y mod RPC) ^ ((kx + y / 16) mod 16)
+    {
+        const int rowl = tid & 31, j = tid >> 5;
+        // twiddles of this thread (j < 8): exp(+2 pi i k / 256) for k = j + 8 s
+        // (pre-processing), exp(+2 pi i 2 jj r / 256) for jj = j + 8 bb, r < 8
+        // (stage 1)
+        cf tp[16], ts[2][8];
+#pragma unroll
+        for (int s = 0; s < 16; ++s) tp[s] = twc_inv(j + 8 * s);
+#pragma unroll
+        for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+            for (int r = 1; r < 8; ++r) ts[bb][r] = twc_inv(2 * (j + 8 * bb) * r);
+        float best = -INFINITY;
+        uint32_t bidx = 0xFFFFFFFFu;
+#pragma unroll 1
+        for (int rr = 0; rr < RPC / 32; ++rr) {
+            const int y = rank * RPC + rr * 32 + rowl;
+            const int ylo = y & (RPC - 1), yhi = y >> 4;
+            auto at = [&](int kx) -> cf * { return A + kx * RPC + (ylo ^ ((kx + yhi) & 15)); };
+            cf v[16];
+#pragma unroll
+            for (int s = 0; s < 16; ++s) {
+                const int k = j + 8 * s;
+                cf Wk, Wm;
+                if (s == 0 && j == 0) {   // column 0 holds W[0] + i W[H]
+                    const cf p = *at(0);
+                    Wk = cmake(p.x, 0.f);
+                    Wm = cmake(p.y, 0.f);
+                } else {
+                    Wk = *at(k);
+                    Wm = *at(H - k);
+                }
+                const cf wc = cconj(Wm);
+                const cf Ek = cadd(Wk, wc);
+                const cf Ok = cmul(csub(Wk, wc), tp[s]);   // exp(+2 pi i k / M)
+                v[s] = cmake(Ek.x - Ok.y, Ek.y + Ok.x);                // E + i O
+            }
+            __syncthreads();   // every W of these rows is in registers
+            // stage 0 (radix 16 over k = j + 8 s): output r to index 16 j + r
+            DFT<16, true>::run(v);
+#pragma unroll
+            for (int r = 0; r < 16; ++r) *at(16 * j + r) = v[r];
+            __syncthreads();
+            // stage 1 (radix 8): butterfly jj = j + 8 bb reads jj + 16 r,
+            // twiddles exp(+2 pi i 2 jj r / 256); output r is pair n = jj + 16 r
+#pragma unroll
+            for (int bb = 0; bb < 2; ++bb) {
+                const int jj = j + 8 * bb;
+#pragma unroll
+                for (int r = 0; r < 8; ++r) v[bb * 8 + r] = *at(jj + 16 * r);
+#pragma unroll
+                for (int r = 1; r < 8; ++r) v[bb * 8 + r] = cmul(v[bb * 8 + r], ts[bb][r]);
+                DFT<8, true>::run(v + bb * 8);
+            }
+            const uint32_t rowbase = ((uint32_t)zc * M + (uint32_t)y) * M;
+            if (EXPORT) {
+#pragma unroll
+                for (int s = 0; s < 16; ++s) {
+                    const uint32_t base = rowbase + 2u * (uint32_t)(j + 8 * (s >> 3) + 16 * (s & 7));
+                    Cout[base] = v[s].x;
+                    Cout[base + 1] = v[s].y;
+                }
+            } else {
+                float m = v[0].x;
+#pragma unroll
+                for (int s = 0; s < 16; ++s) m = fmaxf(m, fmaxf(v[s].x, v[s].y));
+                if (m >= best) {
+                    uint32_t bi = 0xFFFFFFFFu;
+#pragma unroll
+                    for (int s = 0; s < 16; ++s) {
+                        const uint32_t base = rowbase + 2u * (uint32_t)(j + 8 * (s >> 3) + 16 * (s & 7));
+                        if (v[s].x == m) bi = min(bi, base);
+                        if (v[s].y == m) bi = min(bi, base + 1u);
+                    }
+                    if (m > best || bi < bidx) {
+                        best = m;
+                        bidx = bi;
+                    }
+                }
+            }
+        }
+        if (!EXPORT) {
+            unsigned long long kk = (bidx == 0xFFFFFFFFu) ? 0ull : pack_key(best, bidx);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long k2 = __shfl_down_sync(0xFFFFFFFFu, kk, o);
+                kk = k2 > kk ? k2 : kk;
+            }
+            const int lane = tid & 31, warp = tid >> 5;
+            if (lane == 0) wk[warp] = kk;
+            __syncthreads();
+            if (warp == 0) {
+                kk = lane < C::NT / 32 ? wk[lane] : 0ull;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long k2 = __shfl_down_sync(0xFFFFFFFFu, kk, o);
+                    kk = k2 > kk ? k2 : kk;
+                }
+                if (lane == 0 && kk) atomicMax(&reqs[rots[b].req].keys[rots[b].rot], kk);
+            }
+        }
+    }
+    // the bulk copies out of X have read their source before the CTA exits
+    if (tid == 0) bulk_wait_read();
+}
+
+// Fills c_tw256 on the current device once (the module's constant bank is per device).
+static cudaError_t ensure_twiddle_bank()
+{
+    static std::mutex mu;
+    static bool done[256] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return cudaSuccess;
+    float2 h[256];
+    for (int m = 0; m < 256; ++m) {
+        const double a = -2.0 * M_PI * (double)m / 256.0;
+        h[m] = make_float2((float)cos(a), (float)sin(a));
+    }
+    e = cudaMemcpyToSymbol(c_tw256, h, sizeof(h));
+    if (e == cudaSuccess) done[dev] = true;
+    return e;
+}
+
+template <int CL, bool EXPORT>
+static cudaError_t launch_plane_cl_t(int B, const float2 *Z, const float2 *tw, const RotRec *rots, const ReqDev *reqs,
+                                     float *Cout, int *err, cudaStream_t st)
+{
+    using C = PlaneClCfg<CL>;
+    auto kern = k_plane_cl<CL, EXPORT>;
+    cudaError_t e = ensure_twiddle_bank();
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C::M * CL, B);
+    cfg.blockDim = dim3(C::NT);
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, kern, Z, tw, rots, reqs, Cout, err);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+bool plane_cl_supported(int M, int cl) { return M == 256 && (cl == 4 || cl == 8); }
+
+
+cudaError_t launch_plane_cl(const Geo &g, int cl, int B, const float2 *Z, const float2 *tw, const RotRec *rots,
+                            const ReqDev *reqs, int *err, cudaStream_t st)
+{
+    if (!plane_cl_supported(g.M, cl) || B < 1 || B > 65535) return cudaErrorInvalidValue;
+    return cl == 4 ? launch_plane_cl_t<4, false>(B, Z, tw, rots, reqs, nullptr, err, st)
+                   : launch_plane_cl_t<8, false>(B, Z, tw, rots, reqs, nullptr, err, st);
+}
+
+cudaError_t launch_plane_cl_export(const Geo &g, int cl, const float2 *Z, const float2 *tw, float *C, int *err,
+                                   cudaStream_t st)
+{
+    if (!plane_cl_supported(g.M, cl)) return cudaErrorInvalidValue;
+    return cl == 4 ? launch_plane_cl_t<4, true>(1, Z, tw, nullptr, nullptr, C, err, st)
+                   : launch_plane_cl_t<8, true>(1, Z, tw, nullptr, nullptr, C, err, st);
+}
+
+}  // namespace dock

@@ -16,6 +16,7 @@
 
 #include "dock_internal.h"
 #include "fft.cuh"
+#include "peak_key.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -1106,13 +1107,6 @@ cudaError_t launch_zpass(const Geo &g, int B, int group, const float2 *Y, const 
 // cluster; each CTA reads the other half of its rows through distributed
 // shared memory.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long pack_key(float v, uint32_t idx)
-{
-    uint32_t u = __float_as_uint(__fadd_rn(v, 0.0f));   // -0 -> +0: equal scores compare equal
-    uint32_t k = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-    return ((unsigned long long)k << 32) | (unsigned long long)(0xFFFFFFFFu - idx);
-}
-
 template <int M> struct PlaneCfg {
     static constexpr int CL = (M >= 256) ? 2 : 1;          // CTAs per plane
     static constexpr int H = M / 2;
@@ -1401,8 +1395,9 @@ static cudaError_t launch_plane_t(int B, const float2 *Z, const float2 *tw, cons
 }
 
 cudaError_t launch_plane(const Geo &g, int B, const float2 *Z, const float2 *tw, const RotRec *rots,
-                         const ReqDev *reqs, cudaStream_t st)
+                         const ReqDev *reqs, cudaStream_t st, int plane_cl, int *err)
 {
+    if (plane_cl_supported(g.M, plane_cl)) return launch_plane_cl(g, plane_cl, B, Z, tw, rots, reqs, err, st);
     switch (g.M) {
     case 64: return launch_plane_t<64, false>(B, Z, tw, rots, reqs, nullptr, st);
     case 128: return launch_plane_t<128, false>(B, Z, tw, rots, reqs, nullptr, st);
@@ -1412,8 +1407,10 @@ cudaError_t launch_plane(const Geo &g, int B, const float2 *Z, const float2 *tw,
     }
 }
 
-cudaError_t launch_plane_export(const Geo &g, const float2 *Z, const float2 *tw, float *C, cudaStream_t st)
+cudaError_t launch_plane_export(const Geo &g, const float2 *Z, const float2 *tw, float *C, cudaStream_t st,
+                                int plane_cl, int *err)
 {
+    if (plane_cl_supported(g.M, plane_cl)) return launch_plane_cl_export(g, plane_cl, Z, tw, C, err, st);
     switch (g.M) {
     case 64: return launch_plane_t<64, true>(1, Z, tw, nullptr, nullptr, C, st);
     case 128: return launch_plane_t<128, true>(1, Z, tw, nullptr, nullptr, C, st);

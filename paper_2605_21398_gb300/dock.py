@@ -80,7 +80,7 @@ class Request(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int32), ("batch", ctypes.c_int32), ("group", ctypes.c_int32),
-                ("vox_blocks", ctypes.c_int32), ("us_per_rotation", ctypes.c_double)]
+                ("vox_blocks", ctypes.c_int32), ("plane_cl", ctypes.c_int32), ("us_per_rotation", ctypes.c_double)]
 
 
 class KernelStat(ctypes.Structure):
@@ -134,6 +134,7 @@ SIGNATURES = [
     ("dock_autotune", _st, [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_char_p, ctypes.POINTER(Tuning)]),
     ("dock_load_tuning", _st, [_vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32)]),
     ("dock_get_tuning", _st, [_vp, ctypes.c_int32, ctypes.POINTER(Tuning)]),
+    ("dock_set_tuning", _st, [_vp, ctypes.POINTER(Tuning)]),
     ("dock_set_profiling", _st, [_vp, ctypes.c_int]),
     ("dock_get_kernel_stats", ctypes.c_int32, [_vp, ctypes.POINTER(KernelStat), ctypes.c_int32]),
     ("dock_reset_kernel_stats", None, [_vp]),
@@ -354,6 +355,13 @@ class Context:
         self.check(lib().dock_get_tuning(self.h, N, ctypes.byref(t)))
         return tuning_dict(t)
 
+    def set_tuning(self, **shape):
+        """Sets the launch shape of lattice side shape['N'] (other keys as get_tuning)."""
+        cur = self.get_tuning(shape["N"])
+        cur.update(shape)
+        t = Tuning(cur["N"], cur["batch"], cur["group"], cur["vox_blocks"], cur["plane_cl"], cur["us_per_rotation"])
+        self.check(lib().dock_set_tuning(self.h, ctypes.byref(t)))
+
     # -------------------------------------------------------------- profiling
     def set_profiling(self, on):
         self.check(lib().dock_set_profiling(self.h, 1 if on else 0))
@@ -368,7 +376,8 @@ class Context:
 
 
 def tuning_dict(t):
-    return dict(N=t.N, batch=t.batch, group=t.group, vox_blocks=t.vox_blocks, us_per_rotation=t.us_per_rotation)
+    return dict(N=t.N, batch=t.batch, group=t.group, vox_blocks=t.vox_blocks, plane_cl=t.plane_cl,
+                us_per_rotation=t.us_per_rotation)
 
 
 def result_dict(r):

@@ -254,6 +254,10 @@ def test_large_lattice_sampled_parity(ctx, workload):
         assert abs(peaks["score"][i] - sc) <= tol + 1e-4 * abs(sc)
         if sc - _second_best(C, idx) > 2 * tol:
             assert peaks["idx"][i] == idx
+        # at 128^3 the top of the field is flatter than the FP32 error, so the
+        # gap test rarely holds: the chosen shift must then be one of the
+        # oracle's maxima within the tolerance
+        assert C.reshape(-1)[peaks["idx"][i]] >= sc - 2 * tol
         # direct Eq. (7) at a few shifts agrees with the FFT field
         N = w.N
         for _ in range(3):
