@@ -20,9 +20,10 @@
 // Shared memory (complex elements): A [CL][CPC][RPC] holds phase 2's rows of
 // every source CTA at kx RPC (A[rank] is also phase 1's block of its own
 // rows), X [CL - 1][CPC][RPC] phase 1's blocks for the other CTAs.  Element
-// (local column c, row y) sits at offset (y mod RPC) ^ ((c + y / 16) mod 16)
-// of its column in the block: half-warps that read 16 columns at one row and
-// warps that read 32 rows of one column both hit distinct banks.
+// (local column c, row y) sits at offset (y mod RPC) ^ (c mod 16) of its
+// column in the block: half-warps that touch 16 columns at one row and warps
+// that touch 32 rows of one column both hit distinct banks, and most
+// addresses are a per-thread base plus a constant.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -177,16 +178,14 @@ k_plane_cl(const float2 *__restrict__ Z, const float2 *__restrict__ tw, const Ro
             DFT<16, true>::run(v);
             {
                 cf *bq = A + blk((16 * j) >> LR) + col * RPC + ((16 * j) & (RPC - 1));
-                const int u = (col + j) & 15;
 #pragma unroll
-                for (int r = 0; r < 16; ++r) bq[r ^ u] = v[r];
+                for (int r = 0; r < 16; ++r) bq[r ^ c] = v[r];
             }
             __syncthreads();
             // stage 1: inputs j + 16 r, twiddles exp(+2 pi i j r / 256), DFT;
             // output r is row y = j + 16 r, stored where it was read
-            auto at1 = [&](int r) -> cf * {
-                return A + boff[(16 * r) >> LR] + col * RPC + ((16 * r) & (RPC - 1)) + (j ^ ((col + r) & 15));
-            };
+            cf *b1 = A + col * RPC + (j ^ c);
+            auto at1 = [&](int r) -> cf * { return b1 + boff[(16 * r) >> LR] + ((16 * r) & (RPC - 1)); };
 #pragma unroll
             for (int r = 0; r < 16; ++r) v[r] = *at1(r);
 #pragma unroll
@@ -233,7 +232,7 @@ k_plane_cl(const float2 *__restrict__ Z, const float2 *__restrict__ tw, const Ro
     }
 
     // ---- phase 2: C2R along x of my rows, argmax ---------------------------
-    // element (kx, row y) of A: kx RPC + (y mod RPC) ^ ((kx + y / 16) mod 16)
+    // element (kx, row y) of A: kx RPC + (y mod RPC) ^ (kx mod 16)
     {
         const int rowl = tid & 31, j = tid >> 5;
         // twiddles of this thread (j < 8): exp(+2 pi i k / 256) for k = j + 8 s
@@ -251,20 +250,22 @@ k_plane_cl(const float2 *__restrict__ Z, const float2 *__restrict__ tw, const Ro
 #pragma unroll 1
         for (int rr = 0; rr < RPC / 32; ++rr) {
             const int y = rank * RPC + rr * 32 + rowl;
-            const int ylo = y & (RPC - 1), yhi = y >> 4;
-            auto at = [&](int kx) -> cf * { return A + kx * RPC + (ylo ^ ((kx + yhi) & 15)); };
+            const int ylo = y & (RPC - 1);
+            // k = j + 8 s has k mod 16 = j + 8 (s mod 2); H - k has
+            // (16 - j - 8 (s mod 2)) mod 16
+            const cf *pk[2] = {A + j * RPC + (ylo ^ j), A + j * RPC + (ylo ^ (j + 8))};
+            const cf *pm[2] = {A + (H - j) * RPC + (ylo ^ ((16 - j) & 15)), A + (H - j) * RPC + (ylo ^ ((8 - j) & 15))};
             cf v[16];
 #pragma unroll
             for (int s = 0; s < 16; ++s) {
-                const int k = j + 8 * s;
                 cf Wk, Wm;
                 if (s == 0 && j == 0) {   // column 0 holds W[0] + i W[H]
-                    const cf p = *at(0);
+                    const cf p = A[ylo];
                     Wk = cmake(p.x, 0.f);
                     Wm = cmake(p.y, 0.f);
                 } else {
-                    Wk = *at(k);
-                    Wm = *at(H - k);
+                    Wk = pk[s & 1][8 * s * RPC];
+                    Wm = pm[s & 1][-8 * s * RPC];
                 }
                 const cf wc = cconj(Wm);
                 const cf Ek = cadd(Wk, wc);
@@ -274,16 +275,20 @@ k_plane_cl(const float2 *__restrict__ Z, const float2 *__restrict__ tw, const Ro
             __syncthreads();   // every W of these rows is in registers
             // stage 0 (radix 16 over k = j + 8 s): output r to index 16 j + r
             DFT<16, true>::run(v);
+            {
+                cf *b0 = A + 16 * j * RPC;
 #pragma unroll
-            for (int r = 0; r < 16; ++r) *at(16 * j + r) = v[r];
+                for (int r = 0; r < 16; ++r) b0[r * RPC + (ylo ^ r)] = v[r];
+            }
             __syncthreads();
             // stage 1 (radix 8): butterfly jj = j + 8 bb reads jj + 16 r,
             // twiddles exp(+2 pi i 2 jj r / 256); output r is pair n = jj + 16 r
 #pragma unroll
             for (int bb = 0; bb < 2; ++bb) {
                 const int jj = j + 8 * bb;
+                const cf *b1 = A + jj * RPC + (ylo ^ jj);
 #pragma unroll
-                for (int r = 0; r < 8; ++r) v[bb * 8 + r] = *at(jj + 16 * r);
+                for (int r = 0; r < 8; ++r) v[bb * 8 + r] = b1[16 * r * RPC];
 #pragma unroll
                 for (int r = 1; r < 8; ++r) v[bb * 8 + r] = cmul(v[bb * 8 + r], ts[bb][r]);
                 DFT<8, true>::run(v + bb * 8);
