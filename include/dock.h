@@ -377,12 +377,14 @@ DOCK_API dock_status dock_register_batch(dock_ctx *ctx, const dock_request *reqs
  * every GPU that loads the library holds until the process exits.  Limits:
  * lattice side N <= 64 and 1 <= n <= 4096; larger sizes return
  * DOCK_E_INVALID with a message.  The call allocates no device memory (no
- * cudaMalloc, cudaFree or allocating library routine).  The first call on a
- * device looks up the scratch's device address (once per device), so make
- * that first call before any stream capture.  All calls share the scratch,
- * which keeps the last call's contents: calls that overlap on the GPU (from
- * several threads or contexts on one device) race.  The call runs on ctx's
- * stream and returns after the peaks are on the host.
+ * cudaMalloc, cudaFree or allocating library routine): dock_create looks up
+ * the scratch's device address on its device (once per device), which is
+ * where a lazily loaded library places the scratch on the GPU.  The call
+ * copies from pageable host memory and synchronises ctx's stream, so it
+ * returns DOCK_E_INVALID when that stream is being captured.  All calls share
+ * the scratch, which keeps the last call's contents: calls that overlap on the
+ * GPU (from several threads or contexts on one device) race.  The call runs
+ * on ctx's stream and returns after the peaks are on the host.
  */
 DOCK_API dock_status dock_search_peaks_noalloc(dock_ctx *ctx, const dock_object *obj, const dock_sweep *sweep,
                                                const double *quats, int32_t n, dock_peak *peaks);

@@ -488,6 +488,15 @@ dock_status dock_create(dock_ctx **out, int device, size_t hbm_budget_bytes, voi
         return DOCK_E_NOMEM;
     }
     cudaMemset(c->errflag, 0, sizeof(int));
+    // the allocation-free search's scratch is placed on this device now (its
+    // module is loaded by the address lookup), not inside that call
+    e = noalloc_prepare(device);
+    if (e != cudaSuccess) {
+        cudaFree(c->errflag);
+        if (c->own_stream) cudaStreamDestroy(c->stream);
+        delete c;
+        return DOCK_E_CUDA;
+    }
     *out = c;
     return DOCK_OK;
 }
@@ -1639,6 +1648,15 @@ extern "C" dock_status dock_search_peaks_noalloc(dock_ctx *ctx, const dock_objec
     if (sw->mode.load() != 0)
         return fail(ctx, DOCK_E_INVALID,
                     "dock_search_peaks_noalloc rotates the sweep and scores plainly; the sweep asks otherwise");
+    {
+        // its copies come from pageable host memory and it synchronises the
+        // stream: neither can be recorded into a graph
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaError_t ce = cudaStreamIsCapturing(ctx->stream, &cs);
+        if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaStreamIsCapturing");
+        if (cs != cudaStreamCaptureStatusNone)
+            return fail(ctx, DOCK_E_INVALID, "dock_search_peaks_noalloc must not be called on a capturing stream");
+    }
     for (int i = 0; i < n; ++i) {
         const double *a = quats + 4 * (size_t)i;
         double nq = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3]);

@@ -196,6 +196,10 @@ struct NoallocJob {
     dock_peak *peaks;       // host: n peaks out
 };
 cudaError_t noalloc_search_peaks(const NoallocJob &j);
+// Looks up the scratch's device address on `device` (current) once: with
+// lazily loaded modules this is where the scratch is placed on the device, so
+// dock_create calls it and dock_search_peaks_noalloc itself allocates nothing.
+cudaError_t noalloc_prepare(int device);
 size_t noalloc_scratch_bytes();
 
 }  // namespace dock

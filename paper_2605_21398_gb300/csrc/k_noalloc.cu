@@ -57,6 +57,12 @@ static cudaError_t scratch_address(int dev, unsigned char **out)
     return cudaSuccess;
 }
 
+cudaError_t noalloc_prepare(int device)
+{
+    unsigned char *p = nullptr;
+    return scratch_address(device, &p);
+}
+
 // Peak key (ordered score << 32 | ~canvas index, 0 = no peak) to (score, index).
 __global__ void k_keys_to_peaks(const unsigned long long *keys, int n, dock_peak *out)
 {

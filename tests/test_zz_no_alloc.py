@@ -1,6 +1,7 @@
-"""The allocation-free search entry point (dock_search_peaks_noalloc) against
-the per-rotation peaks of dock_search_so3 on the same rotations, on two calls
-in a row with different rotation sets, plus its size limits."""
+"""The allocation-free search entry point (dock_search_peaks_noalloc): its first
+call leaves device memory unchanged, it refuses a capturing stream, its peaks
+equal the per-rotation peaks of dock_search_so3 on the same rotations on two
+calls in a row with different rotation sets, and its size limits."""
 import numpy as np
 import pytest
 
@@ -33,6 +34,45 @@ def _quats(w, n, seed):
     q = synth.random_unit_quats(n, seed)
     q[0] = w.gt_q
     return q
+
+
+def test_first_noalloc_call_leaves_device_memory_unchanged(ctx, workload):
+    # the call's defining property: the first one on a device places nothing
+    # (the scratch is already resident once a context exists).  Runs first in
+    # this file so that no earlier call of the entry point hides a lazy load.
+    torch = pytest.importorskip("torch")
+    w = workload("tiny32")
+    ob, sw = _pair(ctx, w)
+    q = _quats(w, 6, 503)
+    ctx.search_so3(ob, sw, len(q), 1, sampler=3, quats=q)   # the search kernels are loaded by now
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info(0)[0]
+    got = ctx.search_peaks_noalloc(ob, sw, q)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info(0)[0]
+    assert free1 == free0, (free0, free1)
+    assert np.all(np.isfinite(got["score"]))
+
+
+@pytest.mark.filterwarnings("ignore:The CUDA Graph is empty")
+def test_noalloc_rejects_a_capturing_stream(workload):
+    torch = pytest.importorskip("torch")
+    from paper_2605_21398_gb300 import dock
+    w = workload("tiny32")
+    s = torch.cuda.Stream()
+    c = dock.Context(0, stream=s.cuda_stream)
+    try:
+        ob, sw = _pair(c, w)
+        q = _quats(w, 2, 504)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            with pytest.raises(dock.DockError, match="capturing"):
+                c.search_peaks_noalloc(ob, sw, q)
+        # usable once the capture has ended
+        assert np.all(np.isfinite(c.search_peaks_noalloc(ob, sw, q)["score"]))
+    finally:
+        _KEEP.clear()
+        c.close()
 
 
 @pytest.mark.parametrize("name", ["tiny32", "free64"])
