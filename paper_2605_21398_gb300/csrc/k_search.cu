@@ -324,7 +324,9 @@ __device__ void voxelise_slab(const Geo &g, const RotRec &rr, const PoseRec *pos
                               int *next_chunk)
 {
     constexpr int NW = N / 32;
-    constexpr float CORE_M = 0.1f;
+    // twice the bound on the FP32 error of the probe-frame coordinates l
+    // (2e-4 voxels on lattices of <= 256 voxels), times a safety factor 2
+    constexpr float ELB = 8e-4f;
     const float rv = g.rv, lv = g.lv, rv2 = rv * rv;
     const float mz = 8e-4f, mr = 1.6e-3f * rv + 1e-3f;
     const double h = g.h, r2d = g.r * g.r, Ld = g.L;
@@ -384,21 +386,19 @@ __device__ void voxelise_slab(const Geo &g, const RotRec &rr, const PoseRec *pos
         const float iAq = radial_ok ? 1.f / Aq : 0.f;
         const bool cap_ok = fabsf(bx[2]) >= 1e-3f;     // cap crossings located to < 0.25 voxel
         const float ibz = cap_ok ? 1.f / bx[2] : 0.f;
+        const float rsAq = radial_ok ? rsqrtf(Aq) : 0.f;
+        const float ez = cap_ok ? ELB * fabsf(ibz) : 0.f;   // cap crossings: error of l2 / |bz|
         for (int jy = Y0; jy <= Y1; ++jy) {
             const bool act = hit && jy >= y0 && jy <= y1;
-            int st = 0;                      // 0: nothing, 1: verified core, 2: walk voxel by voxel, 3: short
-            int ca = N, cb = -1;
-            int qa = 0, qb = -1;             // st 3: the few candidate voxels
-            int ea = N, eb = -1;             // a voxel beyond the estimate (reliable estimates only)
-            bool rel = true;                 // the lane's voxels on this row lie in [ea, eb]
-            bool want_core = false;
+            int st = 0;            // 0: nothing, 1: exact interval [ia, ib], 2: walk voxel by voxel, 3: few candidates
+            int ia = N, ib = -1;
+            int qa = 0, qb = -1;   // st 3: the candidate voxels
             float l0[3];
             if (act) {
                 const float dyv = (float)jy - c[1], dzv = fz - c[2], dxv = -c[0];
                 for (int k = 0; k < 3; ++k) l0[k] = fmaf(B[0 * 3 + k], dxv, fmaf(B[1 * 3 + k], dyv, B[2 * 3 + k] * dzv));
                 if (!radial_ok) {
                     st = 2;
-                    rel = false;
                 } else {
                     // nearest point of the row to the axis, then the radial chord around it
                     const float js = -fmaf(l0[0], bx[0], l0[1] * bx[1]) * iAq;
@@ -408,11 +408,15 @@ __device__ void voxelise_slab(const Geo &g, const RotRec &rr, const PoseRec *pos
                     if (disc > 0.f) {
                         const float hw = sqrtf(disc) * iAq;
                         float lo = js - hw, hi = js + hw;
+                        // error of the chord ends: a radius error dl moves a crossing
+                        // by about dl rv / (Aq hw), the nearest point by dl / sqrt(Aq)
+                        float E = ELB * (rv * iAq / hw + rsAq);
                         bool empty = false, unsure = false;
                         if (cap_ok) {
                             const float za = -l0[2] * ibz, zb = (lv - l0[2]) * ibz;
                             lo = fmaxf(lo, fminf(za, zb));
                             hi = fminf(hi, fmaxf(za, zb));
+                            E = fmaxf(E, ez);
                         } else {
                             // row nearly parallel to the cap planes: z moves < N/1000 voxels along it
                             const float zA = l0[2], zB = fmaf((float)(N - 1), bx[2], l0[2]);
@@ -420,92 +424,60 @@ __device__ void voxelise_slab(const Geo &g, const RotRec &rr, const PoseRec *pos
                             if (zmax < -0.3f || zmin > lv + 0.3f) empty = true;
                             else if (!(zmin >= 0.3f && zmax <= lv - 0.3f)) unsure = true;
                         }
-                        // the estimate is within a voxel of the exact ends, so an
-                        // interval a voxel beyond the lattice holds no voxel
-                        if (lo > (float)N || hi < -1.f) empty = true;
-                        if (empty) {
+                        E += 1e-5f * fmaxf(fabsf(lo), fabsf(hi));   // rounding of lo, hi themselves
+                        if (empty || lo > (float)N + 1.f || hi < -2.f || lo > hi + 2.f) {
                             st = 0;
-                        } else if (unsure) {
+                        } else if (unsure || E > 0.25f) {
                             st = 2;
-                            rel = false;
-                        } else if (lo <= hi + 2.f) {
-                            ca = max(0, (int)ceilf(fmaxf(lo + CORE_M, -1.f)));
-                            cb = min(N - 1, (int)floorf(fminf(hi - CORE_M, (float)N)));
-                            ea = max(0, (int)floorf(fmaxf(lo, -2.f)) - 1);
-                            eb = min(N - 1, (int)ceilf(fminf(hi, (float)N + 1.f)) + 1);
-                            want_core = ca <= cb;
-                            if (want_core) {
-                                st = 2;
-                            } else {
-                                // chord under ~1.2 voxels: its voxels lie in [ea, eb]
-                                st = 3;
-                                qa = ea;
-                                qb = eb;
-                            }
+                        } else if (hi - lo < 2.f * E + 1.f) {
+                            // short chord: its voxels lie in [lo - E, hi + E]
+                            st = 3;
+                            qa = max(0, (int)floorf(fmaxf(lo - E, -1.f)));
+                            qb = min(N - 1, (int)ceilf(fminf(hi + E, (float)N)));
+                        } else {
+                            // voxels below lo - E are outside, those in (lo + E, hi - E)
+                            // inside (the cylinder is convex); an integer in either
+                            // band is classified exactly
+                            st = 1;
+                            int ka = (int)ceilf(lo - E), kb = (int)floorf(hi + E);
+                            ia = ka;
+                            if ((float)ka <= lo + E && ka >= 0 && ka < N &&
+                                !classify(l0, bx, ka, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz))
+                                ia = ka + 1;
+                            ib = kb;
+                            if ((float)kb >= hi - E && kb >= 0 && kb < N &&
+                                !classify(l0, bx, kb, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz))
+                                ib = kb - 1;
+                            ia = max(ia, 0);
+                            ib = min(ib, N - 1);
+                            if (ia > ib) st = 0;
                         }
                     } else if (disc > -1e-2f * (1.f + fabsf(Aq * rv2))) {
                         // tangent row: the exact chord (if any) is within a quarter
                         // voxel of js
                         st = 3;
-                        qa = ea = max(0, (int)floorf(fmaxf(js, -2.f)) - 1);
-                        qb = eb = min(N - 1, (int)ceilf(fminf(js, (float)N + 1.f)) + 1);
+                        qa = max(0, (int)floorf(fmaxf(js, -2.f)) - 1);
+                        qb = min(N - 1, (int)ceilf(fminf(js, (float)N + 1.f)) + 1);
                     }
                 }
             }
-            // Every voxel the warp could add on this row already set (by the
-            // warp's earlier rows or other warps)?  Then the row is done.  Bits
-            // are only ever set, so a stale read only skips less.
-            if (__all_sync(0xFFFFFFFFu, rel)) {
-                const int A0 = __reduce_min_sync(0xFFFFFFFFu, st != 0 ? ea : N);
-                const int B0 = __reduce_max_sync(0xFFFFFFFFu, st != 0 ? eb : -1);
-                bool cov = true;
-                if (lane < NW && A0 <= B0) {
-                    const int lo = max(A0, 32 * lane) - 32 * lane, hi = min(B0, 32 * lane + 31) - 32 * lane;
-                    if (lo <= hi) {
-                        const uint32_t m = (hi == 31 ? 0xFFFFFFFFu : ((1u << (hi + 1)) - 1u)) & ~((1u << lo) - 1u);
-                        cov = (vb[jy * NW + lane] & m) == m;
-                    }
-                }
-                if (__all_sync(0xFFFFFFFFu, cov)) continue;
-            }
-            if (want_core) {
-                if (classify(l0, bx, ca, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz) &&
-                    classify(l0, bx, cb, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz))
-                    st = 1;
-            }
-            const unsigned cm = __ballot_sync(0xFFFFFFFFu, st == 1);
-            if (cm) {
-                const int cl = __reduce_max_sync(0xFFFFFFFFu, st == 1 ? ca : -1);
-                const int cr = __reduce_min_sync(0xFFFFFFFFu, st == 1 ? cb : N);
-                if (cl <= cr) {
-                    int A = __reduce_min_sync(0xFFFFFFFFu, st == 1 ? ca : N);
-                    int Bm = __reduce_max_sync(0xFFFFFFFFu, st == 1 ? cb : -1);
-                    const volatile uint32_t *row = vb + jy * NW;
-                    int j = A - 1;
-                    for (; j >= 0; --j) {
-                        if ((row[j >> 5] >> (j & 31)) & 1u) continue;
-                        bool in = false;
-                        if (st == 1) in = classify(l0, bx, j, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz);
-                        if (!__any_sync(0xFFFFFFFFu, in)) break;
-                    }
-                    A = j + 1;
-                    j = Bm + 1;
-                    for (; j < N; ++j) {
-                        if ((row[j >> 5] >> (j & 31)) & 1u) continue;
-                        bool in = false;
-                        if (st == 1) in = classify(l0, bx, j, rv2, lv, mr, mz, rr, pr, h, r2d, Ld, jy, jz);
-                        if (!__any_sync(0xFFFFFFFFu, in)) break;
-                    }
-                    Bm = j - 1;
+            // exact intervals: one union when they overlap (the usual case for
+            // consecutive poses), else each lane sets its own
+            if (__any_sync(0xFFFFFFFFu, st == 1)) {
+                const int A = __reduce_min_sync(0xFFFFFFFFu, st == 1 ? ia : N);
+                const int Bm = __reduce_max_sync(0xFFFFFFFFu, st == 1 ? ib : -1);
+                const int mxa = __reduce_max_sync(0xFFFFFFFFu, st == 1 ? ia : -1);
+                const int mnb = __reduce_min_sync(0xFFFFFFFFu, st == 1 ? ib : N);
+                if (mxa <= mnb + 1) {
                     if (lane < NW) {
                         const int lo = max(A, 32 * lane) - 32 * lane, hi = min(Bm, 32 * lane + 31) - 32 * lane;
                         if (lo <= hi) {
                             const uint32_t m = (hi == 31 ? 0xFFFFFFFFu : ((1u << (hi + 1)) - 1u)) & ~((1u << lo) - 1u);
-                            if (m & ~row[lane]) atomicOr(&bits[jy * NW + lane], m);
+                            if (m & ~vb[jy * NW + lane]) atomicOr(&bits[jy * NW + lane], m);
                         }
                     }
                 } else if (st == 1) {
-                    st = 2;
+                    set_bits(bits + jy * NW, ia, ib);
                 }
             }
             // short chords: the lanes classify their few candidate voxels together
