@@ -1337,8 +1337,10 @@ static dock_status check_pair(dock_ctx *ctx, const dock_object *ob, const dock_s
 
 // The launch shape of the search kernels for lattice side N: the tuned one
 // when the autotuner (or its cache) has one, else the defaults.
-// CTAs per plane of the inverse plane pass at canvas 256 when untuned.
+// CTAs per plane of the inverse plane pass and columns per z-pass block at
+// canvas 256 when untuned.
 static const int PLANE_CL_DEFAULT = 4;
+static const int ZPASS_COLS_DEFAULT = 16;
 
 static dock_tuning tuning_for(dock_ctx *ctx, const Geo &g)
 {
@@ -1350,6 +1352,7 @@ static dock_tuning tuning_for(dock_ctx *ctx, const Geo &g)
     t.group = 0;
     t.vox_blocks = 4;
     t.plane_cl = g.M == 256 ? PLANE_CL_DEFAULT : 0;
+    t.zpass_cols = g.M == 256 ? ZPASS_COLS_DEFAULT : 0;
     return t;
 }
 
@@ -1357,7 +1360,8 @@ static bool valid_tuning(const dock_tuning &t)
 {
     return valid_N(t.N) && t.batch >= 1 && t.batch <= 256 && t.group >= 0 && t.group <= 256 &&
            (t.vox_blocks == 3 || t.vox_blocks == 4) &&
-           (t.plane_cl == 0 || t.plane_cl == 2 || t.plane_cl == 4 || t.plane_cl == 8);
+           (t.plane_cl == 0 || t.plane_cl == 2 || t.plane_cl == 4 || t.plane_cl == 8) &&
+           (t.zpass_cols == 0 || t.zpass_cols == 16 || t.zpass_cols == 32);
 }
 
 // Runs records [r0, r1) of rots through the search pipeline; every
@@ -1424,7 +1428,10 @@ static dock_status run_pipeline_rots(dock_ctx *ctx, const Geo &g, const ReqDev *
         }
         {
             Prof pr(ctx, dual ? "zpass_dual" : "zpass");
-            CK(ctx, launch_zpass(g, nb, group, Y, rb, reqs, Z, tw, ctx->stream, Y2));
+            if (g.M == 256 && tc.zpass_cols == 16 && !dual)
+                CK(ctx, launch_zpass16(g, nb, group, Y, rb, reqs, Z, ctx->stream));
+            else
+                CK(ctx, launch_zpass(g, nb, group, Y, rb, reqs, Z, tw, ctx->stream, Y2));
         }
         {
             Prof pr(ctx, "plane");
@@ -1731,8 +1738,8 @@ static dock_status write_tuning(dock_ctx *ctx, const char *path)
         const dock_tuning &t = kv.second;
         fprintf(f,
                 "%s\n  {\"N\": %d, \"batch\": %d, \"group\": %d, \"vox_blocks\": %d, \"plane_cl\": %d, "
-                "\"us_per_rotation\": %.3f}",
-                first ? "" : ",", t.N, t.batch, t.group, t.vox_blocks, t.plane_cl, t.us_per_rotation);
+                "\"zpass_cols\": %d, \"us_per_rotation\": %.3f}",
+                first ? "" : ",", t.N, t.batch, t.group, t.vox_blocks, t.plane_cl, t.zpass_cols, t.us_per_rotation);
         first = false;
     }
     fprintf(f, "\n]}\n");
@@ -1802,13 +1809,19 @@ extern "C" dock_status dock_autotune(dock_ctx *ctx, const dock_object *ob, const
         t.group = gr;
         if ((s = trial(t)) != DOCK_OK) { restore(); return s; }
     }
-    if (g.M == 256)
+    if (g.M == 256) {
         for (int cl : {2, 4, 8}) {
             if (cl == best.plane_cl) continue;
             dock_tuning t = best;
             t.plane_cl = cl;
             if ((s = trial(t)) != DOCK_OK) { restore(); return s; }
         }
+        {
+            dock_tuning t = best;
+            t.zpass_cols = best.zpass_cols == 16 ? 32 : 16;
+            if ((s = trial(t)) != DOCK_OK) { restore(); return s; }
+        }
+    }
     best.us_per_rotation = best_us;
     ctx->tune[g.N] = best;
     if (out) *out = best;
@@ -1855,6 +1868,9 @@ extern "C" dock_status dock_load_tuning(dock_ctx *ctx, const char *path, int32_t
             Geo gt = {};
             gt.M = 2 * t.N;
             t.plane_cl = json_int(e.c_str(), "\"plane_cl\"", &pc) ? (int)pc : (gt.M == 256 ? PLANE_CL_DEFAULT : 0);
+            long zc = 0;
+            t.zpass_cols =
+                json_int(e.c_str(), "\"zpass_cols\"", &zc) ? (int)zc : (gt.M == 256 ? ZPASS_COLS_DEFAULT : 0);
             if (!valid_tuning(t)) {
                 pos = end;
                 continue;
@@ -1934,7 +1950,12 @@ extern "C" dock_status dock_search_scores(dock_ctx *ctx, const dock_object *ob, 
     if (dual && e == cudaSuccess) e = launch_voxelise(g, ctx->reqs, ctx->rots, 1, ctx->bits + bsz, ctx->stream, 4, 1);
     if (dual && e == cudaSuccess)
         e = launch_fwd2d(g, 1, ctx->bits + bsz, Y2, tw, qt, ctx->stream, ctx->bits, ctx->rots, ctx->reqs);
-    if (e == cudaSuccess) e = launch_zpass(g, 1, 1, Y, ctx->rots, ctx->reqs, Y + ysz, tw, ctx->stream, Y2);
+    if (e == cudaSuccess) {
+        if (g.M == 256 && tuning_for(ctx, g).zpass_cols == 16 && !dual)
+            e = launch_zpass16(g, 1, 1, Y, ctx->rots, ctx->reqs, Y + ysz, ctx->stream);
+        else
+            e = launch_zpass(g, 1, 1, Y, ctx->rots, ctx->reqs, Y + ysz, tw, ctx->stream, Y2);
+    }
     if (e == cudaSuccess)
         e = launch_plane_export(g, Y + ysz, tw, dC, ctx->stream, tuning_for(ctx, g).plane_cl, ctx->errflag);
     if (e == cudaSuccess) e = cudaMemcpyAsync(C, dC, csz * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);

@@ -92,11 +92,14 @@ cudaError_t launch_resample(const Geo &g, const ReqDev *reqs, const RotRec *rots
 cudaError_t launch_zpass(const Geo &g, int B, int group, const float2 *Y, const RotRec *rots, const ReqDev *reqs,
                          float2 *Z, const float2 *tw, cudaStream_t st, const float2 *Y2 = nullptr);
 // plane_cl: CTAs per plane at M = 256 (4 or 8: the cluster kernel of
-// k_plane.cu; anything else: the 2-CTA kernel).  err (nullable, device):
+// k_fft256.cu; anything else: the 2-CTA kernel).  err (nullable, device):
 // set to DOCK_E_TIMEOUT if a cluster kernel gave up waiting for its peers.
 cudaError_t launch_plane(const Geo &g, int B, const float2 *Z, const float2 *tw, const RotRec *rots,
                          const ReqDev *reqs, cudaStream_t st, int plane_cl = 0, int *err = nullptr);
-// The cluster plane pass (k_plane.cu): M = 256, cl = 4 or 8.
+// z pass over 16 columns per block (k_fft256.cu): M = 256, plain score only.
+cudaError_t launch_zpass16(const Geo &g, int B, int group, const float2 *Y, const RotRec *rots, const ReqDev *reqs,
+                           float2 *Z, cudaStream_t st);
+// The cluster plane pass (k_fft256.cu): M = 256, cl = 4 or 8.
 bool plane_cl_supported(int M, int cl);
 cudaError_t launch_plane_cl(const Geo &g, int cl, int B, const float2 *Z, const float2 *tw, const RotRec *rots,
                             const ReqDev *reqs, int *err, cudaStream_t st);

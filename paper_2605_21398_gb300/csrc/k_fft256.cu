@@ -1,6 +1,9 @@
-// Inverse plane pass at canvas side M = 256 over a cluster of CL = 4 or 8
-// CTAs per plane (Eq. (7), (9): the last two inverse transforms of
-// C = F^-1(conj(F(O)) . F(S)) and the per-rotation argmax).
+// Search passes at canvas side M = 256 (Eq. (7), (9)): the z pass with the
+// spectrum multiply, and the inverse plane pass with the argmax.
+//
+// Plane pass, over a cluster of CL = 4 or 8 CTAs per plane (the last two
+// inverse transforms of C = F^-1(conj(F(O)) . F(S)) and the per-rotation
+// argmax).
 //
 // Plane z of rotation b holds Z[ky][kx], ky < 256, kx <= 128 (row pitch 130).
 // CTA `rank` of the cluster owns the packed columns kx in [rank CPC,
@@ -345,6 +348,110 @@ k_plane_cl(const float2 *__restrict__ Z, const float2 *__restrict__ tw, const Ro
     if (tid == 0) bulk_wait_read();
 }
 
+// ---------------------------------------------------------------------------
+// z pass at M = 256 over 16 columns per CTA (f = ky P + kx in [16 blockIdx.x,
+// + 16)): for each of the block's `group` rotations, forward FFT along z of
+// the N = 128 non-zero inputs, times conj(F(O)) / M^3 (for a rotated object:
+// the tile conjugated, times F(S) / M^3), inverse FFT along z.  Thread (c, j)
+// (c = column, j < 16) holds z (or kz) = j + 16 s: the inputs come straight
+// from global memory (the next rotation's already in flight), the forward
+// output is in the inverse's input order, and both transforms exchange
+// between their radix-16 stages through one [256][16] buffer.  The block's
+// spectrum tile [kz][16] sits in shared memory (reloaded when the request
+// changes), the stage twiddles of the thread in registers.
+// ---------------------------------------------------------------------------
+struct Zpass16Cfg {
+    static constexpr int M = 256, N = 128, P = 130, NT = 256, COLS = 16;
+    static constexpr size_t SMEM = (size_t)2 * M * COLS * 8;   // exchange + spectrum tile
+};
+
+__global__ void __launch_bounds__(Zpass16Cfg::NT, 3)
+k_zpass16(int B, int group, const float2 *__restrict__ Y, const RotRec *rots, const ReqDev *reqs, float2 *Z)
+{
+    using C = Zpass16Cfg;
+    constexpr int M = C::M, N = C::N, P = C::P, COLS = C::COLS;
+    extern __shared__ __align__(16) unsigned char smem[];
+    cf *xb = reinterpret_cast<cf *>(smem);      // [M][COLS]
+    cf *spt = xb + M * COLS;                     // [M (kz)][COLS]
+    const int tid = threadIdx.x, c = tid & 15, j = tid >> 4;
+    const size_t plane = (size_t)M * P;
+    const int f0 = blockIdx.x * COLS;            // first column of the block
+    const int b0 = blockIdx.y * group, nb = min(group, B - b0);
+    if (nb <= 0) return;
+    cf tw1[16];                                  // exp(-2 pi i j r / 256)
+#pragma unroll
+    for (int r = 1; r < 16; ++r) {
+        const float2 w = c_tw256[(j * r) & 255];
+        tw1[r] = cmake(w.x, w.y);
+    }
+    auto load = [&](int bi, cf *v) {
+        const float2 *src = Y + (size_t)(b0 + bi) * N * plane + f0 + c;
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const float2 a = __ldcs(&src[(size_t)(j + 16 * s) * plane]);
+            v[s] = cmake(a.x, a.y);
+        }
+    };
+    cf nx[8];
+    load(0, nx);
+    int sp_req = -1;
+#pragma unroll 1
+    for (int bi = 0; bi < nb; ++bi) {
+        cf v[16];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) v[s] = nx[s];
+#pragma unroll
+        for (int s = 8; s < 16; ++s) v[s] = cmake(0.f, 0.f);   // z >= N: zero padding
+        if (bi + 1 < nb) load(bi + 1, nx);
+        const int req = rots[b0 + bi].req;
+        if (req != sp_req) {   // block-uniform
+            __syncthreads();   // the previous tile is no longer read
+            const float2 *spec = reqs[req].spec;
+            // tiled spectrum: ((f / 32) M + kz) 32 + f mod 32
+            const float2 *src = spec + (size_t)(f0 / 32) * M * 32 + (f0 & 31) + c;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                const float2 a = __ldg(&src[(size_t)(j + 16 * r) * 32]);
+                spt[(j + 16 * r) * COLS + c] = cmake(a.x, a.y);
+            }
+            sp_req = req;
+        }
+        const float cj = reqs[req].rotate_object ? -1.f : 1.f;
+        // forward, stage 0 (inputs z = j + 16 s) -> index 16 j + r
+        DFT<16, false>::run(v);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) xb[(16 * j + r) * COLS + c] = v[r];
+        __syncthreads();
+        // forward, stage 1 -> kz = j + 16 r; multiply
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = xb[(j + 16 * r) * COLS + c];
+#pragma unroll
+        for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], tw1[r]);
+        DFT<16, false>::run(v);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            cf a = v[r];
+            a.y *= cj;
+            v[r] = cmul(a, spt[(j + 16 * r) * COLS + c]);
+        }
+        __syncthreads();   // every thread has read its forward stage-1 inputs
+        // inverse, stage 0 (inputs kz = j + 16 r) -> index 16 j + r
+        DFT<16, true>::run(v);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) xb[(16 * j + r) * COLS + c] = v[r];
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = xb[(j + 16 * r) * COLS + c];
+#pragma unroll
+        for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], cconj(tw1[r]));
+        DFT<16, true>::run(v);
+        float2 *dst = Z + (size_t)(b0 + bi) * M * plane + f0 + c;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) __stcs(&dst[(size_t)(j + 16 * r) * plane], make_float2(v[r].x, v[r].y));
+        __syncthreads();   // the exchange buffer is free for the next rotation
+    }
+}
+
 // Fills c_tw256 on the current device once (the module's constant bank is per device).
 static cudaError_t ensure_twiddle_bank()
 {
@@ -396,6 +503,21 @@ static cudaError_t launch_plane_cl_t(int B, const float2 *Z, const float2 *tw, c
 }
 
 bool plane_cl_supported(int M, int cl) { return M == 256 && (cl == 4 || cl == 8); }
+
+cudaError_t launch_zpass16(const Geo &g, int B, int group, const float2 *Y, const RotRec *rots, const ReqDev *reqs,
+                           float2 *Z, cudaStream_t st)
+{
+    using C = Zpass16Cfg;
+    if (g.M != C::M || g.P != C::P || B < 1 || group < 1) return cudaErrorInvalidValue;
+    cudaError_t e = ensure_twiddle_bank();
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_zpass16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (e != cudaSuccess) return e;
+    const dim3 grid(C::M * C::P / C::COLS, (B + group - 1) / group);
+    if (grid.y > 65535) return cudaErrorInvalidValue;
+    k_zpass16<<<grid, C::NT, C::SMEM, st>>>(B, group, Y, rots, reqs, Z);
+    return cudaGetLastError();
+}
 
 
 cudaError_t launch_plane_cl(const Geo &g, int cl, int B, const float2 *Z, const float2 *tw, const RotRec *rots,

@@ -1,9 +1,9 @@
-"""The inverse plane pass at canvas 256 in each of its launch shapes (2, 4 or
-8 CTAs per plane) against the FP64 oracle (Eq. (7), (9)): the full
-correlation field within 1e-4 of max |C|, per-rotation peaks within the score
-tolerance, peak indices exact where the oracle's top-two gap exceeds twice
-that tolerance and otherwise one of the oracle's maxima within it, and the
-three shapes giving the same peaks."""
+"""The z pass and the inverse plane pass at canvas 256 in each of their launch
+shapes (16 or 32 columns per z-pass block; 2, 4 or 8 CTAs per plane) against
+the FP64 oracle (Eq. (7), (9)): the full correlation field within 1e-4 of
+max |C|, per-rotation peaks within the score tolerance, peak indices exact
+where the oracle's top-two gap exceeds twice that tolerance and otherwise one
+of the oracle's maxima within it, and every shape giving the same peaks."""
 import numpy as np
 import pytest
 
@@ -12,7 +12,9 @@ from paper_2605_21398_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = (2, 4, 8)
+# (plane_cl, zpass_cols): the 2-CTA plane pass with the 32-column z pass, and
+# the cluster plane passes with either z pass
+SHAPES = ((2, 32), (4, 16), (8, 16), (4, 32))
 
 
 @pytest.fixture(scope="module")
@@ -57,13 +59,14 @@ def test_full_field_at_canvas_256_in_every_shape(ctx, workload):
     fields = {}
     saved = ctx.get_tuning(w.N)
     try:
-        for cl in SHAPES:
-            ctx.set_tuning(N=w.N, plane_cl=cl)
-            assert ctx.get_tuning(w.N)["plane_cl"] == cl
+        for cl, zc in SHAPES:
+            ctx.set_tuning(N=w.N, plane_cl=cl, zpass_cols=zc)
+            t = ctx.get_tuning(w.N)
+            assert (t["plane_cl"], t["zpass_cols"]) == (cl, zc)
             C = ctx.search_scores(ob, sw, q)
             err = np.max(np.abs(C - Co))
-            assert err <= tol, (cl, err, tol)
-            fields[cl] = C
+            assert err <= tol, (cl, zc, err, tol)
+            fields[cl, zc] = C
     finally:
         ctx.set_tuning(**saved)
     # the shapes differ only in the order of FP32 operations
@@ -87,18 +90,18 @@ def test_peaks_at_canvas_256_in_every_shape(ctx, workload):
     got = {}
     saved = ctx.get_tuning(w.N)
     try:
-        for cl in SHAPES:
-            ctx.set_tuning(N=w.N, plane_cl=cl, batch=3)
+        for cl, zc in SHAPES:
+            ctx.set_tuning(N=w.N, plane_cl=cl, zpass_cols=zc, batch=3)
             _, pk = ctx.search_so3(ob, sw, len(quats), 2, sampler=3, quats=quats, want_peaks=True)
             for i, (sc, idx, tol, gap, Cf) in enumerate(ref):
-                assert abs(pk["score"][i] - sc) <= tol + 1e-4 * abs(sc), (cl, i)
+                assert abs(pk["score"][i] - sc) <= tol + 1e-4 * abs(sc), (cl, zc, i)
                 if i in gapped:
-                    assert pk["idx"][i] == idx, (cl, i)
+                    assert pk["idx"][i] == idx, (cl, zc, i)
                 # every rotation: the chosen shift is one of the oracle's
                 # maxima up to the tolerance (several are correct when the
                 # top of the field is flatter than the FP32 error)
-                assert Cf[pk["idx"][i]] >= sc - 2 * tol, (cl, i)
-            got[cl] = pk
+                assert Cf[pk["idx"][i]] >= sc - 2 * tol, (cl, zc, i)
+            got[cl, zc] = pk
     finally:
         ctx.set_tuning(**saved)
     for cl in SHAPES[1:]:
@@ -107,6 +110,7 @@ def test_peaks_at_canvas_256_in_every_shape(ctx, workload):
 
 def test_set_tuning_rejects_out_of_range_shapes(ctx):
     from paper_2605_21398_gb300 import dock
-    for bad in (dict(N=128, plane_cl=3), dict(N=128, batch=0), dict(N=128, vox_blocks=5), dict(N=48)):
+    for bad in (dict(N=128, plane_cl=3), dict(N=128, zpass_cols=8), dict(N=128, batch=0), dict(N=128, vox_blocks=5),
+                dict(N=48)):
         with pytest.raises(dock.DockError):
             ctx.set_tuning(**bad)
