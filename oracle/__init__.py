@@ -24,7 +24,9 @@ adds the steps that are plain definitions or textbook library primitives:
 
 The refinement is solved two ways: a fixed-iteration projected Gauss-Newton
 solver (`refine`, the GPU default) and the L-BFGS-B of Sec. V-C
-(`refine_lbfgsb`, scipy's implementation as the library step).
+(`refine_lbfgsb`, scipy's implementation as the library step).  `register`
+chains the three stages of Fig. 2: global search, local GeoBall-SF search
+about the best global rotation, refinement of the merged top-K.
 
 Parity unpinned: the Super-Fibonacci constants beyond the paper's
 nearest-neighbour statistic (Sec. VI: 8.0 deg at n = 20000), and the
@@ -283,6 +285,86 @@ def search(O, o_o, poses, quats, h, N, r, L, fft=True):
         sc, idx = peak(C)
         out.append(dict(score=sc, idx=idx, dk=canvas_shift(idx, M, N), o_s=o_s, C=C, S=S))
     return out
+
+
+def set_threads(n):
+    """Threads of the oracle's parallel per-pose loops (1 = serial); results
+    do not depend on it (every sum over poses runs in pose order)."""
+    lib().orc_set_threads(int(n))
+
+
+def max_threads():
+    return int(lib().orc_max_threads())
+
+
+def _rotation_peak(args):
+    O, poses, q, h, N, r, L, M = args
+    S, o_s = sweep_grid(poses, q, h, N, r, L)
+    C = correlate_fft(O, S, M)
+    sc, idx = peak(C)
+    return sc, idx, o_s, float(np.max(np.abs(C)))
+
+
+def search_peaks(O, poses, quats, h, N, r, L, workers=1):
+    """`search` without keeping the grids: per rotation the peak score, its
+    canvas index and shift, the swept-lattice origin and max |C| (the scale of
+    the score tolerance).  Rotations are independent; with workers > 1 they
+    run in a thread pool (the C voxeliser and the FFT release the GIL), each
+    rotation computed exactly as alone."""
+    M = canvas_size(N)
+    args = [(O, poses, q, h, N, r, L, M) for q in quats]
+    if workers > 1:
+        import concurrent.futures as cf
+        with cf.ThreadPoolExecutor(workers) as ex:
+            res = list(ex.map(_rotation_peak, args))
+    else:
+        res = [_rotation_peak(a) for a in args]
+    return [dict(score=sc, idx=idx, dk=canvas_shift(idx, M, N), o_s=o_s, cmax=cm) for sc, idx, o_s, cm in res]
+
+
+def register(verts, tris, poses, h, N, r, L, n_global, n_local, theta, n_cand, prm, sampler="sf", workers=1):
+    """The three stages of a registration (Fig. 2; Sec. IV-C, IV-D, V-C):
+
+    1. global search (Sec. IV-C.1): the peak of Eq. (7) for each of n_global
+       Super-Fibonacci (or Hopf) rotations;
+    2. local search (Sec. IV-C.2, Algorithm 1): the peaks of n_local GeoBall-SF
+       rotations in the ball of half-angle theta about the best global
+       rotation (score descending, sample index ascending); these samples are
+       numbered after the global ones;
+    3. the n_cand best peaks of both stages together (same order) become candidate
+       poses by Eq. (8) with the sampled rotation, each is refined (Sec. V-C,
+       the fixed-iteration Gauss-Newton of `refine`) and the candidate with the
+       lowest J wins (ties: the lower candidate index).
+
+    Returns the global and local peaks, the candidates and their refinements,
+    and the winner."""
+    O, o_o, _, fits = object_grid(verts, tris, h, N)
+    if not fits:
+        raise ValueError("mesh does not fit the lattice")
+    qg = super_fibonacci(n_global) if sampler == "sf" else hopf_halton(n_global)
+    pg = search_peaks(O, poses, qg, h, N, r, L, workers)
+    sg = np.array([p["score"] for p in pg])
+    best_g = int(top_k(sg, 1)[0])
+    quats = qg
+    peaks = pg
+    if n_local > 0:
+        ql = geoball_sf(n_local, qg[best_g], theta)
+        pl = search_peaks(O, poses, ql, h, N, r, L, workers)
+        quats = np.concatenate([qg, ql])
+        peaks = pg + pl
+    scores = np.array([p["score"] for p in peaks])
+    order = top_k(scores, n_cand)
+    anchor = mesh_anchor(verts)
+    cands = []
+    for k, i in enumerate(order):
+        R, t = pose_from_peak(quats[i], peaks[i]["dk"], h, peaks[i]["o_s"], o_o)
+        ref = refine(verts, tris, poses, R, t, anchor, prm)
+        cands.append(dict(rot=int(i), q=quats[i], dk=peaks[i]["dk"], score=peaks[i]["score"], R0=R, t0=t,
+                          J=ref["J"], R=ref["R"], p=ref["p"], xi=ref["xi"]))
+    Js = np.array([c["J"] for c in cands])
+    best = int(np.lexsort((np.arange(len(Js)), Js))[0])
+    return dict(quats=quats, peaks=peaks, best_global=best_g, order=order, cands=cands, best=best, anchor=anchor,
+                o_o=o_o)
 
 
 # ----------------------------------------------------------------------------

@@ -58,6 +58,29 @@ ORC_API void orc_quat_to_mat(const double *q, double *R)
 /* triangle (vertex, edge, face), the textbook construction            */
 /* ------------------------------------------------------------------ */
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads of the parallel per-pose loops (1 = serial; results do not depend on it). */
+ORC_API void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}
+
+ORC_API int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
 static double dot3(const double *a, const double *b) { return (a[0] * b[0] + a[1] * b[1]) + a[2] * b[2]; }
 
 static double pt_tri_dist2(const double *p, const double *a, const double *b, const double *c)
@@ -470,36 +493,24 @@ ORC_API double orc_probe_sdf(const double *x, double r, double L, double *g)
 }
 
 /*
- * Contact normal n* of Eq. (23) at x: the unit SDF gradient.  On the medial
- * surface dr == dz inside the cylinder f_p is not differentiable; within
- * KINK_BAND of it the normal blends the two branch gradients linearly in
- * (dr - dz) and renormalises, so that it is continuous and FP32 and FP64
- * evaluations of nearby points give nearby normals.
+ * Contact normal n* of Eq. (23) at x: the unit SDF gradient, where f_p is
+ * not differentiable (the medial surface dr == dz inside the cylinder, the
+ * axis) the gradient of the branch orc_probe_sdf reports (the cap on ties,
+ * +x as the radial direction on the axis).
  */
-#define KINK_BAND 1e-3
 ORC_API void orc_probe_normal(const double *x, double r, double L, double *n)
 {
-    double rho = sqrt(x[0] * x[0] + x[1] * x[1]);
-    double ux = 1.0, uy = 0.0;
-    if (rho > 0.0) { ux = x[0] / rho; uy = x[1] / rho; }
-    double dr = rho - r;
-    double zlo = -x[2], zhi = x[2] - L;
-    double dz = zlo >= zhi ? zlo : zhi;
-    double cz = zlo >= zhi ? -1.0 : 1.0;
-    if (dr <= 0.0 && dz <= 0.0) {
-        double wr = 0.5 + (dr - dz) / (2.0 * KINK_BAND);
-        if (wr > 1.0) wr = 1.0;
-        if (wr < 0.0) wr = 0.0;
-        double gx = wr * ux, gy = wr * uy, gz = (1.0 - wr) * cz;
-        double gn = sqrt((gx * gx + gy * gy) + gz * gz);
-        n[0] = gx / gn; n[1] = gy / gn; n[2] = gz / gn;
-    } else {
-        double g[3];
-        orc_probe_sdf(x, r, L, g);
-        double gn = sqrt((g[0] * g[0] + g[1] * g[1]) + g[2] * g[2]);
-        n[0] = g[0] / gn; n[1] = g[1] / gn; n[2] = g[2] / gn;
-    }
+    double g[3];
+    orc_probe_sdf(x, r, L, g);
+    double gn = sqrt((g[0] * g[0] + g[1] * g[1]) + g[2] * g[2]);
+    n[0] = g[0] / gn; n[1] = g[1] / gn; n[2] = g[2] / gn;
 }
+
+/* Distance (mm) from the medial surface within which a witness is treated
+ * as lying on it: the Danskin rule below then picks the subgradient; off the
+ * surface that rule returns the branch gradient itself for an optimal face
+ * or edge witness, so the width only decides where the rule is evaluated. */
+#define KINK_BAND 1e-3
 
 static void comb(const double *v0, const double *v1, const double *v2, const double *lam, double *x)
 {
@@ -517,8 +528,10 @@ static void comb(const double *v0, const double *v1, const double *v2, const dou
  * vanishes (the optimality condition of the convex minimum; the value then
  * moves with the pose as that subgradient says, by Danskin's theorem):
  * n = lam a + (1 - lam) b with lam minimising |P (lam a + (1 - lam) b)|,
- * P the projection onto the face.  At a vertex witness the condition leaves
- * lam free and the blend of orc_probe_normal is kept.  n is not normalised.
+ * P the projection onto the face.  A vertex of the triangle lies on the
+ * medial surface only by coincidence (a set of poses of measure zero), so at
+ * a vertex witness f_p is differentiable and n is the gradient of its active
+ * branch (orc_probe_normal).  n is not normalised.
  */
 static void witness_subgradient(const double *x, const double loc[3][3], const double *lam, double r, double L,
                                 double *n)
@@ -838,6 +851,8 @@ ORC_API void orc_distances(const double *V, int64_t nv, const int32_t *T, int64_
 {
     (void)nv;
     query_t Q = {r, L, eps, iters};
+    /* poses are independent: each writes only its own outputs */
+#pragma omp parallel for schedule(dynamic, 2)
     for (int64_t i = 0; i < P; ++i) {
         double Ri[9];
         orc_quat_to_mat(poses + 7 * i, Ri);
@@ -891,11 +906,24 @@ ORC_API double orc_objective(const double *V, int64_t nv, const int32_t *T, int6
     double G[6] = {0, 0, 0, 0, 0, 0};
     double HH[36];
     memset(HH, 0, sizeof(HH));
+    /* the per-pose queries are independent (computed in parallel); the sums
+     * below run in pose order, so the result does not depend on the threads */
+    double *qd = (double *)malloc(sizeof(double) * 7 * (size_t)(P > 0 ? P : 1));
+    int64_t *qt = (int64_t *)malloc(sizeof(int64_t) * (size_t)(P > 0 ? P : 1));
+    if (!qd || !qt) {
+        free(qd);
+        free(qt);
+        return NAN;
+    }
+#pragma omp parallel for schedule(dynamic, 2)
     for (int64_t i = 0; i < P; ++i) {
         double Ri[9];
         orc_quat_to_mat(poses + 7 * i, Ri);
-        double d, w[3], n[3];
-        int64_t bt = dist_query(&Q, V, T, nt, R, p, Ri, poses + 7 * i + 4, &d, w, n);
+        qt[i] = dist_query(&Q, V, T, nt, R, p, Ri, poses + 7 * i + 4, qd + 7 * i, qd + 7 * i + 1, qd + 7 * i + 4);
+    }
+    for (int64_t i = 0; i < P; ++i) {
+        const double d = qd[7 * i], *w = qd + 7 * i + 1, *n = qd + 7 * i + 4;
+        const int64_t bt = qt[i];
         if (d_out) d_out[i] = d;
         if (bt < 0) continue;
         double s, s1, s2;
@@ -917,6 +945,8 @@ ORC_API double orc_objective(const double *V, int64_t nv, const int32_t *T, int6
             for (int a = 0; a < 6; ++a)
                 for (int b = 0; b < 6; ++b) HH[6 * a + b] += wgt * g[a] * g[b];
     }
+    free(qd);
+    free(qt);
     double xx = 0.0;
     for (int j = 0; j < 6; ++j) xx += xi[j] * xi[j];
     J += Pp.lambda * xx;

@@ -22,7 +22,7 @@
 
 namespace dock {
 
-#define KINK_BAND 1e-3f   // width of the blend across the medial surface (mm)
+#define KINK_BAND 1e-3f   // distance from the medial surface within which a witness is treated as on it (mm)
 
 // per-candidate data read by the evaluation kernel (FP32)
 struct CandF {
@@ -66,26 +66,13 @@ __device__ __forceinline__ float sdf_cyl(float x, float y, float z, float r, flo
     return f;
 }
 
-// Contact normal n* (Eq. (23)): the unit gradient; inside, within KINK_BAND
-// of the medial surface, a continuous blend of the two branch gradients (used
-// where the witness alone does not select a subgradient: see
-// witness_subgradient).
+// Contact normal n* (Eq. (23)): the unit gradient; where f_p is not
+// differentiable (the medial surface inside, the axis) the gradient of the
+// branch sdf_cyl reports (the cap on ties, +x radially on the axis).
 __device__ __forceinline__ void sdf_normal(const float *x, float r, float L, float *n)
 {
-    float rho = sqrtf(fmaf(x[0], x[0], x[1] * x[1]));
-    float ux = 1.f, uy = 0.f;
-    if (rho > 0.f) { ux = x[0] / rho; uy = x[1] / rho; }
-    float dr = rho - r;
-    float zlo = -x[2], zhi = x[2] - L;
-    float dz = zlo >= zhi ? zlo : zhi;
-    float cz = zlo >= zhi ? -1.f : 1.f;
     float g[3];
-    if (dr <= 0.f && dz <= 0.f) {
-        float wr = fminf(1.f, fmaxf(0.f, 0.5f + (dr - dz) / (2.f * KINK_BAND)));
-        g[0] = wr * ux; g[1] = wr * uy; g[2] = (1.f - wr) * cz;
-    } else {
-        sdf_cyl(x[0], x[1], x[2], r, L, g);
-    }
+    sdf_cyl(x[0], x[1], x[2], r, L, g);
     float gn = sqrtf(fmaf(g[0], g[0], fmaf(g[1], g[1], g[2] * g[2])));
     n[0] = g[0] / gn; n[1] = g[1] / gn; n[2] = g[2] / gn;
 }
@@ -98,8 +85,9 @@ __device__ __forceinline__ float dot3f(const float *a, const float *b) { return 
 // surface inside the probe, the combination lam a + (1 - lam) b of the
 // radial and cap gradients whose component along the witness's face (the
 // triangle's plane, or its edge when a barycentric weight is ~0) vanishes,
-// the element the minimum over the triangle selects (Danskin); at a vertex
-// witness the blend of sdf_normal.  Not normalised.
+// the element the minimum over the triangle selects (Danskin); a vertex lies
+// on the medial surface only by coincidence, so at a vertex witness the
+// gradient of the active branch (sdf_normal).  Not normalised.
 __device__ __noinline__ void witness_subgradient(const float *x, const float lv[3][3], float r, float L, float *n)
 {
     const float rho = sqrtf(fmaf(x[0], x[0], x[1] * x[1]));

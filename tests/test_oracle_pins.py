@@ -694,17 +694,147 @@ def test_lbfgsb_refinement_stops_on_the_box_with_outward_gradients(workload):
     assert np.all(G[held] * np.sign(u[held]) <= 1e-6)
 
 
-def test_refinement_reduces_J_and_moves_toward_the_planted_pose(workload):
+def _gn_case(w, dr_deg, dt_mm):
+    a = O.mesh_anchor(w.obj.verts)
+    prm = O.refine_params(w.radius, w.length)
+    q0 = synth.quat_mul(synth.axis_angle_quat(np.radians(dr_deg)), w.gt_q)
+    return a, prm, O.quat_to_mat(q0), w.gt_t + np.array(dt_mm)
+
+
+def _pose_error(R, p, a, w):
+    Rg = O.quat_to_mat(w.gt_q)
+    e = np.linalg.norm(R @ a + p - (Rg @ a + w.gt_t))
+    ang = math.degrees(math.acos(min(1.0, (np.trace(R @ Rg.T) - 1) / 2)))
+    return e, ang
+
+
+def test_gauss_newton_refinement_converges_to_the_planted_pose(workload, capsys):
+    # Sec. V-C with the normal-equation step: on noise-free raster contacts the
+    # minimiser of Eq. (19) is the planted pose (every d_i = 0 where s = 1 is
+    # the largest score, so J = -N there).  The fixed 20 projected
+    # Gauss-Newton steps (trust region 0.05 mm / 0.5 deg, box of Eq. (20)) must
+    # reach it to 0.01 mm at the anchor and 0.05 deg from both starts.
+    w = workload("tiny32", lines=5, pitch=1.5)
+    for dr, dt in (([0.3, 0.2, -0.1], [0.05, 0.03, -0.04]), ([1.0, -0.5, 0.7], [0.1, -0.05, 0.08])):
+        a, prm, R0, p0 = _gn_case(w, dr, dt)
+        res = O.refine(w.obj.verts, w.obj.tris, w.poses_world, R0, p0, a, prm)
+        e1, ang = _pose_error(res["R"], res["p"], a, w)
+        with capsys.disabled():
+            print("\n  Gauss-Newton from %s deg / %s mm: %.2e mm, %.2e deg, J %.6f (N %d)"
+                  % (dr, dt, e1, ang, res["J"], len(w.poses_world)))
+        assert e1 <= 0.01 and ang <= 0.05, (e1, ang)
+        assert res["J"] <= -(1 - 1e-3) * len(w.poses_world)
+
+
+def test_gauss_newton_refinement_keeps_the_planted_pose(workload):
+    # at the planted pose every contact distance is ~0, where s'(0) = 0: the
+    # gradient of Eq. (28) vanishes, every step is zero and J = -N
+    w = workload("tiny32", lines=5, pitch=1.5)
+    a = O.mesh_anchor(w.obj.verts)
+    prm = O.refine_params(w.radius, w.length)
+    res = O.refine(w.obj.verts, w.obj.tris, w.poses_world, O.quat_to_mat(w.gt_q), w.gt_t, a, prm)
+    assert np.max(np.abs(res["xi"])) <= 1e-8
+    assert abs(res["J"] + len(w.poses_world)) <= 1e-6
+
+
+def test_gauss_newton_steps_stay_in_the_trust_region_and_the_box(workload):
+    # far start (1.5 mm / 8 deg): one step moves each translation component
+    # by at most step_t and each rotation component by at most step_r; after
+    # all steps xi lies in the box |u| <= b_t, |w| <= b_r of Eq. (20)
+    w = workload("tiny32", lines=5, pitch=1.5)
+    a, prm, R0, p0 = _gn_case(w, [5.0, -6.0, 3.0], [1.2, -0.8, 0.4])
+    one = prm.copy()
+    one[10] = 1
+    r1 = O.refine(w.obj.verts, w.obj.tris, w.poses_world, R0, p0, a, one)
+    assert np.max(np.abs(r1["xi"][:3])) <= O.STEP_T * (1 + 1e-12)
+    assert np.max(np.abs(r1["xi"][3:])) <= O.STEP_R * (1 + 1e-12)
+    assert np.max(np.abs(r1["xi"])) > 0
+    rn = O.refine(w.obj.verts, w.obj.tris, w.poses_world, R0, p0, a, prm)
+    assert np.max(np.abs(rn["xi"][:3])) <= O.B_T and np.max(np.abs(rn["xi"][3:])) <= O.B_R
+
+
+def test_gauss_newton_matrix_from_independent_sensitivities(workload):
+    # H = sum_i max(-s''(d_i), 0) g_i g_i^T + (2 lambda + mu) I (Sec. V-C),
+    # rebuilt here from pieces the oracle's H does not use: g_i = d d_i / d xi
+    # by central differences of the distance query, s'' by central
+    # differences of s', and the damping from the parameters.  Poses whose
+    # distance is not smooth at xi (the one-sided differences disagree) or
+    # whose d_i lies next to a junction of the pieces of s are left out of
+    # both sides.
+    w = workload("tiny32", lines=5, pitch=1.5)
+    a, prm, R0, p0 = _gn_case(w, [0.5, -0.3, 0.4], [0.06, -0.04, 0.05])
+    V, T, P = w.obj.verts, w.obj.tris, w.poses_world
+    xi = np.array([0.01, -0.02, 0.015, 0.002, -0.001, 0.0015])
+    _, _, _, d0 = O.objective(V, T, P, R0, p0, a, xi, prm)
+    eps = 1e-6
+    dp, dm = np.empty((6, len(P))), np.empty((6, len(P)))
+    for k in range(6):
+        e = np.zeros(6)
+        e[k] = eps
+        dp[k] = O.objective(V, T, P, R0, p0, a, xi + e, prm)[3]
+        dm[k] = O.objective(V, T, P, R0, p0, a, xi - e, prm)[3]
+    g = ((dp - dm) / (2 * eps)).T                       # (P, 6)
+    fwd, bwd = ((dp - d0) / eps).T, ((d0 - dm) / eps).T
+    tau, r = O.TAU_OUT2, O.TAU_IN2 / O.TAU_OUT2
+    t = d0 / tau
+    smooth = (np.all(np.isfinite(g), axis=1) & (np.max(np.abs(fwd - bwd), axis=1) <= 1e-4 * (1 + np.abs(g).max(axis=1)))
+              & (np.abs(t) > 1e-3) & (np.abs(t + r) > 1e-3) & (np.abs(t - 1) > 1e-3) & (t < 1))
+    assert smooth.sum() >= 20
+    hs = 1e-7
+    s2 = np.array([(O.score(di + hs)[1] - O.score(di - hs)[1]) / (2 * hs) for di in d0[smooth]])
+    wgt = np.maximum(-s2, 0.0)
+    assert (wgt > 0).sum() >= 10 and (s2 > 0).sum() >= 3   # both sides of the clip are exercised
+    H_ind = (g[smooth] * wgt[:, None]).T @ g[smooth] + (2 * O.LAMBDA + O.MU) * np.eye(6)
+    _, _, H, _ = O.objective(V, T, P[smooth], R0, p0, a, xi, prm)
+    assert np.max(np.abs(H - H_ind)) <= 1e-5 * np.max(np.abs(H)), np.max(np.abs(H - H_ind)) / np.max(np.abs(H))
+
+
+def test_objective_without_poses_is_the_regulariser(workload):
+    # no pose: J = lambda |xi|^2, grad = 2 lambda xi, H = (2 lambda + mu) I
+    # (the closed forms of Eq. (19), (28) and the damping of the solver)
     w = workload("tiny32")
     a = O.mesh_anchor(w.obj.verts)
     prm = O.refine_params(w.radius, w.length)
-    q0 = synth.quat_mul(synth.axis_angle_quat(np.radians([0.3, 0.2, -0.1])), w.gt_q)
-    R0 = O.quat_to_mat(q0)
-    p0 = w.gt_t + np.array([0.05, 0.03, -0.04])
-    J0 = O.objective(w.obj.verts, w.obj.tris, w.poses_world, R0, p0, a, np.zeros(6), prm)[0]
-    res = O.refine(w.obj.verts, w.obj.tris, w.poses_world, R0, p0, a, prm)
-    Rg = O.quat_to_mat(w.gt_q)
-    e0 = np.linalg.norm(R0 @ a + p0 - (Rg @ a + w.gt_t))
-    e1 = np.linalg.norm(res["R"] @ a + res["p"] - (Rg @ a + w.gt_t))
-    assert res["J"] < J0
-    assert e1 < 0.5 * e0
+    xi = np.array([0.3, -0.2, 0.1, 0.02, -0.03, 0.01])
+    J, G, H, _ = O.objective(w.obj.verts, w.obj.tris, np.zeros((0, 7)), O.quat_to_mat(w.gt_q), w.gt_t, a, xi, prm)
+    assert abs(J - O.LAMBDA * xi @ xi) <= 1e-15
+    assert np.allclose(G, 2 * O.LAMBDA * xi, rtol=0, atol=1e-15)
+    assert np.allclose(H, (2 * O.LAMBDA + O.MU) * np.eye(6), rtol=0, atol=1e-15)
+
+
+def planted_sample_workload(n_global, j, poses=600):
+    """Noise-free, all-contact 64^3 raster workload whose planted rotation is
+    Super-Fibonacci sample j of n_global (so the global stage can hit it
+    exactly) and whose planted translation is off the lattice."""
+    w = synth.make_workload("free64", poses=poses, noncontact=0.0, noise_t=0.0, noise_r=0.0)
+    qp = O.super_fibonacci(n_global)[j]
+    tp = np.array([0.7, -1.1, 0.4])
+    return w, qp, tp, synth.transform_poses(qp, tp, w.traj.poses_obj)
+
+
+def test_three_stage_registration_recovers_a_planted_sample_pose(capsys):
+    # Fig. 2 end to end (global SF search, GeoBall-SF about its best rotation,
+    # merged top-K, refinement, lowest J): with the planted rotation among
+    # the global samples and noise-free contacts, the global stage must pick
+    # it, and the winning refinement must land on the planted pose (every
+    # d_i = 0, J = -N, the smallest value J can take)
+    ng, nl, K, j = 96, 24, 2, 37
+    w, qp, tp, poses = planted_sample_workload(ng, j)
+    prm = O.refine_params(w.radius, w.length)
+    res = O.register(w.obj.verts, w.obj.tris, poses, w.h, w.N, w.radius, w.length, ng, nl, math.radians(5), K, prm,
+                     workers=os.cpu_count() or 1)
+    assert res["best_global"] == j
+    assert len(res["quats"]) == ng + nl
+    # the local samples lie in the ball about the best global rotation
+    cosd = np.abs(res["quats"][ng:] @ res["quats"][j])
+    assert np.all(2 * np.arccos(np.minimum(cosd, 1.0)) <= 2 * math.radians(5) + 1e-12)
+    best = res["cands"][res["best"]]
+    Rg = O.quat_to_mat(qp)
+    a = res["anchor"]
+    e = np.linalg.norm(best["R"] @ a + best["p"] - (Rg @ a + tp))
+    dr = math.degrees(math.acos(min(1.0, (np.trace(best["R"] @ Rg.T) - 1) / 2)))
+    with capsys.disabled():
+        print("\n  three-stage registration: %.2e mm, %.2e deg, J %.6f (N %d)" % (e, dr, best["J"], len(poses)))
+    assert e <= 0.01 and dr <= 0.05
+    assert best["J"] <= -(1 - 1e-3) * len(poses)
+    assert all(c["J"] >= best["J"] for c in res["cands"])
