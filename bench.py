@@ -104,6 +104,108 @@ def cufft_comparison(ctx, ob, sw, w, stream, n_rot=16, batch=8):
             "max_peak_score_diff": round(diff, 4)}
 
 
+def config4_mix(synth, n_req, n_obj=16, seed=41):
+    """Requests shaped like the batched-instances workload: lattice side
+    uniform over {32, 64, 96, 128} at h = 16 mm / N, trajectories of U[100,
+    5000] poses, probe radius U[0.5, 1.5] mm (length 12 mm), U[1000, 16000]
+    orientation samples (80 % global SF, 20 % local GeoBall-SF), top-8
+    refined; n_obj objects (a quarter per side), each with its own
+    trajectory, shared by the requests."""
+    rng = np.random.default_rng(seed)
+    works = []
+    for k in range(n_obj):
+        N = SERVE_SIZES[k % 4]
+        works.append(synth.make_workload("free64", replicate=200 + k, N=N, h=16.0 / N, n_theta=48, n_phi=96,
+                                         poses=int(rng.integers(100, 5001)), radius=float(rng.uniform(0.5, 1.5)),
+                                         noncontact=0.0, noise_t=0.02, noise_r=0.0, lines=3, pitch=1.5))
+    reqs = []
+    for _ in range(n_req):
+        n = int(rng.integers(1000, 16001))
+        reqs.append((int(rng.integers(0, n_obj)), int(0.8 * n), n - int(0.8 * n)))
+    return works, reqs
+
+
+def batch_study(ctx, synth, n_req):
+    """dock_register_batch on the mix against the plain loop of dock_register
+    (one request at a time), same requests, results compared bit for bit."""
+    works, reqs = config4_mix(synth, n_req)
+    handles = [(ctx.object_grid(w.obj.verts, w.obj.tris, w.h, w.N),
+                ctx.sweep_grid(w.poses_world, w.radius, w.length, w.h, w.N, contact=w.labels)) for w in works]
+    req_t = [(handles[i][0], handles[i][1], ng, nl, THETA, 8) for i, ng, nl in reqs]
+    try:
+        for N in SERVE_SIZES:   # warm every lattice side
+            i = next(k for k, w in enumerate(works) if w.N == N)
+            ctx.register(handles[i][0], handles[i][1], 256, 64, THETA, 8)
+        t0 = time.perf_counter()
+        plain = [ctx.register(*r) for r in req_t]
+        t_plain = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        batch = ctx.register_batch(req_t)
+        t_batch = time.perf_counter() - t0
+        same = all(np.array_equal(a["q"], b["q"]) and np.array_equal(a["t"], b["t"]) and a["J"] == b["J"]
+                   for a, b in zip(plain, batch))
+        evals = sum(ng + nl for _, ng, nl in reqs)
+        return {"requests": len(reqs), "objects": len(works), "evals": evals,
+                "mix": "N uniform over {32,64,96,128} at 16/N mm, 100-5000 poses, r 0.5-1.5 mm, 1000-16000 "
+                       "samples (80% SF + 20% GeoBall-SF), top-8",
+                "plain_regs_per_s": round(len(reqs) / t_plain, 3), "batch_regs_per_s": round(len(reqs) / t_batch, 3),
+                "batch_vs_plain": round(t_plain / t_batch, 3), "plain_s": round(t_plain, 2),
+                "batch_s": round(t_batch, 2), "results_equal_plain": bool(same)}
+    finally:
+        for ob, sw in handles:
+            ob.close()
+            sw.close()
+
+
+def serving_study(ctx, synth, n_req, rates):
+    """Poisson arrivals of n_req requests of the serving mix at each rate
+    (req/s): served regs/s and p50/p99/p99.9 latency (submission to result),
+    every result compared with the request registered alone."""
+    works, reqs = serving_mix(synth, n_req=n_req)
+    handles = [(ctx.object_grid(w.obj.verts, w.obj.tris, w.h, w.N),
+                ctx.sweep_grid(w.poses_world, w.radius, w.length, w.h, w.N, contact=w.labels)) for w in works]
+    req_t = [(handles[wi][0], handles[wi][1], ng, nl, THETA, 8) for wi, ng, nl in reqs]
+    out = []
+    try:
+        ctx.register(*req_t[0])
+        n_plain = min(40, n_req)
+        t0 = time.perf_counter()
+        alone = [ctx.register(*r) for r in req_t[:n_plain]]
+        t_plain = time.perf_counter() - t0
+        for rate in rates:
+            gaps = np.random.default_rng(int(rate * 100)).exponential(1.0 / rate, size=n_req)
+            arrivals = np.cumsum(gaps) - gaps[0]
+            tickets, done = {}, {}
+            t0 = time.perf_counter()
+            nxt = 0
+            while len(done) < n_req:
+                now = time.perf_counter() - t0
+                while nxt < n_req and arrivals[nxt] <= now:
+                    tickets[ctx.submit(req_t[nxt])] = nxt
+                    nxt += 1
+                for t, i in list(tickets.items()):
+                    r = ctx.poll(t, timeout_us=0)
+                    if r is not None:
+                        done[i] = r
+                        del tickets[t]
+                time.sleep(0.0005)
+            span = time.perf_counter() - t0
+            lat = np.array([done[i]["latency_ms"] for i in range(n_req)])
+            same = all(np.array_equal(done[i]["q"], alone[i]["q"]) and done[i]["J"] == alone[i]["J"]
+                       for i in range(n_plain))
+            out.append({"rate_per_s": rate, "requests": n_req, "served_regs_per_s": round(n_req / span, 3),
+                        "p50_ms": round(float(np.percentile(lat, 50)), 1),
+                        "p99_ms": round(float(np.percentile(lat, 99)), 1),
+                        "p999_ms": round(float(np.percentile(lat, 99.9)), 1),
+                        "results_equal_alone": bool(same)})
+        return {"mix": "N uniform over {32,64,96,128}, 100-2000 poses, r 0.5-1.5 mm, 1000-4000 + 25% rotations, "
+                       "top-8, 8 objects", "plain_regs_per_s": round(n_plain / t_plain, 3), "rates": out}
+    finally:
+        for ob, sw in handles:
+            ob.close()
+            sw.close()
+
+
 def synth_rotations(n, seed=5):
     from paper_2605_21398_gb300 import synth
     return synth.random_unit_quats(n, seed)
@@ -163,11 +265,15 @@ def serving_experiment(ctx, synth):
             sw.close()
 
 
-# DRAM bytes (read + write) per rotation of the HBM passes, from one ncu capture of an 8-rotation
-# launch on this workload (profiles/search_kernels_large128_8rot.md); traffic grows in proportion
-# to the rotations of a launch (the z-pass adds one spectrum read per launch).
-NCU_DRAM_BYTES_PER_ROT = {"plane": (545374976 + 3644928) / 8, "fwd2d": (4043776 + 214467584) / 8,
-                          "zpass": (340874240 - 68157440 + 489620992) / 8}
+# Per-rotation counters of the search kernels as they are now, from one ncu capture each of an
+# 8-rotation launch of `bench.py --ncu-case` (dram__bytes_read.sum + dram__bytes_write.sum, and
+# smsp__inst_executed.sum for the voxeliser); a launch of B rotations is scaled from them by B/8
+# (the z pass adds one spectrum read per launch).  A kernel changed since its capture has no entry.
+NCU_DRAM_BYTES_PER_ROT = {"plane": (545349888 + 2881792) / 8, "fwd2d": (4043776 + 214467584) / 8,
+                          "zpass": (340853760 - 68157440 + 489946880) / 8, "voxelise": (1384192 + 256) / 8}
+NCU_WARP_INST_PER_ROT = {"voxelise": 358047414 / 8}
+# SMs x warp schedulers: one warp instruction issued per scheduler per clock
+ISSUE_SLOTS = 152 * 4
 
 
 def max_over_ranks(ms, ws, device):
@@ -264,23 +370,28 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
+def sm_max_mhz():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p)).get("sm_max_mhz", 2070.0))
+    return 2070.0
+
+
 _ORACLE_GRID = {}
 
 
-def cpu_oracle_rate(w, n_rot, seed=0):
-    """The FP64 oracle (sweep + FFT correlation + argmax) on a bounded sample of
-    rotations of the same workload; returns (evals/s, seconds, rotations)."""
+def cpu_oracle_rate(w, n_rot, seed=0, workers=1):
+    """The FP64 oracle's search (sweep + FFT correlation + argmax per rotation)
+    on a bounded sample of rotations of the same workload, its rotations spread
+    over `workers` host threads; returns (evals/s, seconds, rotations)."""
     import oracle as O
     if id(w) not in _ORACLE_GRID:   # the object set-up is not part of an eval
         _ORACLE_GRID[id(w)] = O.object_grid(w.obj.verts, w.obj.tris, w.h, w.N)[:2]
     Go, oo = _ORACLE_GRID[id(w)]
     from paper_2605_21398_gb300 import synth
     quats = synth.random_unit_quats(n_rot, 1234 + seed)
-    M = O.canvas_size(w.N)
     t0 = time.perf_counter()
-    for q in quats:
-        S, o_s = O.sweep_grid(w.poses_world, q, w.h, w.N, w.radius, w.length)
-        O.peak(O.correlate_fft(Go, S, M))
+    O.search_peaks(Go, w.poses_world, quats, w.h, w.N, w.radius, w.length, workers=workers)
     dt = time.perf_counter() - t0
     return n_rot / dt, dt, n_rot
 
@@ -291,12 +402,13 @@ def run_reference(args):
         return 0
     from paper_2605_21398_gb300 import synth
     w = synth.make_workload(WORKLOAD)
-    per_step = 3
+    cores = os.cpu_count() or 1
+    per_step = 2 * cores
     for _ in range(args.warmup):
-        cpu_oracle_rate(w, 1)
+        cpu_oracle_rate(w, cores, workers=cores)
     times = []
     for s in range(args.steps):
-        r, dt, n = cpu_oracle_rate(w, per_step, seed=s)
+        r, dt, n = cpu_oracle_rate(w, per_step, seed=s, workers=cores)
         times.append(dt)
     total = per_step * args.steps
     value = total / sum(times)
@@ -307,8 +419,9 @@ def run_reference(args):
                                    "segments (20% labels flipped, 0.02 mm noise), 65k-triangle star object; the oracle's "
                                    "per-rotation search (sweep + FP64 FFT correlation + argmax) on sampled rotations",
                        "sample": "%d rotations per step" % per_step},
-            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle",
-                             "sample": "%d random rotations per step, sweep + FFT correlation + argmax" % per_step},
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                             "sample": "%d random rotations per step over %d host threads, sweep + FFT correlation "
+                                       "+ argmax" % (per_step, cores)},
             "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -361,6 +474,10 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--ncu-variant", default="plain", choices=["plain", "rotate_object", "label_aware"])
+    ap.add_argument("--batch-study", type=int, default=0, metavar="N_REQ",
+                    help="time dock_register_batch against the plain loop on N_REQ requests of the batched mix")
+    ap.add_argument("--serving-study", type=int, default=0, metavar="N_REQ",
+                    help="Poisson arrivals of N_REQ requests at 1, 2 and 4 req/s: regs/s and latency percentiles")
     ap.add_argument("--ncu-case", action="store_true",
                     help="small fixed case for ncu captures: one search of 8 rotations (batch 8) of the bench workload")
     args = ap.parse_args()
@@ -368,6 +485,18 @@ def main():
         return run_reference(args)
     if args.ncu_case:
         return run_ncu_case(args.ncu_variant)
+    if args.batch_study or args.serving_study:
+        from paper_2605_21398_gb300 import build, dock, synth
+        build.build()
+        ctx = dock.Context(0)
+        out = {}
+        if args.batch_study:
+            out["batch_study"] = batch_study(ctx, synth, args.batch_study)
+        if args.serving_study:
+            out["serving_study"] = serving_study(ctx, synth, args.serving_study, (1.0, 2.0, 4.0))
+        ctx.close()
+        print(json.dumps(out))
+        return 0
 
     import torch
     rank, ws = _dist()
@@ -435,25 +564,47 @@ def main():
     tot_all = sum(v[1] for v in stats.values()) or 1.0
     for k in kernels:
         kernels[k]["share"] = round(stats[k][1] / tot_all, 4)
-    roofline = None
-    hbm = {k: stats[k][1] for k in ("fwd2d", "zpass", "plane") if k in stats}
-    dom = max(hbm, key=lambda k: hbm[k]) if hbm else None
-    if dom:
-        launches, tot_ms = stats[dom]
+    def hbm_roofline(k):
+        launches, tot_ms = stats[k]
         M = 2 * w.N
         P = M // 2 + 2
-        total_bytes = kernel_bytes(dom, w.N) * rot_total
-        if dom == "zpass":
+        total_bytes = kernel_bytes(k, w.N) * rot_total
+        if k == "zpass":
             total_bytes += M * M * P * 8 * launches   # spectrum read once per launch (block column)
         achieved = total_bytes / (tot_ms / 1000.0) / 1e9
         rot_per_launch = rot_total / max(1, launches)
-        traffic = NCU_DRAM_BYTES_PER_ROT[dom] * rot_per_launch
-        if dom == "zpass":
-            traffic += M * M * P * 8
-        roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                    "frac": round(achieved / peak, 4), "traffic": int(traffic), "peak_source": peak_src,
-                    "algorithmic_bytes_per_launch": int(total_bytes / max(1, launches)),
-                    "dominant_overall": max(stats, key=lambda k: stats[k][1])}
+        traffic = None
+        if k in NCU_DRAM_BYTES_PER_ROT:
+            traffic = NCU_DRAM_BYTES_PER_ROT[k] * rot_per_launch + (M * M * P * 8 if k == "zpass" else 0)
+        return {"bound": "hbm", "kernel": k, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": int(traffic) if traffic else None,
+                "traffic_source": "ncu capture of an 8-rotation launch, scaled to %.1f rotations per launch"
+                                  % rot_per_launch, "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": int(total_bytes / max(1, launches))}
+
+    def issue_roofline(k):
+        # the voxeliser moves almost no data: it is bound by instruction issue
+        launches, tot_ms = stats[k]
+        inst = NCU_WARP_INST_PER_ROT[k] * rot_total
+        achieved = inst / (tot_ms / 1000.0) / 1e9
+        pk = ISSUE_SLOTS * sm_max_mhz() / 1e3
+        return {"bound": "alu", "kernel": k, "achieved": round(achieved, 1), "peak": round(pk, 1),
+                "unit": "G warp-instructions/s", "frac": round(achieved / pk, 4),
+                "traffic": int(NCU_DRAM_BYTES_PER_ROT[k] * rot_total / max(1, launches)),
+                "work_source": "smsp__inst_executed.sum of an 8-rotation ncu capture (%.1f M per rotation)"
+                               % (NCU_WARP_INST_PER_ROT[k] / 1e6),
+                "peak_source": "152 SMs x 4 schedulers x %.0f MHz (maximum SM clock)" % sm_max_mhz()}
+
+    search = {k: stats[k][1] for k in ("voxelise", "fwd2d", "zpass", "plane") if k in stats}
+    hbm = {k: v for k, v in search.items() if k != "voxelise"}
+    dom = max(search, key=lambda k: search[k]) if search else None
+    dom_hbm = max(hbm, key=lambda k: hbm[k]) if hbm else None
+    roofline = roofline_hbm = None
+    if dom:
+        roofline = issue_roofline(dom) if dom == "voxelise" else hbm_roofline(dom)
+        roofline["dominant_overall"] = max(stats, key=lambda k: stats[k][1])
+    if dom_hbm:
+        roofline_hbm = hbm_roofline(dom_hbm)
     model_frac = value / ws * model_bytes_per_eval(w.N) / (peak * 1e9)
 
     # end-to-end through the public API from host buffers (object + sweep + register + result)
@@ -537,11 +688,16 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        n_cpu = 4
-        r, dt, n = cpu_oracle_rate(w, n_cpu)
-        cpu = {"value": r, "unit": "evals/s", "cores": 1, "kind": "oracle",
-               "sample": "%d random rotations of the same workload (sweep + FP64 FFT correlation + argmax), %.1f s"
-                         % (n, dt)}
+        # the oracle's search on every host core (rotations spread over threads),
+        # and on one core
+        cores = os.cpu_count() or 1
+        r, dt, n = cpu_oracle_rate(w, 2 * cores, workers=cores)
+        r1, dt1, n1 = cpu_oracle_rate(w, 3, seed=1)
+        cpu = {"value": r, "unit": "evals/s", "cores": cores, "kind": "oracle",
+               "sample": "%d random rotations of the same workload over %d host threads (sweep + FP64 FFT "
+                         "correlation + argmax), %.1f s" % (n, cores, dt),
+               "single_core": {"value": r1, "unit": "evals/s", "cores": 1,
+                               "sample": "%d random rotations, %.1f s" % (n1, dt1)}}
 
     a = np.asarray(w.obj.verts).min(0) * 0.5 + np.asarray(w.obj.verts).max(0) * 0.5
     res = results[-1]
@@ -564,8 +720,9 @@ def main():
                        "l2": "inputs larger than L2 (per-batch FFT intermediates ~4 GB) and a 256 MB L2 flush "
                              "before every step",
                        "parallelism": "replicas" if ws > 1 else "single",
-                       "search_launch_shape": {k: tuning[k] for k in ("batch", "group", "vox_blocks")}},
-            "roofline": roofline, "model_roofline_frac": round(model_frac, 4),
+                       "search_launch_shape": {k: tuning[k] for k in ("batch", "group", "vox_blocks", "plane_cl",
+                                                                      "zpass_cols")}},
+            "roofline": roofline, "roofline_hbm": roofline_hbm, "model_roofline_frac": round(model_frac, 4),
             "model_bytes_per_eval": model_bytes_per_eval(w.N),
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "kernels": kernels,
             "ms_per_eval_search": round(sum(stats[k][1] for k in ("voxelise", "fwd2d", "zpass", "plane") if k in stats)

@@ -170,6 +170,16 @@ typedef struct dock_result {
  * the context may hold (0 = no bound).  cuda_stream is a cudaStream_t or NULL
  * for a stream the context creates and owns. */
 DOCK_API dock_status dock_create(dock_ctx **out, int device, size_t hbm_budget_bytes, void *cuda_stream);
+/* Device memory (bytes) the context and its handles hold now, the most they
+ * have held at any time since dock_create, and the budget (0 = none); any
+ * pointer may be NULL.  Systems form (serving admission); the paper has no
+ * counterpart. */
+DOCK_API dock_status dock_memory_stats(dock_ctx *ctx, size_t *held, size_t *peak, size_t *budget);
+/* Fault injection on the host: the n-th device allocation the context makes
+ * from now on fails as if cudaMalloc had answered out of memory (the call
+ * that makes it returns DOCK_E_NOMEM and the context stays usable); n = 0
+ * turns it off.  No device fault is involved.  DOCK_E_INVALID for n < 0. */
+DOCK_API dock_status dock_fail_allocation(dock_ctx *ctx, int32_t n);
 DOCK_API void dock_destroy(dock_ctx *ctx);
 /* Last error message of the context (valid until the next call on ctx). */
 DOCK_API const char *dock_last_error(const dock_ctx *ctx);

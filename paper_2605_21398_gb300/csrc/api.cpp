@@ -78,6 +78,8 @@ struct dock_ctx {
     bool own_stream = false;
     size_t budget = 0;        // 0 = unbounded
     size_t held = 0;          // bytes currently held by this context and its handles
+    size_t peak_held = 0;     // the most held at any time since creation
+    std::atomic<int> fail_alloc{0};   // host fault injection: the n-th allocation from now fails (0 = off)
     std::string err;
     std::mutex err_mu;        // err is written by the serving thread too
     bool dead = false;
@@ -218,12 +220,19 @@ static dock_status dalloc(dock_ctx *ctx, void **p, size_t bytes, size_t *acct)
     if (ctx->budget && ctx->held + bytes > ctx->budget)
         return fail(ctx, DOCK_E_TOO_LARGE, "device allocation of %zu bytes exceeds the HBM budget (%zu held of %zu)",
                     bytes, ctx->held, ctx->budget);
+    // injected failure (dock_fail_allocation): taken as an out-of-memory answer
+    // of cudaMalloc, before any device memory is touched
+    int n = ctx->fail_alloc.load();
+    while (n > 0 && !ctx->fail_alloc.compare_exchange_weak(n, n - 1)) {
+    }
+    if (n == 1) return fail(ctx, DOCK_E_NOMEM, "cudaMalloc(%zu): injected allocation failure", bytes);
     cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, DOCK_E_NOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
     }
     ctx->held += bytes;
+    if (ctx->held > ctx->peak_held) ctx->peak_held = ctx->held;
     if (acct) *acct += bytes;
     return DOCK_OK;
 }
@@ -596,13 +605,26 @@ static dock_status tables(dock_ctx *ctx, int M, float2 **tw, float2 **qt, double
         }
         float2 *dt = nullptr, *dq = nullptr;
         double2 *dd = nullptr;
-        dock_status s;
-        if ((s = dalloc(ctx, (void **)&dt, sizeof(float2) * M, nullptr)) != DOCK_OK) return s;
-        if ((s = dalloc(ctx, (void **)&dq, sizeof(float2) * (M / 2), nullptr)) != DOCK_OK) return s;
-        if ((s = dalloc(ctx, (void **)&dd, sizeof(double2) * M, nullptr)) != DOCK_OK) return s;
-        CK(ctx, cudaMemcpy(dt, t.data(), sizeof(float2) * M, cudaMemcpyHostToDevice));
-        CK(ctx, cudaMemcpy(dq, q.data(), sizeof(float2) * (M / 2), cudaMemcpyHostToDevice));
-        CK(ctx, cudaMemcpy(dd, td.data(), sizeof(double2) * M, cudaMemcpyHostToDevice));
+        // a failure part way releases what this call allocated
+        auto release = [&] {
+            dfree(ctx, dt, sizeof(float2) * M);
+            dfree(ctx, dq, sizeof(float2) * (M / 2));
+            dfree(ctx, dd, sizeof(double2) * M);
+        };
+        dock_status s = dalloc(ctx, (void **)&dt, sizeof(float2) * M, nullptr);
+        if (s == DOCK_OK) s = dalloc(ctx, (void **)&dq, sizeof(float2) * (M / 2), nullptr);
+        if (s == DOCK_OK) s = dalloc(ctx, (void **)&dd, sizeof(double2) * M, nullptr);
+        if (s != DOCK_OK) {
+            release();
+            return s;
+        }
+        cudaError_t e = cudaMemcpy(dt, t.data(), sizeof(float2) * M, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(dq, q.data(), sizeof(float2) * (M / 2), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(dd, td.data(), sizeof(double2) * M, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            release();
+            return cuda_fail(ctx, e, "uploading the twiddle tables");
+        }
         ctx->tw[M] = dt;
         ctx->qt[M] = dq;
         ctx->twd[M] = dd;
@@ -1896,6 +1918,23 @@ extern "C" dock_status dock_get_tuning(dock_ctx *ctx, int32_t N, dock_tuning *ou
     g.M = 2 * N;
     g.P = N + 2;
     *out = tuning_for(ctx, g);
+    return DOCK_OK;
+}
+
+extern "C" dock_status dock_memory_stats(dock_ctx *ctx, size_t *held, size_t *peak, size_t *budget)
+{
+    if (!ctx) return DOCK_E_INVALID;
+    DevLock dev_lock_(ctx);
+    if (held) *held = ctx->held;
+    if (peak) *peak = ctx->peak_held;
+    if (budget) *budget = ctx->budget;
+    return DOCK_OK;
+}
+
+extern "C" dock_status dock_fail_allocation(dock_ctx *ctx, int32_t n)
+{
+    if (!ctx || n < 0) return DOCK_E_INVALID;
+    ctx->fail_alloc.store(n);
     return DOCK_OK;
 }
 

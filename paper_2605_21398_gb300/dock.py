@@ -136,6 +136,9 @@ SIGNATURES = [
     ("dock_load_tuning", _st, [_vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32)]),
     ("dock_get_tuning", _st, [_vp, ctypes.c_int32, ctypes.POINTER(Tuning)]),
     ("dock_set_tuning", _st, [_vp, ctypes.POINTER(Tuning)]),
+    ("dock_memory_stats", _st, [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
+                                ctypes.POINTER(ctypes.c_size_t)]),
+    ("dock_fail_allocation", _st, [_vp, ctypes.c_int32]),
     ("dock_set_profiling", _st, [_vp, ctypes.c_int]),
     ("dock_get_kernel_stats", ctypes.c_int32, [_vp, ctypes.POINTER(KernelStat), ctypes.c_int32]),
     ("dock_reset_kernel_stats", None, [_vp]),
@@ -355,6 +358,16 @@ class Context:
         t = Tuning()
         self.check(lib().dock_get_tuning(self.h, N, ctypes.byref(t)))
         return tuning_dict(t)
+
+    def memory_stats(self):
+        """(held, peak, budget) device bytes of the context and its handles."""
+        h, p, b = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+        self.check(lib().dock_memory_stats(self.h, ctypes.byref(h), ctypes.byref(p), ctypes.byref(b)))
+        return h.value, p.value, b.value
+
+    def fail_allocation(self, n):
+        """Host fault injection: the n-th device allocation from now on fails (0 = off)."""
+        self.check(lib().dock_fail_allocation(self.h, n))
 
     def set_tuning(self, **shape):
         """Sets the launch shape of lattice side shape['N'] (other keys as get_tuning)."""
