@@ -146,60 +146,57 @@ k_plane_cl(const float2 *__restrict__ Z, const float2 *__restrict__ tw, const Ro
     auto blk = [&](int q) -> int { return q == rank ? rank * BLK : (CL + (q < rank ? q : q - 1)) * BLK; };
 
     // ---- phase 1: inverse FFT along y of my packed columns ----------------
+    // both rounds of 16 columns at once (NR = CPC / 16): every load of the
+    // CTA in flight together, one barrier for the stage exchange
     {
+        constexpr int NR = CPC / 16;
         const int c = tid & 15, j = tid >> 4;
-        cf t1[16];   // exp(+2 pi i j r / 256), r < 16: the stage-1 twiddles of this thread
-#pragma unroll
-        for (int r = 1; r < 16; ++r) t1[r] = twc_inv(j * r);
         int boff[CL];   // indexed by compile-time row blocks only
 #pragma unroll
         for (int q = 0; q < CL; ++q) boff[q] = blk(q);
-        // the columns of round rr: ky = j + 16 s of packed column rank CPC + 16 rr + c
-        auto load_round = [&](int rr, cf *v) {
+        cf v[NR][16];
+#pragma unroll
+        for (int rr = 0; rr < NR; ++rr) {
+            // ky = j + 16 s of packed column rank CPC + 16 rr + c
             const int kx = rank * CPC + rr * 16 + c;
 #pragma unroll
             for (int s = 0; s < 16; ++s) {
                 const float2 a = __ldcs(&Zp[(j + 16 * s) * P + kx]);
-                v[s] = cmake(a.x, a.y);
+                v[rr][s] = cmake(a.x, a.y);
             }
             if (kx == 0) {   // + i * Z[ky][M/2]
 #pragma unroll
                 for (int s = 0; s < 16; ++s) {
                     const float2 u = __ldcs(&Zp[(j + 16 * s) * P + H]);
-                    v[s] = cmake(v[s].x - u.y, v[s].y + u.x);
+                    v[rr][s] = cmake(v[rr][s].x - u.y, v[rr][s].y + u.x);
                 }
             }
-        };
-        constexpr int NR = CPC / 16;
-        cf v[16], nxt[16];
-        load_round(0, v);
+        }
 #pragma unroll
         for (int rr = 0; rr < NR; ++rr) {
-            const int col = rr * 16 + c;
-            if (rr + 1 < NR) load_round(rr + 1, nxt);   // in flight during this round
             // stage 0: DFT over ky = j + 16 s; output r is index 16 j + r
-            DFT<16, true>::run(v);
-            {
-                cf *bq = A + blk((16 * j) >> LR) + col * RPC + ((16 * j) & (RPC - 1));
+            const int col = rr * 16 + c;
+            DFT<16, true>::run(v[rr]);
+            cf *bq = A + blk((16 * j) >> LR) + col * RPC + ((16 * j) & (RPC - 1));
 #pragma unroll
-                for (int r = 0; r < 16; ++r) bq[r ^ c] = v[r];
-            }
-            __syncthreads();
+            for (int r = 0; r < 16; ++r) bq[r ^ c] = v[rr][r];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int rr = 0; rr < NR; ++rr) {
             // stage 1: inputs j + 16 r, twiddles exp(+2 pi i j r / 256), DFT;
             // output r is row y = j + 16 r, stored where it was read
+            const int col = rr * 16 + c;
             cf *b1 = A + col * RPC + (j ^ c);
             auto at1 = [&](int r) -> cf * { return b1 + boff[(16 * r) >> LR] + ((16 * r) & (RPC - 1)); };
+            cf w[16];
 #pragma unroll
-            for (int r = 0; r < 16; ++r) v[r] = *at1(r);
+            for (int r = 0; r < 16; ++r) w[r] = *at1(r);
 #pragma unroll
-            for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], t1[r]);
-            DFT<16, true>::run(v);
+            for (int r = 1; r < 16; ++r) w[r] = cmul(w[r], twc_inv(j * r));
+            DFT<16, true>::run(w);
 #pragma unroll
-            for (int r = 0; r < 16; ++r) *at1(r) = v[r];
-            if (rr + 1 < NR) {
-#pragma unroll
-                for (int s = 0; s < 16; ++s) v[s] = nxt[s];
-            }
+            for (int r = 0; r < 16; ++r) *at1(r) = w[r];
         }
     }
     // ---- push: X[q] -> CTA q's A[rank] -------------------------------------
@@ -235,30 +232,21 @@ k_plane_cl(const float2 *__restrict__ Z, const float2 *__restrict__ tw, const Ro
     }
 
     // ---- phase 2: C2R along x of my rows, argmax ---------------------------
-    // element (kx, row y) of A: kx RPC + (y mod RPC) ^ (kx mod 16)
+    // element (kx, row y) of A: kx RPC + (y mod RPC) ^ (kx mod 16); both rounds
+    // of 32 rows at once (NRR = RPC / 32), one barrier per exchange
     {
-        const int rowl = tid & 31, j = tid >> 5;
-        // twiddles of this thread (j < 8): exp(+2 pi i k / 256) for k = j + 8 s
-        // (pre-processing), exp(+2 pi i 2 jj r / 256) for jj = j + 8 bb, r < 8
-        // (stage 1)
-        cf tp[16], ts[2][8];
-#pragma unroll
-        for (int s = 0; s < 16; ++s) tp[s] = twc_inv(j + 8 * s);
-#pragma unroll
-        for (int bb = 0; bb < 2; ++bb)
-#pragma unroll
-            for (int r = 1; r < 8; ++r) ts[bb][r] = twc_inv(2 * (j + 8 * bb) * r);
+        constexpr int NRR = RPC / 32;
+        const int rowl = tid & 31, j = tid >> 5;   // j is warp-uniform: the twiddle reads broadcast
         float best = -INFINITY;
         uint32_t bidx = 0xFFFFFFFFu;
-#pragma unroll 1
-        for (int rr = 0; rr < RPC / 32; ++rr) {
-            const int y = rank * RPC + rr * 32 + rowl;
-            const int ylo = y & (RPC - 1);
+        cf v[NRR][16];
+#pragma unroll
+        for (int rr = 0; rr < NRR; ++rr) {
+            const int ylo = (rank * RPC + rr * 32 + rowl) & (RPC - 1);
             // k = j + 8 s has k mod 16 = j + 8 (s mod 2); H - k has
             // (16 - j - 8 (s mod 2)) mod 16
             const cf *pk[2] = {A + j * RPC + (ylo ^ j), A + j * RPC + (ylo ^ (j + 8))};
             const cf *pm[2] = {A + (H - j) * RPC + (ylo ^ ((16 - j) & 15)), A + (H - j) * RPC + (ylo ^ ((8 - j) & 15))};
-            cf v[16];
 #pragma unroll
             for (int s = 0; s < 16; ++s) {
                 cf Wk, Wm;
@@ -272,49 +260,57 @@ k_plane_cl(const float2 *__restrict__ Z, const float2 *__restrict__ tw, const Ro
                 }
                 const cf wc = cconj(Wm);
                 const cf Ek = cadd(Wk, wc);
-                const cf Ok = cmul(csub(Wk, wc), tp[s]);   // exp(+2 pi i k / M)
-                v[s] = cmake(Ek.x - Ok.y, Ek.y + Ok.x);                // E + i O
+                const cf Ok = cmul(csub(Wk, wc), twc_inv(j + 8 * s));   // exp(+2 pi i k / M)
+                v[rr][s] = cmake(Ek.x - Ok.y, Ek.y + Ok.x);             // E + i O
             }
-            __syncthreads();   // every W of these rows is in registers
-            // stage 0 (radix 16 over k = j + 8 s): output r to index 16 j + r
-            DFT<16, true>::run(v);
-            {
-                cf *b0 = A + 16 * j * RPC;
+        }
+        __syncthreads();   // every W of these rows is in registers
 #pragma unroll
-                for (int r = 0; r < 16; ++r) b0[r * RPC + (ylo ^ r)] = v[r];
-            }
-            __syncthreads();
+        for (int rr = 0; rr < NRR; ++rr) {
+            // stage 0 (radix 16 over k = j + 8 s): output r to index 16 j + r
+            const int ylo = (rank * RPC + rr * 32 + rowl) & (RPC - 1);
+            DFT<16, true>::run(v[rr]);
+            cf *b0 = A + 16 * j * RPC;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) b0[r * RPC + (ylo ^ r)] = v[rr][r];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int rr = 0; rr < NRR; ++rr) {
+            const int y = rank * RPC + rr * 32 + rowl;
+            const int ylo = y & (RPC - 1);
             // stage 1 (radix 8): butterfly jj = j + 8 bb reads jj + 16 r,
             // twiddles exp(+2 pi i 2 jj r / 256); output r is pair n = jj + 16 r
+            cf w[16];
 #pragma unroll
             for (int bb = 0; bb < 2; ++bb) {
                 const int jj = j + 8 * bb;
                 const cf *b1 = A + jj * RPC + (ylo ^ jj);
 #pragma unroll
-                for (int r = 0; r < 8; ++r) v[bb * 8 + r] = b1[16 * r * RPC];
+                for (int r = 0; r < 8; ++r) w[bb * 8 + r] = b1[16 * r * RPC];
 #pragma unroll
-                for (int r = 1; r < 8; ++r) v[bb * 8 + r] = cmul(v[bb * 8 + r], ts[bb][r]);
-                DFT<8, true>::run(v + bb * 8);
+                for (int r = 1; r < 8; ++r) w[bb * 8 + r] = cmul(w[bb * 8 + r], twc_inv(2 * jj * r));
+                DFT<8, true>::run(w + bb * 8);
             }
             const uint32_t rowbase = ((uint32_t)zc * M + (uint32_t)y) * M;
             if (EXPORT) {
 #pragma unroll
                 for (int s = 0; s < 16; ++s) {
                     const uint32_t base = rowbase + 2u * (uint32_t)(j + 8 * (s >> 3) + 16 * (s & 7));
-                    Cout[base] = v[s].x;
-                    Cout[base + 1] = v[s].y;
+                    Cout[base] = w[s].x;
+                    Cout[base + 1] = w[s].y;
                 }
             } else {
-                float m = v[0].x;
+                float m = w[0].x;
 #pragma unroll
-                for (int s = 0; s < 16; ++s) m = fmaxf(m, fmaxf(v[s].x, v[s].y));
+                for (int s = 0; s < 16; ++s) m = fmaxf(m, fmaxf(w[s].x, w[s].y));
                 if (m >= best) {
                     uint32_t bi = 0xFFFFFFFFu;
 #pragma unroll
                     for (int s = 0; s < 16; ++s) {
                         const uint32_t base = rowbase + 2u * (uint32_t)(j + 8 * (s >> 3) + 16 * (s & 7));
-                        if (v[s].x == m) bi = min(bi, base);
-                        if (v[s].y == m) bi = min(bi, base + 1u);
+                        if (w[s].x == m) bi = min(bi, base);
+                        if (w[s].y == m) bi = min(bi, base + 1u);
                     }
                     if (m > best || bi < bidx) {
                         best = m;
@@ -358,7 +354,7 @@ k_plane_cl(const float2 *__restrict__ Z, const float2 *__restrict__ tw, const Ro
 // output is in the inverse's input order, and both transforms exchange
 // between their radix-16 stages through one [256][16] buffer.  The block's
 // spectrum tile [kz][16] sits in shared memory (reloaded when the request
-// changes), the stage twiddles of the thread in registers.
+// changes), the stage twiddles come from the constant bank.
 // ---------------------------------------------------------------------------
 struct Zpass16Cfg {
     static constexpr int M = 256, N = 128, P = 130, NT = 256, COLS = 16;
@@ -378,12 +374,6 @@ k_zpass16(int B, int group, const float2 *__restrict__ Y, const RotRec *rots, co
     const int f0 = blockIdx.x * COLS;            // first column of the block
     const int b0 = blockIdx.y * group, nb = min(group, B - b0);
     if (nb <= 0) return;
-    cf tw1[16];                                  // exp(-2 pi i j r / 256)
-#pragma unroll
-    for (int r = 1; r < 16; ++r) {
-        const float2 w = c_tw256[(j * r) & 255];
-        tw1[r] = cmake(w.x, w.y);
-    }
     auto load = [&](int bi, cf *v) {
         const float2 *src = Y + (size_t)(b0 + bi) * N * plane + f0 + c;
 #pragma unroll
@@ -426,7 +416,7 @@ k_zpass16(int B, int group, const float2 *__restrict__ Y, const RotRec *rots, co
 #pragma unroll
         for (int r = 0; r < 16; ++r) v[r] = xb[(j + 16 * r) * COLS + c];
 #pragma unroll
-        for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], tw1[r]);
+        for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], cconj(twc_inv(j * r)));   // exp(-2 pi i j r / 256)
         DFT<16, false>::run(v);
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
@@ -443,7 +433,7 @@ k_zpass16(int B, int group, const float2 *__restrict__ Y, const RotRec *rots, co
 #pragma unroll
         for (int r = 0; r < 16; ++r) v[r] = xb[(j + 16 * r) * COLS + c];
 #pragma unroll
-        for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], cconj(tw1[r]));
+        for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], twc_inv(j * r));
         DFT<16, true>::run(v);
         float2 *dst = Z + (size_t)(b0 + bi) * M * plane + f0 + c;
 #pragma unroll

@@ -385,6 +385,15 @@ __device__ int dist_query(const RefineDev &D, const float *A, const float *bvec,
     int qt[QN];
     float ql[QN];
     int nq = 0;
+    // triangles that passed Eq. (21) and the lower-bound test during the
+    // traversal, kept in increasing lower-bound order; their first-order tests
+    // and searches run after the traversal, slot by slot across the warp (the
+    // lanes of a slot in lockstep), and a smaller minimum found early prunes
+    // the later ones
+    constexpr int QC = 16;
+    int ct[QC];
+    float cl[QC];
+    int nc = 0;
     const float eps = D.tau_out;
     float UB = valid ? INFINITY : -INFINITY;     // a lane without a pose needs nothing
     float best = INFINITY;
@@ -454,6 +463,17 @@ __device__ int dist_query(const RefineDev &D, const float *A, const float *bvec,
                     }
                     float lbt = cand ? lin_lower_bound(lv, D.r, D.L) : INFINITY;
                     if (cand && lbt > fminf(UB, best)) cand = false;
+                    if (cand && nc < QC) {
+                        int k = nc++;
+                        while (k > 0 && cl[k - 1] > lbt) {   // insertion in lower-bound order
+                            ct[k] = ct[k - 1];
+                            cl[k] = cl[k - 1];
+                            --k;
+                        }
+                        ct[k] = t;
+                        cl[k] = lbt;
+                        cand = false;
+                    }
                     if (cand) {
                         float u, v, dk;
                         bool done = tri_min_shortcut(lv[0], lv[1], lv[2], fv, D.r, D.L, &dk, &u, &v);
@@ -499,6 +519,33 @@ __device__ int dist_query(const RefineDev &D, const float *A, const float *bvec,
                 } else if (anyr) {
                     sn[sp] = nd.right;
                     sl[sp++] = wr;
+                }
+            }
+        }
+    }
+    // queued triangles: first-order tests slot by slot (a triangle whose lower
+    // bound now exceeds the upper bound or the best minimum found cannot hold
+    // the minimum), the unsettled ones to the search queue
+    for (int s = 0; s < QC; ++s) {
+        bool has = s < nc && !(cl[s] > fminf(UB, best));
+        if (!__any_sync(0xFFFFFFFFu, has)) continue;
+        if (has) {
+            const int t = ct[s];
+            float lv[3][3], fv[3];
+            local_vertices(D, t, A, bvec, lv);
+            for (int m = 0; m < 3; ++m) fv[m] = sdf_cyl(lv[m][0], lv[m][1], lv[m][2], D.r, D.L, nullptr);
+            float u, v, dk;
+            bool done = tri_min_shortcut(lv[0], lv[1], lv[2], fv, D.r, D.L, &dk, &u, &v);
+            if (!done && nq < QN) {
+                qt[nq] = t;
+                ql[nq++] = cl[s];
+            } else {
+                if (!done) dk = tri_min_search(lv[0], lv[1], lv[2], D.r, D.L, D.tri_iters, &u, &v);
+                if (dk < best || (dk == best && t < bt)) {
+                    best = dk;
+                    bt = t;
+                    float w0 = 1.f - u - v;
+                    for (int c = 0; c < 3; ++c) bx[c] = fmaf(w0, lv[0][c], fmaf(u, lv[1][c], v * lv[2][c]));
                 }
             }
         }

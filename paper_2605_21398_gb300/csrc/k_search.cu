@@ -388,6 +388,10 @@ __device__ void voxelise_slab(const Geo &g, const RotRec &rr, const PoseRec *pos
         const float ibz = cap_ok ? 1.f / bx[2] : 0.f;
         const float rsAq = radial_ok ? rsqrtf(Aq) : 0.f;
         const float ez = cap_ok ? ELB * fabsf(ibz) : 0.f;   // cap crossings: error of l2 / |bz|
+        const float erq = ELB * rv * iAq;
+        // l0(jy) = B^T ((0, jy, jz) - c) = B_y^T jy + base: one FMA per coordinate per row
+        float lbase[3];
+        for (int k = 0; k < 3; ++k) lbase[k] = fmaf(B[0 * 3 + k], -c[0], fmaf(B[1 * 3 + k], -c[1], B[2 * 3 + k] * (fz - c[2])));
         for (int jy = Y0; jy <= Y1; ++jy) {
             const bool act = hit && jy >= y0 && jy <= y1;
             int st = 0;            // 0: nothing, 1: exact interval [ia, ib], 2: walk voxel by voxel, 3: few candidates
@@ -395,8 +399,7 @@ __device__ void voxelise_slab(const Geo &g, const RotRec &rr, const PoseRec *pos
             int qa = 0, qb = -1;   // st 3: the candidate voxels
             float l0[3];
             if (act) {
-                const float dyv = (float)jy - c[1], dzv = fz - c[2], dxv = -c[0];
-                for (int k = 0; k < 3; ++k) l0[k] = fmaf(B[0 * 3 + k], dxv, fmaf(B[1 * 3 + k], dyv, B[2 * 3 + k] * dzv));
+                for (int k = 0; k < 3; ++k) l0[k] = fmaf(B[1 * 3 + k], (float)jy, lbase[k]);
                 if (!radial_ok) {
                     st = 2;
                 } else {
@@ -406,11 +409,14 @@ __device__ void voxelise_slab(const Geo &g, const RotRec &rr, const PoseRec *pos
                     const float Cs = fmaf(sa, sa, sb * sb) - rv2;
                     const float disc = -Aq * Cs;
                     if (disc > 0.f) {
-                        const float hw = sqrtf(disc) * iAq;
+                        // (the rounding of an approximate square root and
+                        // reciprocal, a few ulp, is far inside the 1e-5
+                        // relative term added to E below)
+                        const float hw = disc * rsqrtf(disc) * iAq;
                         float lo = js - hw, hi = js + hw;
                         // error of the chord ends: a radius error dl moves a crossing
                         // by about dl rv / (Aq hw), the nearest point by dl / sqrt(Aq)
-                        float E = ELB * (rv * iAq / hw + rsAq);
+                        float E = fmaf(erq, __frcp_rn(hw), ELB * rsAq);
                         bool empty = false, unsure = false;
                         if (cap_ok) {
                             const float za = -l0[2] * ibz, zb = (lv - l0[2]) * ibz;
