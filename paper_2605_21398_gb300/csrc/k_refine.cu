@@ -130,6 +130,23 @@ __device__ __noinline__ void witness_subgradient(const float *x, const float lv[
     for (int i = 0; i < 3; ++i) n[i] = fmaf(lm, a[i], (1.f - lm) * b[i]);
 }
 
+// A number with the sign of g . e, g the subgradient sdf_cyl reports at
+// (x, y, z) (same branch rules), without normalising g: the bisections need
+// only the sign of the directional derivative.
+__device__ __forceinline__ float sdf_slope_sign(float x, float y, float z, float r, float L, const float *e)
+{
+    const float r2 = fmaf(x, x, y * y);
+    const float ri = r2 > 0.f ? rsqrtf(r2) : 0.f;
+    const float rho = r2 * ri;
+    const float se = r2 > 0.f ? fmaf(x, e[0], y * e[1]) : e[0];   // rho (u . e_xy), u = +x on the axis
+    const float dr = rho - r, zlo = -z, zhi = z - L;
+    const float dz = zlo >= zhi ? zlo : zhi;
+    const float ce = zlo >= zhi ? -e[2] : e[2];                    // cz e_z
+    if (dr <= 0.f && dz <= 0.f) return dr > dz ? se : ce;
+    if (dr > 0.f && dz > 0.f) return fmaf(dr * se, r2 > 0.f ? ri : 1.f, dz * ce);
+    return dr > 0.f ? se : ce;
+}
+
 // f_p is differentiable at x: everywhere outside the probe; inside, away
 // (by more than 1e-3 mm) from the medial surfaces where two branches meet
 // and from the axis.
@@ -151,15 +168,14 @@ __device__ __noinline__ float inner_min(const float *v0, const float *e1, const 
                                         int iters, float *v_out)
 {
     const float vmax = fmaxf(0.f, 1.f - u);
-    float x[3], g[3];
+    float x[3];
     for (int a = 0; a < 3; ++a) x[a] = fmaf(u, e1[a], v0[a]);
     float lo = 0.f, hi = vmax;
     for (int k = 0; k < iters; ++k) {
         float mid = 0.5f * (lo + hi);
         float xm[3];
         for (int a = 0; a < 3; ++a) xm[a] = fmaf(mid, e2[a], x[a]);
-        sdf_cyl(xm[0], xm[1], xm[2], r, L, g);
-        if (dot3f(g, e2) < 0.f) lo = mid; else hi = mid;
+        if (sdf_slope_sign(xm[0], xm[1], xm[2], r, L, e2) < 0.f) lo = mid; else hi = mid;
     }
     float v = 0.5f * (lo + hi);
     for (int a = 0; a < 3; ++a) x[a] = fmaf(v, e2[a], x[a]);
@@ -224,17 +240,13 @@ __device__ bool tri_min_shortcut(const float *v0, const float *v1, const float *
         for (int k = 0; k < 3; ++k) {
             const float *pa = vv[k], *pb = vv[(k + 1) % 3], *po = vv[(k + 2) % 3];
             float e[3] = {pb[0] - pa[0], pb[1] - pa[1], pb[2] - pa[2]};
-            float ga[3], gb[3];
-            sdf_cyl(pa[0], pa[1], pa[2], r, L, ga);
-            if (dot3f(ga, e) >= 0.f) continue;       // f grows along the edge from pa
-            sdf_cyl(pb[0], pb[1], pb[2], r, L, gb);
-            if (dot3f(gb, e) <= 0.f) continue;       // f falls all the way to pb
+            if (sdf_slope_sign(pa[0], pa[1], pa[2], r, L, e) >= 0.f) continue;   // f grows along the edge from pa
+            if (sdf_slope_sign(pb[0], pb[1], pb[2], r, L, e) <= 0.f) continue;   // f falls all the way to pb
             float lo = 0.f, hi = 1.f;
             for (int it = 0; it < 24; ++it) {
-                float mid = 0.5f * (lo + hi), xm[3], gm[3];
+                float mid = 0.5f * (lo + hi), xm[3];
                 for (int c = 0; c < 3; ++c) xm[c] = fmaf(mid, e[c], pa[c]);
-                sdf_cyl(xm[0], xm[1], xm[2], r, L, gm);
-                if (dot3f(gm, e) < 0.f) lo = mid; else hi = mid;
+                if (sdf_slope_sign(xm[0], xm[1], xm[2], r, L, e) < 0.f) lo = mid; else hi = mid;
             }
             float s = 0.5f * (lo + hi), x[3], gx[3];
             for (int c = 0; c < 3; ++c) x[c] = fmaf(s, e[c], pa[c]);
