@@ -436,6 +436,8 @@ typedef struct dock_tuning {
                                 0 = the default; other canvases use one fixed shape) */
     int32_t zpass_cols;      /* columns per z-pass block (canvas 256 only: 16 or 32; 0 = the default;
                                 the label-aware score always uses 32) */
+    int32_t vox_overlap;     /* 1: the voxeliser of the next launch runs on a second stream, overlapped
+                                with the FFT passes of the current one (plain score); 0: in order */
     double us_per_rotation;  /* measured device time per rotation of this shape (0 = not measured) */
 } dock_tuning;
 
@@ -458,8 +460,8 @@ DOCK_API dock_status dock_load_tuning(dock_ctx *ctx, const char *cache_path, int
 /* The shape in use for lattice side N (tuned or default). */
 DOCK_API dock_status dock_get_tuning(dock_ctx *ctx, int32_t N, dock_tuning *out);
 /* Sets the shape for lattice side t->N (batch 1..256, group 0..256,
- * vox_blocks 3 or 4, plane_cl 0, 2, 4 or 8, zpass_cols 0, 16 or 32); results
- * do not depend on it.
+ * vox_blocks 3 or 4, plane_cl 0, 2, 4 or 8, zpass_cols 0, 16 or 32,
+ * vox_overlap 0 or 1); results do not depend on it.
  * DOCK_E_INVALID for values out of range. */
 DOCK_API dock_status dock_set_tuning(dock_ctx *ctx, const dock_tuning *t);
 

@@ -97,6 +97,10 @@ struct dock_ctx {
     double *quats = nullptr;
     size_t quats_n = 0;
     int *errflag = nullptr;
+    // the voxeliser of the next launch overlapped with the FFT passes of the
+    // current one: its own stream, double-buffered bits, ordering events
+    cudaStream_t vstream = nullptr;
+    cudaEvent_t vev[5] = {};   // 0, 1: bits[k] written; 2, 3: bits[k] read by fwd2d; 4: entry
     dock_candidate *cands = nullptr;
     size_t cands_n = 0;
     ReqDev *reqs = nullptr;   // request table of the current search launches
@@ -526,6 +530,9 @@ void dock_destroy(dock_ctx *c)
     cudaFree(c->cands);
     cudaFree(c->reqs);
     cudaFree(c->phase);
+    for (auto e : c->vev)
+        if (e) cudaEventDestroy(e);
+    if (c->vstream) cudaStreamDestroy(c->vstream);
     free_refbufs(c->ref);
     for (auto &kv : c->tw) cudaFree(kv.second);
     for (auto &kv : c->qt) cudaFree(kv.second);
@@ -1363,6 +1370,10 @@ static dock_status check_pair(dock_ctx *ctx, const dock_object *ob, const dock_s
 // canvas 256 when untuned.
 static const int PLANE_CL_DEFAULT = 4;
 static const int ZPASS_COLS_DEFAULT = 16;
+// Off by default: overlapped, the voxeliser and the FFT passes slow each other
+// (both fill the register file), 1 % faster in all at 128^3, and per-kernel
+// event times then overlap.
+static const int VOX_OVERLAP_DEFAULT = 0;
 
 static dock_tuning tuning_for(dock_ctx *ctx, const Geo &g)
 {
@@ -1375,6 +1386,7 @@ static dock_tuning tuning_for(dock_ctx *ctx, const Geo &g)
     t.vox_blocks = 4;
     t.plane_cl = g.M == 256 ? PLANE_CL_DEFAULT : 0;
     t.zpass_cols = g.M == 256 ? ZPASS_COLS_DEFAULT : 0;
+    t.vox_overlap = VOX_OVERLAP_DEFAULT;
     return t;
 }
 
@@ -1383,7 +1395,8 @@ static bool valid_tuning(const dock_tuning &t)
     return valid_N(t.N) && t.batch >= 1 && t.batch <= 256 && t.group >= 0 && t.group <= 256 &&
            (t.vox_blocks == 3 || t.vox_blocks == 4) &&
            (t.plane_cl == 0 || t.plane_cl == 2 || t.plane_cl == 4 || t.plane_cl == 8) &&
-           (t.zpass_cols == 0 || t.zpass_cols == 16 || t.zpass_cols == 32);
+           (t.zpass_cols == 0 || t.zpass_cols == 16 || t.zpass_cols == 32) &&
+           (t.vox_overlap == 0 || t.vox_overlap == 1);
 }
 
 // Runs records [r0, r1) of rots through the search pipeline; every
@@ -1415,21 +1428,48 @@ static dock_status run_pipeline_rots(dock_ctx *ctx, const Geo &g, const ReqDev *
     }
     float2 *Y = ctx->Y, *Z = ctx->Y + ysz, *Y2 = dual ? ctx->Y + ysz + zsz : nullptr;
     const size_t bsz = (size_t)B * g.N * g.N * (g.N / 32);
-    if ((s = ensure(ctx, (void **)&ctx->bits, &ctx->bits_n, dual ? 2 * bsz : bsz, sizeof(uint32_t))) != DOCK_OK)
+    // Overlap: the voxeliser of batch k + 1 runs on a second stream while the
+    // FFT passes of batch k run (the voxeliser moves no data and is bound by
+    // instruction issue, the FFT passes by latency); bits double-buffered,
+    // batch k's bits released once its fwd2d has read them.
+    const int nbatch = (int)((r1 - r0 + B - 1) / B);
+    const bool ovl = tc.vox_overlap && !dual && nbatch > 1;
+    if ((s = ensure(ctx, (void **)&ctx->bits, &ctx->bits_n, (dual || ovl) ? 2 * bsz : bsz, sizeof(uint32_t))) !=
+        DOCK_OK)
         return s;
     uint32_t *bits2 = dual ? ctx->bits + bsz : nullptr;
+    if (ovl) {
+        if (!ctx->vstream) CK(ctx, cudaStreamCreateWithFlags(&ctx->vstream, cudaStreamNonBlocking));
+        for (auto &e : ctx->vev)
+            if (!e) CK(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        // everything enqueued before (rotation records, request table, the
+        // previous users of the bits) precedes this call's voxelisations
+        CK(ctx, cudaEventRecord(ctx->vev[4], ctx->stream));
+        CK(ctx, cudaStreamWaitEvent(ctx->vstream, ctx->vev[4], 0));
+    }
     if (ro_any &&
         (s = ensure(ctx, (void **)&ctx->ogr, &ctx->ogr_n, (size_t)B * g.N * g.N * g.N, sizeof(float))) != DOCK_OK)
         return s;
     int chunks = g.M * g.P / 32;
-    for (size_t b0 = r0; b0 < r1; b0 += B) {
+    int k = 0;
+    for (size_t b0 = r0; b0 < r1; b0 += B, ++k) {
         int nb = (int)std::min<size_t>(B, r1 - b0);
         int groups_needed = (2 * 152 + chunks - 1) / chunks;
         int group = tc.group > 0 ? std::min(tc.group, nb) : std::max(1, nb / groups_needed);
         const RotRec *rb = rots + b0;
-        {
+        const int kb = k & 1;
+        uint32_t *bk = ovl ? ctx->bits + kb * bsz : ctx->bits;
+        if (ovl) {
+            if (k >= 2) CK(ctx, cudaStreamWaitEvent(ctx->vstream, ctx->vev[2 + kb], 0));   // fwd2d(k - 2) read bk
+            {
+                Prof pr(ctx, "voxelise", ctx->vstream);
+                CK(ctx, launch_voxelise(g, reqs, rb, nb, bk, ctx->vstream, tc.vox_blocks));
+            }
+            CK(ctx, cudaEventRecord(ctx->vev[kb], ctx->vstream));
+            CK(ctx, cudaStreamWaitEvent(ctx->stream, ctx->vev[kb], 0));
+        } else {
             Prof pr(ctx, "voxelise");
-            CK(ctx, launch_voxelise(g, reqs, rb, nb, ctx->bits, ctx->stream, tc.vox_blocks));
+            CK(ctx, launch_voxelise(g, reqs, rb, nb, bk, ctx->stream, tc.vox_blocks));
         }
         if (dual) {
             Prof pr(ctx, "voxelise_nc");
@@ -1441,9 +1481,9 @@ static dock_status run_pipeline_rots(dock_ctx *ctx, const Geo &g, const ReqDev *
         }
         {
             Prof pr(ctx, "fwd2d");
-            CK(ctx, launch_fwd2d(g, nb, ctx->bits, Y, tw, qt, ctx->stream, nullptr, rb, reqs,
-                                 ro_any ? ctx->ogr : nullptr));
+            CK(ctx, launch_fwd2d(g, nb, bk, Y, tw, qt, ctx->stream, nullptr, rb, reqs, ro_any ? ctx->ogr : nullptr));
         }
+        if (ovl) CK(ctx, cudaEventRecord(ctx->vev[2 + kb], ctx->stream));
         if (dual) {
             Prof pr(ctx, "fwd2d_nc");
             CK(ctx, launch_fwd2d(g, nb, bits2, Y2, tw, qt, ctx->stream, ctx->bits, rb, reqs));
@@ -1760,8 +1800,9 @@ static dock_status write_tuning(dock_ctx *ctx, const char *path)
         const dock_tuning &t = kv.second;
         fprintf(f,
                 "%s\n  {\"N\": %d, \"batch\": %d, \"group\": %d, \"vox_blocks\": %d, \"plane_cl\": %d, "
-                "\"zpass_cols\": %d, \"us_per_rotation\": %.3f}",
-                first ? "" : ",", t.N, t.batch, t.group, t.vox_blocks, t.plane_cl, t.zpass_cols, t.us_per_rotation);
+                "\"zpass_cols\": %d, \"vox_overlap\": %d, \"us_per_rotation\": %.3f}",
+                first ? "" : ",", t.N, t.batch, t.group, t.vox_blocks, t.plane_cl, t.zpass_cols, t.vox_overlap,
+                t.us_per_rotation);
         first = false;
     }
     fprintf(f, "\n]}\n");
@@ -1893,6 +1934,9 @@ extern "C" dock_status dock_load_tuning(dock_ctx *ctx, const char *path, int32_t
             long zc = 0;
             t.zpass_cols =
                 json_int(e.c_str(), "\"zpass_cols\"", &zc) ? (int)zc : (gt.M == 256 ? ZPASS_COLS_DEFAULT : 0);
+            long vo = VOX_OVERLAP_DEFAULT;
+            json_int(e.c_str(), "\"vox_overlap\"", &vo);
+            t.vox_overlap = (int)vo;
             if (!valid_tuning(t)) {
                 pos = end;
                 continue;
@@ -2423,6 +2467,7 @@ extern "C" dock_status dock_distances(dock_ctx *ctx, const dock_object *ob, cons
 // ---------------------------------------------------------------------------
 constexpr int ENGINE_SLOTS = 64;   // jobs admitted at once
 constexpr int ENGINE_MIN_SHARE = 16;
+constexpr int PASS_BATCHES = 4;    // launch batches per pass (the voxeliser of one overlaps the FFT passes of another)
 
 enum JobStage { JOB_QUEUED, JOB_GLOBAL, JOB_LOCAL, JOB_DONE };
 
@@ -2891,7 +2936,8 @@ static bool engine_step(dock_ctx *ctx)
     for (auto &j : E.active)
         if (j->ob->N == pick && j->issued < j->s1 - j->s0) cls.push_back(j.get());
     const Geo g = make_geo(cls[0]->sw);
-    const int B = tuning_for(ctx, g).batch;
+    const int B1 = tuning_for(ctx, g).batch;   // rotations per launch
+    const int B = B1 * PASS_BATCHES;           // rotations per pass
     dock_status s;
     if ((s = ensure(ctx, (void **)&ctx->phase, &ctx->phase_n, (size_t)B, sizeof(RotRec))) != DOCK_OK) {
         for (auto &j : E.active)
@@ -2941,7 +2987,7 @@ static bool engine_step(dock_ctx *ctx)
         ro_any = ro_any || jp->ro;
     }
     if (ce != cudaSuccess) s = cuda_fail(ctx, ce, "gather of rotation records");
-    else s = run_pipeline_rots(ctx, g, E.reqtab, ctx->phase, 0, taken, B, dual, ro_any);
+    else s = run_pipeline_rots(ctx, g, E.reqtab, ctx->phase, 0, taken, B1, dual, ro_any);
     if (s == DOCK_OK) {
         cudaError_t e = cudaEventRecord(E.pass_ev[E.passes % 2], ctx->stream);
         if (e != cudaSuccess) s = cuda_fail(ctx, e, "recording a search pass");
