@@ -465,6 +465,18 @@ DOCK_API dock_status dock_get_tuning(dock_ctx *ctx, int32_t N, dock_tuning *out)
  * DOCK_E_INVALID for values out of range. */
 DOCK_API dock_status dock_set_tuning(dock_ctx *ctx, const dock_tuning *t);
 
+/* Test hook of failure detection (systems form; the paper has no
+ * counterpart): dock_search_scores with the cluster plane pass (canvas 256,
+ * plane_cl 4 or 8) launched so that no CTA receives its peers' blocks.  Every
+ * CTA's wait for them is bounded (about a second of clock cycles); it runs
+ * out, the kernel records DOCK_E_TIMEOUT in the context's error word and
+ * returns, and the call returns DOCK_E_TIMEOUT with C undefined.  No copy is
+ * in flight when a CTA gives up and the context stays usable.  quat: one
+ * unit quaternion; C: host, M^3 floats.  DOCK_E_INVALID for other canvases
+ * or plane shapes. */
+DOCK_API dock_status dock_test_plane_timeout(dock_ctx *ctx, const dock_object *obj, const dock_sweep *sweep,
+                                             const double *quat, float *C);
+
 /* --------------------------------------------------------------- profiling */
 
 /* Per-kernel CUDA-event timing on the context stream (off by default). */

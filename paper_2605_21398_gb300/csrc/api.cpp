@@ -1991,8 +1991,11 @@ extern "C" dock_status dock_set_tuning(dock_ctx *ctx, const dock_tuning *t)
     return DOCK_OK;
 }
 
-extern "C" dock_status dock_search_scores(dock_ctx *ctx, const dock_object *ob, const dock_sweep *sw, const double *quat,
-                                          float *C)
+// The full correlation field of one rotation (the search kernels with the
+// plane pass exporting every value).  withhold: the test hook of the bounded
+// wait of the cluster plane pass (its peers' blocks are never pushed).
+static dock_status search_scores_impl(dock_ctx *ctx, const dock_object *ob, const dock_sweep *sw, const double *quat,
+                                      float *C, int withhold)
 {
     if (!ctx || !ob || !sw || !quat || !C) return DOCK_E_INVALID;
     DevLock dev_lock_(ctx);
@@ -2040,7 +2043,9 @@ extern "C" dock_status dock_search_scores(dock_ctx *ctx, const dock_object *ob, 
             e = launch_zpass(g, 1, 1, Y, ctx->rots, ctx->reqs, Y + ysz, tw, ctx->stream, Y2);
     }
     if (e == cudaSuccess)
-        e = launch_plane_export(g, Y + ysz, tw, dC, ctx->stream, tuning_for(ctx, g).plane_cl, ctx->errflag);
+        e = withhold ? launch_plane_cl_export(g, tuning_for(ctx, g).plane_cl, Y + ysz, tw, dC, ctx->errflag,
+                                              ctx->stream, 1)
+                     : launch_plane_export(g, Y + ysz, tw, dC, ctx->stream, tuning_for(ctx, g).plane_cl, ctx->errflag);
     if (e == cudaSuccess) e = cudaMemcpyAsync(C, dC, csz * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
     int herr = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, ctx->errflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
@@ -2048,8 +2053,27 @@ extern "C" dock_status dock_search_scores(dock_ctx *ctx, const dock_object *ob, 
     dfree(ctx, Y, ybytes);
     dfree(ctx, dC, csz * sizeof(float));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "search_scores");
-    if (herr) return fail(ctx, herr, "device reported error %d during the search", herr);
+    if (herr) {
+        cudaMemsetAsync(ctx->errflag, 0, sizeof(int), ctx->stream);
+        return fail(ctx, herr, "device reported error %d during the search", herr);
+    }
     return DOCK_OK;
+}
+
+extern "C" dock_status dock_search_scores(dock_ctx *ctx, const dock_object *ob, const dock_sweep *sw, const double *quat,
+                                          float *C)
+{
+    return search_scores_impl(ctx, ob, sw, quat, C, 0);
+}
+
+extern "C" dock_status dock_test_plane_timeout(dock_ctx *ctx, const dock_object *ob, const dock_sweep *sw,
+                                               const double *quat, float *C)
+{
+    if (!ctx || !ob || !sw) return DOCK_E_INVALID;
+    Geo g = make_geo(sw);
+    if (!plane_cl_supported(g.M, tuning_for(ctx, g).plane_cl))
+        return fail(ctx, DOCK_E_INVALID, "the timeout hook needs the cluster plane pass (canvas 256, plane_cl 4 or 8)");
+    return search_scores_impl(ctx, ob, sw, quat, C, 1);
 }
 
 extern "C" dock_status dock_sample_so3(const dock_search_desc *d, double *quats)

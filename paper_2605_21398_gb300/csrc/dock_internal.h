@@ -103,8 +103,10 @@ cudaError_t launch_zpass16(const Geo &g, int B, int group, const float2 *Y, cons
 bool plane_cl_supported(int M, int cl);
 cudaError_t launch_plane_cl(const Geo &g, int cl, int B, const float2 *Z, const float2 *tw, const RotRec *rots,
                             const ReqDev *reqs, int *err, cudaStream_t st);
+// withhold = 1 (test hook): the peers' blocks are never pushed, so the
+// bounded waits run out and set err to DOCK_E_TIMEOUT.
 cudaError_t launch_plane_cl_export(const Geo &g, int cl, const float2 *Z, const float2 *tw, float *C, int *err,
-                                   cudaStream_t st);
+                                   cudaStream_t st, int withhold = 0);
 // o_s (nullable, device): the rotate_object pose T = (R, h dk + o_s - o_R);
 // else T = (R, R (h dk + o_s,R - o_o)).
 cudaError_t launch_topk(const unsigned long long *keys, int n, int K, int N, int M, double h, const double *o_o,

@@ -124,7 +124,7 @@ constexpr long long PLANE_WAIT_CYCLES = 1ll << 31;
 template <int CL, bool EXPORT>
 __global__ void __launch_bounds__(PlaneClCfg<CL>::NT, PlaneClCfg<CL>::MINB)
 k_plane_cl(const float2 *__restrict__ Z, const float2 *__restrict__ tw, const RotRec *rots, const ReqDev *reqs,
-           float *Cout, int *err)
+           float *Cout, int *err, int withhold)
 {
     using C = PlaneClCfg<CL>;
     constexpr int M = C::M, H = C::H, P = C::P, CPC = C::CPC, RPC = C::RPC, LR = C::LR, BLK = C::BLK;
@@ -202,7 +202,9 @@ k_plane_cl(const float2 *__restrict__ Z, const float2 *__restrict__ tw, const Ro
     // ---- push: X[q] -> CTA q's A[rank] -------------------------------------
     fence_proxy_async();
     cg::this_cluster().sync();
-    if (tid == 0) {
+    // withhold (test hook of the failure path): no block is pushed, so every
+    // CTA's bounded wait below runs out, reports DOCK_E_TIMEOUT and returns
+    if (tid == 0 && !withhold) {
         const uint32_t mb = smem_u32(mbar);
         const uint32_t dst = smem_u32(A + (size_t)rank * BLK);
 #pragma unroll 1
@@ -465,7 +467,7 @@ static cudaError_t ensure_twiddle_bank()
 
 template <int CL, bool EXPORT>
 static cudaError_t launch_plane_cl_t(int B, const float2 *Z, const float2 *tw, const RotRec *rots, const ReqDev *reqs,
-                                     float *Cout, int *err, cudaStream_t st)
+                                     float *Cout, int *err, cudaStream_t st, int withhold = 0)
 {
     using C = PlaneClCfg<CL>;
     auto kern = k_plane_cl<CL, EXPORT>;
@@ -487,7 +489,7 @@ static cudaError_t launch_plane_cl_t(int B, const float2 *Z, const float2 *tw, c
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, kern, Z, tw, rots, reqs, Cout, err);
+    e = cudaLaunchKernelEx(&cfg, kern, Z, tw, rots, reqs, Cout, err, withhold);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -519,11 +521,11 @@ cudaError_t launch_plane_cl(const Geo &g, int cl, int B, const float2 *Z, const 
 }
 
 cudaError_t launch_plane_cl_export(const Geo &g, int cl, const float2 *Z, const float2 *tw, float *C, int *err,
-                                   cudaStream_t st)
+                                   cudaStream_t st, int withhold)
 {
     if (!plane_cl_supported(g.M, cl)) return cudaErrorInvalidValue;
-    return cl == 4 ? launch_plane_cl_t<4, true>(1, Z, tw, nullptr, nullptr, C, err, st)
-                   : launch_plane_cl_t<8, true>(1, Z, tw, nullptr, nullptr, C, err, st);
+    return cl == 4 ? launch_plane_cl_t<4, true>(1, Z, tw, nullptr, nullptr, C, err, st, withhold)
+                   : launch_plane_cl_t<8, true>(1, Z, tw, nullptr, nullptr, C, err, st, withhold);
 }
 
 }  // namespace dock

@@ -139,6 +139,7 @@ SIGNATURES = [
     ("dock_memory_stats", _st, [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
                                 ctypes.POINTER(ctypes.c_size_t)]),
     ("dock_fail_allocation", _st, [_vp, ctypes.c_int32]),
+    ("dock_test_plane_timeout", _st, [_vp, _vp, _vp, _dp, _fp]),
     ("dock_set_profiling", _st, [_vp, ctypes.c_int]),
     ("dock_get_kernel_stats", ctypes.c_int32, [_vp, ctypes.POINTER(KernelStat), ctypes.c_int32]),
     ("dock_reset_kernel_stats", None, [_vp]),
@@ -251,6 +252,15 @@ class Context:
         peaks = (Peak * max(n, 1))()
         self.check(lib().dock_search_peaks_noalloc(self.h, obj.h, sw.h, q.ctypes.data_as(_dp), n, peaks))
         return np.array([(p.score, p.canvas_idx) for p in peaks[:n]], dtype=[("score", np.float32), ("idx", np.int64)])
+
+    def test_plane_timeout(self, obj, sw, quat):
+        """Runs the search of one rotation with the cluster plane pass's peer
+        blocks withheld (its bounded waits run out); raises DockError (E_TIMEOUT)."""
+        M = 2 * obj.N
+        C = np.empty((M, M, M), dtype=np.float32)
+        q, qp = _d(quat)
+        self.check(lib().dock_test_plane_timeout(self.h, obj.h, sw.h, qp, C.ctypes.data_as(_fp)))
+        return C
 
     def search_scores(self, obj, sw, quat):
         M = 2 * obj.N
