@@ -432,7 +432,8 @@ def run_ncu_case(variant="plain"):
     search kernel launches once with 8 rotations, a few GB on the device), then
     a refinement of 8 candidates near the planted pose.  variant: "plain", or
     the search with the rotated object ("rotate_object") or the label-aware
-    score ("label_aware")."""
+    score ("label_aware"), or the z pass with its DFT stages on the tensor
+    cores ("zpass_tc")."""
     from paper_2605_21398_gb300 import build, dock, synth
     build.build()
     w = synth.make_workload(WORKLOAD)
@@ -443,6 +444,8 @@ def run_ncu_case(variant="plain"):
         sw.set_rotate_object(True)
     elif variant == "label_aware":
         sw.set_label_aware(True)
+    elif variant == "zpass_tc":
+        ctx.set_tuning(N=w.N, zpass_cols=16, zpass_tc=1)
     elif variant != "plain":
         raise ValueError("unknown ncu variant %r" % variant)
     c = ctx.search_so3(ob, sw, 8, 4, batch=8)
@@ -473,7 +476,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--ncu-variant", default="plain", choices=["plain", "rotate_object", "label_aware"])
+    ap.add_argument("--ncu-variant", default="plain", choices=["plain", "rotate_object", "label_aware", "zpass_tc"])
     ap.add_argument("--batch-study", type=int, default=0, metavar="N_REQ",
                     help="time dock_register_batch against the plain loop on N_REQ requests of the batched mix")
     ap.add_argument("--serving-study", type=int, default=0, metavar="N_REQ",
@@ -721,7 +724,7 @@ def main():
                              "before every step",
                        "parallelism": "replicas" if ws > 1 else "single",
                        "search_launch_shape": {k: tuning[k] for k in ("batch", "group", "vox_blocks", "plane_cl",
-                                                                      "zpass_cols")}},
+                                                                      "zpass_cols", "zpass_tc")}},
             "roofline": roofline, "roofline_hbm": roofline_hbm, "model_roofline_frac": round(model_frac, 4),
             "model_bytes_per_eval": model_bytes_per_eval(w.N),
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "kernels": kernels,

@@ -438,6 +438,9 @@ typedef struct dock_tuning {
                                 the label-aware score always uses 32) */
     int32_t vox_overlap;     /* 1: the voxeliser of the next launch runs on a second stream, overlapped
                                 with the FFT passes of the current one (plain score); 0: in order */
+    int32_t zpass_tc;        /* 1: the z pass's radix-16 DFT stages run as 3 x TF32 products on the
+                                tensor cores (canvas 256, zpass_cols 16, plain score); 0: FP32
+                                butterflies on the CUDA cores */
     double us_per_rotation;  /* measured device time per rotation of this shape (0 = not measured) */
 } dock_tuning;
 
@@ -461,7 +464,9 @@ DOCK_API dock_status dock_load_tuning(dock_ctx *ctx, const char *cache_path, int
 DOCK_API dock_status dock_get_tuning(dock_ctx *ctx, int32_t N, dock_tuning *out);
 /* Sets the shape for lattice side t->N (batch 1..256, group 0..256,
  * vox_blocks 3 or 4, plane_cl 0, 2, 4 or 8, zpass_cols 0, 16 or 32,
- * vox_overlap 0 or 1); results do not depend on it.
+ * vox_overlap 0 or 1, zpass_tc 0 or 1); results do not depend on it beyond
+ * rounding (zpass_tc changes the rounding of the z pass's products, within
+ * the FP32 error of the transform).
  * DOCK_E_INVALID for values out of range. */
 DOCK_API dock_status dock_set_tuning(dock_ctx *ctx, const dock_tuning *t);
 

@@ -1374,6 +1374,7 @@ static const int ZPASS_COLS_DEFAULT = 16;
 // (both fill the register file), 1 % faster in all at 128^3, and per-kernel
 // event times then overlap.
 static const int VOX_OVERLAP_DEFAULT = 0;
+static const int ZPASS_TC_DEFAULT = 0;
 
 static dock_tuning tuning_for(dock_ctx *ctx, const Geo &g)
 {
@@ -1387,6 +1388,7 @@ static dock_tuning tuning_for(dock_ctx *ctx, const Geo &g)
     t.plane_cl = g.M == 256 ? PLANE_CL_DEFAULT : 0;
     t.zpass_cols = g.M == 256 ? ZPASS_COLS_DEFAULT : 0;
     t.vox_overlap = VOX_OVERLAP_DEFAULT;
+    t.zpass_tc = g.M == 256 ? ZPASS_TC_DEFAULT : 0;
     return t;
 }
 
@@ -1396,7 +1398,7 @@ static bool valid_tuning(const dock_tuning &t)
            (t.vox_blocks == 3 || t.vox_blocks == 4) &&
            (t.plane_cl == 0 || t.plane_cl == 2 || t.plane_cl == 4 || t.plane_cl == 8) &&
            (t.zpass_cols == 0 || t.zpass_cols == 16 || t.zpass_cols == 32) &&
-           (t.vox_overlap == 0 || t.vox_overlap == 1);
+           (t.vox_overlap == 0 || t.vox_overlap == 1) && (t.zpass_tc == 0 || t.zpass_tc == 1);
 }
 
 // Runs records [r0, r1) of rots through the search pipeline; every
@@ -1490,7 +1492,9 @@ static dock_status run_pipeline_rots(dock_ctx *ctx, const Geo &g, const ReqDev *
         }
         {
             Prof pr(ctx, dual ? "zpass_dual" : "zpass");
-            if (g.M == 256 && tc.zpass_cols == 16 && !dual)
+            if (g.M == 256 && tc.zpass_cols == 16 && tc.zpass_tc && !dual)
+                CK(ctx, launch_zpass_tc(g, nb, group, Y, rb, reqs, Z, ctx->errflag, ctx->stream));
+            else if (g.M == 256 && tc.zpass_cols == 16 && !dual)
                 CK(ctx, launch_zpass16(g, nb, group, Y, rb, reqs, Z, ctx->stream));
             else
                 CK(ctx, launch_zpass(g, nb, group, Y, rb, reqs, Z, tw, ctx->stream, Y2));
@@ -1800,9 +1804,9 @@ static dock_status write_tuning(dock_ctx *ctx, const char *path)
         const dock_tuning &t = kv.second;
         fprintf(f,
                 "%s\n  {\"N\": %d, \"batch\": %d, \"group\": %d, \"vox_blocks\": %d, \"plane_cl\": %d, "
-                "\"zpass_cols\": %d, \"vox_overlap\": %d, \"us_per_rotation\": %.3f}",
+                "\"zpass_cols\": %d, \"vox_overlap\": %d, \"zpass_tc\": %d, \"us_per_rotation\": %.3f}",
                 first ? "" : ",", t.N, t.batch, t.group, t.vox_blocks, t.plane_cl, t.zpass_cols, t.vox_overlap,
-                t.us_per_rotation);
+                t.zpass_tc, t.us_per_rotation);
         first = false;
     }
     fprintf(f, "\n]}\n");
@@ -1882,6 +1886,12 @@ extern "C" dock_status dock_autotune(dock_ctx *ctx, const dock_object *ob, const
         {
             dock_tuning t = best;
             t.zpass_cols = best.zpass_cols == 16 ? 32 : 16;
+            t.zpass_tc = 0;
+            if ((s = trial(t)) != DOCK_OK) { restore(); return s; }
+        }
+        if (best.zpass_cols == 16) {
+            dock_tuning t = best;
+            t.zpass_tc = best.zpass_tc ? 0 : 1;
             if ((s = trial(t)) != DOCK_OK) { restore(); return s; }
         }
     }
@@ -1937,6 +1947,9 @@ extern "C" dock_status dock_load_tuning(dock_ctx *ctx, const char *path, int32_t
             long vo = VOX_OVERLAP_DEFAULT;
             json_int(e.c_str(), "\"vox_overlap\"", &vo);
             t.vox_overlap = (int)vo;
+            long zt = gt.M == 256 ? ZPASS_TC_DEFAULT : 0;
+            json_int(e.c_str(), "\"zpass_tc\"", &zt);
+            t.zpass_tc = (int)zt;
             if (!valid_tuning(t)) {
                 pos = end;
                 continue;
@@ -2037,7 +2050,10 @@ static dock_status search_scores_impl(dock_ctx *ctx, const dock_object *ob, cons
     if (dual && e == cudaSuccess)
         e = launch_fwd2d(g, 1, ctx->bits + bsz, Y2, tw, qt, ctx->stream, ctx->bits, ctx->rots, ctx->reqs);
     if (e == cudaSuccess) {
-        if (g.M == 256 && tuning_for(ctx, g).zpass_cols == 16 && !dual)
+        const dock_tuning tc = tuning_for(ctx, g);
+        if (g.M == 256 && tc.zpass_cols == 16 && tc.zpass_tc && !dual)
+            e = launch_zpass_tc(g, 1, 1, Y, ctx->rots, ctx->reqs, Y + ysz, ctx->errflag, ctx->stream);
+        else if (g.M == 256 && tc.zpass_cols == 16 && !dual)
             e = launch_zpass16(g, 1, 1, Y, ctx->rots, ctx->reqs, Y + ysz, ctx->stream);
         else
             e = launch_zpass(g, 1, 1, Y, ctx->rots, ctx->reqs, Y + ysz, tw, ctx->stream, Y2);

@@ -444,6 +444,326 @@ k_zpass16(int B, int group, const float2 *__restrict__ Y, const RotRec *rots, co
     }
 }
 
+// ---------------------------------------------------------------------------
+// z pass with its DFT stages on the tensor cores (tcgen05, kind::tf32).
+//
+// The same transforms as k_zpass16 -- along z, per column of a block of 16,
+// the forward 256-point DFT of the zero-padded S column, the product with
+// conj(F(O)), the inverse DFT -- as four radix-16 stages, each one dense
+// product of the block's 256 vectors with the 16-point DFT matrix:
+//   D[v][n] = sum_k A[v][k] W[k][n],
+// row v of A holding one 16-point input vector as 32 reals (re, im
+// interleaved) and W the real 32 x 32 form of the DFT matrix (forward or
+// inverse).  Each stage is two products of M = 128 rows (N = 32, K = 8 per
+// instruction) issued by one thread; A is read from tensor memory, W from
+// shared memory, D accumulates in FP32 in tensor memory.  Thread v owns row
+// v: lane v mod 128 of the columns of tile v / 128, where it writes its A row
+// (tcgen05.st) and reads its D row (tcgen05.ld).
+// 3 x TF32: each operand is split x = hi + lo, hi = x rounded to TF32 and
+// lo = (x - hi) rounded to TF32 (the tensor cores would truncate it), and
+// D = Ahi Whi + Ahi Wlo + Alo Whi; x - hi - lo and the dropped Alo Wlo term
+// are below 2^-22 |x| |w|.
+//
+// Rows v = 16 j + c (thread v: column c, index j); z = z2 + 16 z1 on the
+// way in, kz = k1 + 16 k2 in the spectrum, z = b + 16 a on the way out:
+//   stage  row (j, c) holds          product over   thread v then
+//   F0     z2 = j;  z1 < 8 (K = 16)  z1 -> k1       twiddles w^(z2 k1), sends k1 to row (k1, c)
+//   F1     k1 = j;  z2               z2 -> k2       multiplies by the spectrum at kz, keeps its row
+//   I0     k1 = j;  k2               k2 -> b        twiddles w^-(b k1), sends b to row (b, c)
+//   I1     b = j;   k1               k1 -> a        stores z = b + 16 a
+// (w = exp(-2 pi i / 256)).  The two transposes go through shared memory
+// (X[row index][K index][c], c fastest: both directions conflict-free).
+//
+// Shared memory: W (forward hi, lo; inverse hi, lo) in the canonical
+// K-major layout without swizzle (core matrices of 8 rows x 16 bytes:
+// element (n, k) at byte (k / 4) 512 + (n / 8) 128 + (n mod 8) 16 +
+// (k mod 4) 4), the exchange buffer and the spectrum tile [kz][16]: 80 KB.
+// Tensor memory (256 columns): D at 32 t, A hi at 64 + 32 t, A lo at
+// 128 + 32 t for tile t.  Two blocks per SM fill its 512 columns.
+// ---------------------------------------------------------------------------
+namespace {
+
+__device__ __forceinline__ float tf32_rna(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+// tcgen05 shared-memory matrix descriptor: start, leading- and stride-
+// dimension byte offsets (16-byte units), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+// D (tensor memory) (+)= A (tensor memory) . B (shared memory descriptor)
+__device__ __forceinline__ void umma_tf32_ta(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}" ::"r"(d),
+                 "r"(a), "l"(b), "r"(idesc), "r"(acc)
+                 : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t *m)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(m))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// this warp's 32 lanes, 32 consecutive columns of tensor memory from ta
+__device__ __forceinline__ void tmem_ld32(uint32_t ta, float *f)
+{
+    uint32_t r[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(ta)
+                 : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) f[i] = __uint_as_float(r[i]);
+}
+#define DOCK_R16(a, o)                                                                                           \
+    "r"(a[o + 0]), "r"(a[o + 1]), "r"(a[o + 2]), "r"(a[o + 3]), "r"(a[o + 4]), "r"(a[o + 5]), "r"(a[o + 6]),     \
+        "r"(a[o + 7]), "r"(a[o + 8]), "r"(a[o + 9]), "r"(a[o + 10]), "r"(a[o + 11]), "r"(a[o + 12]),             \
+        "r"(a[o + 13]), "r"(a[o + 14]), "r"(a[o + 15])
+// 16 or 32 consecutive columns of this warp's lanes from ta
+__device__ __forceinline__ void tmem_st16(uint32_t ta, const uint32_t *v)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16};" ::"r"(ta),
+                 DOCK_R16(v, 0)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_st32(uint32_t ta, const uint32_t *v)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(ta),
+                 DOCK_R16(v, 0), DOCK_R16(v, 16)
+                 : "memory");
+}
+#undef DOCK_R16
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+// a thread's A row (K = 2 NV reals) split into TF32 hi and lo, into tensor memory
+template <int NV> __device__ __forceinline__ void put_row(uint32_t ta_hi, uint32_t ta_lo, const cf *v)
+{
+    uint32_t h[2 * NV], l[2 * NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        const float hx = tf32_rna(v[i].x), hy = tf32_rna(v[i].y);
+        h[2 * i] = __float_as_uint(hx);
+        h[2 * i + 1] = __float_as_uint(hy);
+        l[2 * i] = __float_as_uint(tf32_rna(v[i].x - hx));
+        l[2 * i + 1] = __float_as_uint(tf32_rna(v[i].y - hy));
+    }
+    if (NV == 8) {
+        tmem_st16(ta_hi, h);
+        tmem_st16(ta_lo, l);
+    } else {
+        tmem_st32(ta_hi, h);
+        tmem_st32(ta_lo, l);
+    }
+    tmem_wait_st();
+}
+
+}  // namespace
+
+struct ZpassTcCfg {
+    static constexpr int M = 256, N = 128, P = 130, NT = 256, COLS = 16;
+    static constexpr uint32_t LBO_W = 512, SBO = 128, W_BYTES = 4096;
+    static constexpr size_t X_OFF = 4 * W_BYTES, SP_OFF = X_OFF + (size_t)M * COLS * 8;
+    static constexpr size_t SMEM = SP_OFF + (size_t)M * COLS * 8;
+    static constexpr uint32_t TMEM_COLS = 256;
+    // D FP32, A and B TF32, both K-major, N = 32, M = 128
+    static constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+    static constexpr long long WAIT_CYCLES = 1ll << 31;
+    // two blocks per SM (their tensor memory fills the SM's 512 columns), not three
+    static_assert((SMEM + 64 + 1024) * 2 <= 228 * 1024 && (SMEM + 1024) * 3 > 228 * 1024, "two blocks per SM");
+};
+
+__global__ void __launch_bounds__(ZpassTcCfg::NT, 2)
+k_zpass_tc(int B, int group, const float2 *__restrict__ Y, const RotRec *rots, const ReqDev *reqs, float2 *Z,
+           int *err)
+{
+    using C = ZpassTcCfg;
+    constexpr int M = C::M, N = C::N, P = C::P, COLS = C::COLS;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tslot;
+    __shared__ int s_fail;
+    unsigned char *W = smem;                                // forward hi, forward lo, inverse hi, inverse lo
+    cf *xb = reinterpret_cast<cf *>(smem + C::X_OFF);      // [16 (row index)][16 (K index)][COLS]
+    cf *spt = reinterpret_cast<cf *>(smem + C::SP_OFF);    // [M (kz)][COLS]
+    const int tid = threadIdx.x, c = tid & 15, j = tid >> 4, warp = tid >> 5;
+    const size_t plane = (size_t)M * P;
+    const int f0 = blockIdx.x * COLS;
+    const int b0 = blockIdx.y * group, nb = min(group, B - b0);
+    if (nb <= 0) return;
+
+    // the real forms of the forward and inverse 16-point DFT matrices:
+    // output (re, im) of index kout from input (re, im) of index kin
+    for (int i = tid; i < 2048; i += C::NT) {
+        const int inv = i >> 10, n = (i >> 5) & 31, k = i & 31;
+        const float2 w = c_tw256[(16 * (k >> 1) * (n >> 1)) & 255];   // exp(-2 pi i kin kout / 16)
+        const float wr = w.x, wi = inv ? -w.y : w.y;
+        const float x = (n & 1) == 0 ? ((k & 1) == 0 ? wr : -wi) : ((k & 1) == 0 ? wi : wr);
+        const float hi = tf32_rna(x);
+        const uint32_t off = (k >> 2) * C::LBO_W + (n >> 3) * C::SBO + (n & 7) * 16 + (k & 3) * 4;
+        *reinterpret_cast<float *>(W + 2 * inv * C::W_BYTES + off) = hi;
+        *reinterpret_cast<float *>(W + (2 * inv + 1) * C::W_BYTES + off) = tf32_rna(x - hi);
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tslot)),
+                     "r"(C::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(&mbar, 1);
+        fence_mbar_init();
+        s_fail = 0;
+    }
+    fence_proxy_async();
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = tslot;
+    const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16, tcol = (uint32_t)(32 * (warp >> 2));
+    const uint32_t t_d = tmem + lanes + tcol, t_hi = tmem + lanes + 64 + tcol, t_lo = tmem + lanes + 128 + tcol;
+    const uint32_t w_u32 = smem_u32(W);
+    uint32_t phase = 0;
+    int lost = -1;   // parity of a product this thread stopped waiting for
+
+    // every thread has put its A row: one thread issues the stage's products
+    // (nks K-steps of 8 against the W pair `mat`), all wait for them and read
+    // their D rows; false when the block gave up
+    // (the issue is unrolled with the descriptors as constant offsets from one
+    // base: built in the loop, the issuing thread's arithmetic doubled a
+    // stage's round trip)
+    const uint64_t wdesc = umma_desc(w_u32, C::LBO_W, C::SBO);
+    auto stage = [&](int nks, int mat, float *d) -> bool {
+        tc_before_sync();
+        __syncthreads();
+        tc_after_sync();
+        if (s_fail) return false;
+        if (tid == 0) {
+#pragma unroll
+            for (int t = 0; t < 2; ++t)
+#pragma unroll
+                for (int p = 0; p < 3; ++p)
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks)
+                        if (ks < nks)
+                            umma_tf32_ta(tmem + 32 * t, tmem + (p == 2 ? 128 : 64) + 32 * t + 8 * ks,
+                                         wdesc + (((mat + (p == 1)) * C::W_BYTES + ks * 2 * C::LBO_W) >> 4), C::IDESC,
+                                         (p | ks) != 0);
+            umma_commit(&mbar);
+        }
+        // every thread polls (bounded): one waiter releasing the others through
+        // a block barrier measured 5 % slower
+        const long long t0 = clock64();
+        bool ok = true;
+        while (!mbar_try_wait(&mbar, phase))
+            if (clock64() - t0 > C::WAIT_CYCLES) {
+                ok = false;
+                break;
+            }
+        if (!ok) {
+            lost = (int)phase;
+            s_fail = 1;
+            if (err) atomicExch(err, DOCK_E_TIMEOUT);
+        }
+        phase ^= 1;
+        tc_after_sync();
+        tmem_ld32(t_d, d);
+        return true;
+    };
+
+    auto load = [&](int bi, cf *v) {
+        const float2 *src = Y + (size_t)(b0 + bi) * N * plane + f0 + c;
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const float2 a = __ldcs(&src[(size_t)(j + 16 * s) * plane]);
+            v[s] = cmake(a.x, a.y);
+        }
+    };
+    cf nx[8];
+    load(0, nx);
+    int sp_req = -1;
+#pragma unroll 1
+    for (int bi = 0; bi < nb; ++bi) {
+        float d[32];
+        cf v[16];
+        // F0 row: x[z2 + 16 z1], z1 < 8 (z >= N is zero padding, not read by the products)
+        put_row<8>(t_hi, t_lo, nx);
+        if (bi + 1 < nb) load(bi + 1, nx);
+        const int req = rots[b0 + bi].req;
+        if (req != sp_req) {   // block-uniform; the last reads of the old tile precede three barriers
+            const float2 *src = reqs[req].spec + (size_t)(f0 / 32) * M * 32 + (f0 & 31) + c;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                const float2 a = __ldg(&src[(size_t)(j + 16 * r) * 32]);
+                spt[(j + 16 * r) * COLS + c] = cmake(a.x, a.y);
+            }
+            sp_req = req;
+        }
+        const float cj = reqs[req].rotate_object ? -1.f : 1.f;
+        if (!stage(2, 0, d)) break;
+        // F0 -> F1: k1 = r goes to row (k1, c), K index z2 = j
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            cf a = cmake(d[2 * r], d[2 * r + 1]);
+            if (r) a = cmul(a, cconj(twc_inv(j * r)));   // exp(-2 pi i j r / 256)
+            xb[(r * 16 + j) * COLS + c] = a;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = xb[(j * 16 + k) * COLS + c];
+        put_row<16>(t_hi, t_lo, v);
+        if (!stage(4, 0, d)) break;
+        // F1 -> I0: X[kz = j + 16 r] conj(F(O))[kz], the same row
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            cf a = cmake(d[2 * r], d[2 * r + 1]);
+            a.y *= cj;
+            v[r] = cmul(a, spt[(j + 16 * r) * COLS + c]);
+        }
+        put_row<16>(t_hi, t_lo, v);
+        if (!stage(4, 2, d)) break;
+        // I0 -> I1: b = r goes to row (b, c), K index k1 = j
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            cf a = cmake(d[2 * r], d[2 * r + 1]);
+            if (r) a = cmul(a, twc_inv(j * r));
+            xb[(r * 16 + j) * COLS + c] = a;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = xb[(j * 16 + k) * COLS + c];
+        put_row<16>(t_hi, t_lo, v);
+        if (!stage(4, 2, d)) break;
+        float2 *dst = Z + (size_t)(b0 + bi) * M * plane + f0 + c;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) __stcs(&dst[(size_t)(j + 16 * r) * plane], make_float2(d[2 * r], d[2 * r + 1]));
+    }
+    // a product still in flight after a timeout: wait for it (bounded) before
+    // its tensor memory is released
+    if (lost >= 0 && tid == 0) {
+        const long long t0 = clock64();
+        while (!mbar_try_wait(&mbar, (uint32_t)lost) && clock64() - t0 < C::WAIT_CYCLES) {
+        }
+    }
+    tc_before_sync();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
+}
+
 // Fills c_tw256 on the current device once (the module's constant bank is per device).
 static cudaError_t ensure_twiddle_bank()
 {
@@ -511,6 +831,21 @@ cudaError_t launch_zpass16(const Geo &g, int B, int group, const float2 *Y, cons
     return cudaGetLastError();
 }
 
+
+cudaError_t launch_zpass_tc(const Geo &g, int B, int group, const float2 *Y, const RotRec *rots, const ReqDev *reqs,
+                            float2 *Z, int *err, cudaStream_t st)
+{
+    using C = ZpassTcCfg;
+    if (g.M != C::M || g.P != C::P || B < 1 || group < 1) return cudaErrorInvalidValue;
+    cudaError_t e = ensure_twiddle_bank();
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_zpass_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (e != cudaSuccess) return e;
+    const dim3 grid(C::M * C::P / C::COLS, (B + group - 1) / group);
+    if (grid.y > 65535) return cudaErrorInvalidValue;
+    k_zpass_tc<<<grid, C::NT, C::SMEM, st>>>(B, group, Y, rots, reqs, Z, err);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_plane_cl(const Geo &g, int cl, int B, const float2 *Z, const float2 *tw, const RotRec *rots,
                             const ReqDev *reqs, int *err, cudaStream_t st)

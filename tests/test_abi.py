@@ -48,3 +48,38 @@ def test_binding_fails_loudly_without_the_library(monkeypatch):
     monkeypatch.setattr(dock, "LIB_PATH", os.path.join(ROOT, "does-not-exist", "libdock.so"))
     with pytest.raises(RuntimeError):
         dock.lib()
+
+
+# ctypes structure of the binding -> the C struct of include/dock.h it mirrors
+_STRUCTS = {"Params": "dock_params", "Probe": "dock_probe", "Candidate": "dock_candidate", "Peak": "dock_peak",
+            "SearchDesc": "dock_search_desc", "Refined": "dock_refined", "RegisterDesc": "dock_register_desc",
+            "Result": "dock_result", "Request": "dock_request", "Tuning": "dock_tuning",
+            "KernelStat": "dock_kernel_stat"}
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every ctypes structure has the size and field offsets that a C compiler
+    gives the header's struct (a field added to one side only fails here)."""
+    import shutil
+    import subprocess
+    from paper_2605_21398_gb300 import dock
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "dock.h"', 'int main(void) {']
+    for py, c in _STRUCTS.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (py, c))
+        for name, _ in getattr(dock, py)._fields_:
+            cname = name[:-1] if name.endswith("_") else name   # lambda_ (a Python keyword) is lambda in C
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (py, name, c, cname))
+    lines += ['return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(l.rsplit(" ", 1) for l in subprocess.check_output([str(exe)], text=True).splitlines())
+    for py in _STRUCTS:
+        cls = getattr(dock, py)
+        assert int(got["%s size" % py]) == ctypes.sizeof(cls), py
+        for name, _ in cls._fields_:
+            assert int(got["%s.%s" % (py, name)]) == getattr(cls, name).offset, (py, name)
