@@ -441,6 +441,9 @@ typedef struct dock_tuning {
     int32_t zpass_tc;        /* 1: the z pass's radix-16 DFT stages run as 3 x TF32 products on the
                                 tensor cores (canvas 256, zpass_cols 16, plain score); 0: FP32
                                 butterflies on the CUDA cores */
+    int32_t plane_tma;       /* 1 (canvas 256, plane_cl 4 or 8): the plane pass as persistent clusters that
+                                load the next plane's columns with the tensor-memory-access unit
+                                during the current plane's C2R; 0: one cluster per plane */
     double us_per_rotation;  /* measured device time per rotation of this shape (0 = not measured) */
 } dock_tuning;
 
@@ -464,7 +467,7 @@ DOCK_API dock_status dock_load_tuning(dock_ctx *ctx, const char *cache_path, int
 DOCK_API dock_status dock_get_tuning(dock_ctx *ctx, int32_t N, dock_tuning *out);
 /* Sets the shape for lattice side t->N (batch 1..256, group 0..256,
  * vox_blocks 3 or 4, plane_cl 0, 2, 4 or 8, zpass_cols 0, 16 or 32,
- * vox_overlap 0 or 1, zpass_tc 0 or 1); results do not depend on it beyond
+ * vox_overlap 0 or 1, zpass_tc 0 or 1, plane_tma 0 or 1); results do not depend on it beyond
  * rounding (zpass_tc changes the rounding of the z pass's products, within
  * the FP32 error of the transform).
  * DOCK_E_INVALID for values out of range. */
@@ -472,9 +475,11 @@ DOCK_API dock_status dock_set_tuning(dock_ctx *ctx, const dock_tuning *t);
 
 /* Test hook of failure detection (systems form; the paper has no
  * counterpart): dock_search_scores with the cluster plane pass (canvas 256,
- * plane_cl 4 or 8) launched so that no CTA receives its peers' blocks.  Every
- * CTA's wait for them is bounded (about a second of clock cycles); it runs
- * out, the kernel records DOCK_E_TIMEOUT in the context's error word and
+ * plane_cl 4 or 8; the persistent form when plane_tma is set) launched so
+ * that no CTA receives its peers' blocks.  Every CTA's wait for them is
+ * bounded (about a second of clock cycles); it runs out, the kernel records
+ * DOCK_E_TIMEOUT in the context's error word (a persistent cluster stops at
+ * its next cluster barrier, every CTA told through its shared memory) and
  * returns, and the call returns DOCK_E_TIMEOUT with C undefined.  No copy is
  * in flight when a CTA gives up and the context stays usable.  quat: one
  * unit quaternion; C: host, M^3 floats.  DOCK_E_INVALID for other canvases

@@ -1368,13 +1368,14 @@ static dock_status check_pair(dock_ctx *ctx, const dock_object *ob, const dock_s
 // when the autotuner (or its cache) has one, else the defaults.
 // CTAs per plane of the inverse plane pass and columns per z-pass block at
 // canvas 256 when untuned.
-static const int PLANE_CL_DEFAULT = 4;
+static const int PLANE_CL_DEFAULT = 8;
 static const int ZPASS_COLS_DEFAULT = 16;
 // Off by default: overlapped, the voxeliser and the FFT passes slow each other
 // (both fill the register file), 1 % faster in all at 128^3, and per-kernel
 // event times then overlap.
 static const int VOX_OVERLAP_DEFAULT = 0;
 static const int ZPASS_TC_DEFAULT = 0;
+static const int PLANE_TMA_DEFAULT = 1;
 
 static dock_tuning tuning_for(dock_ctx *ctx, const Geo &g)
 {
@@ -1389,6 +1390,7 @@ static dock_tuning tuning_for(dock_ctx *ctx, const Geo &g)
     t.zpass_cols = g.M == 256 ? ZPASS_COLS_DEFAULT : 0;
     t.vox_overlap = VOX_OVERLAP_DEFAULT;
     t.zpass_tc = g.M == 256 ? ZPASS_TC_DEFAULT : 0;
+    t.plane_tma = g.M == 256 ? PLANE_TMA_DEFAULT : 0;
     return t;
 }
 
@@ -1398,7 +1400,8 @@ static bool valid_tuning(const dock_tuning &t)
            (t.vox_blocks == 3 || t.vox_blocks == 4) &&
            (t.plane_cl == 0 || t.plane_cl == 2 || t.plane_cl == 4 || t.plane_cl == 8) &&
            (t.zpass_cols == 0 || t.zpass_cols == 16 || t.zpass_cols == 32) &&
-           (t.vox_overlap == 0 || t.vox_overlap == 1) && (t.zpass_tc == 0 || t.zpass_tc == 1);
+           (t.vox_overlap == 0 || t.vox_overlap == 1) && (t.zpass_tc == 0 || t.zpass_tc == 1) &&
+           (t.plane_tma == 0 || t.plane_tma == 1);
 }
 
 // Runs records [r0, r1) of rots through the search pipeline; every
@@ -1501,7 +1504,7 @@ static dock_status run_pipeline_rots(dock_ctx *ctx, const Geo &g, const ReqDev *
         }
         {
             Prof pr(ctx, "plane");
-            CK(ctx, launch_plane(g, nb, Z, tw, rb, reqs, ctx->stream, tc.plane_cl, ctx->errflag));
+            CK(ctx, launch_plane(g, nb, Z, tw, rb, reqs, ctx->stream, tc.plane_cl, ctx->errflag, tc.plane_tma));
         }
     }
     return DOCK_OK;
@@ -1804,9 +1807,9 @@ static dock_status write_tuning(dock_ctx *ctx, const char *path)
         const dock_tuning &t = kv.second;
         fprintf(f,
                 "%s\n  {\"N\": %d, \"batch\": %d, \"group\": %d, \"vox_blocks\": %d, \"plane_cl\": %d, "
-                "\"zpass_cols\": %d, \"vox_overlap\": %d, \"zpass_tc\": %d, \"us_per_rotation\": %.3f}",
+                "\"zpass_cols\": %d, \"vox_overlap\": %d, \"zpass_tc\": %d, \"plane_tma\": %d, \"us_per_rotation\": %.3f}",
                 first ? "" : ",", t.N, t.batch, t.group, t.vox_blocks, t.plane_cl, t.zpass_cols, t.vox_overlap,
-                t.zpass_tc, t.us_per_rotation);
+                t.zpass_tc, t.plane_tma, t.us_per_rotation);
         first = false;
     }
     fprintf(f, "\n]}\n");
@@ -1883,6 +1886,11 @@ extern "C" dock_status dock_autotune(dock_ctx *ctx, const dock_object *ob, const
             t.plane_cl = cl;
             if ((s = trial(t)) != DOCK_OK) { restore(); return s; }
         }
+        if (best.plane_cl == 4 || best.plane_cl == 8) {
+            dock_tuning t = best;
+            t.plane_tma = best.plane_tma ? 0 : 1;
+            if ((s = trial(t)) != DOCK_OK) { restore(); return s; }
+        }
         {
             dock_tuning t = best;
             t.zpass_cols = best.zpass_cols == 16 ? 32 : 16;
@@ -1950,6 +1958,9 @@ extern "C" dock_status dock_load_tuning(dock_ctx *ctx, const char *path, int32_t
             long zt = gt.M == 256 ? ZPASS_TC_DEFAULT : 0;
             json_int(e.c_str(), "\"zpass_tc\"", &zt);
             t.zpass_tc = (int)zt;
+            long pt = gt.M == 256 ? PLANE_TMA_DEFAULT : 0;
+            json_int(e.c_str(), "\"plane_tma\"", &pt);
+            t.plane_tma = (int)pt;
             if (!valid_tuning(t)) {
                 pos = end;
                 continue;
@@ -2049,8 +2060,8 @@ static dock_status search_scores_impl(dock_ctx *ctx, const dock_object *ob, cons
     if (dual && e == cudaSuccess) e = launch_voxelise(g, ctx->reqs, ctx->rots, 1, ctx->bits + bsz, ctx->stream, 4, 1);
     if (dual && e == cudaSuccess)
         e = launch_fwd2d(g, 1, ctx->bits + bsz, Y2, tw, qt, ctx->stream, ctx->bits, ctx->rots, ctx->reqs);
+    const dock_tuning tc = tuning_for(ctx, g);
     if (e == cudaSuccess) {
-        const dock_tuning tc = tuning_for(ctx, g);
         if (g.M == 256 && tc.zpass_cols == 16 && tc.zpass_tc && !dual)
             e = launch_zpass_tc(g, 1, 1, Y, ctx->rots, ctx->reqs, Y + ysz, ctx->errflag, ctx->stream);
         else if (g.M == 256 && tc.zpass_cols == 16 && !dual)
@@ -2059,9 +2070,10 @@ static dock_status search_scores_impl(dock_ctx *ctx, const dock_object *ob, cons
             e = launch_zpass(g, 1, 1, Y, ctx->rots, ctx->reqs, Y + ysz, tw, ctx->stream, Y2);
     }
     if (e == cudaSuccess)
-        e = withhold ? launch_plane_cl_export(g, tuning_for(ctx, g).plane_cl, Y + ysz, tw, dC, ctx->errflag,
-                                              ctx->stream, 1)
-                     : launch_plane_export(g, Y + ysz, tw, dC, ctx->stream, tuning_for(ctx, g).plane_cl, ctx->errflag);
+        e = withhold ? (tc.plane_tma && plane_ps_supported(g.M, tc.plane_cl)
+                            ? launch_plane_ps_export(g, tc.plane_cl, Y + ysz, dC, ctx->errflag, ctx->stream, 1)
+                            : launch_plane_cl_export(g, tc.plane_cl, Y + ysz, tw, dC, ctx->errflag, ctx->stream, 1))
+                     : launch_plane_export(g, Y + ysz, tw, dC, ctx->stream, tc.plane_cl, ctx->errflag, tc.plane_tma);
     if (e == cudaSuccess) e = cudaMemcpyAsync(C, dC, csz * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
     int herr = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, ctx->errflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);

@@ -92,10 +92,12 @@ cudaError_t launch_resample(const Geo &g, const ReqDev *reqs, const RotRec *rots
 cudaError_t launch_zpass(const Geo &g, int B, int group, const float2 *Y, const RotRec *rots, const ReqDev *reqs,
                          float2 *Z, const float2 *tw, cudaStream_t st, const float2 *Y2 = nullptr);
 // plane_cl: CTAs per plane at M = 256 (4 or 8: the cluster kernel of
-// k_fft256.cu; anything else: the 2-CTA kernel).  err (nullable, device):
+// k_fft256.cu; anything else: the 2-CTA kernel); plane_tma with plane_cl 4
+// or 8: the persistent cluster kernel with TMA staging.  err (nullable, device):
 // set to DOCK_E_TIMEOUT if a cluster kernel gave up waiting for its peers.
 cudaError_t launch_plane(const Geo &g, int B, const float2 *Z, const float2 *tw, const RotRec *rots,
-                         const ReqDev *reqs, cudaStream_t st, int plane_cl = 0, int *err = nullptr);
+                         const ReqDev *reqs, cudaStream_t st, int plane_cl = 0, int *err = nullptr,
+                         int plane_tma = 0);
 // z pass over 16 columns per block (k_fft256.cu): M = 256, plain score only.
 cudaError_t launch_zpass16(const Geo &g, int B, int group, const float2 *Y, const RotRec *rots, const ReqDev *reqs,
                            float2 *Z, cudaStream_t st);
@@ -103,6 +105,12 @@ cudaError_t launch_zpass16(const Geo &g, int B, int group, const float2 *Y, cons
 // z pass with its DFT stages as 3 x TF32 products on the tensor cores (canvas 256, plain score)
 cudaError_t launch_zpass_tc(const Geo &g, int B, int group, const float2 *Y, const RotRec *rots, const ReqDev *reqs,
                             float2 *Z, int *err, cudaStream_t st);
+// persistent cluster plane pass with TMA staging of the columns (canvas 256, 4 or 8 CTAs per plane)
+bool plane_ps_supported(int M, int cl);
+cudaError_t launch_plane_ps(const Geo &g, int cl, int B, const float2 *Z, const RotRec *rots, const ReqDev *reqs,
+                            int *err, cudaStream_t st);
+cudaError_t launch_plane_ps_export(const Geo &g, int cl, const float2 *Z, float *C, int *err, cudaStream_t st,
+                                   int withhold = 0);
 bool plane_cl_supported(int M, int cl);
 cudaError_t launch_plane_cl(const Geo &g, int cl, int B, const float2 *Z, const float2 *tw, const RotRec *rots,
                             const ReqDev *reqs, int *err, cudaStream_t st);
@@ -118,7 +126,7 @@ cudaError_t launch_topk(const unsigned long long *keys, int n, int K, int N, int
 cudaError_t launch_vox_export(const Geo &g, const ReqDev *reqs, const RotRec *rots, int B, uint8_t *bits,
                               cudaStream_t st, int pose_set = 0);
 cudaError_t launch_plane_export(const Geo &g, const float2 *Z, const float2 *tw, float *C, cudaStream_t st,
-                                int plane_cl = 0, int *err = nullptr);
+                                int plane_cl = 0, int *err = nullptr, int plane_tma = 0);
 // Corner cells of O for trilinear interpolation ((N+1)^3 float4).
 cudaError_t launch_corner_cells(const float *O, int N, float4 *cells, cudaStream_t st);
 // S of rotation 0 (pose set 0) as N^3 floats 0/1.

@@ -28,10 +28,13 @@
 // that touch 32 rows of one column both hit distinct banks, and most
 // addresses are a per-thread base plus a constant.
 #include <cooperative_groups.h>
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "dock_internal.h"
@@ -344,6 +347,289 @@ k_plane_cl(const float2 *__restrict__ Z, const float2 *__restrict__ tw, const Ro
     }
     // the bulk copies out of X have read their source before the CTA exits
     if (tid == 0) bulk_wait_read();
+}
+
+// ---------------------------------------------------------------------------
+// Persistent plane pass with TMA staging (canvas 256, clusters of CL = 4 or 8
+// CTAs; one CTA of 512 threads per SM for CL = 4, three of 256 for CL = 8).
+// The same transforms as k_plane_cl (CTA `rank` owns packed columns
+// [CPC rank, CPC (rank + 1)) in phase 1 and rows [RPC rank, RPC (rank + 1))
+// in phase 2, CPC = 128 / CL, RPC = 256 / CL), but each cluster walks the
+// planes p = cluster + G i of the launch (G clusters), and the
+// tensor-memory-access unit loads the next plane's columns from HBM into the
+// staging buffer U (one 2-D box of 256 rows x CPC complex, plus the Nyquist
+// column for rank 0) while phase 2 of the current plane runs:
+//   phase 1  in place in U: radix 16 x 16 inverse FFT along y; thread (c, j)
+//            (tid = CPC j + c) holds column c at rows j + 16 s; the last stage
+//            writes row y's column c at c ^ (y mod CPC), so that phase 2's
+//            warps (32 rows of one column) hit distinct banks
+//   push     U's row block q (RPC rows, contiguous) to CTA q's V[rank]
+//            by the bulk-copy engine, completion counted in bytes on CTA q's
+//            mbarrier (the own block included)
+//   phase 2  C2R along x of rows [64 rank, +64) from V, the exchange in place
+//            in V, argmax with the lowest canvas index on ties
+// Per plane one cluster barrier: after it every CTA has finished phase 1 of
+// this plane and phase 2 of the previous one, so V may be overwritten.  Every
+// wait is bounded; a CTA that gave up tells its peers through their shared
+// memory before the next cluster barrier and the whole cluster stops there.
+// ---------------------------------------------------------------------------
+template <int CL_> struct PlanePsCfg {
+    static constexpr int M = 256, H = 128, P = 130, CL = CL_, CPC = H / CL, RPC = M / CL;
+    static constexpr int NT = 8 * RPC;                             // phase 2: 8 threads per row
+    static constexpr int MINB = CL == 4 ? 1 : 3;                   // resident CTAs per SM
+    static constexpr int BLK = RPC * CPC;                          // complex elements of one row block
+    static constexpr uint32_t BOX_BYTES = M * CPC * 8;             // all rows of my packed columns
+    static constexpr uint32_t NYQ_BYTES = M * 16;                  // all rows of kx = 128, 129
+    static constexpr uint32_t BLK_BYTES = BLK * 8;
+    static constexpr size_t U_OFF = 0, V_OFF = BOX_BYTES, N_OFF = V_OFF + (size_t)CL * BLK_BYTES;
+    static constexpr size_t MB_OFF = N_OFF + NYQ_BYTES;            // two mbarriers, the stop flag, warp keys
+    static constexpr size_t SMEM = MB_OFF + 32 + 8 * (NT / 32);
+    static constexpr long long WAIT_CYCLES = 1ll << 31;
+    static_assert(MINB * (SMEM + 1024) <= 228 * 1024, "resident CTAs per SM");
+    static_assert(NT == 16 * CPC && RPC % CPC == 0 && RPC % 32 == 0, "thread mappings of the two phases");
+    static_assert(BLK_BYTES % 16 == 0 && V_OFF % 128 == 0 && N_OFF % 128 == 0, "bulk and tensor copy alignment");
+};
+
+namespace {
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
+        : "memory");
+}
+__device__ __forceinline__ void st_cluster_u32(uint32_t addr, uint32_t v)
+{
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *m, uint32_t parity, long long cycles)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(m, parity))
+        if (clock64() - t0 > cycles) return false;
+    return true;
+}
+}  // namespace
+
+template <int CL, bool EXPORT>
+__global__ void __launch_bounds__(PlanePsCfg<CL>::NT, PlanePsCfg<CL>::MINB)
+k_plane_ps(const __grid_constant__ CUtensorMap zmap, const __grid_constant__ CUtensorMap nmap, int n_planes,
+           const RotRec *rots, const ReqDev *reqs, float *Cout, int *err, int withhold)
+{
+    using C = PlanePsCfg<CL>;
+    constexpr int M = C::M, H = C::H, CPC = C::CPC, RPC = C::RPC, BLK = C::BLK;
+    extern __shared__ __align__(128) unsigned char smem[];
+    cf *U = reinterpret_cast<cf *>(smem + C::U_OFF);    // [M (y)][CPC]: my packed columns
+    cf *V = reinterpret_cast<cf *>(smem + C::V_OFF);    // [CL (source)][RPC (y)][CPC]; then phase 2's exchange
+    cf *Nq = reinterpret_cast<cf *>(smem + C::N_OFF);   // [M][2]: kx = 128, 129
+    uint64_t *tma_bar = reinterpret_cast<uint64_t *>(smem + C::MB_OFF);
+    uint64_t *v_bar = tma_bar + 1;
+    int *s_stop = reinterpret_cast<int *>(smem + C::MB_OFF + 16);
+    unsigned long long *wk = reinterpret_cast<unsigned long long *>(smem + C::MB_OFF + 32);
+    const int tid = threadIdx.x;
+    const int rank = (int)cg::this_cluster().block_rank();
+    const int cid = blockIdx.x / C::CL, G = gridDim.x / C::CL;
+    // the tensor copies want 128-byte aligned destinations (the layout is the
+    // same in every CTA, so the whole cluster returns together)
+    if (smem_u32(smem) & 127) {
+        if (tid == 0 && err) atomicExch(err, DOCK_E_CUDA);
+        return;
+    }
+    auto tma_issue = [&](int p) {
+        mbar_arrive_expect_tx(tma_bar, C::BOX_BYTES + (rank == 0 ? C::NYQ_BYTES : 0u));
+        tma_load_2d(smem_u32(U), &zmap, 2 * CPC * rank, p * M, smem_u32(tma_bar));
+        if (rank == 0) tma_load_2d(smem_u32(Nq), &nmap, 2 * H, p * M, smem_u32(tma_bar));
+    };
+    int tma_out = -1, v_out = -1;   // (thread 0) parity of a copy in flight that no wait has seen complete
+    if (tid == 0) {
+        mbar_init(tma_bar, 1);
+        mbar_init(v_bar, 1);
+        *s_stop = 0;
+        fence_mbar_init();
+        if (cid < n_planes) {
+            tma_issue(cid);
+            tma_out = 0;
+        }
+    }
+    // the barriers and the stop flag are initialised before any peer touches them
+    cg::this_cluster().sync();
+
+    bool fail = false;   // block-uniform: a wait of this CTA ran out
+    int i = 0;
+#pragma unroll 1
+    for (int p = cid; p < n_planes; p += G, ++i) {
+        const uint32_t par = (uint32_t)(i & 1);
+        if (!fail) {
+            if (tid == 0) mbar_arrive_expect_tx(v_bar, C::CL * C::BLK_BYTES);
+            const bool tma_ok = mbar_wait_bounded(tma_bar, par, C::WAIT_CYCLES);
+            if (__syncthreads_or(!tma_ok)) {
+                fail = true;
+                if (tid == 0 && err) atomicExch(err, DOCK_E_TIMEOUT);
+            } else if (tid == 0) {
+                tma_out = -1;
+            }
+        }
+        if (!fail) {
+            // ---- phase 1: inverse FFT along y of my packed columns, in place ----
+            const int c = tid % CPC, j = tid / CPC;
+            cf v[16];
+#pragma unroll
+            for (int s = 0; s < 16; ++s) v[s] = U[(j + 16 * s) * CPC + c];
+            if (rank == 0 && c == 0) {   // packed column 0: + i Z[ky][H]
+#pragma unroll
+                for (int s = 0; s < 16; ++s) {
+                    const cf u = Nq[(j + 16 * s) * 2];
+                    v[s] = cmake(v[s].x - u.y, v[s].y + u.x);
+                }
+            }
+            // stage 0: DFT over ky = j + 16 s; output r is index 16 j + r
+            DFT<16, true>::run(v);
+            __syncthreads();   // every stage-0 input has been read
+#pragma unroll
+            for (int r = 0; r < 16; ++r) U[(16 * j + r) * CPC + c] = v[r];
+            __syncthreads();
+            // stage 1: inputs j + 16 r (rows of this warp's threads alone), twiddles
+            // exp(+2 pi i j r / 256); output r is row y = j + 16 r
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = U[(j + 16 * r) * CPC + c];
+            __syncwarp();
+#pragma unroll
+            for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], twc_inv(j * r));
+            DFT<16, true>::run(v);
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                const int y = j + 16 * r;
+                U[y * CPC + (c ^ (y & (CPC - 1)))] = v[r];
+            }
+        }
+        fence_proxy_async();   // U is read next by the bulk-copy engine
+        if (fail && tid < C::CL) st_cluster_u32(cluster_addr(smem_u32(s_stop), (uint32_t)tid), 1u);
+        cg::this_cluster().sync();
+        if (*reinterpret_cast<volatile int *>(s_stop)) break;   // the same decision in every CTA of the cluster
+
+        // ---- push: U's row block q -> CTA q's V[rank] -----------------------
+        // withhold (test hook of the failure path): no block is pushed, every
+        // CTA's bounded wait runs out and the clusters stop at their next barrier
+        if (tid == 0 && !withhold) {
+            const uint32_t dst = smem_u32(V + (size_t)rank * BLK), mb = smem_u32(v_bar);
+#pragma unroll 1
+            for (int q = 0; q < C::CL; ++q)
+                bulk_push(cluster_addr(dst, (uint32_t)q), smem_u32(U + (size_t)q * BLK), C::BLK_BYTES,
+                          cluster_addr(mb, (uint32_t)q));
+            bulk_commit();
+        }
+        const bool v_ok = mbar_wait_bounded(v_bar, par, C::WAIT_CYCLES);
+        if (__syncthreads_or(!v_ok)) {
+            fail = true;   // told to the peers at the next cluster barrier
+            if (tid == 0) {
+                v_out = (int)par;
+                if (err) atomicExch(err, DOCK_E_TIMEOUT);
+            }
+        }
+        if (tid == 0) {
+            bulk_wait_read();   // U has been read by the pushes
+            if (!fail && p + G < n_planes) {   // the next plane loads during phase 2
+                tma_issue(p + G);
+                tma_out = (int)((i + 1) & 1);
+            }
+        }
+        if (fail) continue;   // no phase 2 on missing data; the next barrier stops the cluster
+
+        // ---- phase 2: C2R along x of my rows, argmax -------------------------
+        {
+            const int rowl = tid & 31, j = (tid >> 5) & 7, rr = tid >> 8;   // j, rr warp-uniform
+            const int ylo = rr * 32 + rowl, y = rank * RPC + ylo;
+            // element (kx, local row ylo) of V: source kx / CPC, column
+            // (kx mod CPC) ^ (y mod CPC) (RPC is a multiple of CPC)
+            auto vat = [&](int kx) -> cf {
+                return V[(kx / CPC) * BLK + ylo * CPC + ((kx % CPC) ^ (ylo & (CPC - 1)))];
+            };
+            cf v[16];
+#pragma unroll
+            for (int s = 0; s < 16; ++s) {
+                const int k = j + 8 * s;
+                cf Wk, Wm;
+                if (s == 0 && j == 0) {   // packed column 0 holds W[0] + i W[H]
+                    const cf q0 = vat(0);
+                    Wk = cmake(q0.x, 0.f);
+                    Wm = cmake(q0.y, 0.f);
+                } else {
+                    Wk = vat(k);
+                    Wm = vat(H - k);
+                }
+                const cf wc = cconj(Wm);
+                const cf Ek = cadd(Wk, wc);
+                const cf Ok = cmul(csub(Wk, wc), twc_inv(k));   // exp(+2 pi i k / M)
+                v[s] = cmake(Ek.x - Ok.y, Ek.y + Ok.x);           // E + i O
+            }
+            __syncthreads();   // every V value of these rows is in registers
+            // stage 0 (radix 16 over k = j + 8 s): output r to index 16 j + r,
+            // stored at [index][row ^ (index mod 16)] in V
+            DFT<16, true>::run(v);
+#pragma unroll
+            for (int r = 0; r < 16; ++r) V[(16 * j + r) * RPC + (ylo ^ r)] = v[r];
+            __syncthreads();
+            // stage 1 (radix 8): butterfly jj = j + 8 bb reads jj + 16 r,
+            // twiddles exp(+2 pi i 2 jj r / 256); output r is pair n = jj + 16 r
+            cf w[16];
+#pragma unroll
+            for (int bb = 0; bb < 2; ++bb) {
+                const int jj = j + 8 * bb;
+#pragma unroll
+                for (int r = 0; r < 8; ++r) w[bb * 8 + r] = V[(jj + 16 * r) * RPC + (ylo ^ jj)];
+#pragma unroll
+                for (int r = 1; r < 8; ++r) w[bb * 8 + r] = cmul(w[bb * 8 + r], twc_inv(2 * jj * r));
+                DFT<8, true>::run(w + bb * 8);
+            }
+            const int b = p >> 8, zc = p & (M - 1);
+            const uint32_t rowbase = ((uint32_t)zc * M + (uint32_t)y) * M;
+            if (EXPORT) {
+#pragma unroll
+                for (int s = 0; s < 16; ++s) {
+                    const uint32_t base = rowbase + 2u * (uint32_t)(j + 8 * (s >> 3) + 16 * (s & 7));
+                    Cout[base] = w[s].x;
+                    Cout[base + 1] = w[s].y;
+                }
+            } else {
+                float m = w[0].x;
+#pragma unroll
+                for (int s = 0; s < 16; ++s) m = fmaxf(m, fmaxf(w[s].x, w[s].y));
+                uint32_t bi = 0xFFFFFFFFu;
+#pragma unroll
+                for (int s = 0; s < 16; ++s) {
+                    const uint32_t base = rowbase + 2u * (uint32_t)(j + 8 * (s >> 3) + 16 * (s & 7));
+                    if (w[s].x == m) bi = min(bi, base);
+                    if (w[s].y == m) bi = min(bi, base + 1u);
+                }
+                unsigned long long kk = (bi == 0xFFFFFFFFu) ? 0ull : pack_key(m, bi);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long k2 = __shfl_down_sync(0xFFFFFFFFu, kk, o);
+                    kk = k2 > kk ? k2 : kk;
+                }
+                const int lane = tid & 31, warp = tid >> 5;
+                if (lane == 0) wk[warp] = kk;
+                __syncthreads();
+                if (warp == 0) {
+                    kk = lane < C::NT / 32 ? wk[lane] : 0ull;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const unsigned long long k2 = __shfl_down_sync(0xFFFFFFFFu, kk, o);
+                        kk = k2 > kk ? k2 : kk;
+                    }
+                    if (lane == 0 && kk) atomicMax(&reqs[rots[b].req].keys[rots[b].rot], kk);
+                }
+            }
+        }
+    }
+    // copies this CTA stopped waiting for: wait (bounded) before its shared
+    // memory is released
+    if (tid == 0) {
+        if (tma_out >= 0) mbar_wait_bounded(tma_bar, (uint32_t)tma_out, C::WAIT_CYCLES);
+        if (v_out >= 0) mbar_wait_bounded(v_bar, (uint32_t)v_out, C::WAIT_CYCLES);
+        bulk_wait_read();
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -845,6 +1131,95 @@ cudaError_t launch_zpass_tc(const Geo &g, int B, int group, const float2 *Y, con
     if (grid.y > 65535) return cudaErrorInvalidValue;
     k_zpass_tc<<<grid, C::NT, C::SMEM, st>>>(B, group, Y, rots, reqs, Z, err);
     return cudaGetLastError();
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to
+// the driver library)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static std::mutex mu;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!tried) {
+        tried = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }
+    return fn;
+}
+
+// Z as a 2-D FP32 tensor (2 P floats per canvas row, `rows` rows), boxes of
+// box_x floats x 256 rows
+static cudaError_t z_tensor_map(CUtensorMap *m, const float2 *Z, size_t rows, uint32_t box_x)
+{
+    using C = PlanePsCfg<4>;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t gdim[2] = {2 * (cuuint64_t)C::P, (cuuint64_t)rows};
+    const cuuint64_t gstride[1] = {2 * (cuuint64_t)C::P * sizeof(float)};
+    const cuuint32_t box[2] = {box_x, (cuuint32_t)C::M};
+    const cuuint32_t estride[2] = {1, 1};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2 *>(Z), gdim, gstride, box, estride,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int CL, bool EXPORT>
+static cudaError_t launch_plane_ps_t(int n_planes, const float2 *Z, const RotRec *rots, const ReqDev *reqs,
+                                     float *Cout, int *err, cudaStream_t st, int withhold = 0)
+{
+    using C = PlanePsCfg<CL>;
+    auto kern = k_plane_ps<CL, EXPORT>;
+    if (n_planes < 1) return cudaErrorInvalidValue;
+    cudaError_t e = ensure_twiddle_bank();
+    if (e != cudaSuccess) return e;
+    CUtensorMap zm, nm;
+    if ((e = z_tensor_map(&zm, Z, (size_t)n_planes * C::M, 2 * C::CPC)) != cudaSuccess) return e;
+    if ((e = z_tensor_map(&nm, Z, (size_t)n_planes * C::M, 4)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM)) != cudaSuccess)
+        return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(C::NT);
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C::CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    // as many clusters as are resident at once (each walks its share of planes)
+    cfg.gridDim = dim3(C::CL * 1024);
+    int resident = 0;
+    if ((e = cudaOccupancyMaxActiveClusters(&resident, kern, &cfg)) != cudaSuccess) return e;
+    if (resident < 1) return cudaErrorInvalidConfiguration;
+    cfg.gridDim = dim3(C::CL * (unsigned)std::min(resident, n_planes));
+    return cudaLaunchKernelEx(&cfg, kern, zm, nm, n_planes, rots, reqs, Cout, err, withhold);
+}
+
+bool plane_ps_supported(int M, int cl) { return M == 256 && (cl == 4 || cl == 8); }
+
+cudaError_t launch_plane_ps(const Geo &g, int cl, int B, const float2 *Z, const RotRec *rots, const ReqDev *reqs,
+                            int *err, cudaStream_t st)
+{
+    if (!plane_ps_supported(g.M, cl) || g.P != PlanePsCfg<4>::P || B < 1 || B > 65535) return cudaErrorInvalidValue;
+    return cl == 4 ? launch_plane_ps_t<4, false>(B * g.M, Z, rots, reqs, nullptr, err, st)
+                   : launch_plane_ps_t<8, false>(B * g.M, Z, rots, reqs, nullptr, err, st);
+}
+
+cudaError_t launch_plane_ps_export(const Geo &g, int cl, const float2 *Z, float *C, int *err, cudaStream_t st,
+                                   int withhold)
+{
+    if (!plane_ps_supported(g.M, cl) || g.P != PlanePsCfg<4>::P) return cudaErrorInvalidValue;
+    return cl == 4 ? launch_plane_ps_t<4, true>(g.M, Z, nullptr, nullptr, C, err, st, withhold)
+                   : launch_plane_ps_t<8, true>(g.M, Z, nullptr, nullptr, C, err, st, withhold);
 }
 
 cudaError_t launch_plane_cl(const Geo &g, int cl, int B, const float2 *Z, const float2 *tw, const RotRec *rots,

@@ -1,6 +1,7 @@
 """The z pass and the inverse plane pass at canvas 256 in each of their launch
 shapes (16 or 32 columns per z-pass block, the 16-column one with its DFT
-stages on the CUDA cores or on the tensor cores; 2, 4 or 8 CTAs per plane) against
+stages on the CUDA cores or on the tensor cores; 2, 4 or 8 CTAs per plane, the
+cluster ones also as persistent clusters with TMA staging) against
 the FP64 oracle (Eq. (7), (9)): the full correlation field within 1e-4 of
 max |C|, per-rotation peaks within the score tolerance, peak indices exact
 where the oracle's top-two gap exceeds twice that tolerance and otherwise one
@@ -13,9 +14,11 @@ from paper_2605_21398_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-# (plane_cl, zpass_cols, zpass_tc): the 2-CTA plane pass with the 32-column z
-# pass, and the cluster plane passes with each z pass
-SHAPES = ((2, 32, 0), (4, 16, 0), (8, 16, 0), (4, 32, 0), (4, 16, 1), (8, 16, 1))
+# (plane_cl, zpass_cols, zpass_tc, plane_tma): the 2-CTA plane pass with the
+# 32-column z pass, the cluster plane passes with each z pass, and the
+# persistent cluster plane passes
+SHAPES = ((2, 32, 0, 0), (4, 16, 0, 0), (8, 16, 0, 0), (4, 32, 0, 0), (4, 16, 1, 0), (8, 16, 1, 0), (4, 16, 0, 1),
+          (8, 16, 0, 1), (4, 32, 0, 1))
 
 
 @pytest.fixture(scope="module")
@@ -60,14 +63,15 @@ def test_full_field_at_canvas_256_in_every_shape(ctx, workload):
     fields = {}
     saved = ctx.get_tuning(w.N)
     try:
-        for cl, zc, tc in SHAPES:
-            ctx.set_tuning(N=w.N, plane_cl=cl, zpass_cols=zc, zpass_tc=tc)
+        for shape in SHAPES:
+            cl, zc, tc, tma = shape
+            ctx.set_tuning(N=w.N, plane_cl=cl, zpass_cols=zc, zpass_tc=tc, plane_tma=tma)
             t = ctx.get_tuning(w.N)
-            assert (t["plane_cl"], t["zpass_cols"], t["zpass_tc"]) == (cl, zc, tc)
+            assert (t["plane_cl"], t["zpass_cols"], t["zpass_tc"], t["plane_tma"]) == shape
             C = ctx.search_scores(ob, sw, q)
             err = np.max(np.abs(C - Co))
-            assert err <= tol, (cl, zc, tc, err, tol)
-            fields[cl, zc, tc] = C
+            assert err <= tol, (shape, err, tol)
+            fields[shape] = C
     finally:
         ctx.set_tuning(**saved)
     # the shapes differ only in the order of FP32 operations
@@ -91,18 +95,19 @@ def test_peaks_at_canvas_256_in_every_shape(ctx, workload):
     got = {}
     saved = ctx.get_tuning(w.N)
     try:
-        for cl, zc, tc in SHAPES:
-            ctx.set_tuning(N=w.N, plane_cl=cl, zpass_cols=zc, zpass_tc=tc, batch=3)
+        for shape in SHAPES:
+            cl, zc, tc, tma = shape
+            ctx.set_tuning(N=w.N, plane_cl=cl, zpass_cols=zc, zpass_tc=tc, plane_tma=tma, batch=3)
             _, pk = ctx.search_so3(ob, sw, len(quats), 2, sampler=3, quats=quats, want_peaks=True)
             for i, (sc, idx, tol, gap, Cf) in enumerate(ref):
-                assert abs(pk["score"][i] - sc) <= tol + 1e-4 * abs(sc), (cl, zc, tc, i)
+                assert abs(pk["score"][i] - sc) <= tol + 1e-4 * abs(sc), (shape, i)
                 if i in gapped:
-                    assert pk["idx"][i] == idx, (cl, zc, tc, i)
+                    assert pk["idx"][i] == idx, (shape, i)
                 # every rotation: the chosen shift is one of the oracle's
                 # maxima up to the tolerance (several are correct when the
                 # top of the field is flatter than the FP32 error)
-                assert Cf[pk["idx"][i]] >= sc - 2 * tol, (cl, zc, tc, i)
-            got[cl, zc, tc] = pk
+                assert Cf[pk["idx"][i]] >= sc - 2 * tol, (shape, i)
+            got[shape] = pk
     finally:
         ctx.set_tuning(**saved)
     for cl in SHAPES[1:]:
@@ -112,6 +117,6 @@ def test_peaks_at_canvas_256_in_every_shape(ctx, workload):
 def test_set_tuning_rejects_out_of_range_shapes(ctx):
     from paper_2605_21398_gb300 import dock
     for bad in (dict(N=128, plane_cl=3), dict(N=128, zpass_cols=8), dict(N=128, batch=0), dict(N=128, vox_blocks=5),
-                dict(N=128, zpass_tc=2), dict(N=48)):
+                dict(N=128, zpass_tc=2), dict(N=128, plane_tma=-1), dict(N=48)):
         with pytest.raises(dock.DockError):
             ctx.set_tuning(**bad)
