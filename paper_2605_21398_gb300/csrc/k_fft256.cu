@@ -359,19 +359,23 @@ k_plane_cl(const float2 *__restrict__ Z, const float2 *__restrict__ tw, const Ro
 // tensor-memory-access unit loads the next plane's columns from HBM into the
 // staging buffer U (one 2-D box of 256 rows x CPC complex, plus the Nyquist
 // column for rank 0) while phase 2 of the current plane runs:
-//   phase 1  in place in U: radix 16 x 16 inverse FFT along y; thread (c, j)
-//            (tid = CPC j + c) holds column c at rows j + 16 s; the last stage
-//            writes row y's column c at c ^ (y mod CPC), so that phase 2's
-//            warps (32 rows of one column) hit distinct banks
+//   phase 1  radix 16 x 16 inverse FFT along y, from U through V (idle until
+//            the pushes) back into U; thread (c, j) (tid = CPC j + c) holds
+//            column c at rows j + 16 s; the last stage writes row y's column
+//            c at c ^ (y mod CPC), so that phase 2's warps (32 rows of one
+//            column) hit distinct banks
 //   push     U's row block q (RPC rows, contiguous) to CTA q's V[rank]
 //            by the bulk-copy engine, completion counted in bytes on CTA q's
 //            mbarrier (the own block included)
 //   phase 2  C2R along x of rows [64 rank, +64) from V, the exchange in place
 //            in V, argmax with the lowest canvas index on ties
-// Per plane one cluster barrier: after it every CTA has finished phase 1 of
-// this plane and phase 2 of the previous one, so V may be overwritten.  Every
-// wait is bounded; a CTA that gave up tells its peers through their shared
-// memory before the next cluster barrier and the whole cluster stops there.
+// Per plane one cluster barrier (after it every CTA has finished phase 1 of
+// this plane and phase 2 of the previous one, so V may be overwritten) and
+// four block barriers; the waits' failure checks ride on two of them, and the
+// plane's peak key collects in shared memory and leaves after the next one.
+// Every wait is bounded; a CTA that gave up tells its peers through their
+// shared memory before the next cluster barrier and the whole cluster stops
+// there.
 // ---------------------------------------------------------------------------
 template <int CL_> struct PlanePsCfg {
     static constexpr int M = 256, H = 128, P = 130, CL = CL_, CPC = H / CL, RPC = M / CL;
@@ -382,8 +386,8 @@ template <int CL_> struct PlanePsCfg {
     static constexpr uint32_t NYQ_BYTES = M * 16;                  // all rows of kx = 128, 129
     static constexpr uint32_t BLK_BYTES = BLK * 8;
     static constexpr size_t U_OFF = 0, V_OFF = BOX_BYTES, N_OFF = V_OFF + (size_t)CL * BLK_BYTES;
-    static constexpr size_t MB_OFF = N_OFF + NYQ_BYTES;            // two mbarriers, the stop flag, warp keys
-    static constexpr size_t SMEM = MB_OFF + 32 + 8 * (NT / 32);
+    static constexpr size_t MB_OFF = N_OFF + NYQ_BYTES;            // two mbarriers, the stop flag, two plane keys
+    static constexpr size_t SMEM = MB_OFF + 48;
     static constexpr long long WAIT_CYCLES = 1ll << 31;
     static_assert(MINB * (SMEM + 1024) <= 228 * 1024, "resident CTAs per SM");
     static_assert(NT == 16 * CPC && RPC % CPC == 0 && RPC % 32 == 0, "thread mappings of the two phases");
@@ -426,7 +430,7 @@ k_plane_ps(const __grid_constant__ CUtensorMap zmap, const __grid_constant__ CUt
     uint64_t *tma_bar = reinterpret_cast<uint64_t *>(smem + C::MB_OFF);
     uint64_t *v_bar = tma_bar + 1;
     int *s_stop = reinterpret_cast<int *>(smem + C::MB_OFF + 16);
-    unsigned long long *wk = reinterpret_cast<unsigned long long *>(smem + C::MB_OFF + 32);
+    unsigned long long *s_key = reinterpret_cast<unsigned long long *>(smem + C::MB_OFF + 32);   // by plane parity
     const int tid = threadIdx.x;
     const int rank = (int)cg::this_cluster().block_rank();
     const int cid = blockIdx.x / C::CL, G = gridDim.x / C::CL;
@@ -446,6 +450,7 @@ k_plane_ps(const __grid_constant__ CUtensorMap zmap, const __grid_constant__ CUt
         mbar_init(tma_bar, 1);
         mbar_init(v_bar, 1);
         *s_stop = 0;
+        s_key[0] = s_key[1] = 0ull;
         fence_mbar_init();
         if (cid < n_planes) {
             tma_issue(cid);
@@ -456,6 +461,18 @@ k_plane_ps(const __grid_constant__ CUtensorMap zmap, const __grid_constant__ CUt
     cg::this_cluster().sync();
 
     bool fail = false;   // block-uniform: a wait of this CTA ran out
+    int key_b = -1;      // (thread 0) rotation whose plane key waits in s_key[key_par]
+    uint32_t key_par = 0;
+    // the previous plane's key (every warp has added to it before the barrier
+    // that precedes this call) goes to its rotation's key array
+    auto flush_key = [&]() {
+        if (!EXPORT && tid == 0 && key_b >= 0) {
+            const unsigned long long kk = s_key[key_par];
+            if (kk) atomicMax(&reqs[rots[key_b].req].keys[rots[key_b].rot], kk);
+            s_key[key_par] = 0ull;
+            key_b = -1;
+        }
+    };
     int i = 0;
 #pragma unroll 1
     for (int p = cid; p < n_planes; p += G, ++i) {
@@ -463,15 +480,9 @@ k_plane_ps(const __grid_constant__ CUtensorMap zmap, const __grid_constant__ CUt
         if (!fail) {
             if (tid == 0) mbar_arrive_expect_tx(v_bar, C::CL * C::BLK_BYTES);
             const bool tma_ok = mbar_wait_bounded(tma_bar, par, C::WAIT_CYCLES);
-            if (__syncthreads_or(!tma_ok)) {
-                fail = true;
-                if (tid == 0 && err) atomicExch(err, DOCK_E_TIMEOUT);
-            } else if (tid == 0) {
-                tma_out = -1;
-            }
-        }
-        if (!fail) {
-            // ---- phase 1: inverse FFT along y of my packed columns, in place ----
+            // ---- phase 1: inverse FFT along y of my packed columns ----------
+            // stage 0 from U into V (idle until the pushes of this plane),
+            // stage 1 from V back into U
             const int c = tid % CPC, j = tid / CPC;
             cf v[16];
 #pragma unroll
@@ -485,25 +496,32 @@ k_plane_ps(const __grid_constant__ CUtensorMap zmap, const __grid_constant__ CUt
             }
             // stage 0: DFT over ky = j + 16 s; output r is index 16 j + r
             DFT<16, true>::run(v);
-            __syncthreads();   // every stage-0 input has been read
+            // after this barrier every warp has left the previous plane's
+            // phase 2 (V is free, its warp keys are in) and read its U inputs
+            if (__syncthreads_or(!tma_ok)) {
+                fail = true;
+                if (tid == 0 && err) atomicExch(err, DOCK_E_TIMEOUT);
+            } else {
+                if (tid == 0) tma_out = -1;
+                flush_key();
 #pragma unroll
-            for (int r = 0; r < 16; ++r) U[(16 * j + r) * CPC + c] = v[r];
-            __syncthreads();
-            // stage 1: inputs j + 16 r (rows of this warp's threads alone), twiddles
-            // exp(+2 pi i j r / 256); output r is row y = j + 16 r
+                for (int r = 0; r < 16; ++r) V[(16 * j + r) * CPC + c] = v[r];
+                __syncthreads();
+                // stage 1: inputs j + 16 r, twiddles exp(+2 pi i j r / 256);
+                // output r is row y = j + 16 r
 #pragma unroll
-            for (int r = 0; r < 16; ++r) v[r] = U[(j + 16 * r) * CPC + c];
-            __syncwarp();
+                for (int r = 0; r < 16; ++r) v[r] = V[(j + 16 * r) * CPC + c];
 #pragma unroll
-            for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], twc_inv(j * r));
-            DFT<16, true>::run(v);
+                for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], twc_inv(j * r));
+                DFT<16, true>::run(v);
 #pragma unroll
-            for (int r = 0; r < 16; ++r) {
-                const int y = j + 16 * r;
-                U[y * CPC + (c ^ (y & (CPC - 1)))] = v[r];
+                for (int r = 0; r < 16; ++r) {
+                    const int y = j + 16 * r;
+                    U[y * CPC + (c ^ (y & (CPC - 1)))] = v[r];
+                }
             }
         }
-        fence_proxy_async();   // U is read next by the bulk-copy engine
+        fence_proxy_async();   // U is read next, and V written, by the bulk-copy engine
         if (fail && tid < C::CL) st_cluster_u32(cluster_addr(smem_u32(s_stop), (uint32_t)tid), 1u);
         cg::this_cluster().sync();
         if (*reinterpret_cast<volatile int *>(s_stop)) break;   // the same decision in every CTA of the cluster
@@ -520,109 +538,101 @@ k_plane_ps(const __grid_constant__ CUtensorMap zmap, const __grid_constant__ CUt
             bulk_commit();
         }
         const bool v_ok = mbar_wait_bounded(v_bar, par, C::WAIT_CYCLES);
-        if (__syncthreads_or(!v_ok)) {
-            fail = true;   // told to the peers at the next cluster barrier
-            if (tid == 0) {
-                v_out = (int)par;
-                if (err) atomicExch(err, DOCK_E_TIMEOUT);
-            }
-        }
         if (tid == 0) {
             bulk_wait_read();   // U has been read by the pushes
-            if (!fail && p + G < n_planes) {   // the next plane loads during phase 2
+            if (v_ok && p + G < n_planes) {   // the next plane loads during phase 2
                 tma_issue(p + G);
                 tma_out = (int)((i + 1) & 1);
             }
         }
-        if (fail) continue;   // no phase 2 on missing data; the next barrier stops the cluster
 
         // ---- phase 2: C2R along x of my rows, argmax -------------------------
-        {
-            const int rowl = tid & 31, j = (tid >> 5) & 7, rr = tid >> 8;   // j, rr warp-uniform
-            const int ylo = rr * 32 + rowl, y = rank * RPC + ylo;
-            // element (kx, local row ylo) of V: source kx / CPC, column
-            // (kx mod CPC) ^ (y mod CPC) (RPC is a multiple of CPC)
-            auto vat = [&](int kx) -> cf {
-                return V[(kx / CPC) * BLK + ylo * CPC + ((kx % CPC) ^ (ylo & (CPC - 1)))];
-            };
-            cf v[16];
+        const int rowl = tid & 31, j = (tid >> 5) & 7, rr = tid >> 8;   // j, rr warp-uniform
+        const int ylo = rr * 32 + rowl, y = rank * RPC + ylo;
+        // element (kx, local row ylo) of V: source kx / CPC, column
+        // (kx mod CPC) ^ (y mod CPC) (RPC is a multiple of CPC)
+        auto vat = [&](int kx) -> cf { return V[(kx / CPC) * BLK + ylo * CPC + ((kx % CPC) ^ (ylo & (CPC - 1)))]; };
+        cf v[16];
+#pragma unroll
+        for (int s = 0; s < 16; ++s) {
+            const int k = j + 8 * s;
+            cf Wk, Wm;
+            if (s == 0 && j == 0) {   // packed column 0 holds W[0] + i W[H]
+                const cf q0 = vat(0);
+                Wk = cmake(q0.x, 0.f);
+                Wm = cmake(q0.y, 0.f);
+            } else {
+                Wk = vat(k);
+                Wm = vat(H - k);
+            }
+            const cf wc = cconj(Wm);
+            const cf Ek = cadd(Wk, wc);
+            const cf Ok = cmul(csub(Wk, wc), twc_inv(k));   // exp(+2 pi i k / M)
+            v[s] = cmake(Ek.x - Ok.y, Ek.y + Ok.x);           // E + i O
+        }
+        if (__syncthreads_or(!v_ok)) {   // (also: every V value of these rows is in registers)
+            fail = true;                 // told to the peers at the next cluster barrier
+            if (tid == 0) {
+                v_out = (int)par;
+                if (err) atomicExch(err, DOCK_E_TIMEOUT);
+            }
+            continue;   // no phase 2 on missing data
+        }
+        // stage 0 (radix 16 over k = j + 8 s): output r to index 16 j + r,
+        // stored at [index][row ^ (index mod 16)] in V
+        DFT<16, true>::run(v);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) V[(16 * j + r) * RPC + (ylo ^ r)] = v[r];
+        __syncthreads();
+        // stage 1 (radix 8): butterfly jj = j + 8 bb reads jj + 16 r,
+        // twiddles exp(+2 pi i 2 jj r / 256); output r is pair n = jj + 16 r
+        cf w[16];
+#pragma unroll
+        for (int bb = 0; bb < 2; ++bb) {
+            const int jj = j + 8 * bb;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) w[bb * 8 + r] = V[(jj + 16 * r) * RPC + (ylo ^ jj)];
+#pragma unroll
+            for (int r = 1; r < 8; ++r) w[bb * 8 + r] = cmul(w[bb * 8 + r], twc_inv(2 * jj * r));
+            DFT<8, true>::run(w + bb * 8);
+        }
+        const int b = p >> 8, zc = p & (M - 1);
+        const uint32_t rowbase = ((uint32_t)zc * M + (uint32_t)y) * M;
+        if (EXPORT) {
 #pragma unroll
             for (int s = 0; s < 16; ++s) {
-                const int k = j + 8 * s;
-                cf Wk, Wm;
-                if (s == 0 && j == 0) {   // packed column 0 holds W[0] + i W[H]
-                    const cf q0 = vat(0);
-                    Wk = cmake(q0.x, 0.f);
-                    Wm = cmake(q0.y, 0.f);
-                } else {
-                    Wk = vat(k);
-                    Wm = vat(H - k);
-                }
-                const cf wc = cconj(Wm);
-                const cf Ek = cadd(Wk, wc);
-                const cf Ok = cmul(csub(Wk, wc), twc_inv(k));   // exp(+2 pi i k / M)
-                v[s] = cmake(Ek.x - Ok.y, Ek.y + Ok.x);           // E + i O
+                const uint32_t base = rowbase + 2u * (uint32_t)(j + 8 * (s >> 3) + 16 * (s & 7));
+                Cout[base] = w[s].x;
+                Cout[base + 1] = w[s].y;
             }
-            __syncthreads();   // every V value of these rows is in registers
-            // stage 0 (radix 16 over k = j + 8 s): output r to index 16 j + r,
-            // stored at [index][row ^ (index mod 16)] in V
-            DFT<16, true>::run(v);
+        } else {
+            float m = w[0].x;
 #pragma unroll
-            for (int r = 0; r < 16; ++r) V[(16 * j + r) * RPC + (ylo ^ r)] = v[r];
-            __syncthreads();
-            // stage 1 (radix 8): butterfly jj = j + 8 bb reads jj + 16 r,
-            // twiddles exp(+2 pi i 2 jj r / 256); output r is pair n = jj + 16 r
-            cf w[16];
+            for (int s = 0; s < 16; ++s) m = fmaxf(m, fmaxf(w[s].x, w[s].y));
+            uint32_t bi = 0xFFFFFFFFu;
 #pragma unroll
-            for (int bb = 0; bb < 2; ++bb) {
-                const int jj = j + 8 * bb;
-#pragma unroll
-                for (int r = 0; r < 8; ++r) w[bb * 8 + r] = V[(jj + 16 * r) * RPC + (ylo ^ jj)];
-#pragma unroll
-                for (int r = 1; r < 8; ++r) w[bb * 8 + r] = cmul(w[bb * 8 + r], twc_inv(2 * jj * r));
-                DFT<8, true>::run(w + bb * 8);
+            for (int s = 0; s < 16; ++s) {
+                const uint32_t base = rowbase + 2u * (uint32_t)(j + 8 * (s >> 3) + 16 * (s & 7));
+                if (w[s].x == m) bi = min(bi, base);
+                if (w[s].y == m) bi = min(bi, base + 1u);
             }
-            const int b = p >> 8, zc = p & (M - 1);
-            const uint32_t rowbase = ((uint32_t)zc * M + (uint32_t)y) * M;
-            if (EXPORT) {
+            unsigned long long kk = (bi == 0xFFFFFFFFu) ? 0ull : pack_key(m, bi);
 #pragma unroll
-                for (int s = 0; s < 16; ++s) {
-                    const uint32_t base = rowbase + 2u * (uint32_t)(j + 8 * (s >> 3) + 16 * (s & 7));
-                    Cout[base] = w[s].x;
-                    Cout[base + 1] = w[s].y;
-                }
-            } else {
-                float m = w[0].x;
-#pragma unroll
-                for (int s = 0; s < 16; ++s) m = fmaxf(m, fmaxf(w[s].x, w[s].y));
-                uint32_t bi = 0xFFFFFFFFu;
-#pragma unroll
-                for (int s = 0; s < 16; ++s) {
-                    const uint32_t base = rowbase + 2u * (uint32_t)(j + 8 * (s >> 3) + 16 * (s & 7));
-                    if (w[s].x == m) bi = min(bi, base);
-                    if (w[s].y == m) bi = min(bi, base + 1u);
-                }
-                unsigned long long kk = (bi == 0xFFFFFFFFu) ? 0ull : pack_key(m, bi);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const unsigned long long k2 = __shfl_down_sync(0xFFFFFFFFu, kk, o);
-                    kk = k2 > kk ? k2 : kk;
-                }
-                const int lane = tid & 31, warp = tid >> 5;
-                if (lane == 0) wk[warp] = kk;
-                __syncthreads();
-                if (warp == 0) {
-                    kk = lane < C::NT / 32 ? wk[lane] : 0ull;
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        const unsigned long long k2 = __shfl_down_sync(0xFFFFFFFFu, kk, o);
-                        kk = k2 > kk ? k2 : kk;
-                    }
-                    if (lane == 0 && kk) atomicMax(&reqs[rots[b].req].keys[rots[b].rot], kk);
-                }
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long k2 = __shfl_down_sync(0xFFFFFFFFu, kk, o);
+                kk = k2 > kk ? k2 : kk;
+            }
+            // the plane's key in shared memory; thread 0 sends it on after the
+            // next barrier (the next plane's, or the one after the loop)
+            if ((tid & 31) == 0 && kk) atomicMax(&s_key[par], kk);
+            if (tid == 0) {
+                key_b = b;
+                key_par = par;
             }
         }
     }
+    __syncthreads();
+    if (!fail) flush_key();
     // copies this CTA stopped waiting for: wait (bounded) before its shared
     // memory is released
     if (tid == 0) {
