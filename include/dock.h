@@ -444,6 +444,9 @@ typedef struct dock_tuning {
     int32_t plane_tma;       /* 1 (canvas 256, plane_cl 4 or 8): the plane pass as persistent clusters that
                                 load the next plane's columns with the tensor-memory-access unit
                                 during the current plane's C2R; 0: one cluster per plane */
+    int32_t fwd_runs;        /* 1 (canvas 256): the forward x and y passes of binary slabs from their
+                                run lists, 16 kx columns per round (three blocks per SM); 0: all
+                                columns of a slab at once (one block per SM) */
     double us_per_rotation;  /* measured device time per rotation of this shape (0 = not measured) */
 } dock_tuning;
 
@@ -467,9 +470,9 @@ DOCK_API dock_status dock_load_tuning(dock_ctx *ctx, const char *cache_path, int
 DOCK_API dock_status dock_get_tuning(dock_ctx *ctx, int32_t N, dock_tuning *out);
 /* Sets the shape for lattice side t->N (batch 1..256, group 0..256,
  * vox_blocks 3 or 4, plane_cl 0, 2, 4 or 8, zpass_cols 0, 16 or 32,
- * vox_overlap 0 or 1, zpass_tc 0 or 1, plane_tma 0 or 1); results do not depend on it beyond
- * rounding (zpass_tc changes the rounding of the z pass's products, within
- * the FP32 error of the transform).
+ * vox_overlap 0 or 1, zpass_tc 0 or 1, plane_tma 0 or 1, fwd_runs 0 or 1);
+ * results do not depend on it beyond rounding (zpass_tc and fwd_runs change
+ * the order of FP32 operations, within the error of the transforms).
  * DOCK_E_INVALID for values out of range. */
 DOCK_API dock_status dock_set_tuning(dock_ctx *ctx, const dock_tuning *t);
 

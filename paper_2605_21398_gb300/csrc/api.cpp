@@ -1376,6 +1376,7 @@ static const int ZPASS_COLS_DEFAULT = 16;
 static const int VOX_OVERLAP_DEFAULT = 0;
 static const int ZPASS_TC_DEFAULT = 0;
 static const int PLANE_TMA_DEFAULT = 1;
+static const int FWD_RUNS_DEFAULT = 1;
 
 static dock_tuning tuning_for(dock_ctx *ctx, const Geo &g)
 {
@@ -1391,6 +1392,7 @@ static dock_tuning tuning_for(dock_ctx *ctx, const Geo &g)
     t.vox_overlap = VOX_OVERLAP_DEFAULT;
     t.zpass_tc = g.M == 256 ? ZPASS_TC_DEFAULT : 0;
     t.plane_tma = g.M == 256 ? PLANE_TMA_DEFAULT : 0;
+    t.fwd_runs = g.M == 256 ? FWD_RUNS_DEFAULT : 0;
     return t;
 }
 
@@ -1401,7 +1403,18 @@ static bool valid_tuning(const dock_tuning &t)
            (t.plane_cl == 0 || t.plane_cl == 2 || t.plane_cl == 4 || t.plane_cl == 8) &&
            (t.zpass_cols == 0 || t.zpass_cols == 16 || t.zpass_cols == 32) &&
            (t.vox_overlap == 0 || t.vox_overlap == 1) && (t.zpass_tc == 0 || t.zpass_tc == 1) &&
-           (t.plane_tma == 0 || t.plane_tma == 1);
+           (t.plane_tma == 0 || t.plane_tma == 1) && (t.fwd_runs == 0 || t.fwd_runs == 1);
+}
+
+// The forward x and y passes of a batch: the run-list kernel at canvas 256
+// when the shape asks for it and no request of the batch rotates its object
+// (those transform the resampled object grid), else k_fwd2d.
+static cudaError_t fwd_pass(const dock_tuning &tc, const Geo &g, int B, const uint32_t *bits, float2 *Y,
+                            const float2 *tw, const float2 *qt, cudaStream_t st, const uint32_t *mask,
+                            const RotRec *rots, const ReqDev *reqs, const float *ogrids, bool ro_any)
+{
+    if (g.M == 256 && tc.fwd_runs && !ro_any) return launch_fwd2d_runs(g, B, bits, Y, qt, mask, st);
+    return launch_fwd2d(g, B, bits, Y, tw, qt, st, mask, rots, reqs, ogrids);
 }
 
 // Runs records [r0, r1) of rots through the search pipeline; every
@@ -1486,12 +1499,12 @@ static dock_status run_pipeline_rots(dock_ctx *ctx, const Geo &g, const ReqDev *
         }
         {
             Prof pr(ctx, "fwd2d");
-            CK(ctx, launch_fwd2d(g, nb, bk, Y, tw, qt, ctx->stream, nullptr, rb, reqs, ro_any ? ctx->ogr : nullptr));
+            CK(ctx, fwd_pass(tc, g, nb, bk, Y, tw, qt, ctx->stream, nullptr, rb, reqs, ro_any ? ctx->ogr : nullptr, ro_any));
         }
         if (ovl) CK(ctx, cudaEventRecord(ctx->vev[2 + kb], ctx->stream));
         if (dual) {
             Prof pr(ctx, "fwd2d_nc");
-            CK(ctx, launch_fwd2d(g, nb, bits2, Y2, tw, qt, ctx->stream, ctx->bits, rb, reqs));
+            CK(ctx, fwd_pass(tc, g, nb, bits2, Y2, tw, qt, ctx->stream, ctx->bits, rb, reqs, nullptr, ro_any));
         }
         {
             Prof pr(ctx, dual ? "zpass_dual" : "zpass");
@@ -1807,9 +1820,9 @@ static dock_status write_tuning(dock_ctx *ctx, const char *path)
         const dock_tuning &t = kv.second;
         fprintf(f,
                 "%s\n  {\"N\": %d, \"batch\": %d, \"group\": %d, \"vox_blocks\": %d, \"plane_cl\": %d, "
-                "\"zpass_cols\": %d, \"vox_overlap\": %d, \"zpass_tc\": %d, \"plane_tma\": %d, \"us_per_rotation\": %.3f}",
+                "\"zpass_cols\": %d, \"vox_overlap\": %d, \"zpass_tc\": %d, \"plane_tma\": %d, \"fwd_runs\": %d, \"us_per_rotation\": %.3f}",
                 first ? "" : ",", t.N, t.batch, t.group, t.vox_blocks, t.plane_cl, t.zpass_cols, t.vox_overlap,
-                t.zpass_tc, t.plane_tma, t.us_per_rotation);
+                t.zpass_tc, t.plane_tma, t.fwd_runs, t.us_per_rotation);
         first = false;
     }
     fprintf(f, "\n]}\n");
@@ -1893,6 +1906,11 @@ extern "C" dock_status dock_autotune(dock_ctx *ctx, const dock_object *ob, const
         }
         {
             dock_tuning t = best;
+            t.fwd_runs = best.fwd_runs ? 0 : 1;
+            if ((s = trial(t)) != DOCK_OK) { restore(); return s; }
+        }
+        {
+            dock_tuning t = best;
             t.zpass_cols = best.zpass_cols == 16 ? 32 : 16;
             t.zpass_tc = 0;
             if ((s = trial(t)) != DOCK_OK) { restore(); return s; }
@@ -1961,6 +1979,9 @@ extern "C" dock_status dock_load_tuning(dock_ctx *ctx, const char *path, int32_t
             long pt = gt.M == 256 ? PLANE_TMA_DEFAULT : 0;
             json_int(e.c_str(), "\"plane_tma\"", &pt);
             t.plane_tma = (int)pt;
+            long fr = gt.M == 256 ? FWD_RUNS_DEFAULT : 0;
+            json_int(e.c_str(), "\"fwd_runs\"", &fr);
+            t.fwd_runs = (int)fr;
             if (!valid_tuning(t)) {
                 pos = end;
                 continue;
@@ -2054,13 +2075,14 @@ static dock_status search_scores_impl(dock_ctx *ctx, const dock_object *ob, cons
     if ((s = dalloc(ctx, (void **)&Y, ybytes, nullptr)) != DOCK_OK) return s;
     if ((s = dalloc(ctx, (void **)&dC, csz * sizeof(float), nullptr)) != DOCK_OK) { dfree(ctx, Y, ybytes); return s; }
     float2 *Y2 = dual ? Y + ysz + zsz : nullptr;
+    const dock_tuning tc = tuning_for(ctx, g);
     cudaError_t e = cudaMemsetAsync(ctx->errflag, 0, sizeof(int), ctx->stream);
     if (e == cudaSuccess) e = launch_voxelise(g, ctx->reqs, ctx->rots, 1, ctx->bits, ctx->stream);
-    if (e == cudaSuccess) e = launch_fwd2d(g, 1, ctx->bits, Y, tw, qt, ctx->stream, nullptr, ctx->rots, ctx->reqs);
+    if (e == cudaSuccess)
+        e = fwd_pass(tc, g, 1, ctx->bits, Y, tw, qt, ctx->stream, nullptr, ctx->rots, ctx->reqs, nullptr, ro);
     if (dual && e == cudaSuccess) e = launch_voxelise(g, ctx->reqs, ctx->rots, 1, ctx->bits + bsz, ctx->stream, 4, 1);
     if (dual && e == cudaSuccess)
-        e = launch_fwd2d(g, 1, ctx->bits + bsz, Y2, tw, qt, ctx->stream, ctx->bits, ctx->rots, ctx->reqs);
-    const dock_tuning tc = tuning_for(ctx, g);
+        e = fwd_pass(tc, g, 1, ctx->bits + bsz, Y2, tw, qt, ctx->stream, ctx->bits, ctx->rots, ctx->reqs, nullptr, ro);
     if (e == cudaSuccess) {
         if (g.M == 256 && tc.zpass_cols == 16 && tc.zpass_tc && !dual)
             e = launch_zpass_tc(g, 1, 1, Y, ctx->rots, ctx->reqs, Y + ysz, ctx->errflag, ctx->stream);

@@ -105,6 +105,10 @@ cudaError_t launch_zpass16(const Geo &g, int B, int group, const float2 *Y, cons
 // z pass with its DFT stages as 3 x TF32 products on the tensor cores (canvas 256, plain score)
 cudaError_t launch_zpass_tc(const Geo &g, int B, int group, const float2 *Y, const RotRec *rots, const ReqDev *reqs,
                             float2 *Z, int *err, cudaStream_t st);
+// forward x and y passes of binary slabs at canvas 256 from their run lists
+// (bits & ~mask when mask is given); no rotated-object requests
+cudaError_t launch_fwd2d_runs(const Geo &g, int B, const uint32_t *bits, float2 *Y, const float2 *q,
+                              const uint32_t *mask, cudaStream_t st);
 // persistent cluster plane pass with TMA staging of the columns (canvas 256, 4 or 8 CTAs per plane)
 bool plane_ps_supported(int M, int cl);
 cudaError_t launch_plane_ps(const Geo &g, int cl, int B, const float2 *Z, const RotRec *rots, const ReqDev *reqs,

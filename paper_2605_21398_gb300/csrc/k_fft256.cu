@@ -643,6 +643,155 @@ k_plane_ps(const __grid_constant__ CUtensorMap zmap, const __grid_constant__ CUt
 }
 
 // ---------------------------------------------------------------------------
+// Forward x and y transforms of a slab of binary S at canvas 256 from its run
+// list (Eq. (9), the first two of the three 1-D passes; the bits path of
+// k_fwd2d with a footprint that lets three blocks share an SM).
+//
+// Block (slab jz, rotation b), 256 threads.  Each row's runs of set bits
+// [a, e) are extracted once into shared memory (at most 64 per row of 128).
+// Then, for each round of 16 kx columns p0 .. p0 + 15:
+//   x  X[y][c] = q(kx) sum over runs (w^(kx a) - w^(kx e)), kx = p0 + c,
+//      q(kx) = 1 / (1 - w^kx), w = exp(-2 pi i / 256) (kx = 0: the count of
+//      set bits, with the Nyquist column, sum of (-1)^x, packed as its
+//      imaginary part); a half-warp per row, lane c on kx;
+//   y  forward 256-point DFT of each column (rows >= 128 are zero padding):
+//      radix 16 x 16, thread (c, j) holding rows j + 16 s, one exchange
+//      through shared memory, outputs ky = j + 16 r written to Y[ky][kx]
+//      (a warp writes two rows of 16 consecutive kx).
+// Packed column 0 is unpacked into kx = 0 and kx = 128 at the end.
+// ---------------------------------------------------------------------------
+struct FwdRunsCfg {
+    static constexpr int M = 256, N = 128, H = 128, P = 130, NW = N / 32, NT = 256, COLS = 16;
+    static constexpr size_t BITS_OFF = 0, RUNS_OFF = BITS_OFF + (size_t)N * NW * 4;
+    static constexpr size_t CNT_OFF = RUNS_OFF + (size_t)N * (N / 2) * 2;
+    static constexpr size_t TW_OFF = CNT_OFF + (size_t)N * 4;
+    static constexpr size_t X_OFF = TW_OFF + (size_t)M * 8;
+    static constexpr size_t XB_OFF = X_OFF + (size_t)N * COLS * 8;
+    static constexpr size_t C0_OFF = XB_OFF + (size_t)M * COLS * 8;
+    static constexpr size_t SMEM = C0_OFF + (size_t)M * 8;
+    static_assert(3 * (SMEM + 1024) <= 228 * 1024, "three blocks per SM");
+};
+
+__global__ void __launch_bounds__(FwdRunsCfg::NT, 3)
+k_fwd2d_runs(const uint32_t *__restrict__ bits_g, const uint32_t *__restrict__ mask_g, float2 *Y,
+             const float2 *__restrict__ q_g)
+{
+    using C = FwdRunsCfg;
+    constexpr int M = C::M, N = C::N, H = C::H, P = C::P, NW = C::NW, COLS = C::COLS;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint32_t *bits = reinterpret_cast<uint32_t *>(smem + C::BITS_OFF);   // [N][NW]
+    uchar2 *runs = reinterpret_cast<uchar2 *>(smem + C::RUNS_OFF);       // [N][N / 2]: (a, e - 1)
+    int *cnt = reinterpret_cast<int *>(smem + C::CNT_OFF);              // [N]
+    cf *tw = reinterpret_cast<cf *>(smem + C::TW_OFF);                  // [M]: w^m
+    cf *X = reinterpret_cast<cf *>(smem + C::X_OFF);                    // [N][COLS]
+    cf *xb = reinterpret_cast<cf *>(smem + C::XB_OFF);                  // [M][COLS]
+    cf *c0 = reinterpret_cast<cf *>(smem + C::C0_OFF);                  // [M]: packed column 0 after y
+    const int tid = threadIdx.x, jz = blockIdx.x, b = blockIdx.y;
+    const uint32_t *bg = bits_g + ((size_t)b * N + jz) * N * NW;
+    if (mask_g) {
+        const uint32_t *mg = mask_g + ((size_t)b * N + jz) * N * NW;
+        for (int i = tid; i < N * NW; i += C::NT) bits[i] = bg[i] & ~mg[i];
+    } else {
+        for (int i = tid; i < N * NW; i += C::NT) bits[i] = bg[i];
+    }
+    for (int m = tid; m < M; m += C::NT) {
+        const float2 w = c_tw256[m];
+        tw[m] = cmake(w.x, w.y);
+    }
+    __syncthreads();
+    // the runs of row y (thread y): [a, e) with e - 1 stored (e <= 128)
+    if (tid < N) {
+        int n = 0, open = -1;
+        uint32_t prevw = 0;
+        for (int w = 0; w <= NW; ++w) {
+            const uint32_t cur = w < NW ? bits[tid * NW + w] : 0u;
+            const uint32_t prev = (cur << 1) | (prevw >> 31);
+            uint32_t ev = (cur & ~prev) | (~cur & prev);   // rises and falls
+            while (ev) {
+                const int bp = __ffs(ev) - 1;
+                ev &= ev - 1;
+                const int x = 32 * w + bp;
+                if ((cur >> bp) & 1u) {
+                    open = x;
+                } else {
+                    runs[tid * (N / 2) + n] = make_uchar2((unsigned char)open, (unsigned char)(x - 1));
+                    ++n;
+                }
+            }
+            prevw = cur;
+        }
+        cnt[tid] = n;
+    }
+    __syncthreads();
+
+    float2 *Yb = Y + ((size_t)b * N + jz) * (size_t)M * P;
+    const int hw = tid >> 4, c = tid & 15, j = tid >> 4;   // hw: half-warp (x), j: row class (y)
+#pragma unroll 1
+    for (int p0 = 0; p0 < H; p0 += COLS) {
+        // ---- x: half-warp hw on rows hw + 16 i, lane c on kx = p0 + c ----
+        const int kx = p0 + c;
+        const float2 qq = q_g[kx];
+        const cf q = cmake(qq.x, qq.y);
+#pragma unroll 1
+        for (int y = hw; y < N; y += C::NT / 16) {
+            const int n = cnt[y];
+            const uchar2 *rr = runs + y * (N / 2);
+            cf acc = cmake(0.f, 0.f);
+            if (kx == 0) {
+                float ones = 0.f, nyq = 0.f;
+                for (int k = 0; k < n; ++k) {
+                    const int a = rr[k].x, e = rr[k].y + 1, len = e - a;
+                    ones += (float)len;
+                    if (len & 1) nyq += (a & 1) ? -1.f : 1.f;
+                }
+                acc = cmake(ones, nyq);
+            } else {
+                for (int k = 0; k < n; ++k) {
+                    const int a = rr[k].x, e = rr[k].y + 1;
+                    acc = cadd(acc, cmul(csub(tw[(kx * a) & (M - 1)], tw[(kx * e) & (M - 1)]), q));
+                }
+            }
+            X[y * COLS + c] = acc;
+        }
+        __syncthreads();   // X complete; the previous round's exchange reads are done
+        // ---- y: forward DFT of column c; stage 0 over rows j + 16 s --------
+        cf v[16];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) v[s] = X[(j + 16 * s) * COLS + c];
+#pragma unroll
+        for (int s = 8; s < 16; ++s) v[s] = cmake(0.f, 0.f);   // rows >= N: zero padding
+        DFT<16, false>::run(v);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) xb[(16 * j + r) * COLS + c] = v[r];
+        __syncthreads();
+        // stage 1: inputs j + 16 r, twiddles exp(-2 pi i j r / 256); output ky = j + 16 r
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = xb[(j + 16 * r) * COLS + c];
+#pragma unroll
+        for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], cconj(twc_inv(j * r)));
+        DFT<16, false>::run(v);
+        if (kx == 0) {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) c0[j + 16 * r] = v[r];
+        } else {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) Yb[(size_t)(j + 16 * r) * P + kx] = make_float2(v[r].x, v[r].y);
+        }
+    }
+    __syncthreads();
+    // packed column 0 = Y0 + i YH (both the transforms of real columns)
+    for (int ky = tid; ky < M; ky += C::NT) {
+        const cf val = c0[ky], oc = cconj(c0[(M - ky) & (M - 1)]);
+        const cf y0 = cscale(cadd(val, oc), 0.5f);
+        const cf w = csub(val, oc);
+        float2 *row = Yb + (size_t)ky * P;
+        row[0] = make_float2(y0.x, y0.y);
+        row[H] = make_float2(0.5f * w.y, -0.5f * w.x);
+        row[H + 1] = make_float2(0.f, 0.f);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // z pass at M = 256 over 16 columns per CTA (f = ky P + kx in [16 blockIdx.x,
 // + 16)): for each of the block's `group` rotations, forward FFT along z of
 // the N = 128 non-zero inputs, times conj(F(O)) / M^3 (for a rotated object:
@@ -1230,6 +1379,19 @@ cudaError_t launch_plane_ps_export(const Geo &g, int cl, const float2 *Z, float 
     if (!plane_ps_supported(g.M, cl) || g.P != PlanePsCfg<4>::P) return cudaErrorInvalidValue;
     return cl == 4 ? launch_plane_ps_t<4, true>(g.M, Z, nullptr, nullptr, C, err, st, withhold)
                    : launch_plane_ps_t<8, true>(g.M, Z, nullptr, nullptr, C, err, st, withhold);
+}
+
+cudaError_t launch_fwd2d_runs(const Geo &g, int B, const uint32_t *bits, float2 *Y, const float2 *q,
+                              const uint32_t *mask, cudaStream_t st)
+{
+    using C = FwdRunsCfg;
+    if (g.M != C::M || g.N != C::N || g.P != C::P || B < 1 || B > 65535) return cudaErrorInvalidValue;
+    cudaError_t e = ensure_twiddle_bank();
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_fwd2d_runs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (e != cudaSuccess) return e;
+    k_fwd2d_runs<<<dim3(C::N, B), C::NT, C::SMEM, st>>>(bits, mask, Y, q);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_plane_cl(const Geo &g, int cl, int B, const float2 *Z, const float2 *tw, const RotRec *rots,

@@ -202,11 +202,21 @@ def test_bad_label_aware_flag_is_rejected(ctx, workload):
     sw.set_label_aware(False)
 
 
-@pytest.mark.parametrize("N", [96, 128])
-def test_label_aware_parity_on_the_192_and_256_canvases(ctx, workload, N):
+@pytest.mark.parametrize("N,runs", [(96, 0), (128, 0), (128, 1)])
+def test_label_aware_parity_on_the_192_and_256_canvases(ctx, workload, N, runs):
     # the dual z pass on the radix-3 (192) and 256 canvases: split grids,
-    # field and peaks against the oracle (30 % retreat poses non-contact)
+    # field and peaks against the oracle (30 % retreat poses non-contact);
+    # at 256 also with the forward pass from run lists (its masked grid too)
     w = workload("free64", N=N, h=16.0 / N, poses=300, n_theta=48, n_phi=96, lines=3, noncontact=0.3)
+    shape0 = ctx.get_tuning(N)
+    ctx.set_tuning(N=N, fwd_runs=runs)
+    try:
+        _label_aware_parity(ctx, w, N)
+    finally:
+        ctx.set_tuning(**shape0)
+
+
+def _label_aware_parity(ctx, w, N):
     lab = w.labels
     assert 0 < int((lab == 0).sum()) < len(lab)
     ob, sw = _pair(ctx, w, lab)

@@ -1,5 +1,6 @@
 """The z pass and the inverse plane pass at canvas 256 in each of their launch
-shapes (16 or 32 columns per z-pass block, the 16-column one with its DFT
+shapes (the forward pass over a whole slab or from run lists; 16 or 32
+columns per z-pass block, the 16-column one with its DFT
 stages on the CUDA cores or on the tensor cores; 2, 4 or 8 CTAs per plane, the
 cluster ones also as persistent clusters with TMA staging) against
 the FP64 oracle (Eq. (7), (9)): the full correlation field within 1e-4 of
@@ -14,11 +15,11 @@ from paper_2605_21398_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-# (plane_cl, zpass_cols, zpass_tc, plane_tma): the 2-CTA plane pass with the
-# 32-column z pass, the cluster plane passes with each z pass, and the
-# persistent cluster plane passes
-SHAPES = ((2, 32, 0, 0), (4, 16, 0, 0), (8, 16, 0, 0), (4, 32, 0, 0), (4, 16, 1, 0), (8, 16, 1, 0), (4, 16, 0, 1),
-          (8, 16, 0, 1), (4, 32, 0, 1))
+# (plane_cl, zpass_cols, zpass_tc, plane_tma, fwd_runs): the 2-CTA plane pass
+# with the 32-column z pass, the cluster plane passes with each z pass, the
+# persistent cluster plane passes, and the forward pass from run lists
+SHAPES = ((2, 32, 0, 0, 0), (4, 16, 0, 0, 0), (8, 16, 0, 0, 0), (4, 32, 0, 0, 0), (4, 16, 1, 0, 0), (8, 16, 1, 0, 0),
+          (4, 16, 0, 1, 0), (8, 16, 0, 1, 0), (4, 32, 0, 1, 0), (8, 16, 0, 1, 1), (2, 32, 0, 0, 1))
 
 
 @pytest.fixture(scope="module")
@@ -64,10 +65,10 @@ def test_full_field_at_canvas_256_in_every_shape(ctx, workload):
     saved = ctx.get_tuning(w.N)
     try:
         for shape in SHAPES:
-            cl, zc, tc, tma = shape
-            ctx.set_tuning(N=w.N, plane_cl=cl, zpass_cols=zc, zpass_tc=tc, plane_tma=tma)
+            cl, zc, tc, tma, runs = shape
+            ctx.set_tuning(N=w.N, plane_cl=cl, zpass_cols=zc, zpass_tc=tc, plane_tma=tma, fwd_runs=runs)
             t = ctx.get_tuning(w.N)
-            assert (t["plane_cl"], t["zpass_cols"], t["zpass_tc"], t["plane_tma"]) == shape
+            assert (t["plane_cl"], t["zpass_cols"], t["zpass_tc"], t["plane_tma"], t["fwd_runs"]) == shape
             C = ctx.search_scores(ob, sw, q)
             err = np.max(np.abs(C - Co))
             assert err <= tol, (shape, err, tol)
@@ -96,8 +97,8 @@ def test_peaks_at_canvas_256_in_every_shape(ctx, workload):
     saved = ctx.get_tuning(w.N)
     try:
         for shape in SHAPES:
-            cl, zc, tc, tma = shape
-            ctx.set_tuning(N=w.N, plane_cl=cl, zpass_cols=zc, zpass_tc=tc, plane_tma=tma, batch=3)
+            cl, zc, tc, tma, runs = shape
+            ctx.set_tuning(N=w.N, plane_cl=cl, zpass_cols=zc, zpass_tc=tc, plane_tma=tma, fwd_runs=runs, batch=3)
             _, pk = ctx.search_so3(ob, sw, len(quats), 2, sampler=3, quats=quats, want_peaks=True)
             for i, (sc, idx, tol, gap, Cf) in enumerate(ref):
                 assert abs(pk["score"][i] - sc) <= tol + 1e-4 * abs(sc), (shape, i)
@@ -117,6 +118,6 @@ def test_peaks_at_canvas_256_in_every_shape(ctx, workload):
 def test_set_tuning_rejects_out_of_range_shapes(ctx):
     from paper_2605_21398_gb300 import dock
     for bad in (dict(N=128, plane_cl=3), dict(N=128, zpass_cols=8), dict(N=128, batch=0), dict(N=128, vox_blocks=5),
-                dict(N=128, zpass_tc=2), dict(N=128, plane_tma=-1), dict(N=48)):
+                dict(N=128, zpass_tc=2), dict(N=128, plane_tma=-1), dict(N=128, fwd_runs=2), dict(N=48)):
         with pytest.raises(dock.DockError):
             ctx.set_tuning(**bad)
