@@ -434,8 +434,7 @@ typedef struct dock_tuning {
     int32_t vox_blocks;      /* voxeliser register target: 3 or 4 resident blocks per SM */
     int32_t plane_cl;        /* CTAs per plane of the inverse plane pass (canvas 256 only: 2, 4 or 8;
                                 0 = the default; other canvases use one fixed shape) */
-    int32_t zpass_cols;      /* columns per z-pass block (canvas 256 only: 16 or 32; 0 = the default;
-                                the label-aware score always uses 32) */
+    int32_t zpass_cols;      /* columns per z-pass block (canvas 256 only: 16 or 32; 0 = the default) */
     int32_t vox_overlap;     /* 1: the voxeliser of the next launch runs on a second stream, overlapped
                                 with the FFT passes of the current one (plain score); 0: in order */
     int32_t zpass_tc;        /* 1: the z pass's radix-16 DFT stages run as 3 x TF32 products on the

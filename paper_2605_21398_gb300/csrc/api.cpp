@@ -1512,6 +1512,8 @@ static dock_status run_pipeline_rots(dock_ctx *ctx, const Geo &g, const ReqDev *
                 CK(ctx, launch_zpass_tc(g, nb, group, Y, rb, reqs, Z, ctx->errflag, ctx->stream));
             else if (g.M == 256 && tc.zpass_cols == 16 && !dual)
                 CK(ctx, launch_zpass16(g, nb, group, Y, rb, reqs, Z, ctx->stream));
+            else if (g.M == 256 && tc.zpass_cols == 16)
+                CK(ctx, launch_zpass16_dual(g, nb, group, Y, Y2, rb, reqs, Z, ctx->stream));
             else
                 CK(ctx, launch_zpass(g, nb, group, Y, rb, reqs, Z, tw, ctx->stream, Y2));
         }
@@ -2088,6 +2090,8 @@ static dock_status search_scores_impl(dock_ctx *ctx, const dock_object *ob, cons
             e = launch_zpass_tc(g, 1, 1, Y, ctx->rots, ctx->reqs, Y + ysz, ctx->errflag, ctx->stream);
         else if (g.M == 256 && tc.zpass_cols == 16 && !dual)
             e = launch_zpass16(g, 1, 1, Y, ctx->rots, ctx->reqs, Y + ysz, ctx->stream);
+        else if (g.M == 256 && tc.zpass_cols == 16)
+            e = launch_zpass16_dual(g, 1, 1, Y, Y2, ctx->rots, ctx->reqs, Y + ysz, ctx->stream);
         else
             e = launch_zpass(g, 1, 1, Y, ctx->rots, ctx->reqs, Y + ysz, tw, ctx->stream, Y2);
     }

@@ -102,6 +102,9 @@ cudaError_t launch_plane(const Geo &g, int B, const float2 *Z, const float2 *tw,
 cudaError_t launch_zpass16(const Geo &g, int B, int group, const float2 *Y, const RotRec *rots, const ReqDev *reqs,
                            float2 *Z, cudaStream_t st);
 // The cluster plane pass (k_fft256.cu): M = 256, cl = 4 or 8.
+// z pass of the label-aware score over 16 columns per block: M = 256
+cudaError_t launch_zpass16_dual(const Geo &g, int B, int group, const float2 *Y, const float2 *Y2, const RotRec *rots,
+                                const ReqDev *reqs, float2 *Z, cudaStream_t st);
 // z pass with its DFT stages as 3 x TF32 products on the tensor cores (canvas 256, plain score)
 cudaError_t launch_zpass_tc(const Geo &g, int B, int group, const float2 *Y, const RotRec *rots, const ReqDev *reqs,
                             float2 *Z, int *err, cudaStream_t st);

@@ -1209,6 +1209,131 @@ k_zpass_tc(int B, int group, const float2 *__restrict__ Y, const RotRec *rots, c
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// z pass of the label-aware score at M = 256 over 16 columns per CTA (the
+// dual form of k_zpass16): per rotation the forward FFTs along z of Y (the
+// contact sweep) and of Y2 (the non-contact sweep), the products with the
+// object's spectrum conj(F(O)) / M^3 and with conj(F(min(O, 0))) / M^3 (the
+// second only for requests with non-contact poses), summed before one inverse
+// FFT.  Both spectrum tiles sit in shared memory (reloaded when the request
+// changes), both inputs of the next rotation are in flight during the current
+// one, and the three transforms share one [256][16] exchange buffer.
+// ---------------------------------------------------------------------------
+struct Zpass16DualCfg {
+    static constexpr int M = 256, N = 128, P = 130, NT = 256, COLS = 16;
+    static constexpr size_t SMEM = (size_t)3 * M * COLS * 8;   // exchange + two spectrum tiles
+    static_assert(2 * (SMEM + 1024) <= 228 * 1024, "two blocks per SM");
+};
+
+__global__ void __launch_bounds__(Zpass16DualCfg::NT, 2)
+k_zpass16_dual(int B, int group, const float2 *__restrict__ Y, const float2 *__restrict__ Y2, const RotRec *rots,
+               const ReqDev *reqs, float2 *Z)
+{
+    using C = Zpass16DualCfg;
+    constexpr int M = C::M, N = C::N, P = C::P, COLS = C::COLS;
+    extern __shared__ __align__(16) unsigned char smem[];
+    cf *xb = reinterpret_cast<cf *>(smem);    // [M][COLS]
+    cf *spt = xb + M * COLS;                   // [M (kz)][COLS]: conj(F(O)) / M^3
+    cf *ppt = spt + M * COLS;                  // [M (kz)][COLS]: conj(F(min(O, 0))) / M^3
+    const int tid = threadIdx.x, c = tid & 15, j = tid >> 4;
+    const size_t plane = (size_t)M * P;
+    const int f0 = blockIdx.x * COLS;
+    const int b0 = blockIdx.y * group, nb = min(group, B - b0);
+    if (nb <= 0) return;
+    auto load = [&](const float2 *src0, int bi, cf *v) {
+        const float2 *src = src0 + (size_t)(b0 + bi) * N * plane + f0 + c;
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const float2 a = __ldcs(&src[(size_t)(j + 16 * s) * plane]);
+            v[s] = cmake(a.x, a.y);
+        }
+    };
+    // forward DFT of the zero-padded column held as inputs z = j + 16 s
+    // (s < 8): on return v[r] holds kz = j + 16 r
+    auto forward = [&](cf *v) {
+#pragma unroll
+        for (int s = 8; s < 16; ++s) v[s] = cmake(0.f, 0.f);
+        DFT<16, false>::run(v);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) xb[(16 * j + r) * COLS + c] = v[r];
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = xb[(j + 16 * r) * COLS + c];
+#pragma unroll
+        for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], cconj(twc_inv(j * r)));   // exp(-2 pi i j r / 256)
+        DFT<16, false>::run(v);
+    };
+    cf nx[8], nx2[8];
+    load(Y, 0, nx);
+    load(Y2, 0, nx2);
+    int sp_req = -1;
+#pragma unroll 1
+    for (int bi = 0; bi < nb; ++bi) {
+        cf v[16], w[16];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) v[s] = nx[s];
+        if (bi + 1 < nb) load(Y, bi + 1, nx);
+        const int req = rots[b0 + bi].req;
+        const bool pen = reqs[req].P_nc > 0;
+        if (req != sp_req) {   // block-uniform
+            __syncthreads();   // the previous tiles are no longer read
+            // tiled spectra: ((f / 32) M + kz) 32 + f mod 32
+            const size_t off = (size_t)(f0 / 32) * M * 32 + (f0 & 31) + c;
+            const float2 *src = reqs[req].spec + off;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                const float2 a = __ldg(&src[(size_t)(j + 16 * r) * 32]);
+                spt[(j + 16 * r) * COLS + c] = cmake(a.x, a.y);
+            }
+            if (pen) {
+                const float2 *srcp = reqs[req].spec_pen + off;
+#pragma unroll
+                for (int r = 0; r < 16; ++r) {
+                    const float2 a = __ldg(&srcp[(size_t)(j + 16 * r) * 32]);
+                    ppt[(j + 16 * r) * COLS + c] = cmake(a.x, a.y);
+                }
+            }
+            sp_req = req;
+        }
+        const float cj = reqs[req].rotate_object ? -1.f : 1.f;
+        // contact sweep: w = F(S) conj(F(O)) / M^3 (a rotated object: conj(F(O_R)) F(S) / M^3)
+        forward(v);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            cf a = v[r];
+            a.y *= cj;
+            w[r] = cmul(a, spt[(j + 16 * r) * COLS + c]);
+        }
+        if (pen) {   // block-uniform
+            // non-contact sweep: w += F(S_nc) conj(F(min(O, 0))) / M^3
+#pragma unroll
+            for (int s = 0; s < 8; ++s) v[s] = nx2[s];
+            if (bi + 1 < nb) load(Y2, bi + 1, nx2);
+            __syncthreads();   // every thread has read its forward stage-1 inputs
+            forward(v);
+#pragma unroll
+            for (int r = 0; r < 16; ++r) w[r] = cadd(w[r], cmul(v[r], ppt[(j + 16 * r) * COLS + c]));
+        } else if (bi + 1 < nb) {
+            load(Y2, bi + 1, nx2);
+        }
+        __syncthreads();   // every thread has read its last forward stage-1 inputs
+        // inverse, stage 0 (inputs kz = j + 16 r) -> index 16 j + r
+        DFT<16, true>::run(w);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) xb[(16 * j + r) * COLS + c] = w[r];
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 16; ++r) w[r] = xb[(j + 16 * r) * COLS + c];
+#pragma unroll
+        for (int r = 1; r < 16; ++r) w[r] = cmul(w[r], twc_inv(j * r));
+        DFT<16, true>::run(w);
+        float2 *dst = Z + (size_t)(b0 + bi) * M * plane + f0 + c;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) __stcs(&dst[(size_t)(j + 16 * r) * plane], make_float2(w[r].x, w[r].y));
+        __syncthreads();   // the exchange buffer is free for the next rotation
+    }
+}
+
 // Fills c_tw256 on the current device once (the module's constant bank is per device).
 static cudaError_t ensure_twiddle_bank()
 {
@@ -1391,6 +1516,21 @@ cudaError_t launch_fwd2d_runs(const Geo &g, int B, const uint32_t *bits, float2 
     e = cudaFuncSetAttribute(k_fwd2d_runs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if (e != cudaSuccess) return e;
     k_fwd2d_runs<<<dim3(C::N, B), C::NT, C::SMEM, st>>>(bits, mask, Y, q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zpass16_dual(const Geo &g, int B, int group, const float2 *Y, const float2 *Y2, const RotRec *rots,
+                                const ReqDev *reqs, float2 *Z, cudaStream_t st)
+{
+    using C = Zpass16DualCfg;
+    if (g.M != C::M || g.P != C::P || B < 1 || group < 1) return cudaErrorInvalidValue;
+    cudaError_t e = ensure_twiddle_bank();
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_zpass16_dual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (e != cudaSuccess) return e;
+    const dim3 grid(C::M * C::P / C::COLS, (B + group - 1) / group);
+    if (grid.y > 65535) return cudaErrorInvalidValue;
+    k_zpass16_dual<<<grid, C::NT, C::SMEM, st>>>(B, group, Y, Y2, rots, reqs, Z);
     return cudaGetLastError();
 }
 

@@ -202,14 +202,15 @@ def test_bad_label_aware_flag_is_rejected(ctx, workload):
     sw.set_label_aware(False)
 
 
-@pytest.mark.parametrize("N,runs", [(96, 0), (128, 0), (128, 1)])
-def test_label_aware_parity_on_the_192_and_256_canvases(ctx, workload, N, runs):
+@pytest.mark.parametrize("N,runs,zc", [(96, 0, 0), (128, 0, 16), (128, 1, 16), (128, 1, 32)])
+def test_label_aware_parity_on_the_192_and_256_canvases(ctx, workload, N, runs, zc):
     # the dual z pass on the radix-3 (192) and 256 canvases: split grids,
     # field and peaks against the oracle (30 % retreat poses non-contact);
-    # at 256 also with the forward pass from run lists (its masked grid too)
+    # at 256 with the forward pass over whole slabs or from run lists (its
+    # masked grid too) and the dual z pass over 16 or 32 columns per block
     w = workload("free64", N=N, h=16.0 / N, poses=300, n_theta=48, n_phi=96, lines=3, noncontact=0.3)
     shape0 = ctx.get_tuning(N)
-    ctx.set_tuning(N=N, fwd_runs=runs)
+    ctx.set_tuning(N=N, fwd_runs=runs, zpass_cols=zc)
     try:
         _label_aware_parity(ctx, w, N)
     finally:
