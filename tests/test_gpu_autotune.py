@@ -59,3 +59,38 @@ def test_tuned_shape_keeps_results_and_round_trips(ctx, workload, tmp_path):
         c2.close()
     r = ctx.register(ob, sw, 200, 50, math.radians(5), 2)
     assert r["n_evals"] == 250
+
+
+def test_canvas_256_shape_round_trips_every_field(ctx, workload, tmp_path):
+    # at canvas 256 the autotuner also times the FFT passes' variants (z-pass
+    # width and tensor-core stages, plane-pass cluster size and persistent
+    # form, forward pass from run lists); every field survives the JSON cache,
+    # and the tuned shape's peaks agree with the default shape's (the variants
+    # differ only in the order of FP32 operations)
+    from paper_2605_21398_gb300 import dock, synth
+    w = workload("large128", poses=1500)
+    ob, sw = _pair(ctx, w)
+    quats = synth.random_unit_quats(24, 5)
+    default = ctx.get_tuning(w.N)
+    _, ref = ctx.search_so3(ob, sw, len(quats), 2, sampler=3, quats=quats, want_peaks=True)
+    path = str(tmp_path / "tune256.json")
+    try:
+        t = ctx.autotune(ob, sw, n_rot=64, cache_path=path)
+        keys = ("batch", "group", "vox_blocks", "plane_cl", "plane_tma", "fwd_runs", "zpass_cols", "zpass_tc",
+                "vox_overlap")
+        assert t["plane_cl"] in (2, 4, 8) and t["zpass_cols"] in (16, 32)
+        assert t["plane_tma"] in (0, 1) and t["fwd_runs"] in (0, 1) and t["zpass_tc"] in (0, 1)
+        _, got = ctx.search_so3(ob, sw, len(quats), 2, sampler=3, quats=quats, want_peaks=True)
+        # (the variants' FP32 differences move peak scores by about 1 on peaks of
+        # about 2000 here, far inside the oracle tolerance of 1e-4 of max |C|)
+        scale = np.max(np.abs(ref["score"]))
+        assert np.max(np.abs(got["score"] - ref["score"])) <= 2e-3 * scale
+        c2 = dock.Context(0)
+        try:
+            assert c2.load_tuning(path) >= 1
+            t2 = c2.get_tuning(w.N)
+            assert {k: t2[k] for k in keys} == {k: t[k] for k in keys}
+        finally:
+            c2.close()
+    finally:
+        ctx.set_tuning(**default)
