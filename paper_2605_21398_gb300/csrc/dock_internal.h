@@ -114,6 +114,7 @@ cudaError_t launch_fwd2d_runs(const Geo &g, int B, const uint32_t *bits, float2 
                               const uint32_t *mask, cudaStream_t st);
 // persistent cluster plane pass with TMA staging of the columns (canvas 256, 4 or 8 CTAs per plane)
 bool plane_ps_supported(int M, int cl);
+bool plane_ps_unavailable(cudaError_t e);
 cudaError_t launch_plane_ps(const Geo &g, int cl, int B, const float2 *Z, const RotRec *rots, const ReqDev *reqs,
                             int *err, cudaStream_t st);
 cudaError_t launch_plane_ps_export(const Geo &g, int cl, const float2 *Z, float *C, int *err, cudaStream_t st,

@@ -1490,6 +1490,17 @@ static cudaError_t launch_plane_ps_t(int n_planes, const float2 *Z, const RotRec
 
 bool plane_ps_supported(int M, int cl) { return M == 256 && (cl == 4 || cl == 8); }
 
+// The persistent pass refused before launching: no tensor-map encoder in the
+// driver, or no cluster of its size resident on this device right now.  The
+// error recorded by the failed query is cleared; the caller uses the
+// one-cluster-per-plane pass instead.
+bool plane_ps_unavailable(cudaError_t e)
+{
+    if (e != cudaErrorNotSupported && e != cudaErrorInvalidConfiguration) return false;
+    (void)cudaGetLastError();
+    return true;
+}
+
 cudaError_t launch_plane_ps(const Geo &g, int cl, int B, const float2 *Z, const RotRec *rots, const ReqDev *reqs,
                             int *err, cudaStream_t st)
 {

@@ -1375,7 +1375,10 @@ static cudaError_t launch_plane_t(int B, const float2 *Z, const float2 *tw, cons
 cudaError_t launch_plane(const Geo &g, int B, const float2 *Z, const float2 *tw, const RotRec *rots,
                          const ReqDev *reqs, cudaStream_t st, int plane_cl, int *err, int plane_tma)
 {
-    if (plane_tma && plane_ps_supported(g.M, plane_cl)) return launch_plane_ps(g, plane_cl, B, Z, rots, reqs, err, st);
+    if (plane_tma && plane_ps_supported(g.M, plane_cl)) {
+        const cudaError_t e = launch_plane_ps(g, plane_cl, B, Z, rots, reqs, err, st);
+        if (!plane_ps_unavailable(e)) return e;
+    }
     if (plane_cl_supported(g.M, plane_cl)) return launch_plane_cl(g, plane_cl, B, Z, tw, rots, reqs, err, st);
     switch (g.M) {
     case 64: return launch_plane_t<64, false>(B, Z, tw, rots, reqs, nullptr, st);
@@ -1389,7 +1392,10 @@ cudaError_t launch_plane(const Geo &g, int B, const float2 *Z, const float2 *tw,
 cudaError_t launch_plane_export(const Geo &g, const float2 *Z, const float2 *tw, float *C, cudaStream_t st,
                                 int plane_cl, int *err, int plane_tma)
 {
-    if (plane_tma && plane_ps_supported(g.M, plane_cl)) return launch_plane_ps_export(g, plane_cl, Z, C, err, st);
+    if (plane_tma && plane_ps_supported(g.M, plane_cl)) {
+        const cudaError_t e = launch_plane_ps_export(g, plane_cl, Z, C, err, st);
+        if (!plane_ps_unavailable(e)) return e;
+    }
     if (plane_cl_supported(g.M, plane_cl)) return launch_plane_cl_export(g, plane_cl, Z, tw, C, err, st);
     switch (g.M) {
     case 64: return launch_plane_t<64, true>(1, Z, tw, nullptr, nullptr, C, st);
