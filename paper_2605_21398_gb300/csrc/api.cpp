@@ -1780,7 +1780,11 @@ static dock_status time_shape(dock_ctx *ctx, const Geo &g, int n, const dock_tun
 {
     ctx->tune[g.N] = t;
     dock_status s;
+    // every run starts from cleared peak keys, as a search does (the plane
+    // passes skip work for rows below a rotation's best score so far)
+    CK(ctx, cudaMemsetAsync(ctx->keys, 0, sizeof(unsigned long long) * n, ctx->stream));
     if ((s = run_pipeline_rots(ctx, g, ctx->reqs, ctx->rots, 0, n, 0)) != DOCK_OK) return s;   // warm-up
+    CK(ctx, cudaMemsetAsync(ctx->keys, 0, sizeof(unsigned long long) * n, ctx->stream));
     cudaEvent_t a = nullptr, b = nullptr;
     CK(ctx, cudaEventCreate(&a));
     cudaError_t e = cudaEventCreate(&b);

@@ -549,6 +549,11 @@ k_plane_ps(const __grid_constant__ CUtensorMap zmap, const __grid_constant__ CUt
         // ---- phase 2: C2R along x of my rows, argmax -------------------------
         const int rowl = tid & 31, j = (tid >> 5) & 7, rr = tid >> 8;   // j, rr warp-uniform
         const int ylo = rr * 32 + rowl, y = rank * RPC + ylo;
+        const int b = p >> 8, zc = p & (M - 1);
+        // the rotation's best key so far (from the planes done before; a stale
+        // value is only lower): a row whose maximum scores below it cannot
+        // hold the rotation's peak and skips the search for its index
+        const uint32_t thr = EXPORT ? 0u : (uint32_t)(__ldcg(&reqs[rots[b].req].keys[rots[b].rot]) >> 32);
         // element (kx, local row ylo) of V: source kx / CPC, column
         // (kx mod CPC) ^ (y mod CPC) (RPC is a multiple of CPC)
         auto vat = [&](int kx) -> cf { return V[(kx / CPC) * BLK + ylo * CPC + ((kx % CPC) ^ (ylo & (CPC - 1)))]; };
@@ -596,7 +601,6 @@ k_plane_ps(const __grid_constant__ CUtensorMap zmap, const __grid_constant__ CUt
             for (int r = 1; r < 8; ++r) w[bb * 8 + r] = cmul(w[bb * 8 + r], twc_inv(2 * jj * r));
             DFT<8, true>::run(w + bb * 8);
         }
-        const int b = p >> 8, zc = p & (M - 1);
         const uint32_t rowbase = ((uint32_t)zc * M + (uint32_t)y) * M;
         if (EXPORT) {
 #pragma unroll
@@ -610,11 +614,13 @@ k_plane_ps(const __grid_constant__ CUtensorMap zmap, const __grid_constant__ CUt
 #pragma unroll
             for (int s = 0; s < 16; ++s) m = fmaxf(m, fmaxf(w[s].x, w[s].y));
             uint32_t bi = 0xFFFFFFFFu;
+            if ((uint32_t)(pack_key(m, 0u) >> 32) >= thr) {
 #pragma unroll
-            for (int s = 0; s < 16; ++s) {
-                const uint32_t base = rowbase + 2u * (uint32_t)(j + 8 * (s >> 3) + 16 * (s & 7));
-                if (w[s].x == m) bi = min(bi, base);
-                if (w[s].y == m) bi = min(bi, base + 1u);
+                for (int s = 0; s < 16; ++s) {
+                    const uint32_t base = rowbase + 2u * (uint32_t)(j + 8 * (s >> 3) + 16 * (s & 7));
+                    if (w[s].x == m) bi = min(bi, base);
+                    if (w[s].y == m) bi = min(bi, base + 1u);
+                }
             }
             unsigned long long kk = (bi == 0xFFFFFFFFu) ? 0ull : pack_key(m, bi);
 #pragma unroll
