@@ -367,8 +367,10 @@ k_plane_cl(const float2 *__restrict__ Z, const float2 *__restrict__ tw, const Ro
 //   push     U's row block q (RPC rows, contiguous) to CTA q's V[rank]
 //            by the bulk-copy engine, completion counted in bytes on CTA q's
 //            mbarrier (the own block included)
-//   phase 2  C2R along x of rows [64 rank, +64) from V, the exchange in place
-//            in V, argmax with the lowest canvas index on ties
+//   phase 2  C2R along x of rows [RPC rank, RPC (rank + 1)) from V, the
+//            exchange in place in V, argmax with the lowest canvas index on
+//            ties (a row whose maximum scores below the rotation's best key
+//            so far, written by planes done before, skips the index search)
 // Per plane one cluster barrier (after it every CTA has finished phase 1 of
 // this plane and phase 2 of the previous one, so V may be overwritten) and
 // four block barriers; the waits' failure checks ride on two of them, and the
