@@ -720,7 +720,7 @@ def main():
                                    "rotations, 5000 probe poses on 3 raster segments (20%% labels flipped, 0.02 mm "
                                    "noise), 65k-triangle star object, top-%d refined (20 Gauss-Newton iterations)"
                                    % (args.n_global, args.n_local, TOP_K),
-                       "l2": "inputs larger than L2 (per-batch FFT intermediates ~4 GB) and a 256 MB L2 flush "
+                       "l2": "inputs larger than L2 (per-batch FFT intermediates ~13 GB) and a 256 MB L2 flush "
                              "before every step",
                        "parallelism": "replicas" if ws > 1 else "single",
                        "search_launch_shape": {k: tuning[k] for k in ("batch", "group", "vox_blocks", "plane_cl",
