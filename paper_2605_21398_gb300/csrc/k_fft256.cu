@@ -1,5 +1,13 @@
-// Search passes at canvas side M = 256 (Eq. (7), (9)): the z pass with the
-// spectrum multiply, and the inverse plane pass with the argmax.
+// Search passes at canvas side M = 256 (Eq. (7), (9)), the lattice side of
+// the 128^3 workload:
+//   k_fwd2d_runs     forward x and y transforms of binary slabs from their run
+//                    lists (the default forward pass)
+//   k_zpass16        z pass with the spectrum multiply, 16 columns per block
+//   k_zpass16_dual   the same for the label-aware score (two sweeps, two spectra)
+//   k_zpass_tc       the z pass with its DFT stages on the tensor cores
+//   k_plane_cl       inverse plane pass with the argmax, one cluster per plane
+//   k_plane_ps       the same as persistent clusters with TMA-loaded columns
+//                    (the default plane pass)
 //
 // Plane pass, over a cluster of CL = 4 or 8 CTAs per plane (the last two
 // inverse transforms of C = F^-1(conj(F(O)) . F(S)) and the per-rotation
