@@ -270,8 +270,8 @@ def serving_experiment(ctx, synth):
 # smsp__inst_executed.sum for the voxeliser); a launch of B rotations is scaled from them by B/8
 # (the z pass adds one spectrum read per launch).  A kernel changed since its capture has no entry.
 NCU_DRAM_BYTES_PER_ROT = {"plane": (545298176 + 3637760) / 8, "fwd2d": (18521856 + 229523456) / 8,
-                          "zpass": (340853760 - 68157440 + 489946880) / 8, "voxelise": (1384192 + 256) / 8}
-NCU_WARP_INST_PER_ROT = {"voxelise": 358047414 / 8}
+                          "zpass": (340853760 - 68157440 + 489946880) / 8, "voxelise": (1056256 + 0) / 8}
+NCU_WARP_INST_PER_ROT = {"voxelise": 343219446 / 8}
 # SMs x warp schedulers: one warp instruction issued per scheduler per clock
 ISSUE_SLOTS = 152 * 4
 

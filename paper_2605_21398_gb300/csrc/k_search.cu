@@ -517,8 +517,9 @@ __device__ __forceinline__ Geo req_geo(const Geo &g, const ReqDev &q)
 }
 
 // S_b slab bits to global memory: bits[((b * N + jz) * N + jy) * NW + w].
-// MINB: resident blocks per SM the register allocation is built for (3: up
-// to 80 registers; 4: 64 registers, a few spills); the autotuner picks one.
+// MINB: resident 256-thread blocks per SM the register allocation is built for
+// (3: up to 80 registers; 4: 64 registers, a few spills); the autotuner picks
+// one.  The launches use blocks of 128 threads, twice as many per SM.
 template <int N, int MINB>
 __global__ void __launch_bounds__(256, MINB)
 k_voxelise(Geo g, const ReqDev *reqs, const RotRec *rots, uint32_t *bits_out, int pose_set)
@@ -548,10 +549,12 @@ static cudaError_t launch_voxelise_t(const Geo &g, const ReqDev *reqs, const Rot
                                      cudaStream_t st, int ps)
 {
     dim3 grid(B, g.N);
-    // the non-contact poses of a label-aware request are few: with 4 warps a
-    // slab block waits less at its barriers for the warps that found poses
-    // (38 -> 34 us per rotation at 128^3 with 1000 of 5000 poses)
-    const int nt = ps ? 128 : 256;
+    // 4 warps per slab block: a block waits at its barriers for the warps
+    // that found poses, and smaller blocks wait less (38 -> 34 us per rotation
+    // at 128^3 for the label-aware pass's 1000 non-contact poses, 48.6 -> 48.0
+    // us for the 5000 contact poses); the register target is that of
+    // 256-thread blocks, so twice as many blocks are resident
+    const int nt = 128;
     switch (g.N) {
     case 32: k_voxelise<32, MINB><<<grid, nt, 0, st>>>(g, reqs, rots, bits, ps); break;
     case 64: k_voxelise<64, MINB><<<grid, nt, 0, st>>>(g, reqs, rots, bits, ps); break;
