@@ -724,7 +724,8 @@ def main():
                              "before every step",
                        "parallelism": "replicas" if ws > 1 else "single",
                        "search_launch_shape": {k: tuning[k] for k in ("batch", "group", "vox_blocks", "plane_cl",
-                                                                      "plane_tma", "fwd_runs", "zpass_cols", "zpass_tc")}},
+                                                                      "plane_tma", "fwd_runs", "zpass_cols", "zpass_tc",
+                                                                      "fft_plan")}},
             "roofline": roofline, "roofline_hbm": roofline_hbm, "model_roofline_frac": round(model_frac, 4),
             "model_bytes_per_eval": model_bytes_per_eval(w.N),
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "kernels": kernels,

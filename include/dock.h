@@ -446,19 +446,26 @@ typedef struct dock_tuning {
     int32_t fwd_runs;        /* 1 (canvas 256): the forward x and y passes of binary slabs from their
                                 run lists, 16 kx columns per round (three blocks per SM); 0: all
                                 columns of a slab at once (one block per SM) */
+    int32_t fft_plan;        /* radix plan of the FFT passes at canvases 64 and 128 (lattice sides 32
+                                and 64): 0: 8 x 8 and 16 x 8; 1: 16 x 4 and 8 x 8 x 2 (other canvases:
+                                0 only) */
     double us_per_rotation;  /* measured device time per rotation of this shape (0 = not measured) */
 } dock_tuning;
 
 /*
  * Autotuner (systems form; the paper has no counterpart).  Times the search
  * kernels on n_rot SF rotations of (obj, sweep) under candidate launch shapes
- * -- the voxeliser's register target, the rotations per launch and the
- * rotations per z-pass block -- one knob at a time, with CUDA events on the
- * context's stream, and keeps the fastest for obj's lattice side on ctx (all
- * later searches, registrations and serving passes of that side use it).
- * Results do not depend on the shape.  With cache_path non-NULL the context's
- * tuned shapes are written there as JSON (with the device name).  Takes about
- * 13 timed searches of n_rot rotations; n_rot in [16, 65536].
+ * -- the voxeliser's register target, the rotations per launch, the
+ * rotations per z-pass block, at canvases 64 and 128 the FFTs' radix plan,
+ * and at canvas 256 the FFT passes' variants (plane-pass cluster size and
+ * persistent form, z-pass width and tensor-core stages, forward pass from
+ * run lists) -- one knob at a time, with CUDA events on the context's
+ * stream, and keeps the fastest for obj's lattice side on ctx (all later
+ * searches, registrations and serving passes of that side use it).  Results
+ * do not depend on the shape beyond FP32 rounding.  With cache_path non-NULL
+ * the context's tuned shapes are written there as JSON (with the device
+ * name).  Takes about 13 to 18 timed searches of n_rot rotations; n_rot in
+ * [16, 65536].
  */
 DOCK_API dock_status dock_autotune(dock_ctx *ctx, const dock_object *obj, const dock_sweep *sweep, int32_t n_rot,
                                    const char *cache_path, dock_tuning *out);
@@ -469,9 +476,10 @@ DOCK_API dock_status dock_load_tuning(dock_ctx *ctx, const char *cache_path, int
 DOCK_API dock_status dock_get_tuning(dock_ctx *ctx, int32_t N, dock_tuning *out);
 /* Sets the shape for lattice side t->N (batch 1..256, group 0..256,
  * vox_blocks 3 or 4, plane_cl 0, 2, 4 or 8, zpass_cols 0, 16 or 32,
- * vox_overlap 0 or 1, zpass_tc 0 or 1, plane_tma 0 or 1, fwd_runs 0 or 1);
- * results do not depend on it beyond rounding (zpass_tc and fwd_runs change
- * the order of FP32 operations, within the error of the transforms).
+ * vox_overlap 0 or 1, zpass_tc 0 or 1, plane_tma 0 or 1, fwd_runs 0 or 1,
+ * fft_plan 0, or 1 for N 32 or 64); results do not depend on it beyond
+ * rounding (zpass_tc, fwd_runs and fft_plan change the order of FP32
+ * operations, within the error of the transforms).
  * DOCK_E_INVALID for values out of range. */
 DOCK_API dock_status dock_set_tuning(dock_ctx *ctx, const dock_tuning *t);
 

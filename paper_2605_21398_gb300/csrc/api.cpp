@@ -1379,6 +1379,7 @@ static const int VOX_OVERLAP_DEFAULT = 0;
 static const int ZPASS_TC_DEFAULT = 0;
 static const int PLANE_TMA_DEFAULT = 1;
 static const int FWD_RUNS_DEFAULT = 1;
+static const int FFT_PLAN_DEFAULT = 0;
 
 static dock_tuning tuning_for(dock_ctx *ctx, const Geo &g)
 {
@@ -1395,6 +1396,7 @@ static dock_tuning tuning_for(dock_ctx *ctx, const Geo &g)
     t.zpass_tc = g.M == 256 ? ZPASS_TC_DEFAULT : 0;
     t.plane_tma = g.M == 256 ? PLANE_TMA_DEFAULT : 0;
     t.fwd_runs = g.M == 256 ? FWD_RUNS_DEFAULT : 0;
+    t.fft_plan = FFT_PLAN_DEFAULT;
     return t;
 }
 
@@ -1405,7 +1407,8 @@ static bool valid_tuning(const dock_tuning &t)
            (t.plane_cl == 0 || t.plane_cl == 2 || t.plane_cl == 4 || t.plane_cl == 8) &&
            (t.zpass_cols == 0 || t.zpass_cols == 16 || t.zpass_cols == 32) &&
            (t.vox_overlap == 0 || t.vox_overlap == 1) && (t.zpass_tc == 0 || t.zpass_tc == 1) &&
-           (t.plane_tma == 0 || t.plane_tma == 1) && (t.fwd_runs == 0 || t.fwd_runs == 1);
+           (t.plane_tma == 0 || t.plane_tma == 1) && (t.fwd_runs == 0 || t.fwd_runs == 1) &&
+           (t.fft_plan == 0 || (t.fft_plan == 1 && (t.N == 32 || t.N == 64)));
 }
 
 // The forward x and y passes of a batch: the run-list kernel at canvas 256
@@ -1416,7 +1419,7 @@ static cudaError_t fwd_pass(const dock_tuning &tc, const Geo &g, int B, const ui
                             const RotRec *rots, const ReqDev *reqs, const float *ogrids, bool ro_any)
 {
     if (g.M == 256 && tc.fwd_runs && !ro_any) return launch_fwd2d_runs(g, B, bits, Y, qt, mask, st);
-    return launch_fwd2d(g, B, bits, Y, tw, qt, st, mask, rots, reqs, ogrids);
+    return launch_fwd2d(g, B, bits, Y, tw, qt, st, mask, rots, reqs, ogrids, tc.fft_plan);
 }
 
 // Runs records [r0, r1) of rots through the search pipeline; every
@@ -1517,11 +1520,11 @@ static dock_status run_pipeline_rots(dock_ctx *ctx, const Geo &g, const ReqDev *
             else if (g.M == 256 && tc.zpass_cols == 16)
                 CK(ctx, launch_zpass16_dual(g, nb, group, Y, Y2, rb, reqs, Z, ctx->stream));
             else
-                CK(ctx, launch_zpass(g, nb, group, Y, rb, reqs, Z, tw, ctx->stream, Y2));
+                CK(ctx, launch_zpass(g, nb, group, Y, rb, reqs, Z, tw, ctx->stream, Y2, tc.fft_plan));
         }
         {
             Prof pr(ctx, "plane");
-            CK(ctx, launch_plane(g, nb, Z, tw, rb, reqs, ctx->stream, tc.plane_cl, ctx->errflag, tc.plane_tma));
+            CK(ctx, launch_plane(g, nb, Z, tw, rb, reqs, ctx->stream, tc.plane_cl, ctx->errflag, tc.plane_tma, tc.fft_plan));
         }
     }
     return DOCK_OK;
@@ -1828,9 +1831,9 @@ static dock_status write_tuning(dock_ctx *ctx, const char *path)
         const dock_tuning &t = kv.second;
         fprintf(f,
                 "%s\n  {\"N\": %d, \"batch\": %d, \"group\": %d, \"vox_blocks\": %d, \"plane_cl\": %d, "
-                "\"zpass_cols\": %d, \"vox_overlap\": %d, \"zpass_tc\": %d, \"plane_tma\": %d, \"fwd_runs\": %d, \"us_per_rotation\": %.3f}",
+                "\"zpass_cols\": %d, \"vox_overlap\": %d, \"zpass_tc\": %d, \"plane_tma\": %d, \"fwd_runs\": %d, \"fft_plan\": %d, \"us_per_rotation\": %.3f}",
                 first ? "" : ",", t.N, t.batch, t.group, t.vox_blocks, t.plane_cl, t.zpass_cols, t.vox_overlap,
-                t.zpass_tc, t.plane_tma, t.fwd_runs, t.us_per_rotation);
+                t.zpass_tc, t.plane_tma, t.fwd_runs, t.fft_plan, t.us_per_rotation);
         first = false;
     }
     fprintf(f, "\n]}\n");
@@ -1898,6 +1901,11 @@ extern "C" dock_status dock_autotune(dock_ctx *ctx, const dock_object *ob, const
         if (gr > best.batch) continue;
         dock_tuning t = best;
         t.group = gr;
+        if ((s = trial(t)) != DOCK_OK) { restore(); return s; }
+    }
+    if (g.M == 64 || g.M == 128) {   // the alternative radix plan of the FFTs
+        dock_tuning t = best;
+        t.fft_plan = best.fft_plan ? 0 : 1;
         if ((s = trial(t)) != DOCK_OK) { restore(); return s; }
     }
     if (g.M == 256) {
@@ -1990,6 +1998,9 @@ extern "C" dock_status dock_load_tuning(dock_ctx *ctx, const char *path, int32_t
             long fr = gt.M == 256 ? FWD_RUNS_DEFAULT : 0;
             json_int(e.c_str(), "\"fwd_runs\"", &fr);
             t.fwd_runs = (int)fr;
+            long fp = FFT_PLAN_DEFAULT;
+            json_int(e.c_str(), "\"fft_plan\"", &fp);
+            t.fft_plan = (int)fp;
             if (!valid_tuning(t)) {
                 pos = end;
                 continue;
@@ -2099,13 +2110,13 @@ static dock_status search_scores_impl(dock_ctx *ctx, const dock_object *ob, cons
         else if (g.M == 256 && tc.zpass_cols == 16)
             e = launch_zpass16_dual(g, 1, 1, Y, Y2, ctx->rots, ctx->reqs, Y + ysz, ctx->stream);
         else
-            e = launch_zpass(g, 1, 1, Y, ctx->rots, ctx->reqs, Y + ysz, tw, ctx->stream, Y2);
+            e = launch_zpass(g, 1, 1, Y, ctx->rots, ctx->reqs, Y + ysz, tw, ctx->stream, Y2, tc.fft_plan);
     }
     if (e == cudaSuccess)
         e = withhold ? (tc.plane_tma && plane_ps_supported(g.M, tc.plane_cl)
                             ? launch_plane_ps_export(g, tc.plane_cl, Y + ysz, dC, ctx->errflag, ctx->stream, 1)
                             : launch_plane_cl_export(g, tc.plane_cl, Y + ysz, tw, dC, ctx->errflag, ctx->stream, 1))
-                     : launch_plane_export(g, Y + ysz, tw, dC, ctx->stream, tc.plane_cl, ctx->errflag, tc.plane_tma);
+                     : launch_plane_export(g, Y + ysz, tw, dC, ctx->stream, tc.plane_cl, ctx->errflag, tc.plane_tma, tc.fft_plan);
     if (e == cudaSuccess) e = cudaMemcpyAsync(C, dC, csz * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
     int herr = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, ctx->errflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);

@@ -84,20 +84,24 @@ cudaError_t launch_voxelise(const Geo &g, const ReqDev *reqs, const RotRec *rots
 // launch_resample, read instead of resampling inside the x stage.
 cudaError_t launch_fwd2d(const Geo &g, int B, const uint32_t *bits, float2 *Y, const float2 *tw, const float2 *q,
                          cudaStream_t st, const uint32_t *mask = nullptr, const RotRec *rots = nullptr,
-                         const ReqDev *reqs = nullptr, const float *ogrids = nullptr);
+                         const ReqDev *reqs = nullptr, const float *ogrids = nullptr, int fft_plan = 0);
+// (fft_plan, here and in launch_zpass / launch_plane: the radix plan of the
+// FFTs at canvases 64 and 128, 0 the default, 1 the alternative of fft.cuh;
+// other canvases have one plan)
 // The rotated object grids of the rotate_object rotations of a launch into out (B x N^3 floats).
 cudaError_t launch_resample(const Geo &g, const ReqDev *reqs, const RotRec *rots, int B, float *out, cudaStream_t st);
 // Y2 (nullable): transforms of the label-aware second grids; when given, the
 // product with each request's spec_pen is added before the inverse FFT.
 cudaError_t launch_zpass(const Geo &g, int B, int group, const float2 *Y, const RotRec *rots, const ReqDev *reqs,
-                         float2 *Z, const float2 *tw, cudaStream_t st, const float2 *Y2 = nullptr);
+                         float2 *Z, const float2 *tw, cudaStream_t st, const float2 *Y2 = nullptr,
+                         int fft_plan = 0);
 // plane_cl: CTAs per plane at M = 256 (4 or 8: the cluster kernel of
 // k_fft256.cu; anything else: the 2-CTA kernel); plane_tma with plane_cl 4
 // or 8: the persistent cluster kernel with TMA staging.  err (nullable, device):
 // set to DOCK_E_TIMEOUT if a cluster kernel gave up waiting for its peers.
 cudaError_t launch_plane(const Geo &g, int B, const float2 *Z, const float2 *tw, const RotRec *rots,
                          const ReqDev *reqs, cudaStream_t st, int plane_cl = 0, int *err = nullptr,
-                         int plane_tma = 0);
+                         int plane_tma = 0, int fft_plan = 0);
 // z pass over 16 columns per block (k_fft256.cu): M = 256, plain score only.
 cudaError_t launch_zpass16(const Geo &g, int B, int group, const float2 *Y, const RotRec *rots, const ReqDev *reqs,
                            float2 *Z, cudaStream_t st);
@@ -134,7 +138,7 @@ cudaError_t launch_topk(const unsigned long long *keys, int n, int K, int N, int
 cudaError_t launch_vox_export(const Geo &g, const ReqDev *reqs, const RotRec *rots, int B, uint8_t *bits,
                               cudaStream_t st, int pose_set = 0);
 cudaError_t launch_plane_export(const Geo &g, const float2 *Z, const float2 *tw, float *C, cudaStream_t st,
-                                int plane_cl = 0, int *err = nullptr, int plane_tma = 0);
+                                int plane_cl = 0, int *err = nullptr, int plane_tma = 0, int fft_plan = 0);
 // Corner cells of O for trilinear interpolation ((N+1)^3 float4).
 cudaError_t launch_corner_cells(const float *O, int N, float4 *cells, cudaStream_t st);
 // S of rotation 0 (pose set 0) as N^3 floats 0/1.

@@ -4,8 +4,10 @@
 // columns goes through shared memory laid out [element][column], so threads
 // with consecutive column indices touch consecutive words (no bank conflicts).
 //
-// Plan<M>: T threads per column, each holding E complex values; stage s has
-// radix R[s] and every thread computes E / R[s] butterflies of it.
+// Plan<M, V>: T threads per column, each holding E complex values; stage s has
+// radix R[s] and every thread computes E / R[s] butterflies of it.  V selects
+// one of the radix plans of a length (0: the default; 1: the alternative the
+// autotuner may pick, canvases 64 and 128).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -166,16 +168,21 @@ template <bool INV> struct DFT<12, INV> {
 // ---------------------------------------------------------------------------
 // plans
 // ---------------------------------------------------------------------------
-template <int M> struct Plan;
+template <int M, int V = 0> struct Plan;
 template <> struct Plan<32>  { static constexpr int T = 4,  E = 8,  S = 2; __host__ __device__ static constexpr int R(int s) { return s == 0 ? 8 : 4; } };
 template <> struct Plan<64>  { static constexpr int T = 8,  E = 8,  S = 2; __host__ __device__ static constexpr int R(int s) { return 8; } };
 template <> struct Plan<96>  { static constexpr int T = 8,  E = 12, S = 3; __host__ __device__ static constexpr int R(int s) { return s == 0 ? 12 : (s == 1 ? 4 : 2); } };
 template <> struct Plan<128> { static constexpr int T = 8,  E = 16, S = 2; __host__ __device__ static constexpr int R(int s) { return s == 0 ? 16 : 8; } };
 template <> struct Plan<192> { static constexpr int T = 16, E = 12, S = 3; __host__ __device__ static constexpr int R(int s) { return s == 0 ? 12 : 4; } };
 template <> struct Plan<256> { static constexpr int T = 16, E = 16, S = 2; __host__ __device__ static constexpr int R(int s) { return 16; } };
+// alternatives: 64 = 16 x 4 (4 threads per column), 128 = 8 x 8 x 2 (16 threads per column)
+template <> struct Plan<64, 1>  { static constexpr int T = 4,  E = 16, S = 2; __host__ __device__ static constexpr int R(int s) { return s == 0 ? 16 : 4; } };
+template <> struct Plan<128, 1> { static constexpr int T = 16, E = 8,  S = 3; __host__ __device__ static constexpr int R(int s) { return s == 2 ? 2 : 8; } };
+// whether length M has plan V
+template <int M, int V> struct HasPlan { static constexpr bool value = V == 0 || ((M == 64 || M == 128) && V == 1); };
 
-template <int M, int s> struct Ns { static constexpr int v = Ns<M, s - 1>::v * Plan<M>::R(s - 1); };
-template <int M> struct Ns<M, 0> { static constexpr int v = 1; };
+template <int M, int s, int V = 0> struct Ns { static constexpr int v = Ns<M, s - 1, V>::v * Plan<M, V>::R(s - 1); };
+template <int M, int V> struct Ns<M, 0, V> { static constexpr int v = 1; };
 
 // tw[m] = exp(-2 pi i m / M) for m in [0, M)
 template <bool INV> __device__ __forceinline__ cf twiddle(const cf *tw, int m)
@@ -187,10 +194,10 @@ template <bool INV> __device__ __forceinline__ cf twiddle(const cf *tw, int m)
 // One Stockham stage on the thread's registers.  Input element of butterfly
 // j, leg r: index j + r M/R; output index (j / Ns) Ns R + (j % Ns) + r Ns.
 // `v` holds E values: butterfly b (j = t + T b) occupies v[b R .. b R + R).
-template <int M, int s, bool INV, int TWS = 1>
+template <int M, int s, bool INV, int TWS = 1, int V = 0>
 __device__ __forceinline__ void stage_compute(cf *v, int t, const cf *tw)
 {
-    constexpr int R = Plan<M>::R(s), E = Plan<M>::E, T = Plan<M>::T, NS = Ns<M, s>::v;
+    constexpr int R = Plan<M, V>::R(s), E = Plan<M, V>::E, T = Plan<M, V>::T, NS = Ns<M, s, V>::v;
 #pragma unroll
     for (int b = 0; b < E / R; ++b) {
         int j = t + T * b;
@@ -204,10 +211,10 @@ __device__ __forceinline__ void stage_compute(cf *v, int t, const cf *tw)
 }
 
 // Load the inputs of stage s from an [M][ncol] buffer.
-template <int M, int s>
+template <int M, int s, int V = 0>
 __device__ __forceinline__ void stage_load(cf *v, int t, const cf *buf, int col, int ncol)
 {
-    constexpr int R = Plan<M>::R(s), E = Plan<M>::E, T = Plan<M>::T;
+    constexpr int R = Plan<M, V>::R(s), E = Plan<M, V>::E, T = Plan<M, V>::T;
 #pragma unroll
     for (int b = 0; b < E / R; ++b) {
         int j = t + T * b;
@@ -216,10 +223,10 @@ __device__ __forceinline__ void stage_load(cf *v, int t, const cf *buf, int col,
     }
 }
 
-template <int M, int s>
+template <int M, int s, int V = 0>
 __device__ __forceinline__ void stage_store(const cf *v, int t, cf *buf, int col, int ncol)
 {
-    constexpr int R = Plan<M>::R(s), E = Plan<M>::E, T = Plan<M>::T, NS = Ns<M, s>::v;
+    constexpr int R = Plan<M, V>::R(s), E = Plan<M, V>::E, T = Plan<M, V>::T, NS = Ns<M, s, V>::v;
 #pragma unroll
     for (int b = 0; b < E / R; ++b) {
         int j = t + T * b;
@@ -230,10 +237,10 @@ __device__ __forceinline__ void stage_store(const cf *v, int t, cf *buf, int col
 }
 
 // Natural-order output index of register slot (b, r) after the last stage.
-template <int M>
+template <int M, int V = 0>
 __device__ __forceinline__ int out_index(int t, int slot)
 {
-    constexpr int s = Plan<M>::S - 1, R = Plan<M>::R(s), T = Plan<M>::T, NS = Ns<M, s>::v;
+    constexpr int s = Plan<M, V>::S - 1, R = Plan<M, V>::R(s), T = Plan<M, V>::T, NS = Ns<M, s, V>::v;
     int b = slot / R, r = slot % R;
     int j = t + T * b;
     return (j / NS) * NS * R + (j % NS) + r * NS;
@@ -243,18 +250,18 @@ __device__ __forceinline__ int out_index(int t, int slot)
 // with one butterfly per thread (E = R0) and M / R0 = T, slot s reads
 // j + T s, which is below M/2 exactly when s < R0/2, whatever the thread j.
 // Zero-padded inputs (the upper half) then need no load.
-template <int M>
+template <int M, int V = 0>
 __device__ __forceinline__ constexpr bool slot_in_lower_half(int s)
 {
-    static_assert(Plan<M>::E == Plan<M>::R(0) && M / Plan<M>::R(0) == Plan<M>::T, "first-stage layout");
-    return s < Plan<M>::R(0) / 2;
+    static_assert(Plan<M, V>::E == Plan<M, V>::R(0) && M / Plan<M, V>::R(0) == Plan<M, V>::T, "first-stage layout");
+    return s < Plan<M, V>::R(0) / 2;
 }
 
 // Input index of register slot (b, r) for the first stage.
-template <int M>
+template <int M, int V = 0>
 __device__ __forceinline__ int in_index(int t, int slot)
 {
-    constexpr int R = Plan<M>::R(0), T = Plan<M>::T;
+    constexpr int R = Plan<M, V>::R(0), T = Plan<M, V>::T;
     int b = slot / R, r = slot % R;
     return t + T * b + r * (M / R);
 }
@@ -264,23 +271,23 @@ __device__ __forceinline__ int in_index(int t, int slot)
 // is the [M][ncol] exchange buffer shared by the block; all threads of the
 // block must call this together (it contains __syncthreads()).  The twiddle
 // table holds exp(-2 pi i m / (M TWS)); entry m TWS is used for exponent m.
-template <int M, bool INV, int TWS = 1>
+template <int M, bool INV, int TWS = 1, int V = 0>
 __device__ __forceinline__ void fft_column(cf *v, int t, cf *xb, int col, int ncol, const cf *tw)
 {
-    stage_compute<M, 0, INV, TWS>(v, t, tw);
-    if constexpr (Plan<M>::S >= 2) {
-        stage_store<M, 0>(v, t, xb, col, ncol);
+    stage_compute<M, 0, INV, TWS, V>(v, t, tw);
+    if constexpr (Plan<M, V>::S >= 2) {
+        stage_store<M, 0, V>(v, t, xb, col, ncol);
         __syncthreads();
-        stage_load<M, 1>(v, t, xb, col, ncol);
+        stage_load<M, 1, V>(v, t, xb, col, ncol);
         __syncthreads();
-        stage_compute<M, 1, INV, TWS>(v, t, tw);
+        stage_compute<M, 1, INV, TWS, V>(v, t, tw);
     }
-    if constexpr (Plan<M>::S >= 3) {
-        stage_store<M, 1>(v, t, xb, col, ncol);
+    if constexpr (Plan<M, V>::S >= 3) {
+        stage_store<M, 1, V>(v, t, xb, col, ncol);
         __syncthreads();
-        stage_load<M, 2>(v, t, xb, col, ncol);
+        stage_load<M, 2, V>(v, t, xb, col, ncol);
         __syncthreads();
-        stage_compute<M, 2, INV, TWS>(v, t, tw);
+        stage_compute<M, 2, INV, TWS, V>(v, t, tw);
     }
 }
 

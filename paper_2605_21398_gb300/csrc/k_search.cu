@@ -601,11 +601,11 @@ template <int M> struct Fwd2dSmem {
 // the upper half of X's bytes as float2 [N/2][N + 1]: the pairs a round reads
 // are loaded into registers before its outputs overwrite that memory, and
 // later rounds' pairs lie above what a round writes.
-template <int M>
+template <int M, int V = 0>
 __device__ __forceinline__ void resampled_x_stage(const RotRec &rr, const ReqDev &q, int jz, cf *X, cf *xbt, cf *xb,
                                                   const cf *tw, const float *slab)
 {
-    constexpr int N = M / 2, H = M / 2, COLS = 32, E = Plan<M>::E, NP = N / 2, PP = N + 1;
+    constexpr int N = M / 2, H = M / 2, COLS = 32, E = Plan<M, V>::E, NP = N / 2, PP = N + 1;
     float2 *pairs = reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(X) + (size_t)N * H * 4);
     if (slab) {
         // the slab resampled beforehand by k_resample (N x N floats)
@@ -629,15 +629,15 @@ __device__ __forceinline__ void resampled_x_stage(const RotRec &rr, const ReqDev
         cf v[E];
 #pragma unroll
         for (int s = 0; s < E; ++s) {
-            const int x = in_index<M>(j, s);
+            const int x = in_index<M, V>(j, s);
             float2 t = make_float2(0.f, 0.f);
-            if (slot_in_lower_half<M>(s) && p < NP) t = pairs[p * PP + x];   // x < N
+            if (slot_in_lower_half<M, V>(s) && p < NP) t = pairs[p * PP + x];   // x < N
             v[s] = cmake(t.x, t.y);
         }
-        fft_column<M, false>(v, j, xb, c, COLS, tw);
+        fft_column<M, false, 1, V>(v, j, xb, c, COLS, tw);
         __syncthreads();   // every pair of this round is in registers before X is written
 #pragma unroll
-        for (int s = 0; s < E; ++s) xbt[c * (M + 1) + out_index<M>(j, s)] = v[s];
+        for (int s = 0; s < E; ++s) xbt[c * (M + 1) + out_index<M, V>(j, s)] = v[s];
         __syncthreads();
         for (int e = threadIdx.x; e < COLS * H; e += blockDim.x) {
             const int kx = e % H, cc = e / H, pp = p0 + cc;
@@ -732,12 +732,12 @@ __device__ __forceinline__ void bits_x_stage(const uint32_t *bits_g, const uint3
     }
 }
 
-template <int M>
-__global__ void __launch_bounds__(Plan<M>::T * 32)
+template <int M, int V = 0>
+__global__ void __launch_bounds__(Plan<M, V>::T * 32)
 k_fwd2d(int P, const uint32_t *bits_g, float2 *Y, const float2 *tw_g, const float2 *q_g, const uint32_t *mask_g,
         const RotRec *rots, const ReqDev *reqs, const float *ogrids)
 {
-    constexpr int N = M / 2, H = M / 2, COLS = 32, E = Plan<M>::E;
+    constexpr int N = M / 2, H = M / 2, COLS = 32, E = Plan<M, V>::E;
     using L = Fwd2dSmem<M>;
     extern __shared__ __align__(16) unsigned char smem[];
     cf *X = reinterpret_cast<cf *>(smem);                       // [N][H] packed columns
@@ -752,7 +752,7 @@ k_fwd2d(int P, const uint32_t *bits_g, float2 *Y, const float2 *tw_g, const floa
     for (int i = threadIdx.x; i < M; i += blockDim.x) { float2 w = tw_g[i]; tw[i] = cmake(w.x, w.y); }
     if (resample) {
         __syncthreads();
-        resampled_x_stage<M>(rots[b], reqs[rots[b].req], jz, X, xb, xb, tw,
+        resampled_x_stage<M, V>(rots[b], reqs[rots[b].req], jz, X, xb, xb, tw,
                              ogrids ? ogrids + ((size_t)b * (M / 2) + jz) * (M / 2) * (M / 2) : nullptr);
     } else {
         bits_x_stage<M>(bits_g, mask_g, b, jz, X, bits, tw, q_g);
@@ -769,14 +769,14 @@ k_fwd2d(int P, const uint32_t *bits_g, float2 *Y, const float2 *tw_g, const floa
         cf v[E];
 #pragma unroll
         for (int s = 0; s < E; ++s) {
-            int yy = in_index<M>(j, s);
-            v[s] = slot_in_lower_half<M>(s) ? X[yy * H + p0 + c] : cmake(0.f, 0.f);   // yy < N
+            int yy = in_index<M, V>(j, s);
+            v[s] = slot_in_lower_half<M, V>(s) ? X[yy * H + p0 + c] : cmake(0.f, 0.f);   // yy < N
         }
-        fft_column<M, false>(v, j, xb, c, COLS, tw);
+        fft_column<M, false, 1, V>(v, j, xb, c, COLS, tw);
         const int kx = p0 + c;
 #pragma unroll
         for (int s = 0; s < E; ++s) {
-            int ky = out_index<M>(j, s);
+            int ky = out_index<M, V>(j, s);
             if (kx == 0) c0[ky] = v[s];
             else Yb[ky * P + kx] = make_float2(v[s].x, v[s].y);
         }
@@ -793,26 +793,30 @@ k_fwd2d(int P, const uint32_t *bits_g, float2 *Y, const float2 *tw_g, const floa
     }
 }
 
-template <int M>
+template <int M, int V = 0>
 static cudaError_t launch_fwd2d_t(const Geo &g, int B, const uint32_t *bits, float2 *Y, const float2 *tw,
                                   const float2 *q, cudaStream_t st, const uint32_t *mask, const RotRec *rots,
                                   const ReqDev *reqs, const float *ogrids)
 {
     size_t sm = Fwd2dSmem<M>::BYTES;
-    cudaError_t e = cudaFuncSetAttribute(k_fwd2d<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_fwd2d<M, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_fwd2d<M><<<dim3(M / 2, B), Plan<M>::T * 32, sm, st>>>(g.P, bits, Y, tw, q, mask, rots, reqs, ogrids);
+    k_fwd2d<M, V><<<dim3(M / 2, B), Plan<M, V>::T * 32, sm, st>>>(g.P, bits, Y, tw, q, mask, rots, reqs, ogrids);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fwd2d(const Geo &g, int B, const uint32_t *bits, float2 *Y, const float2 *tw, const float2 *q,
                          cudaStream_t st, const uint32_t *mask, const RotRec *rots, const ReqDev *reqs,
-                         const float *ogrids)
+                         const float *ogrids, int fft_plan)
 {
     if ((rots == nullptr) != (reqs == nullptr)) return cudaErrorInvalidValue;
     switch (g.M) {
-    case 64: return launch_fwd2d_t<64>(g, B, bits, Y, tw, q, st, mask, rots, reqs, ogrids);
-    case 128: return launch_fwd2d_t<128>(g, B, bits, Y, tw, q, st, mask, rots, reqs, ogrids);
+    case 64:
+        return fft_plan == 1 ? launch_fwd2d_t<64, 1>(g, B, bits, Y, tw, q, st, mask, rots, reqs, ogrids)
+                             : launch_fwd2d_t<64>(g, B, bits, Y, tw, q, st, mask, rots, reqs, ogrids);
+    case 128:
+        return fft_plan == 1 ? launch_fwd2d_t<128, 1>(g, B, bits, Y, tw, q, st, mask, rots, reqs, ogrids)
+                             : launch_fwd2d_t<128>(g, B, bits, Y, tw, q, st, mask, rots, reqs, ogrids);
     case 192: return launch_fwd2d_t<192>(g, B, bits, Y, tw, q, st, mask, rots, reqs, ogrids);
     case 256: return launch_fwd2d_t<256>(g, B, bits, Y, tw, q, st, mask, rots, reqs, ogrids);
     default: return cudaErrorInvalidValue;
@@ -951,13 +955,13 @@ cudaError_t launch_rot_export(const Geo &g, const ReqDev *reqs, const RotRec *ro
 // inverse transform yields the sum of both correlations.  Requests without
 // non-contact poses skip the addition and keep the plain result bit for bit.
 // ---------------------------------------------------------------------------
-template <int M, bool DUAL>
-__global__ void __launch_bounds__(Plan<M>::T * 32)
+template <int M, bool DUAL, int V = 0>
+__global__ void __launch_bounds__(Plan<M, V>::T * 32)
 k_zpass(int P, int B, int group, const float2 *Y, const float2 *Y2, const RotRec *rots, const ReqDev *reqs, float2 *Z,
         const float2 *tw_g)
 {
-    constexpr int N = M / 2, E = Plan<M>::E, COLS = 32;
-    constexpr int R_LAST = Plan<M>::R(Plan<M>::S - 1);
+    constexpr int N = M / 2, E = Plan<M, V>::E, COLS = 32;
+    constexpr int R_LAST = Plan<M, V>::R(Plan<M, V>::S - 1);
     constexpr int TPR = DUAL ? 2 : 1;        // tiles per rotation
     extern __shared__ __align__(16) unsigned char smem[];
     cf *xb = reinterpret_cast<cf *>(smem);   // [M][COLS]
@@ -1010,10 +1014,10 @@ k_zpass(int P, int B, int group, const float2 *Y, const float2 *Y2, const RotRec
         cf v[E];
 #pragma unroll
         for (int s = 0; s < E; ++s) {
-            int z = in_index<M>(j, s);
-            v[s] = slot_in_lower_half<M>(s) ? src[z * COLS + c] : cmake(0.f, 0.f);   // z < N
+            int z = in_index<M, V>(j, s);
+            v[s] = slot_in_lower_half<M, V>(s) ? src[z * COLS + c] : cmake(0.f, 0.f);   // z < N
         }
-        fft_column<M, false>(v, j, xb, c, COLS, tw);
+        fft_column<M, false, 1, V>(v, j, xb, c, COLS, tw);
         // forward output slot (bb, r) holds kz = j + (M/E)(bb + (E/R_LAST) r)
         if (!second) {
             // a rotated object: this tile is F(O_R) and spec is F(S) / M^3,
@@ -1041,11 +1045,11 @@ k_zpass(int P, int B, int group, const float2 *Y, const float2 *Y2, const RotRec
         }
         if (!DUAL || second) {
             __syncthreads();
-            fft_column<M, true>(w, j, xb, c, COLS, tw);
+            fft_column<M, true, 1, V>(w, j, xb, c, COLS, tw);
             float2 *Zb = Z + (size_t)(b0 + bi) * M * plane + f0 + c;
 #pragma unroll
             for (int s = 0; s < E; ++s) {
-                int z = out_index<M>(j, s);
+                int z = out_index<M, V>(j, s);
                 Zb[(size_t)z * plane] = make_float2(w[s].x, w[s].y);
             }
         }
@@ -1053,28 +1057,34 @@ k_zpass(int P, int B, int group, const float2 *Y, const float2 *Y2, const RotRec
     }
 }
 
-template <int MM, bool DUAL>
+template <int MM, bool DUAL, int V = 0>
 static cudaError_t launch_zpass_t(const Geo &g, dim3 grid, int B, int group, const float2 *Y, const float2 *Y2,
                                   const RotRec *rots, const ReqDev *reqs, float2 *Z, const float2 *tw, cudaStream_t st)
 {
     size_t sm = sizeof(cf) * ((size_t)MM * 32 + MM + (size_t)MM * 32);
-    cudaError_t e = cudaFuncSetAttribute(k_zpass<MM, DUAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_zpass<MM, DUAL, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_zpass<MM, DUAL><<<grid, Plan<MM>::T * 32, sm, st>>>(g.P, B, group, Y, Y2, rots, reqs, Z, tw);
+    k_zpass<MM, DUAL, V><<<grid, Plan<MM, V>::T * 32, sm, st>>>(g.P, B, group, Y, Y2, rots, reqs, Z, tw);
     return cudaGetLastError();
 }
 
 cudaError_t launch_zpass(const Geo &g, int B, int group, const float2 *Y, const RotRec *rots, const ReqDev *reqs,
-                         float2 *Z, const float2 *tw, cudaStream_t st, const float2 *Y2)
+                         float2 *Z, const float2 *tw, cudaStream_t st, const float2 *Y2, int fft_plan)
 {
     int chunks = g.M * g.P / 32;
     dim3 grid(chunks, (B + group - 1) / group);
     switch (g.M) {
-#define ZCASE(MM)                                                                                    \
-    case MM:                                                                                         \
-        return Y2 ? launch_zpass_t<MM, true>(g, grid, B, group, Y, Y2, rots, reqs, Z, tw, st)        \
-                  : launch_zpass_t<MM, false>(g, grid, B, group, Y, nullptr, rots, reqs, Z, tw, st);
-        ZCASE(64) ZCASE(128) ZCASE(192) ZCASE(256)
+#define ZCASE(MM, V)                                                                                 \
+        return Y2 ? launch_zpass_t<MM, true, V>(g, grid, B, group, Y, Y2, rots, reqs, Z, tw, st)     \
+                  : launch_zpass_t<MM, false, V>(g, grid, B, group, Y, nullptr, rots, reqs, Z, tw, st);
+    case 64:
+        if (fft_plan == 1) ZCASE(64, 1)
+        ZCASE(64, 0)
+    case 128:
+        if (fft_plan == 1) ZCASE(128, 1)
+        ZCASE(128, 0)
+    case 192: ZCASE(192, 0)
+    case 256: ZCASE(256, 0)
 #undef ZCASE
     default: return cudaErrorInvalidValue;
     }
@@ -1088,14 +1098,15 @@ cudaError_t launch_zpass(const Geo &g, int B, int group, const float2 *Y, const 
 // cluster; each CTA reads the other half of its rows through distributed
 // shared memory.
 // ---------------------------------------------------------------------------
-template <int M> struct PlaneCfg {
+template <int M, int V = 0> struct PlaneCfg {
     static constexpr int CL = (M >= 256) ? 2 : 1;          // CTAs per plane
     static constexpr int H = M / 2;
+    static constexpr int VH = HasPlan<H, V>::value ? V : 0;   // the C2R's plan (length H)
     static constexpr int PC = H / CL;                      // packed columns per CTA
     static constexpr int PP = PC + 1;                      // odd pitch: a warp's rows hit distinct banks
-    static constexpr int NT = Plan<M>::T * 32;             // threads
+    static constexpr int NT = Plan<M, V>::T * 32;             // threads
     static constexpr int COLS = 32;                        // columns per round of the y transform
-    static constexpr int RPR = NT / Plan<H>::T;            // rows per round of the C2R
+    static constexpr int RPR = NT / Plan<H, VH>::T;            // rows per round of the C2R
     static constexpr int S1 = M * COLS;                    // phase-1 exchange
     static constexpr int S2 = CL > 1 ? (M / CL) * PP : 0;  // peer rows (cluster only)
     static constexpr int S3 = H * RPR;                     // phase-2 exchange (single CTA)
@@ -1104,12 +1115,13 @@ template <int M> struct PlaneCfg {
     static_assert(SMEM <= 227 * 1024, "plane pass exceeds the shared memory of one CTA");
 };
 
-template <int M, bool EXPORT>
+template <int M, bool EXPORT, int V = 0>
 __device__ __forceinline__ void plane_body(const float2 *Zp, const float2 *tw_g, unsigned long long *key, float *Cout,
                                            int zc, cf *pb, cf *stg, cf *tw, int rank)
 {
-    using C = PlaneCfg<M>;
-    constexpr int H = M / 2, CL = C::CL, PC = C::PC, PP = C::PP, E = Plan<M>::E, COLS = C::COLS;
+    using C = PlaneCfg<M, V>;
+    constexpr int VH = C::VH;
+    constexpr int H = M / 2, CL = C::CL, PC = C::PC, PP = C::PP, E = Plan<M, V>::E, COLS = C::COLS;
     const int P = H + 2;
     for (int i = threadIdx.x; i < M; i += blockDim.x) { float2 w = tw_g[i]; tw[i] = cmake(w.x, w.y); }
     __syncthreads();
@@ -1149,11 +1161,11 @@ __device__ __forceinline__ void plane_body(const float2 *Zp, const float2 *tw_g,
             const bool act = pl < PC;
             cf v[E];
 #pragma unroll
-            for (int s = 0; s < E; ++s) v[s] = act ? pb[in_index<M>(j, s) * PP + pl] : cmake(0.f, 0.f);
-            fft_column<M, true>(v, j, stg, c, COLS, tw);
+            for (int s = 0; s < E; ++s) v[s] = act ? pb[in_index<M, V>(j, s) * PP + pl] : cmake(0.f, 0.f);
+            fft_column<M, true, 1, V>(v, j, stg, c, COLS, tw);
             if (act) {
 #pragma unroll
-                for (int s = 0; s < E; ++s) pb[out_index<M>(j, s) * PP + pl] = v[s];
+                for (int s = 0; s < E; ++s) pb[out_index<M, V>(j, s) * PP + pl] = v[s];
             }
             __syncthreads();
         }
@@ -1193,7 +1205,7 @@ __device__ __forceinline__ void plane_body(const float2 *Zp, const float2 *tw_g,
     }
     // phase 2: C2R along x of my rows by a half-length complex inverse FFT
     {
-        constexpr int EH = Plan<H>::E, RPR = C::RPR;
+        constexpr int EH = Plan<H, VH>::E, RPR = C::RPR;
         const int rowl = threadIdx.x % RPR, j = threadIdx.x / RPR;
         float best = -INFINITY;
         uint32_t bidx = 0xFFFFFFFFu;
@@ -1204,7 +1216,7 @@ __device__ __forceinline__ void plane_body(const float2 *Zp, const float2 *tw_g,
             cf v[EH];
 #pragma unroll
             for (int s = 0; s < EH; ++s) {
-                int k = in_index<H>(j, s);
+                int k = in_index<H, VH>(j, s);
                 cf Ek = cmake(0.f, 0.f), Ok = cmake(0.f, 0.f);
                 if (act) {
                     // W[k] and W[H - k]; column 0 holds W[0] + i W[H]
@@ -1228,13 +1240,13 @@ __device__ __forceinline__ void plane_body(const float2 *Zp, const float2 *tw_g,
                 }
                 v[s] = cmake(Ek.x - Ok.y, Ek.y + Ok.x);   // E + i O
             }
-            fft_column<H, true, 2>(v, j, xb2, rowl, RPR, tw);
+            fft_column<H, true, 2, VH>(v, j, xb2, rowl, RPR, tw);
             if (act) {
                 const uint32_t rowbase = ((uint32_t)zc * M + (uint32_t)y) * M;
                 if (EXPORT) {
 #pragma unroll
                     for (int s = 0; s < EH; ++s) {
-                        const uint32_t base = rowbase + 2u * out_index<H>(j, s);
+                        const uint32_t base = rowbase + 2u * out_index<H, VH>(j, s);
                         Cout[base] = v[s].x;
                         Cout[base + 1] = v[s].y;
                     }
@@ -1249,7 +1261,7 @@ __device__ __forceinline__ void plane_body(const float2 *Zp, const float2 *tw_g,
 #pragma unroll
                     for (int s = 0; s < EH; ++s) {
                         if (v[s].x == m || v[s].y == m) {
-                            const uint32_t base = rowbase + 2u * out_index<H>(j, s);
+                            const uint32_t base = rowbase + 2u * out_index<H, VH>(j, s);
                             if (v[s].x == m) bi = min(bi, base);
                             if (v[s].y == m) bi = min(bi, base + 1u);
                         }
@@ -1281,11 +1293,11 @@ __device__ __forceinline__ void plane_body(const float2 *Zp, const float2 *tw_g,
     }
 }
 
-template <int M>
-__global__ void __launch_bounds__(PlaneCfg<M>::NT)
+template <int M, int V = 0>
+__global__ void __launch_bounds__(PlaneCfg<M, V>::NT)
 k_plane(int B, const float2 *Z, const float2 *tw_g, const RotRec *rots, const ReqDev *reqs, int ahead)
 {
-    using C = PlaneCfg<M>;
+    using C = PlaneCfg<M, V>;
     extern __shared__ __align__(16) unsigned char smem[];
     cf *pb = reinterpret_cast<cf *>(smem);    // [M][PP]
     cf *stg = pb + M * C::PP;                 // [STG]
@@ -1316,14 +1328,14 @@ k_plane(int B, const float2 *Z, const float2 *tw_g, const RotRec *rots, const Re
             asm volatile("prefetch.global.L2 [%0];" ::"l"(row + off));
         }
     }
-    plane_body<M, false>(Zp, tw_g, &reqs[rots[b].req].keys[rots[b].rot], nullptr, zc, pb, stg, tw, rank);
+    plane_body<M, false, V>(Zp, tw_g, &reqs[rots[b].req].keys[rots[b].rot], nullptr, zc, pb, stg, tw, rank);
 }
 
-template <int M>
-__global__ void __launch_bounds__(PlaneCfg<M>::NT)
+template <int M, int V = 0>
+__global__ void __launch_bounds__(PlaneCfg<M, V>::NT)
 k_plane_export(const float2 *Z, const float2 *tw_g, float *C)
 {
-    using Cf = PlaneCfg<M>;
+    using Cf = PlaneCfg<M, V>;
     extern __shared__ __align__(16) unsigned char smem[];
     cf *pb = reinterpret_cast<cf *>(smem);
     cf *stg = pb + M * Cf::PP;
@@ -1332,21 +1344,21 @@ k_plane_export(const float2 *Z, const float2 *tw_g, float *C)
     int rank = 0;
     if constexpr (Cf::CL > 1) rank = (int)cg::this_cluster().block_rank();
     const size_t plane = (size_t)M * (M / 2 + 2);
-    plane_body<M, true>(Z + (size_t)zc * plane, tw_g, nullptr, C, zc, pb, stg, tw, rank);
+    plane_body<M, true, V>(Z + (size_t)zc * plane, tw_g, nullptr, C, zc, pb, stg, tw, rank);
 }
 
-template <int M>
-static size_t plane_smem() { return PlaneCfg<M>::SMEM; }
+template <int M, int V = 0>
+static size_t plane_smem() { return PlaneCfg<M, V>::SMEM; }
 
-template <int M, bool EXPORT>
+template <int M, bool EXPORT, int V = 0>
 static cudaError_t launch_plane_t(int B, const float2 *Z, const float2 *tw, const RotRec *rots,
                                   const ReqDev *reqs, float *C, cudaStream_t st)
 {
-    constexpr int CL = PlaneCfg<M>::CL;
-    size_t sm = plane_smem<M>();
+    constexpr int CL = PlaneCfg<M, V>::CL;
+    size_t sm = plane_smem<M, V>();
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(M * CL, EXPORT ? 1 : B);
-    cfg.blockDim = dim3(PlaneCfg<M>::NT);
+    cfg.blockDim = dim3(PlaneCfg<M, V>::NT);
     cfg.dynamicSmemBytes = sm;
     cfg.stream = st;
     cudaLaunchAttribute at[1];
@@ -1358,25 +1370,25 @@ static cudaError_t launch_plane_t(int B, const float2 *Z, const float2 *tw, cons
     cfg.numAttrs = 1;
     cudaError_t e;
     if (EXPORT) {
-        e = cudaFuncSetAttribute(k_plane_export<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        e = cudaFuncSetAttribute(k_plane_export<M, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        e = cudaLaunchKernelEx(&cfg, k_plane_export<M>, Z, tw, C);
+        e = cudaLaunchKernelEx(&cfg, k_plane_export<M, V>, Z, tw, C);
     } else {
-        e = cudaFuncSetAttribute(k_plane<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        e = cudaFuncSetAttribute(k_plane<M, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         // planes in flight at one CTA per SM: the next CTA on an SM takes
         // roughly the plane this many further on
         int dev = 0, sms = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        e = cudaLaunchKernelEx(&cfg, k_plane<M>, B, Z, tw, rots, reqs, sms / CL);
+        e = cudaLaunchKernelEx(&cfg, k_plane<M, V>, B, Z, tw, rots, reqs, sms / CL);
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
 cudaError_t launch_plane(const Geo &g, int B, const float2 *Z, const float2 *tw, const RotRec *rots,
-                         const ReqDev *reqs, cudaStream_t st, int plane_cl, int *err, int plane_tma)
+                         const ReqDev *reqs, cudaStream_t st, int plane_cl, int *err, int plane_tma, int fft_plan)
 {
     if (plane_tma && plane_ps_supported(g.M, plane_cl)) {
         const cudaError_t e = launch_plane_ps(g, plane_cl, B, Z, rots, reqs, err, st);
@@ -1384,8 +1396,12 @@ cudaError_t launch_plane(const Geo &g, int B, const float2 *Z, const float2 *tw,
     }
     if (plane_cl_supported(g.M, plane_cl)) return launch_plane_cl(g, plane_cl, B, Z, tw, rots, reqs, err, st);
     switch (g.M) {
-    case 64: return launch_plane_t<64, false>(B, Z, tw, rots, reqs, nullptr, st);
-    case 128: return launch_plane_t<128, false>(B, Z, tw, rots, reqs, nullptr, st);
+    case 64:
+        return fft_plan == 1 ? launch_plane_t<64, false, 1>(B, Z, tw, rots, reqs, nullptr, st)
+                             : launch_plane_t<64, false>(B, Z, tw, rots, reqs, nullptr, st);
+    case 128:
+        return fft_plan == 1 ? launch_plane_t<128, false, 1>(B, Z, tw, rots, reqs, nullptr, st)
+                             : launch_plane_t<128, false>(B, Z, tw, rots, reqs, nullptr, st);
     case 192: return launch_plane_t<192, false>(B, Z, tw, rots, reqs, nullptr, st);
     case 256: return launch_plane_t<256, false>(B, Z, tw, rots, reqs, nullptr, st);
     default: return cudaErrorInvalidValue;
@@ -1393,7 +1409,7 @@ cudaError_t launch_plane(const Geo &g, int B, const float2 *Z, const float2 *tw,
 }
 
 cudaError_t launch_plane_export(const Geo &g, const float2 *Z, const float2 *tw, float *C, cudaStream_t st,
-                                int plane_cl, int *err, int plane_tma)
+                                int plane_cl, int *err, int plane_tma, int fft_plan)
 {
     if (plane_tma && plane_ps_supported(g.M, plane_cl)) {
         const cudaError_t e = launch_plane_ps_export(g, plane_cl, Z, C, err, st);
@@ -1401,8 +1417,12 @@ cudaError_t launch_plane_export(const Geo &g, const float2 *Z, const float2 *tw,
     }
     if (plane_cl_supported(g.M, plane_cl)) return launch_plane_cl_export(g, plane_cl, Z, tw, C, err, st);
     switch (g.M) {
-    case 64: return launch_plane_t<64, true>(1, Z, tw, nullptr, nullptr, C, st);
-    case 128: return launch_plane_t<128, true>(1, Z, tw, nullptr, nullptr, C, st);
+    case 64:
+        return fft_plan == 1 ? launch_plane_t<64, true, 1>(1, Z, tw, nullptr, nullptr, C, st)
+                             : launch_plane_t<64, true>(1, Z, tw, nullptr, nullptr, C, st);
+    case 128:
+        return fft_plan == 1 ? launch_plane_t<128, true, 1>(1, Z, tw, nullptr, nullptr, C, st)
+                             : launch_plane_t<128, true>(1, Z, tw, nullptr, nullptr, C, st);
     case 192: return launch_plane_t<192, true>(1, Z, tw, nullptr, nullptr, C, st);
     case 256: return launch_plane_t<256, true>(1, Z, tw, nullptr, nullptr, C, st);
     default: return cudaErrorInvalidValue;

@@ -82,7 +82,8 @@ class Tuning(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int32), ("batch", ctypes.c_int32), ("group", ctypes.c_int32),
                 ("vox_blocks", ctypes.c_int32), ("plane_cl", ctypes.c_int32), ("zpass_cols", ctypes.c_int32),
                 ("vox_overlap", ctypes.c_int32), ("zpass_tc", ctypes.c_int32),
-                ("plane_tma", ctypes.c_int32), ("fwd_runs", ctypes.c_int32), ("us_per_rotation", ctypes.c_double)]
+                ("plane_tma", ctypes.c_int32), ("fwd_runs", ctypes.c_int32), ("fft_plan", ctypes.c_int32),
+                ("us_per_rotation", ctypes.c_double)]
 
 
 class KernelStat(ctypes.Structure):
@@ -385,7 +386,8 @@ class Context:
         cur = self.get_tuning(shape["N"])
         cur.update(shape)
         t = Tuning(cur["N"], cur["batch"], cur["group"], cur["vox_blocks"], cur["plane_cl"], cur["zpass_cols"],
-                   cur["vox_overlap"], cur["zpass_tc"], cur["plane_tma"], cur["fwd_runs"], cur["us_per_rotation"])
+                   cur["vox_overlap"], cur["zpass_tc"], cur["plane_tma"], cur["fwd_runs"], cur["fft_plan"],
+                   cur["us_per_rotation"])
         self.check(lib().dock_set_tuning(self.h, ctypes.byref(t)))
 
     # -------------------------------------------------------------- profiling
@@ -404,7 +406,7 @@ class Context:
 def tuning_dict(t):
     return dict(N=t.N, batch=t.batch, group=t.group, vox_blocks=t.vox_blocks, plane_cl=t.plane_cl,
                 zpass_cols=t.zpass_cols, vox_overlap=t.vox_overlap, zpass_tc=t.zpass_tc, plane_tma=t.plane_tma,
-                fwd_runs=t.fwd_runs,
+                fwd_runs=t.fwd_runs, fft_plan=t.fft_plan,
                 us_per_rotation=t.us_per_rotation)
 
 
