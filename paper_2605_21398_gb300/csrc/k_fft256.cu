@@ -612,7 +612,7 @@ k_plane_ps(const __grid_constant__ CUtensorMap zmap, const __grid_constant__ CUt
             DFT<8, true>::run(w + bb * 8);
         }
         const uint32_t rowbase = ((uint32_t)zc * M + (uint32_t)y) * M;
-        if (EXPORT) {
+        if constexpr (EXPORT) {
 #pragma unroll
             for (int s = 0; s < 16; ++s) {
                 const uint32_t base = rowbase + 2u * (uint32_t)(j + 8 * (s >> 3) + 16 * (s & 7));

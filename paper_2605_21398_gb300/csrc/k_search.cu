@@ -642,15 +642,15 @@ __device__ __forceinline__ void resampled_x_stage(const RotRec &rr, const ReqDev
         for (int e = threadIdx.x; e < COLS * H; e += blockDim.x) {
             const int kx = e % H, cc = e / H, pp = p0 + cc;
             if (pp >= NP) continue;
-            const cf *V = xbt + cc * (M + 1);
-            const cf a = V[kx];
+            const cf *col = xbt + cc * (M + 1);
+            const cf a = col[kx];
             cf A, B;
             if (kx == 0) {
-                const cf hq = V[H];
+                const cf hq = col[H];
                 A = cmake(a.x, hq.x);
                 B = cmake(a.y, hq.y);
             } else {
-                const cf r = V[M - kx];
+                const cf r = col[M - kx];
                 A = cmake(0.5f * (a.x + r.x), 0.5f * (a.y - r.y));
                 B = cmake(0.5f * (a.y + r.y), -0.5f * (a.x - r.x));
             }
